@@ -1,0 +1,320 @@
+"""Benchmark: particle-steps/s of the IFE-PIC hot path, including the IFE solve.
+
+Workload (default): the 64^3-cell sphere-charging problem -- 64^3 cubic cells of
+0.5 Debye length (1.31M tets), sphere radius 6 centred, eps 4 inside, e- and H+
+(mass ratio 100) at 64 particles/cell/species (~33.5M particles), phi = 0 on
+the faces, Maxwellian flux injection, dt = 0.05.  One step = push + object
+collection + injection + rebin + scatter + IFE PCG solve + node field.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica (the method's single-GPU path does not shard) and rank 0 prints the
+aggregate; the reference arm runs on rank 0 only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+BYTES_PER_PARTICLE_STEP = {"fp64": 96, "mixed": 56}     # read + write of the particle state
+
+
+def _peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(name):
+    from paper_2011_10214_gb300 import workloads as wl
+    return {"sphere64": wl.SPHERE64, "sphere16": wl.SPHERE16}[name]
+
+
+def cfg_desc(cfg, precision, extra=None):
+    n = cfg["n"]
+    ppc = cfg["species"][0]["ppc"]
+    d = {"workload": f"sphere charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={cfg['object']['radius']}, "
+                     f"eps_in={cfg['object']['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e=100), "
+                     f"dt={cfg['dt']}, flux injection, phi=0 faces",
+         "precision": precision, "pcg_tol": 1e-6, "pcg_max_iter": 150,
+         "l2_flush": "inputs larger than L2 (particle state > 1 GB per step)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_2011_10214_gb300 import capi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = workload(args.workload)
+    prec = capi.MIXED if args.precision == "mixed" else capi.FP64
+    stream = torch.cuda.Stream()
+    sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream)
+    sim.solve()
+    sim.leapfrog_init()
+    if args.warmup > 0:
+        sim.step(args.warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    barrier()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = sim.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    pushed = sum(st["pushed"])
+    t = torch.tensor([ms / 1e3, float(pushed)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        tmax = t.clone(); dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        t = torch.stack([tmax[0], t[1]])
+    secs, total = float(t[0]), float(t[1])
+    value = total / secs
+
+    # dominant kernel: the fused gather/push/collect/deposit launch (phase 0)
+    push_ms = st["phase_ms"][0] / args.steps
+    per_launch_particles = pushed / args.steps
+    bpp = BYTES_PER_PARTICLE_STEP[args.precision]
+    alg_bytes = per_launch_particles * bpp
+    peaks, src = _peaks()
+    achieved = alg_bytes / (push_ms / 1e3) / 1e9
+    roof = {"kernel": "k_push_bins (fused gather+push+collect+deposit)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": src, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": push_ms}
+
+    # end to end through the C ABI from host buffers: the initial particle state
+    # is copied host -> device (pinned) inside the timed region, and every step
+    # reads the potential and the step statistics back to host memory
+    e2e = None
+    if not args.no_e2e:
+        state = [sim.particles(s) for s in range(len(cfg["species"]))]
+        sim2 = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream, load=False)
+        pinned = []
+        for P in state:
+            pinned.append({k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory().numpy()
+                           for k in ("x", "y", "z", "vx", "vy", "vz")})
+        nn = sim2.sizes()["nnodes"]
+        phi_host = torch.empty(nn, dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for s, P in enumerate(pinned):
+            sim2.load_particles(s, P["x"], P["y"], P["z"], P["vx"], P["vy"], P["vz"])
+        sim2.solve()
+        pushed2 = 0
+        for _ in range(args.steps):
+            st2 = sim2.step(1)
+            pushed2 += sum(st2["pushed"])
+            capi.lib.pifepic_get_potential(sim2._c, phi_host.ctypes.data, capi.HOST)
+        barrier()
+        t1 = time.perf_counter()
+        h2d = sum(P[k].nbytes for P in pinned for k in P)
+        e2e = {"value": pushed2 / (t1 - t0), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d / args.steps),
+               "d2h_bytes_per_step": int(phi_host.nbytes + 512),
+               "note": "initial particle state h2d (amortised over the steps) + per-step phi and stats d2h"}
+        sim2.close()
+
+    out = {
+        "metric": "particle-steps/s incl. IFE solve", "value": value, "unit": "particle-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded Philox load and injection)",
+        "config": cfg_desc(cfg, args.precision, {"particles": int(per_launch_particles),
+                                                  "parallelism": f"replicas x{world}"}),
+        "roofline": roof, "clocks": ck, "e2e": e2e,
+        "gpu_launches": int(st["kernel_launches"]),
+        "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
+        "phase_ms_per_step": {k: v / args.steps for k, v in zip(("push", "movers", "inject", "rebin", "rhs", "solve",
+                                                                  "node_E", "other"), st["phase_ms"]) if v},
+    }
+    sim.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_subprocess(args)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------
+def oracle_rate(workload_name, sample_frac, steps):
+    """Time the oracle on a bounded sample: the full mesh and IFE solve, a
+    random 1/sample_frac of the particles.  Particle work scales with the
+    particle count, so the rate at full size is extrapolated as
+    N / (t_particles * N / n_sample + t_field)."""
+    import numpy as np
+    from oracle.geometry import Mesh, Sphere
+    from oracle.pic import Simulation
+    from oracle import particles as pt
+    from paper_2011_10214_gb300 import workloads as wl
+    cfg = workload(workload_name)
+    m = Mesh(*cfg["n"], cfg["h"])
+    ob = cfg["object"]
+    sim = Simulation(m, Sphere(m, ob["center"], ob["radius"], ob["eps_in"], ob["eps_out"]), cfg["face_bc"],
+                     cfg["dt"])
+    g = np.random.default_rng(0)
+    nfull = 0
+    for s, sp in enumerate(cfg["species"]):
+        sim.add_species(sp["q"], sp["m"], wl.macro_weight(cfg, sp))
+        sim.load_maxwellian(s, sp["ppc"] // sample_frac if sp["ppc"] >= sample_frac else 1, sp["vth"], sp["drift"],
+                            cfg["seed"])
+        nfull += sp["ppc"] * m.ncells
+        sim.set_injection(s, cfg["inject_faces"], sp["density"], sp["vth"], sp["drift"], cfg["seed"])
+        # injection at the sample's weight keeps the density; rates scale with 1/w
+    sim.solve()
+    sim.leapfrog_init()
+    tp = tf = 0.0
+    npush = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st = sim.step()
+        t1 = time.perf_counter()
+        npush += sum(st["pushed"])
+        tf_step = sim.last.get("_t_field", None)
+        tp += t1 - t0
+    # separate the field solve: time it once more on its own
+    t0 = time.perf_counter()
+    F = sim.node_load()
+    phi, it, rr = sim.fs.solve(F, sim.qT, phi0=sim.phi, tol=sim.tol, maxit=sim.maxit)
+    sim.fs.node_E(phi, sim.qT)
+    tf = time.perf_counter() - t0
+    tpart = max(tp / steps - tf, 1e-9)
+    nsample = npush / steps
+    full_step = tpart * nfull / nsample + tf
+    return {"value": nfull / full_step, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{workload_name}: full mesh + IFE solve, {nsample:.0f} particles (1/{sample_frac} of the "
+                      f"{nfull} load), {steps} steps; particle time scaled to the full count",
+            "seconds": tp}
+
+
+def cpu_baseline_subprocess(args):
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "2", "--warmup", "0",
+           "--workload", args.workload, "--as-baseline"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900,
+                           env=dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1"))
+        line = [l for l in r.stdout.splitlines() if l.startswith("{")][-1]
+        d = json.loads(line)
+        return d["cpu_baseline"]
+    except Exception as e:
+        return {"value": None, "error": str(e)[:200]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    frac = 16
+    t0 = time.perf_counter()
+    cb = oracle_rate(args.workload, frac, max(1, args.steps))
+    t1 = time.perf_counter()
+    cfg = workload(args.workload)
+    out = {"impl": "reference", "metric": "particle-steps/s incl. IFE solve", "value": cb["value"],
+           "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Philox load and injection)", "config": cfg_desc(cfg, "fp64"),
+           "cpu_baseline": dict(cb), "e2e": {"value": cb["value"], "unit": "particle-steps/s",
+                                             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": t1 - t0}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="sphere64", choices=["sphere64", "sphere16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--as-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * pifepic.h -- C ABI of libpifepic, a single-GPU (sm_103a) implementation of
+ * the hot path of the non-homogeneous IFE-PIC method of arXiv:2011.10214
+ * (PIFE-PIC): the per-step particle cycle (gather, push, object collection
+ * with surface charging, scatter) and the linear-IFE PCG field solve it drives.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a pifepic_status; 0 is success.  The library never
+ *    aborts, throws or prints.  After a non-zero status,
+ *    pifepic_last_error(ctx) returns a context-owned, NUL-terminated message
+ *    that stays valid until the next call on the same context.
+ *  - Units are the plasma units the paper's experiments are stated in
+ *    (Sec. 3.1, Sec. 5.1): lengths in Debye lengths, time in 1/omega_pe,
+ *    potential in kT_e/e, density in the reference density, eps_0 = 1.
+ *  - Node arrays are indexed n = i + (nx+1) * (j + (ny+1) * k); cell arrays
+ *    c = i + nx * (j + ny * k).  A node vector (E) is interleaved xyz.
+ *  - Pointers passed in are borrowed for the duration of the call only.
+ *    mem_kind says where they live: PIFEPIC_HOST (pageable or pinned host
+ *    memory) or PIFEPIC_DEVICE (device memory of the context's GPU, e.g. a
+ *    torch CUDA tensor's data_ptr()).  The library owns all of its device
+ *    state and frees it in pifepic_destroy.
+ *  - Work is enqueued on the CUDA stream given to pifepic_create (NULL = the
+ *    legacy default stream).  Calls that return data or statistics
+ *    synchronise that stream before returning.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PIFEPIC_H
+#define PIFEPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIFEPIC_OK = 0,
+    PIFEPIC_EINVAL = 1,     /* bad argument or descriptor                        */
+    PIFEPIC_ENOMEM = 2,     /* device allocation failed / capacity exhausted     */
+    PIFEPIC_ESTATE = 3,     /* call out of order (e.g. step before set_object)   */
+    PIFEPIC_ECUDA = 4,      /* a CUDA runtime or driver call failed              */
+    PIFEPIC_ETIMEOUT = 5,   /* a bounded device-side wait gave up                */
+    PIFEPIC_ENOTCONV = 6    /* reserved: the PCG cap is recorded in the stats, not
+                               returned, because the paper caps iterations        */
+} pifepic_status;
+
+enum { PIFEPIC_HOST = 0, PIFEPIC_DEVICE = 1 };
+
+/* Arithmetic of the particle cycle and the PCG (BASIS: the paper states no
+ * precision).  FP64: everything in double.  MIXED: push in FP32 with an int32
+ * packed cell index plus FP32 in-cell offset, PCG in FP32 inside an FP64
+ * iterative refinement whose residuals and dot products are FP64. */
+enum { PIFEPIC_FP64 = 0, PIFEPIC_MIXED = 1 };
+
+/* Uniform Cartesian PIC mesh of nx*ny*nz cubic cells of edge h, each cut into
+ * 5 tetrahedra; the IFE mesh equals the PIC mesh (Sec. 3.1.1). */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+    double origin[3];
+} pifepic_mesh_desc;
+
+/* Time step and field-solver controls.  pcg_tol is the relative-residual
+ * tolerance ||r|| <= tol ||b|| and pcg_max_iter the iteration cap (the paper
+ * uses 1e-6 with caps of 60 and 150, Sec. 3.2, Sec. 4, Sec. 5.2.2).  In MIXED
+ * mode pcg_max_iter caps the FP32 inner iterations summed over refinements.
+ * track_ids = 1 carries an int64 id with every particle (parity tests). */
+typedef struct {
+    double dt;
+    int precision;
+    double pcg_tol;
+    int pcg_max_iter;
+    int track_ids;
+} pifepic_solver_desc;
+
+/* Immersed object (Sec. 2.1: the interface Gamma splits the box into Omega^-
+ * (object, eps_in) and Omega^+ (plasma, eps_out)), as an analytic level set
+ * L >= 0 in the plasma:
+ *   SPHERE:     params = {cx, cy, cz, R}                    (Sec. 3.1.1)
+ *   CAP_CRATER: params = {z_ground, xc, yc, rim_radius, depth}; planar ground
+ *               with a spherical-cap crater             (reading of Sec. 5.2.1)
+ *   PLANE:      params = {n_x, n_y, n_z, d0} in cell units: L = n.xi - d0
+ *   NONE:       no object. */
+enum { PIFEPIC_OBJ_NONE = 0, PIFEPIC_OBJ_SPHERE = 1, PIFEPIC_OBJ_CAP_CRATER = 2, PIFEPIC_OBJ_PLANE = 3 };
+typedef struct {
+    int kind;
+    double params[8];
+    double eps_in, eps_out;
+} pifepic_object_desc;
+
+/* Field boundary of one face (Eqs. 2.2-2.3): Dirichlet phi = value, or zero
+ * Neumann.  Faces are ordered x-, x+, y-, y+, z-, z+. */
+enum { PIFEPIC_BC_DIRICHLET = 0, PIFEPIC_BC_NEUMANN = 1 };
+typedef struct {
+    int kind;
+    double value;
+} pifepic_face_bc;
+
+/* Statistics of the last call (one entry per species where indexed). */
+#define PIFEPIC_MAX_SPECIES 8
+typedef struct {
+    int64_t steps;                             /* PIC steps taken so far        */
+    int64_t pushed[PIFEPIC_MAX_SPECIES];       /* particle-steps in this call   */
+    int64_t count[PIFEPIC_MAX_SPECIES];        /* particles alive now           */
+    int64_t injected[PIFEPIC_MAX_SPECIES];     /* entered through open faces    */
+    int64_t absorbed[PIFEPIC_MAX_SPECIES];     /* left through absorbing faces  */
+    int64_t collected[PIFEPIC_MAX_SPECIES];    /* hit the object                */
+    int64_t lost_charge[PIFEPIC_MAX_SPECIES];  /* hits with no cut cell nearby  */
+    int64_t inj_rejected[PIFEPIC_MAX_SPECIES]; /* injection starts in the object*/
+    int64_t spilled[PIFEPIC_MAX_SPECIES];      /* waiting in the overflow list  */
+    int64_t dropped[PIFEPIC_MAX_SPECIES];      /* lost: all buffers full (error)*/
+    int64_t pcg_iters_total;                   /* PCG iterations in this call   */
+    int64_t kernel_launches;                   /* kernels launched in this call */
+    int pcg_iters;                             /* last solve                    */
+    int pcg_converged;
+    double pcg_relres;
+    double surface_charge;                     /* total charge on the object    */
+    double surface_potential;                  /* area-mean phi on Gamma_h      */
+    double phase_ms[8];                        /* GPU time per phase, this call:
+                                                  push, movers, inject, rebin,
+                                                  rhs, pcg, node_E, other        */
+} pifepic_stats;
+
+typedef struct pifepic_ctx pifepic_ctx;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (may
+ * be NULL).  Fails with EINVAL on a degenerate mesh (n < 1 or h <= 0), with
+ * ENOMEM if the mesh arrays do not fit. */
+pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solver_desc* solver,
+                              void* stream, pifepic_ctx** out);
+void pifepic_destroy(pifepic_ctx* ctx);
+const char* pifepic_last_error(const pifepic_ctx* ctx);
+
+/* Object and field boundary set-up (Sec. 2.1, Sec. 3.1.2, Sec. 5.2.2): node
+ * level set, tet classification, per-interface-tet linear IFE basis (a 4x4
+ * FP64 solve each), stiffness patch rows, cut cells.  Must precede particle
+ * calls.  set_field_bc may be called before or after set_object. */
+pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* obj);
+pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
+
+/* Species with charge q, mass m (q/m sets the push) and macro-particle
+ * weight w (charge per macro-particle = q*w; w = density*h^3/ppc).  At most
+ * PIFEPIC_MAX_SPECIES. */
+pifepic_status pifepic_add_species(pifepic_ctx* ctx, double q, double m, double w, int* species_id);
+
+/* Pre-load (Sec. 3.1.3): ppc particles per cell uniform in the cell,
+ * velocities Maxwellian (thermal speed vth) plus drift, drawn from
+ * Philox4x64-10 keyed by seed; particles inside the object are dropped. */
+pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int species, int ppc, double vth,
+                                       const double drift[3], uint64_t seed);
+
+/* Append n explicit particles: positions in cell units xi = (x-origin)/h,
+ * physical velocities, optional int64 ids (NULL: consecutive ids).  All must
+ * lie inside the box; EINVAL otherwise is not checked on the device, so the
+ * caller guarantees it. */
+pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int species, size_t n, const double* x,
+                                      const double* y, const double* z, const double* vx,
+                                      const double* vy, const double* vz, const int64_t* ids,
+                                      int mem_kind);
+
+/* Injection at open faces every step (Sec. 3.1.3, Sec. 5.2.2): for each face
+ * f with bit f of face_mask set, floor(rate + carry) particles per step with
+ * rate = one-way drifting-Maxwellian flux * face area * dt / w. */
+pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int species, int face_mask, double density,
+                                     double vth, const double drift[3], uint64_t seed);
+pifepic_status pifepic_get_injection_rate(pifepic_ctx* ctx, int species, double rate[6]);
+
+/* Freeze the node field to the given (nnodes x 3) array: steps then skip the
+ * field solve (particle-only parity runs).  E == NULL unfreezes. */
+pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem_kind);
+
+/* Scatter all particles, solve the IFE system, compute the node field (the
+ * initial field solve, Sec. 3.2.1). */
+pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* stats);
+
+/* Leapfrog start: v <- v - (q/m)(dt/2) E(x) with the current node field. */
+pifepic_status pifepic_leapfrog_init(pifepic_ctx* ctx);
+
+/* nsteps PIC steps (Sec. 2.1 Fig. 1): push + collection + injection, rebin,
+ * scatter, IFE solve, node field.  A PCG that reaches its cap is recorded in
+ * stats (pcg_converged = 0), not returned as an error.  stats may be NULL. */
+pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* stats);
+
+/* Read-back.  Arrays are caller-owned with the stated sizes. */
+pifepic_status pifepic_get_sizes(pifepic_ctx* ctx, int64_t* nnodes, int64_t* ncells,
+                                 int64_t* n_interface_tets, int64_t* n_cut_cells);
+pifepic_status pifepic_get_potential(pifepic_ctx* ctx, double* phi, int mem_kind);        /* nnodes   */
+pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind);             /* nnodes*3 */
+pifepic_status pifepic_get_node_charge(pifepic_ctx* ctx, int species, int64_t* W, int mem_kind); /* nnodes, 2^32 per particle */
+pifepic_status pifepic_get_surface_charge(pifepic_ctx* ctx, int species, int64_t* counts,
+                                          int mem_kind);                                   /* n_cut_cells */
+pifepic_status pifepic_get_cut_cells(pifepic_ctx* ctx, int32_t* cells, double* area);      /* n_cut_cells */
+pifepic_status pifepic_get_cell_target(pifepic_ctx* ctx, int32_t* target);                  /* ncells: cut index or -1 */
+/* Interface tets, ordered by (cell, local tet): cell, local tet (0..4),
+ * sub-volumes, Gamma_h area, element stiffness (16, row-major) and the
+ * unit-jump load vector (4). Any pointer may be NULL. */
+pifepic_status pifepic_get_interface(pifepic_ctx* ctx, int32_t* cell, int32_t* tet, double* vol_plus,
+                                     double* vol_minus, double* area, double* K, double* c);
+pifepic_status pifepic_get_particle_count(pifepic_ctx* ctx, int species, int64_t* n);
+/* Copies up to cap particles (any order); *n receives the number copied.
+ * ids may be NULL (it must be NULL when track_ids is 0). */
+pifepic_status pifepic_get_particles(pifepic_ctx* ctx, int species, int64_t cap, double* x, double* y,
+                                     double* z, double* vx, double* vy, double* vz, int64_t* ids,
+                                     int64_t* n, int mem_kind);
+pifepic_status pifepic_get_stats(pifepic_ctx* ctx, pifepic_stats* stats);
+
+/* Field solve on its own (Sec. 2.1 Eqs. 2.1-2.5, PCG level of Sec. 2.5): node
+ * load F (nnodes, FP64) and flux jump q per interface tet (n_interface_tets,
+ * in pifepic_get_interface order) -> phi and the node field.  Used by the
+ * solver parity tests; F and q may be host or device arrays. */
+pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const double* q, int mem_kind,
+                                   int* iters, double* relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIFEPIC_H */

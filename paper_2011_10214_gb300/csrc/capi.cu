@@ -1,0 +1,894 @@
+// libpifepic C ABI: context lifecycle, set-up, the PIC step and read-back.
+// Host code here only orders kernel launches, owns device memory and converts
+// descriptors; every step of the particle cycle and the field solve runs in
+// the kernels of setup.cu, particles.cu, particles_mixed.cu and field.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+
+#include "internal.h"
+
+namespace pf {
+cudaError_t set_field_tables(const TetTables& t);
+cudaError_t set_particle_tables(const TetTables& t);
+cudaError_t set_mixed_tables(const TetTables& t);
+cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double* relres);
+cudaError_t read_pcg_state(Ctx& c);
+int solve_graph_fixed_kernels(const Ctx& c);
+cudaError_t build_pcg_graph_mixed(Ctx& c);
+cudaError_t launch_pcg_mixed(Ctx& c);
+
+// 5-tet split tables, computed from the definition (reading of Sec. 3.1.1)
+static TetTables make_tables() {
+    TetTables t;
+    memset(&t, 0, sizeof(t));
+    for (int p = 0; p < 2; ++p) {
+        int even[4], odd[4], ne = 0, no = 0;
+        for (int l = 0; l < 8; ++l) {
+            int s = (l & 1) + ((l >> 1) & 1) + ((l >> 2) & 1);
+            if ((s & 1) == p) even[ne++] = l; else odd[no++] = l;
+        }
+        for (int v = 0; v < 4; ++v) t.vert[p][0][v] = even[v];
+        for (int q = 0; q < 4; ++q) {
+            int o = odd[q];
+            t.vert[p][1 + q][0] = o; t.vert[p][1 + q][1] = o ^ 1; t.vert[p][1 + q][2] = o ^ 2; t.vert[p][1 + q][3] = o ^ 4;
+        }
+        for (int tt = 0; tt < 5; ++tt) {
+            // P1 gradients (h = 1): invert [1 x y z] rows of the 4 vertices
+            double M[4][4], I[4][4];
+            for (int v = 0; v < 4; ++v) {
+                int l = t.vert[p][tt][v];
+                M[v][0] = 1; M[v][1] = l & 1; M[v][2] = (l >> 1) & 1; M[v][3] = (l >> 2) & 1;
+                for (int q = 0; q < 4; ++q) I[v][q] = v == q;
+            }
+            for (int cc = 0; cc < 4; ++cc) {
+                int piv = cc;
+                for (int r = cc + 1; r < 4; ++r) if (fabs(M[r][cc]) > fabs(M[piv][cc])) piv = r;
+                for (int q = 0; q < 4; ++q) { std::swap(M[cc][q], M[piv][q]); std::swap(I[cc][q], I[piv][q]); }
+                double d = M[cc][cc];
+                for (int q = 0; q < 4; ++q) { M[cc][q] /= d; I[cc][q] /= d; }
+                for (int r = 0; r < 4; ++r) {
+                    if (r == cc) continue;
+                    double f = M[r][cc];
+                    for (int q = 0; q < 4; ++q) { M[r][q] -= f * M[cc][q]; I[r][q] -= f * I[cc][q]; }
+                }
+            }
+            // column v of the inverse holds basis v's coefficients (a, gx, gy, gz)
+            for (int v = 0; v < 4; ++v)
+                for (int d = 0; d < 3; ++d) t.grad[p][tt][v][d] = I[1 + d][v];
+        }
+    }
+    t.vol[0] = 1.0 / 3.0;
+    for (int q = 1; q < 5; ++q) t.vol[q] = 1.0 / 6.0;
+    const int off[19][3] = {{0, 0, 0},  {-1, 0, 0},  {1, 0, 0},  {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
+                            {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                            {1, 0, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+    for (int q = 0; q < 27; ++q) t.slot[q] = -1;
+    for (int s = 0; s < 19; ++s) {
+        for (int d = 0; d < 3; ++d) t.off[s][d] = off[s][d];
+        t.slot[(off[s][2] + 1) * 9 + (off[s][1] + 1) * 3 + (off[s][0] + 1)] = s;
+    }
+    return t;
+}
+
+__global__ void k_pack_E(long long n, const double* E3, double4* E, float4* Ef) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 e = make_double4(E3[3 * i], E3[3 * i + 1], E3[3 * i + 2], 0.0);
+    E[i] = e;
+    Ef[i] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.0f);
+}
+__global__ void k_unpack_E(long long n, const double4* E, double* E3) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 e = E[i];
+    E3[3 * i] = e.x; E3[3 * i + 1] = e.y; E3[3 * i + 2] = e.z;
+}
+__global__ void k_max_id(long long n, const long long* id, unsigned long long* out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, (unsigned long long)id[i]);
+}
+__global__ void k_seq_id(long long n, long long base, long long* id) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) id[i] = base + i;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+struct pifepic_ctx {
+    Ctx c;
+};
+
+#define FAIL(code, ...)                                                              \
+    do {                                                                             \
+        char _b[512];                                                                \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                                       \
+        ctx->c.err = _b;                                                             \
+        return code;                                                                 \
+    } while (0)
+#define CUDA_OK(x)                                                                            \
+    do {                                                                                      \
+        cudaError_t _e = (x);                                                                 \
+        if (_e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "%s: %s", #x, cudaGetErrorString(_e));     \
+    } while (0)
+#define ALLOC(ptr, bytes)                                                                        \
+    do {                                                                                         \
+        cudaError_t _e = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (size_t)(bytes) : (size_t)16); \
+        if (_e != cudaSuccess) FAIL(PIFEPIC_ENOMEM, "cudaMalloc(%lld bytes) failed: %s",         \
+                                    (long long)(bytes), cudaGetErrorString(_e));                 \
+    } while (0)
+#define NEED(ptr) do { if (!(ptr)) return PIFEPIC_EINVAL; } while (0)
+
+static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+
+static PArr alloc_parr_raw(long long n, bool id, cudaError_t* err) {
+    PArr a{};
+    double** arr[6] = {&a.x, &a.y, &a.z, &a.vx, &a.vy, &a.vz};
+    *err = cudaSuccess;
+    for (auto p : arr) {
+        cudaError_t e = cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1));
+        if (e != cudaSuccess) *err = e;
+    }
+    if (id) {
+        cudaError_t e = cudaMalloc(&a.id, sizeof(long long) * (n > 0 ? n : 1));
+        if (e != cudaSuccess) *err = e;
+    }
+    return a;
+}
+static void free_parr(PArr& a) {
+    cudaFree(a.x); cudaFree(a.y); cudaFree(a.z); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz); cudaFree(a.id);
+    a = PArr{};
+}
+
+extern "C" {
+
+pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solver_desc* solver, void* stream,
+                              pifepic_ctx** out) {
+    if (!mesh || !solver || !out) return PIFEPIC_EINVAL;
+    *out = nullptr;
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->h > 0.0) || !(solver->dt > 0.0))
+        return PIFEPIC_EINVAL;
+    if (mesh->nx > 2047 || mesh->ny > 2047 || mesh->nz > 1023) return PIFEPIC_EINVAL;
+    if (solver->precision != PIFEPIC_FP64 && solver->precision != PIFEPIC_MIXED) return PIFEPIC_EINVAL;
+    pifepic_ctx* ctx = new (std::nothrow) pifepic_ctx();
+    if (!ctx) return PIFEPIC_ENOMEM;
+    *out = ctx;
+    Ctx& c = ctx->c;
+    c.stream = (cudaStream_t)stream;
+    CUDA_OK(cudaGetDevice(&c.device));
+    Mesh& m = c.mesh;
+    m.nx = mesh->nx; m.ny = mesh->ny; m.nz = mesh->nz;
+    m.NX = m.nx + 1; m.NY = m.ny + 1; m.NZ = m.nz + 1;
+    m.nnodes = (long long)m.NX * m.NY * m.NZ;
+    m.ncells = (long long)m.nx * m.ny * m.nz;
+    m.h = mesh->h;
+    for (int d = 0; d < 3; ++d) c.origin[d] = mesh->origin[d];
+    c.dt = solver->dt;
+    c.dth = solver->dt / mesh->h;
+    c.precision = solver->precision;
+    c.tol = solver->pcg_tol > 0 ? solver->pcg_tol : 1e-6;
+    c.maxit = solver->pcg_max_iter > 0 ? solver->pcg_max_iter : 150;
+    c.track = solver->track_ids ? 1 : 0;
+    c.nbx = (m.nx + BLK - 1) / BLK; c.nby = (m.ny + BLK - 1) / BLK; c.nbz = (m.nz + BLK - 1) / BLK;
+    c.nblocks = c.nbx * c.nby * c.nbz;
+    for (int f = 0; f < 6; ++f) { c.bc[f].kind = PIFEPIC_BC_DIRICHLET; c.bc[f].value = 0.0; }
+    long long N = m.nnodes, C = m.ncells;
+    ALLOC(c.Lnode, sizeof(double) * N);
+    ALLOC(c.ntype, sizeof(int) * N);
+    ALLOC(c.gdir, sizeof(double) * N);
+    ALLOC(c.lift, sizeof(double) * N);
+    ALLOC(c.invdiag, sizeof(double) * N);
+    ALLOC(c.invdiagf, sizeof(float) * N);
+    ALLOC(c.phi, sizeof(double) * N);
+    ALLOC(c.u, sizeof(double) * N);
+    ALLOC(c.b, sizeof(double) * N);
+    ALLOC(c.r, sizeof(double) * N);
+    ALLOC(c.p, sizeof(double) * N);
+    ALLOC(c.q, sizeof(double) * N);
+    ALLOC(c.rf, sizeof(float) * N);
+    ALLOC(c.pf, sizeof(float) * N);
+    ALLOC(c.qf, sizeof(float) * N);
+    ALLOC(c.uf, sizeof(float) * N);
+    ALLOC(c.E, sizeof(double4) * N);
+    ALLOC(c.Ef, sizeof(float4) * N);
+    ALLOC(c.Wall, sizeof(unsigned long long) * MAX_SPECIES * N);
+    ALLOC(c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR);
+    ALLOC(c.imask, C);
+    ALLOC(c.ibase, sizeof(int) * C);
+    ALLOC(c.cell_acc, sizeof(int) * C);
+    ALLOC(c.red, sizeof(double) * 4 * (N / 128 + 1024));
+    ALLOC(c.scal, sizeof(double) * 64);
+    ALLOC(c.red_ticket, sizeof(unsigned) * 4);
+    ALLOC(c.err_word, sizeof(int));
+    ALLOC(c.next_id, sizeof(long long) * MAX_SPECIES);
+    ALLOC(c.inj_count, sizeof(int) * MAX_SPECIES * 6);
+    ALLOC(c.inj_base, sizeof(long long) * MAX_SPECIES * 6);
+    ALLOC(c.inj_carry, sizeof(double) * MAX_SPECIES * 6);
+    ALLOC(c.inj_dev, sizeof(InjectDev) * MAX_SPECIES * 6);
+    CUDA_OK(cudaMemset(c.phi, 0, sizeof(double) * N));
+    CUDA_OK(cudaMemset(c.E, 0, sizeof(double4) * N));
+    CUDA_OK(cudaMemset(c.Ef, 0, sizeof(float4) * N));
+    CUDA_OK(cudaMemset(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * N));
+    CUDA_OK(cudaMemset(c.ctrall, 0, sizeof(unsigned long long) * MAX_SPECIES * NCTR));
+    CUDA_OK(cudaMemset(c.scal, 0, sizeof(double) * 64));
+    CUDA_OK(cudaMemset(c.red_ticket, 0, sizeof(unsigned) * 4));
+    CUDA_OK(cudaMemset(c.err_word, 0, sizeof(int)));
+    CUDA_OK(cudaMemset(c.next_id, 0, sizeof(long long) * MAX_SPECIES));
+    CUDA_OK(cudaMemset(c.inj_carry, 0, sizeof(double) * MAX_SPECIES * 6));
+    TetTables t = make_tables();
+    CUDA_OK(set_tet_tables(t));
+    CUDA_OK(set_field_tables(t));
+    CUDA_OK(set_particle_tables(t));
+    for (int e = 0; e < 16; ++e) CUDA_OK(cudaEventCreate(&c.ev[e]));
+    c.ev_ok = true;
+    return PIFEPIC_OK;
+}
+
+void pifepic_destroy(pifepic_ctx* ctx) {
+    if (!ctx) return;
+    Ctx& c = ctx->c;
+    if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
+    void* ptrs[] = {c.Lnode, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q,
+                    c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
+                    c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
+                    c.patch_coef, c.patch_coeff, c.red, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,
+                    c.inj_base, c.inj_carry, c.next_id};
+    for (void* p : ptrs) cudaFree(p);
+    for (auto& s : c.sp) {
+        free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
+        cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.mov_n);
+        cudaFree(s.binsF.cell); cudaFree(s.binsF.fx); cudaFree(s.binsF.fy); cudaFree(s.binsF.fz);
+        cudaFree(s.binsF.vx); cudaFree(s.binsF.vy); cudaFree(s.binsF.vz); cudaFree(s.binsF.id);
+        for (int q = 0; q < 2; ++q) {
+            cudaFree(s.movF[q].cell); cudaFree(s.movF[q].fx); cudaFree(s.movF[q].fy); cudaFree(s.movF[q].fz);
+            cudaFree(s.movF[q].vx); cudaFree(s.movF[q].vy); cudaFree(s.movF[q].vz); cudaFree(s.movF[q].id);
+        }
+    }
+    if (c.pcg_exec) cudaGraphExecDestroy(c.pcg_exec);
+    if (c.pcg_graph) cudaGraphDestroy(c.pcg_graph);
+    if (c.ev_ok) for (int e = 0; e < 16; ++e) cudaEventDestroy(c.ev[e]);
+    delete ctx;
+}
+
+const char* pifepic_last_error(const pifepic_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+static pifepic_status encode_tmaps(pifepic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled not available");
+    EncodeFn enc = (EncodeFn)fn;
+    const Mesh& m = c.mesh;
+    cuuint64_t dims[4] = {4, (cuuint64_t)m.NX, (cuuint64_t)m.NY, (cuuint64_t)m.NZ};
+    cuuint32_t box[4] = {4, TILE, TILE, TILE};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    cuuint64_t sd[3] = {32, (cuuint64_t)m.NX * 32, (cuuint64_t)m.NX * m.NY * 32};
+    CUresult r = enc(&c.tmapE, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c.E, dims, sd, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled(E) failed: %d", (int)r);
+    cuuint64_t sf[3] = {16, (cuuint64_t)m.NX * 16, (cuuint64_t)m.NX * m.NY * 16};
+    r = enc(&c.tmapEf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c.Ef, dims, sf, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled(Ef) failed: %d", (int)r);
+    c.tmap_ok = true;
+    return PIFEPIC_OK;
+}
+
+static pifepic_status do_setup(pifepic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    // free a previous interface set-up
+    void* old[] = {c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut,
+                   c.patch_node, c.patch_coef, c.patch_coeff, c.surfall};
+    for (void* p : old) cudaFree(p);
+    c.it_cell = c.it_t = c.it_acc = c.cut_cell = nullptr;
+    c.it_data = c.qT = c.cut_area = c.qcut = c.patch_coef = nullptr;
+    c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr;
+    CUDA_OK(launch_setup(c));
+    ALLOC(c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1));
+    CUDA_OK(cudaMemset(c.surfall, 0, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1)));
+    for (size_t s = 0; s < c.sp.size(); ++s) c.sp[s].surf = c.surfall + s * (c.ncut > 0 ? c.ncut : 1);
+    CUDA_OK(launch_field_lift(c));
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(build_pcg_graph(c));
+    if (c.precision == PIFEPIC_MIXED) CUDA_OK(build_pcg_graph_mixed(c));
+    pifepic_status st = encode_tmaps(ctx);
+    if (st) return st;
+    c.have_object = true;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* o) {
+    NEED(ctx); NEED(o);
+    Ctx& c = ctx->c;
+    if (!c.sp.empty()) FAIL(PIFEPIC_ESTATE, "set_object must precede add_species");
+    if (!(o->eps_in > 0) || !(o->eps_out > 0)) FAIL(PIFEPIC_EINVAL, "permittivities must be positive");
+    Object ob{};
+    ob.eps_minus = o->eps_in;
+    ob.eps_plus = o->eps_out;
+    double h = c.mesh.h;
+    const double* q = o->params;
+    switch (o->kind) {
+    case PIFEPIC_OBJ_NONE: ob.kind = 0; ob.eps_minus = ob.eps_plus = o->eps_out; break;
+    case PIFEPIC_OBJ_SPHERE: {
+        if (!(q[3] > 0)) FAIL(PIFEPIC_EINVAL, "sphere radius must be positive");
+        ob.kind = 1;
+        ob.a0 = (q[0] - c.origin[0]) / h; ob.a1 = (q[1] - c.origin[1]) / h; ob.a2 = (q[2] - c.origin[2]) / h;
+        double r = q[3] / h;
+        ob.a3 = r * r;
+        break;
+    }
+    case PIFEPIC_OBJ_CAP_CRATER: {
+        if (!(q[3] > 0) || !(q[4] > 0)) FAIL(PIFEPIC_EINVAL, "crater rim radius and depth must be positive");
+        ob.kind = 2;
+        double zg = (q[0] - c.origin[2]) / h, xc = (q[1] - c.origin[0]) / h, yc = (q[2] - c.origin[1]) / h;
+        double a = q[3] / h, D = q[4] / h;
+        double Rs = (a * a + D * D) / (2.0 * D);
+        ob.a0 = zg; ob.a1 = xc; ob.a2 = yc; ob.a3 = a * a; ob.a4 = Rs * Rs; ob.a5 = (zg - D) + Rs;
+        break;
+    }
+    case PIFEPIC_OBJ_PLANE:
+        ob.kind = 3; ob.a0 = q[0]; ob.a1 = q[1]; ob.a2 = q[2]; ob.a3 = q[3];
+        break;
+    default: FAIL(PIFEPIC_EINVAL, "unknown object kind %d", o->kind);
+    }
+    c.obj = ob;
+    return do_setup(ctx);
+}
+
+pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]) {
+    NEED(ctx); NEED(bc);
+    Ctx& c = ctx->c;
+    for (int f = 0; f < 6; ++f)
+        if (bc[f].kind != PIFEPIC_BC_DIRICHLET && bc[f].kind != PIFEPIC_BC_NEUMANN)
+            FAIL(PIFEPIC_EINVAL, "face %d: unknown boundary kind", f);
+    for (int f = 0; f < 6; ++f) c.bc[f] = bc[f];
+    if (c.have_object) {
+        if (!c.sp.empty()) FAIL(PIFEPIC_ESTATE, "field boundaries must be set before species are added");
+        return do_setup(ctx);
+    }
+    return PIFEPIC_OK;
+}
+
+static pifepic_status upload_species_params(pifepic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    double co[MAX_SPECIES] = {0};
+    for (size_t s = 0; s < c.sp.size(); ++s) co[s] = c.sp[s].q * c.sp[s].w;
+    int ns = (int)c.sp.size();
+    CUDA_OK(cudaMemcpy(c.scal + 16, co, sizeof(co), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy((int*)(c.scal + 24), &ns, sizeof(int), cudaMemcpyHostToDevice));
+    return PIFEPIC_OK;
+}
+
+static pifepic_status ensure_movers(pifepic_ctx* ctx, int s, long long need) {
+    Ctx& c = ctx->c;
+    Species& q = c.sp[s];
+    if (need <= q.mcap) return PIFEPIC_OK;
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    long long keep = 0;
+    if (q.mov_n) {
+        unsigned long long n0 = 0;
+        CUDA_OK(cudaMemcpy(&n0, q.mov_n, sizeof(n0), cudaMemcpyDeviceToHost));
+        keep = (long long)n0;
+    }
+    cudaError_t e;
+    PArr a0 = alloc_parr_raw(need, c.track != 0, &e);
+    if (e != cudaSuccess) { free_parr(a0); FAIL(PIFEPIC_ENOMEM, "mover list allocation failed"); }
+    PArr a1 = alloc_parr_raw(need, c.track != 0, &e);
+    if (e != cudaSuccess) { free_parr(a0); free_parr(a1); FAIL(PIFEPIC_ENOMEM, "mover list allocation failed"); }
+    if (keep > 0) {   // carry the waiting list over
+        double* src[6] = {q.mov[0].x, q.mov[0].y, q.mov[0].z, q.mov[0].vx, q.mov[0].vy, q.mov[0].vz};
+        double* dst[6] = {a0.x, a0.y, a0.z, a0.vx, a0.vy, a0.vz};
+        for (int d = 0; d < 6; ++d) CUDA_OK(cudaMemcpy(dst[d], src[d], sizeof(double) * keep, cudaMemcpyDeviceToDevice));
+        if (c.track) CUDA_OK(cudaMemcpy(a0.id, q.mov[0].id, sizeof(long long) * keep, cudaMemcpyDeviceToDevice));
+    }
+    free_parr(q.mov[0]); free_parr(q.mov[1]);
+    q.mov[0] = a0; q.mov[1] = a1;
+    q.mcap = need;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_add_species(pifepic_ctx* ctx, double qq, double mm, double w, int* id) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object must precede add_species");
+    if ((int)c.sp.size() >= MAX_SPECIES) FAIL(PIFEPIC_EINVAL, "at most %d species", MAX_SPECIES);
+    if (!(mm > 0) || !(w > 0)) FAIL(PIFEPIC_EINVAL, "mass and weight must be positive");
+    Species s;
+    s.q = qq; s.m = mm; s.w = w;
+    s.k = (qq / mm) * c.dt;
+    int idx = (int)c.sp.size();
+    c.sp.push_back(s);
+    Species& q = c.sp.back();
+    q.W = c.Wall + (long long)idx * c.mesh.nnodes;
+    q.surf = c.surfall + (long long)idx * (c.ncut > 0 ? c.ncut : 1);
+    q.ctr = c.ctrall + idx * NCTR;
+    ALLOC(q.mov_n, 2 * sizeof(unsigned long long));
+    CUDA_OK(cudaMemset(q.mov_n, 0, 2 * sizeof(unsigned long long)));
+    pifepic_status st = ensure_movers(ctx, idx, 1 << 16);
+    if (st) return st;
+    // empty bins
+    PArr none{};
+    CUDA_OK(launch_build_bins(c, idx, none, 0, true));
+    st = upload_species_params(ctx);
+    if (st) return st;
+    if (id) *id = idx;
+    return PIFEPIC_OK;
+}
+
+static long long count_particles(Ctx& c, int s);
+
+// flatten species s (bins + waiting list) into a fresh flat array with room for extra
+static pifepic_status flatten(pifepic_ctx* ctx, int s, long long extra, PArr* flat, unsigned long long** nflat,
+                              long long* nexist) {
+    Ctx& c = ctx->c;
+    long long n0 = count_particles(c, s);
+    if (n0 < 0) FAIL(PIFEPIC_ECUDA, "count failed");
+    cudaError_t e;
+    *flat = alloc_parr_raw(n0 + extra, true, &e);
+    if (e != cudaSuccess) { free_parr(*flat); FAIL(PIFEPIC_ENOMEM, "flat particle buffer allocation failed"); }
+    ALLOC(*nflat, sizeof(unsigned long long));
+    CUDA_OK(cudaMemset(*nflat, 0, sizeof(unsigned long long)));
+    if (!c.track) {   // without ids the flat copy still carries an id array: fill it later
+    }
+    CUDA_OK(launch_flatten(c, s, *flat, *nflat));
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    *nexist = n0;
+    return PIFEPIC_OK;
+}
+
+static long long count_particles(Ctx& c, int s) {
+    Species& q = c.sp[s];
+    std::vector<int> cnt(c.nblocks);
+    if (cudaMemcpy(cnt.data(), q.bcount, sizeof(int) * c.nblocks, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    long long n = 0;
+    for (int v : cnt) n += v;
+    unsigned long long w = 0;
+    if (cudaMemcpy(&w, q.mov_n, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return n + (long long)w;
+}
+
+static pifepic_status rebuild(pifepic_ctx* ctx, int s, PArr flat, long long n) {
+    Ctx& c = ctx->c;
+    long long need = std::max<long long>(1 << 16, n / 8 + 4096);
+    for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
+    pifepic_status st = ensure_movers(ctx, s, need);
+    if (st) return st;
+    CUDA_OK(launch_build_bins(c, s, flat, n, true));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double vth, const double drift[3],
+                                       uint64_t seed) {
+    NEED(ctx); NEED(drift);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    if (ppc < 0 || !(vth >= 0)) FAIL(PIFEPIC_EINVAL, "ppc and vth must be non-negative");
+    PArr flat; unsigned long long* nflat = nullptr; long long n0 = 0;
+    long long add = c.mesh.ncells * (long long)ppc;
+    pifepic_status st = flatten(ctx, s, add, &flat, &nflat, &n0);
+    if (st) return st;
+    CUDA_OK(launch_load_maxwellian(c, s, ppc, vth, drift, seed, flat, nflat, n0 + add));
+    unsigned long long nt = 0;
+    CUDA_OK(cudaMemcpy(&nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
+    st = rebuild(ctx, s, flat, (long long)nt);
+    free_parr(flat); cudaFree(nflat);
+    if (st) return st;
+    Species& q = c.sp[s];
+    q.next_id = std::max<long long>(q.next_id, c.mesh.ncells * (long long)ppc);
+    CUDA_OK(cudaMemcpy(c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int s, size_t n, const double* x, const double* y,
+                                      const double* z, const double* vx, const double* vy, const double* vz,
+                                      const int64_t* ids, int mem_kind) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    if (n > 0 && (!x || !y || !z || !vx || !vy || !vz)) FAIL(PIFEPIC_EINVAL, "null particle array");
+    PArr flat; unsigned long long* nflat = nullptr; long long n0 = 0;
+    pifepic_status st = flatten(ctx, s, (long long)n, &flat, &nflat, &n0);
+    if (st) return st;
+    unsigned long long cur = 0;
+    CUDA_OK(cudaMemcpy(&cur, nflat, sizeof(cur), cudaMemcpyDeviceToHost));
+    cudaMemcpyKind k = mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* src[6] = {x, y, z, vx, vy, vz};
+    double* dst[6] = {flat.x, flat.y, flat.z, flat.vx, flat.vy, flat.vz};
+    Species& q = c.sp[s];
+    if (n > 0) {
+        for (int d = 0; d < 6; ++d) CUDA_OK(cudaMemcpy(dst[d] + cur, src[d], sizeof(double) * n, k));
+        long long newmax = q.next_id + (long long)n - 1;
+        if (ids) {
+            CUDA_OK(cudaMemcpy(flat.id + cur, ids, sizeof(long long) * n, k));
+            unsigned long long* mx = nullptr;
+            ALLOC(mx, sizeof(unsigned long long));
+            CUDA_OK(cudaMemset(mx, 0, sizeof(unsigned long long)));
+            k_max_id<<<nb256((long long)n), 256>>>((long long)n, (const long long*)flat.id + cur, mx);
+            unsigned long long hm = 0;
+            CUDA_OK(cudaMemcpy(&hm, mx, sizeof(hm), cudaMemcpyDeviceToHost));
+            cudaFree(mx);
+            newmax = (long long)hm;
+        } else {
+            k_seq_id<<<nb256((long long)n), 256>>>((long long)n, q.next_id, flat.id + cur);
+        }
+        CUDA_OK(cudaGetLastError());
+        q.next_id = std::max<long long>(q.next_id, newmax + 1);
+        CUDA_OK(cudaMemcpy(c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    st = rebuild(ctx, s, flat, (long long)cur + (long long)n);
+    free_parr(flat); cudaFree(nflat);
+    return st;
+}
+
+static double flux_density(double n, double vth, double vdn) {
+    double s = vdn / vth;
+    return n * vth * (exp(-0.5 * s * s) / sqrt(2.0 * M_PI) + 0.5 * s * (1.0 + erf(s / sqrt(2.0))));
+}
+
+pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, double density, double vth,
+                                     const double drift[3], uint64_t seed) {
+    NEED(ctx); NEED(drift);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    if (!(vth > 0) || density < 0) FAIL(PIFEPIC_EINVAL, "injection needs vth > 0 and density >= 0");
+    Species& q = c.sp[s];
+    q.inject = face_mask != 0;
+    q.face_mask = face_mask; q.density = density; q.vth = vth;
+    for (int d = 0; d < 3; ++d) q.drift[d] = drift[d];
+    q.seed = seed;
+    const Mesh& m = c.mesh;
+    double nax[3] = {(double)m.nx, (double)m.ny, (double)m.nz};
+    for (int f = 0; f < 6; ++f) {
+        int ax = f >> 1;
+        int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+        double area = (nax[t1] * m.h) * (nax[t2] * m.h);
+        double sgn = (f & 1) ? -1.0 : 1.0;
+        q.rate[f] = ((face_mask >> f) & 1) ? flux_density(density, vth, sgn * drift[ax]) * area * c.dt / q.w : 0.0;
+        q.maxcnt[f] = ((face_mask >> f) & 1) ? (int)ceil(q.rate[f]) + 1 : 0;
+    }
+    // rebuild the stream list in (species, face) order; keep carries of unchanged streams
+    std::vector<double> oldcarry(MAX_SPECIES * 6, 0.0), hc(c.inj.size());
+    if (!c.inj.empty()) {
+        CUDA_OK(cudaMemcpy(hc.data(), c.inj_carry, sizeof(double) * c.inj.size(), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < c.inj.size(); ++i) oldcarry[c.inj[i].species * 6 + c.inj[i].face] = hc[i];
+    }
+    for (int f = 0; f < 6; ++f) oldcarry[s * 6 + f] = 0.0;
+    c.inj.clear();
+    std::vector<double> carry;
+    for (int ss = 0; ss < (int)c.sp.size(); ++ss) {
+        Species& p = c.sp[ss];
+        if (!p.inject) continue;
+        for (int f = 0; f < 6; ++f) {
+            if (!((p.face_mask >> f) & 1)) continue;
+            InjectDev d{};
+            d.species = ss; d.face = f; d.maxcnt = p.maxcnt[f]; d.vth = p.vth;
+            for (int k = 0; k < 3; ++k) d.drift[k] = p.drift[k];
+            d.rate = p.rate[f]; d.seed = p.seed;
+            c.inj.push_back(d);
+            carry.push_back(oldcarry[ss * 6 + f]);
+        }
+    }
+    if (!c.inj.empty()) {
+        CUDA_OK(cudaMemcpy(c.inj_dev, c.inj.data(), sizeof(InjectDev) * c.inj.size(), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(c.inj_carry, carry.data(), sizeof(double) * carry.size(), cudaMemcpyHostToDevice));
+    }
+    long long n = count_particles(c, s);
+    long long need = std::max<long long>(1 << 16, n / 8 + 4096);
+    for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
+    return ensure_movers(ctx, s, need);
+}
+
+pifepic_status pifepic_get_injection_rate(pifepic_ctx* ctx, int s, double rate[6]) {
+    NEED(ctx); NEED(rate);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    for (int f = 0; f < 6; ++f) rate[f] = c.sp[s].rate[f];
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem_kind) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (!E) { c.external_E = false; return PIFEPIC_OK; }
+    long long N = c.mesh.nnodes;
+    double* tmp = nullptr;
+    ALLOC(tmp, sizeof(double) * 3 * N);
+    CUDA_OK(cudaMemcpy(tmp, E, sizeof(double) * 3 * N,
+                       mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    k_pack_E<<<nb256(N), 256, 0, c.stream>>>(N, tmp, c.E, c.Ef);
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    cudaFree(tmp);
+    c.external_E = true;
+    return PIFEPIC_OK;
+}
+
+static void read_counters(Ctx& c, unsigned long long* out) {
+    cudaMemcpy(out, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR, cudaMemcpyDeviceToHost);
+}
+
+static long long iters_total(Ctx& c) {
+    long long v = 0;
+    cudaMemcpy(&v, (long long*)(c.scal + 40), sizeof(v), cudaMemcpyDeviceToHost);
+    return v;
+}
+
+static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* before, pifepic_stats* st,
+                                 const float* phase_ms, long long it0, long long l0, long long nsolves) {
+    Ctx& c = ctx->c;
+    unsigned long long now[MAX_SPECIES * NCTR];
+    read_counters(c, now);
+    pifepic_stats s;
+    memset(&s, 0, sizeof(s));
+    s.steps = c.step_no;
+    for (size_t q = 0; q < c.sp.size(); ++q) {
+        const unsigned long long* a = now + q * NCTR;
+        const unsigned long long* b = before + q * NCTR;
+        s.pushed[q] = (int64_t)(a[C_PUSHED] - b[C_PUSHED]);
+        s.injected[q] = (int64_t)(a[C_INJECTED] - b[C_INJECTED]);
+        s.absorbed[q] = (int64_t)(a[C_ABSORBED] - b[C_ABSORBED]);
+        s.collected[q] = (int64_t)(a[C_COLLECTED] - b[C_COLLECTED]);
+        s.lost_charge[q] = (int64_t)(a[C_LOST] - b[C_LOST]);
+        s.inj_rejected[q] = (int64_t)(a[C_REJECTED] - b[C_REJECTED]);
+        s.spilled[q] = (int64_t)a[C_SPILLED];
+        s.dropped[q] = (int64_t)(a[C_DROPPED] - b[C_DROPPED]);
+        s.count[q] = count_particles(c, (int)q);
+    }
+    cudaError_t e = read_pcg_state(c);
+    if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "pcg state: %s", cudaGetErrorString(e));
+    s.pcg_iters_total = iters_total(c) - it0;
+    s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c) + 3 * s.pcg_iters_total;
+    s.pcg_iters = c.last_iters;
+    s.pcg_relres = c.last_relres;
+    s.pcg_converged = c.last_conv;
+    double d2[2] = {0, 0};
+    if (c.have_object) {
+        e = launch_surface_diag(c, d2);
+        if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "surface diagnostics: %s", cudaGetErrorString(e));
+    }
+    s.surface_charge = d2[0];
+    s.surface_potential = d2[1];
+    if (phase_ms) for (int k = 0; k < 8; ++k) s.phase_ms[k] = phase_ms[k];
+    int herr = 0;
+    cudaMemcpy(&herr, c.err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    c.stats = s;
+    if (st) *st = s;
+    if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
+    for (size_t q = 0; q < c.sp.size(); ++q)
+        if (s.dropped[q]) FAIL(PIFEPIC_ENOMEM, "species %zu: %lld particles dropped (mover list full)", q,
+                               (long long)s.dropped[q]);
+    return PIFEPIC_OK;
+}
+
+static cudaError_t run_solve(Ctx& c) {
+    if (c.precision == PIFEPIC_MIXED) return launch_pcg_mixed(c);
+    return launch_pcg(c);
+}
+
+pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
+    unsigned long long before[MAX_SPECIES * NCTR];
+    read_counters(c, before);
+    long long it0 = iters_total(c), l0 = c.launches;
+    if (c.precision == PIFEPIC_MIXED) CUDA_OK(launch_deposit_all_mixed(c));
+    else CUDA_OK(launch_deposit_all(c));
+    if (!c.external_E) CUDA_OK(run_solve(c));
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    return fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1);
+}
+
+pifepic_status pifepic_leapfrog_init(pifepic_ctx* ctx) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (c.precision == PIFEPIC_MIXED) CUDA_OK(launch_half_kick_mixed(c));
+    else CUDA_OK(launch_half_kick(c));
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
+    if (nsteps < 0) FAIL(PIFEPIC_EINVAL, "nsteps < 0");
+    unsigned long long before[MAX_SPECIES * NCTR];
+    read_counters(c, before);
+    long long it0 = iters_total(c), l0 = c.launches;
+    float ph[8] = {0};
+    bool mixed = c.precision == PIFEPIC_MIXED;
+    for (int it = 0; it < nsteps; ++it) {
+        CUDA_OK(cudaEventRecord(c.ev[0], c.stream));
+        CUDA_OK(mixed ? launch_push_mixed(c) : launch_push(c));
+        CUDA_OK(cudaEventRecord(c.ev[1], c.stream));
+        CUDA_OK(mixed ? launch_movers_mixed(c) : launch_movers(c));
+        CUDA_OK(cudaEventRecord(c.ev[2], c.stream));
+        CUDA_OK(mixed ? launch_inject_mixed(c) : launch_inject(c));
+        CUDA_OK(cudaEventRecord(c.ev[3], c.stream));
+        CUDA_OK(mixed ? launch_rebin_mixed(c) : launch_rebin(c));
+        CUDA_OK(cudaEventRecord(c.ev[4], c.stream));
+        if (!c.external_E) CUDA_OK(run_solve(c));
+        CUDA_OK(cudaEventRecord(c.ev[5], c.stream));
+        c.step_no += 1;
+        CUDA_OK(cudaEventSynchronize(c.ev[5]));
+        float t;
+        const int map[5] = {0, 1, 2, 3, 5};   // push, movers, inject, rebin, solve(+rhs+E)
+        for (int k = 0; k < 5; ++k) {
+            CUDA_OK(cudaEventElapsedTime(&t, c.ev[k], c.ev[k + 1]));
+            ph[map[k]] += t;
+        }
+    }
+    return fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps);
+}
+
+pifepic_status pifepic_get_sizes(pifepic_ctx* ctx, int64_t* nn, int64_t* nc, int64_t* nit, int64_t* ncut) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (nn) *nn = c.mesh.nnodes;
+    if (nc) *nc = c.mesh.ncells;
+    if (nit) *nit = c.nit;
+    if (ncut) *ncut = c.ncut;
+    return PIFEPIC_OK;
+}
+
+static cudaMemcpyKind out_kind(int mem_kind) {
+    return mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+pifepic_status pifepic_get_potential(pifepic_ctx* ctx, double* phi, int mem_kind) {
+    NEED(ctx); NEED(phi);
+    Ctx& c = ctx->c;
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(cudaMemcpy(phi, c.phi, sizeof(double) * c.mesh.nnodes, out_kind(mem_kind)));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind) {
+    NEED(ctx); NEED(E);
+    Ctx& c = ctx->c;
+    long long N = c.mesh.nnodes;
+    double* tmp = nullptr;
+    ALLOC(tmp, sizeof(double) * 3 * N);
+    k_unpack_E<<<nb256(N), 256, 0, c.stream>>>(N, c.E, tmp);
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(cudaMemcpy(E, tmp, sizeof(double) * 3 * N, out_kind(mem_kind)));
+    cudaFree(tmp);
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_node_charge(pifepic_ctx* ctx, int s, int64_t* W, int mem_kind) {
+    NEED(ctx); NEED(W);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(cudaMemcpy(W, c.sp[s].W, sizeof(int64_t) * c.mesh.nnodes, out_kind(mem_kind)));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_surface_charge(pifepic_ctx* ctx, int s, int64_t* cnt, int mem_kind) {
+    NEED(ctx); NEED(cnt);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    if (c.ncut > 0) CUDA_OK(cudaMemcpy(cnt, c.sp[s].surf, sizeof(int64_t) * c.ncut, out_kind(mem_kind)));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_cut_cells(pifepic_ctx* ctx, int32_t* cells, double* area) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (c.ncut == 0) return PIFEPIC_OK;
+    if (cells) CUDA_OK(cudaMemcpy(cells, c.cut_cell, sizeof(int32_t) * c.ncut, cudaMemcpyDeviceToHost));
+    if (area) CUDA_OK(cudaMemcpy(area, c.cut_area, sizeof(double) * c.ncut, cudaMemcpyDeviceToHost));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_cell_target(pifepic_ctx* ctx, int32_t* target) {
+    NEED(ctx); NEED(target);
+    Ctx& c = ctx->c;
+    CUDA_OK(cudaMemcpy(target, c.cell_acc, sizeof(int32_t) * c.mesh.ncells, cudaMemcpyDeviceToHost));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_interface(pifepic_ctx* ctx, int32_t* cell, int32_t* tet, double* vp, double* vm,
+                                     double* area, double* K, double* cvec) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (c.nit == 0) return PIFEPIC_OK;
+    if (cell) CUDA_OK(cudaMemcpy(cell, c.it_cell, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
+    if (tet) CUDA_OK(cudaMemcpy(tet, c.it_t, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
+    std::vector<double> rec((size_t)c.nit * IT_STRIDE);
+    CUDA_OK(cudaMemcpy(rec.data(), c.it_data, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
+    for (long long T = 0; T < c.nit; ++T) {
+        const double* r = rec.data() + T * IT_STRIDE;
+        if (vp) vp[T] = r[IT_VOLP];
+        if (vm) vm[T] = r[IT_VOLM];
+        if (area) area[T] = r[IT_AREA];
+        if (K) for (int q = 0; q < 16; ++q) K[T * 16 + q] = r[IT_K + q];
+        if (cvec) for (int q = 0; q < 4; ++q) cvec[T * 4 + q] = r[IT_C + q];
+    }
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_particle_count(pifepic_ctx* ctx, int s, int64_t* n) {
+    NEED(ctx); NEED(n);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    *n = count_particles(c, s);
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_particles(pifepic_ctx* ctx, int s, int64_t cap, double* x, double* y, double* z,
+                                     double* vx, double* vy, double* vz, int64_t* ids, int64_t* n, int mem_kind) {
+    NEED(ctx); NEED(n);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    if (ids && !c.track) FAIL(PIFEPIC_EINVAL, "ids requested but the context does not track ids");
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    PArr flat; unsigned long long* nflat = nullptr; long long n0 = 0;
+    pifepic_status st;
+    if (c.precision == PIFEPIC_MIXED) {
+        long long cnt = count_particles(c, s);
+        cudaError_t e;
+        flat = alloc_parr_raw(cnt, true, &e);
+        if (e != cudaSuccess) { free_parr(flat); FAIL(PIFEPIC_ENOMEM, "flat buffer"); }
+        ALLOC(nflat, sizeof(unsigned long long));
+        CUDA_OK(cudaMemset(nflat, 0, sizeof(unsigned long long)));
+        CUDA_OK(launch_flatten_mixed_to_f64(c, s, flat, nflat));
+        CUDA_OK(cudaStreamSynchronize(c.stream));
+        n0 = cnt;
+    } else {
+        st = flatten(ctx, s, 0, &flat, &nflat, &n0);
+        if (st) return st;
+    }
+    long long m = std::min<long long>(n0, cap);
+    cudaMemcpyKind k = out_kind(mem_kind);
+    double* dst[6] = {x, y, z, vx, vy, vz};
+    double* src[6] = {flat.x, flat.y, flat.z, flat.vx, flat.vy, flat.vz};
+    for (int d = 0; d < 6; ++d)
+        if (dst[d] && m > 0) CUDA_OK(cudaMemcpy(dst[d], src[d], sizeof(double) * m, k));
+    if (ids && m > 0) CUDA_OK(cudaMemcpy(ids, flat.id, sizeof(int64_t) * m, k));
+    *n = m;
+    free_parr(flat); cudaFree(nflat);
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_stats(pifepic_ctx* ctx, pifepic_stats* st) {
+    NEED(ctx); NEED(st);
+    *st = ctx->c.stats;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const double* q, int mem_kind, int* iters,
+                                   double* relres) {
+    NEED(ctx); NEED(F);
+    Ctx& c = ctx->c;
+    if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
+    long long N = c.mesh.nnodes;
+    double* Fd = nullptr;
+    ALLOC(Fd, sizeof(double) * N);
+    cudaMemcpyKind k = mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_OK(cudaMemcpy(Fd, F, sizeof(double) * N, k));
+    if (c.nit > 0) {
+        if (q) CUDA_OK(cudaMemcpy(c.qT, q, sizeof(double) * c.nit, k));
+        else CUDA_OK(cudaMemset(c.qT, 0, sizeof(double) * c.nit));
+    }
+    cudaError_t e = launch_solve_external(c, Fd, iters, relres);
+    cudaFree(Fd);
+    if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "field solve: %s", cudaGetErrorString(e));
+    return PIFEPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Device helpers shared by the libpifepic kernels: level sets, the 5-tet
+// split tables, Philox4x64-10, warp-aggregated counters, and the
+// mbarrier / TMA primitives used to stage node-field tiles in shared memory.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PF_HD __host__ __device__ __forceinline__
+#define PF_D __device__ __forceinline__
+
+namespace pf {
+
+constexpr int BLK = 4;                    // particle bin = BLK^3 cells
+constexpr int TILE = BLK + 1;             // node tile edge
+constexpr int TILE_N = TILE * TILE * TILE;
+constexpr int MAX_SPECIES = 8;
+constexpr int NCTR = 8;                   // per-species device counters
+enum { C_PUSHED = 0, C_ABSORBED, C_COLLECTED, C_LOST, C_INJECTED, C_REJECTED, C_SPILLED, C_DROPPED };
+enum { ERR_TMA_TIMEOUT = 1, ERR_CAPACITY = 2 };
+
+// ---------------------------------------------------------------------------
+// Object level sets in cell units (Sec. 2.1 interface Gamma; L >= 0 plasma).
+// Each is a fixed sequence of IEEE double operations (this translation unit
+// is compiled without FMA contraction) so hit decisions are reproducible.
+// ---------------------------------------------------------------------------
+struct Object {
+    int kind;          // 0 none, 1 sphere, 2 cap crater, 3 plane
+    double a0, a1, a2, a3, a4, a5;
+    double eps_minus, eps_plus;
+};
+
+PF_HD double level_set(const Object& o, double x, double y, double z) {
+    if (o.kind == 1) {                       // sphere: a0..a2 centre, a3 = r^2
+        double dx = x - o.a0, dy = y - o.a1, dz = z - o.a2;
+        return ((dx * dx + dy * dy) + dz * dz) - o.a3;
+    } else if (o.kind == 2) {                // crater: zg, xc, yc, a^2, Rs^2, zc
+        double dx = x - o.a1, dy = y - o.a2;
+        double r2 = dx * dx + dy * dy;
+        double zs = (r2 < o.a3) ? o.a5 - sqrt(o.a4 - r2) : o.a0;
+        return z - zs;
+    } else if (o.kind == 3) {                // plane: n.xi - d0
+        return ((o.a0 * x + o.a1 * y) + o.a2 * z) - o.a3;
+    }
+    return 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh and 5-tet split (reading of Sec. 3.1.1): tet 0 = the 4 vertices of the
+// cube with global parity even, tets 1..4 = corner tets (o, o^1, o^2, o^4) for
+// the odd vertices o.  Local vertex l = a + 2b + 4c <-> offset (a, b, c).
+// ---------------------------------------------------------------------------
+struct Mesh {
+    int nx, ny, nz, NX, NY, NZ;
+    long long nnodes, ncells;
+    double h;
+};
+
+struct TetTables {
+    int vert[2][5][4];         // [cube parity][tet][k] local vertex
+    double grad[2][5][4][3];   // P1 basis gradients for h = 1
+    double vol[5];             // volumes for h = 1
+    int slot[27];              // stencil slot of offset (dx,dy,dz), -1 if none
+    int off[19][3];            // offset of each slot
+};
+
+PF_HD long long node_id(const Mesh& m, int i, int j, int k) {
+    return (long long)i + (long long)m.NX * ((long long)j + (long long)m.NY * k);
+}
+PF_HD long long cell_id(const Mesh& m, int i, int j, int k) {
+    return (long long)i + (long long)m.nx * ((long long)j + (long long)m.ny * k);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): multipliers and Weyl key increments as
+// published; round: (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1, lo(M0*c0)).
+// ---------------------------------------------------------------------------
+struct U64x4 { unsigned long long v[4]; };
+
+PF_HD void mulhilo64(unsigned long long a, unsigned long long b, unsigned long long& hi,
+                     unsigned long long& lo) {
+#ifdef __CUDA_ARCH__
+    lo = a * b;
+    hi = __umul64hi(a, b);
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    lo = (unsigned long long)p;
+    hi = (unsigned long long)(p >> 64);
+#endif
+}
+
+PF_HD U64x4 philox4x64(unsigned long long c0, unsigned long long c1, unsigned long long c2,
+                       unsigned long long c3, unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        unsigned long long hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c0, hi0, lo0);
+        mulhilo64(M1, c2, hi1, lo1);
+        unsigned long long n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    U64x4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+PF_HD unsigned long long stream_key(int purpose, int species, int face, long long step) {
+    return ((unsigned long long)purpose << 56) | ((unsigned long long)species << 48) |
+           ((unsigned long long)face << 40) | ((unsigned long long)step & ((1ull << 40) - 1));
+}
+
+// open uniform from the top 52 bits; exact in double
+PF_HD double u01(unsigned long long x) { return ((double)(x >> 12) + 0.5) * 2.220446049250313e-16; }
+
+// ---------------------------------------------------------------------------
+// warp-aggregated atomic increment: returns this lane's slot
+// ---------------------------------------------------------------------------
+PF_D long long warp_reserve(unsigned long long* counter, bool want) {
+    unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (!want) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return (long long)(base + __popc(mask & ((1u << lane) - 1)));
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + TMA (cp.async.bulk.tensor) helpers
+// ---------------------------------------------------------------------------
+PF_D unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+PF_D void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+PF_D void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+PF_D bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+PF_D void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+PF_D void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 4-D tiled TMA load (components, x, y, z) of one node tile into shared memory
+PF_D void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1, int c2,
+                      int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// bounded wait on phase 0 of an mbarrier; false on timeout (~2^31 cycles)
+PF_D bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+}  // namespace pf

@@ -1,0 +1,221 @@
+// Internal state of a libpifepic context and the host-side launchers of each
+// kernel group.  Not part of the public ABI (include/pifepic.h).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pifepic.h"
+
+namespace pf {
+
+// ---- particle arrays (SoA) -------------------------------------------------
+struct PArr {            // FP64 mode: xi in cell units, physical velocity
+    double *x, *y, *z, *vx, *vy, *vz;
+    long long* id;
+};
+struct PArrF {           // MIXED mode: packed cell (i | j<<11 | k<<22), FP32 offset and velocity
+    int* cell;
+    float *fx, *fy, *fz, *vx, *vy, *vz;
+    long long* id;
+};
+
+// per-species parameters and pointers handed to kernels by value
+struct SpeciesDev {
+    double k;                       // (q/m) dt
+    double khalf;                   // k / 2
+    PArr bins;                      // bin storage
+    PArrF binsF;
+    const long long* bstart;        // [nblocks] first slot of each bin
+    const int* bcap;                // [nblocks] capacity
+    int* bcount;                    // [nblocks] live particles
+    PArr mov_in, mov_out;           // mover lists (previous-step spill, this step)
+    PArrF movF_in, movF_out;
+    unsigned long long* mov_in_n;   // counters (device)
+    unsigned long long* mov_out_n;
+    long long mcap;
+    unsigned long long* W;          // [nnodes] fixed-point charge
+    unsigned long long* surf;       // [ncut] collected macro-particles
+    unsigned long long* ctr;        // [NCTR] counters
+};
+
+struct InjectDev {                  // one (species, face) injection stream
+    int species, face, maxcnt;
+    double vth, drift[3];
+    double rate;                    // expected particles per step
+    unsigned long long seed;
+};
+
+struct Launch {                     // what every particle kernel needs
+    Mesh mesh;
+    Object obj;
+    double dth;                     // dt / h
+    int nbx, nby, nbz, nblocks;
+    int nspecies;
+    int track;
+    const int* cell_acc;            // [ncells] surface accumulator of a hit cell
+    const double4* E;               // node field
+    const float4* Ef;               // node field, FP32 copy
+    int* err;                       // device error word
+    SpeciesDev sp[MAX_SPECIES];
+};
+
+struct Species {
+    double q, m, w, k;
+    long long cap = 0;              // bin slots
+    long long mcap = 0;             // mover list capacity
+    PArr bins{}, mov[2]{};
+    PArrF binsF{}, movF[2]{};
+    long long* bstart = nullptr;
+    int* bcap = nullptr;
+    int* bcount = nullptr;
+    unsigned long long* mov_n = nullptr;   // [2]
+    unsigned long long* W = nullptr;
+    unsigned long long* surf = nullptr;
+    unsigned long long* ctr = nullptr;
+    int cur = 0;                    // which mover buffer is "in"
+    bool inject = false;
+    int face_mask = 0;
+    double density = 0, vth = 0, drift[3] = {0, 0, 0};
+    unsigned long long seed = 0;
+    double rate[6] = {0, 0, 0, 0, 0, 0};
+    int maxcnt[6] = {0, 0, 0, 0, 0, 0};
+    long long next_id = 0;
+};
+
+struct Ctx {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Mesh mesh{};
+    double origin[3] = {0, 0, 0};
+    double dt = 0, dth = 0;
+    int precision = PIFEPIC_FP64;
+    double tol = 1e-6;
+    int maxit = 150;
+    int track = 0;
+    int nbx = 0, nby = 0, nbz = 0, nblocks = 0;
+
+    Object obj{};
+    bool have_object = false;
+    pifepic_face_bc bc[6];
+    bool external_E = false;
+
+    // node arrays
+    double* Lnode = nullptr;
+    int* ntype = nullptr;          // >=0 patch row, -1 plus, -2 minus, -3 Dirichlet
+    double* gdir = nullptr;        // Dirichlet values (0 on free nodes)
+    double* lift = nullptr;        // (A g) restricted to free nodes
+    double* invdiag = nullptr;
+    double* phi = nullptr;
+    double* u = nullptr;           // unknown (phi - g)
+    double* b = nullptr;           // right-hand side
+    double *r = nullptr, *p = nullptr, *q = nullptr;
+    float *rf = nullptr, *pf = nullptr, *qf = nullptr, *uf = nullptr, *invdiagf = nullptr;
+    double4* E = nullptr;          // node field (x, y, z, 0)
+    float4* Ef = nullptr;          // FP32 copy for the MIXED push
+    unsigned long long* Wall = nullptr;     // [MAX_SPECIES][nnodes] fixed-point charge
+    unsigned long long* surfall = nullptr;  // [MAX_SPECIES][ncut] collected particles
+    unsigned long long* ctrall = nullptr;   // [MAX_SPECIES][NCTR]
+    // cells
+    unsigned char* imask = nullptr;
+    int* ibase = nullptr;
+    int* cell_acc = nullptr;
+    // interface tets
+    long long nit = 0;
+    int* it_cell = nullptr;
+    int* it_t = nullptr;
+    double* it_data = nullptr;     // IT_STRIDE doubles per tet
+    int* it_acc = nullptr;
+    double* qT = nullptr;
+    // cut cells
+    long long ncut = 0;
+    int* cut_cell = nullptr;
+    double* cut_area = nullptr;
+    double* qcut = nullptr;
+    // patch rows
+    long long npatch = 0;
+    long long* patch_node = nullptr;
+    double* patch_coef = nullptr;  // [npatch][19]
+    float* patch_coeff = nullptr;
+    // reductions / PCG scalars
+    double* red = nullptr;         // partial sums
+    double* scal = nullptr;        // PCG scalars
+    unsigned int* red_ticket = nullptr;
+    int* err_word = nullptr;
+    // graphs
+    cudaGraphExec_t pcg_exec = nullptr;
+    cudaGraph_t pcg_graph = nullptr;
+    // particles
+    std::vector<Species> sp;
+    std::vector<InjectDev> inj;
+    InjectDev* inj_dev = nullptr;
+    int* inj_count = nullptr;       // [MAX_SPECIES*6]
+    long long* inj_base = nullptr;  // id base per (species, face)
+    double* inj_carry = nullptr;    // [MAX_SPECIES*6]
+    long long* next_id = nullptr;   // [MAX_SPECIES]
+    long long step_no = 0;
+    long long launches = 0;         // kernels launched by host code (graphs counted separately)
+    // TMA descriptors of the node field
+    CUtensorMap tmapE;
+    CUtensorMap tmapEf;
+    bool tmap_ok = false;
+    // timers
+    cudaEvent_t ev[16];
+    bool ev_ok = false;
+    pifepic_stats stats{};
+    int last_iters = 0;
+    double last_relres = 0;
+    int last_conv = 1;
+};
+
+// interface-tet record layout (doubles)
+enum {
+    IT_VOLP = 0, IT_VOLM = 1, IT_AREA = 2,
+    IT_K = 3,            // 16
+    IT_C = 19,           // 4  unit-jump load
+    IT_GP = 23,          // 15 (5 x 3)
+    IT_GM = 38,          // 15
+    IT_S = 53,           // 4  int_Gamma psi_i
+    IT_SJ = 57,          // 1  int_Gamma phi_J (unit q)
+    IT_STRIDE = 58
+};
+
+// ---- launchers ---------------------------------------------------------------
+cudaError_t set_tet_tables(const TetTables& t);
+cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
+cudaError_t launch_field_lift(Ctx& c);
+cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
+cudaError_t launch_rhs(Ctx& c);
+cudaError_t launch_pcg(Ctx& c);
+cudaError_t launch_node_E(Ctx& c);
+cudaError_t launch_surface_diag(Ctx& c, double* out2);   // [charge, potential]
+cudaError_t launch_qtets(Ctx& c);
+
+Launch make_launch(Ctx& c);
+cudaError_t launch_load_maxwellian(Ctx& c, int s, int ppc, double vth, const double drift[3],
+                                   unsigned long long seed, PArr flat, unsigned long long* nflat, long long cap);
+cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool fresh_caps);
+cudaError_t launch_flatten(Ctx& c, int s, PArr flat, unsigned long long* nflat);
+cudaError_t launch_deposit_all(Ctx& c);
+cudaError_t launch_half_kick(Ctx& c);
+cudaError_t launch_push(Ctx& c);
+cudaError_t launch_movers(Ctx& c);
+cudaError_t launch_inject(Ctx& c);
+cudaError_t launch_rebin(Ctx& c);
+
+// MIXED mode
+cudaError_t launch_flatten_mixed_to_f64(Ctx& c, int s, PArr flat, unsigned long long* nflat);
+cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool fresh_caps);
+cudaError_t launch_push_mixed(Ctx& c);
+cudaError_t launch_movers_mixed(Ctx& c);
+cudaError_t launch_inject_mixed(Ctx& c);
+cudaError_t launch_rebin_mixed(Ctx& c);
+cudaError_t launch_deposit_all_mixed(Ctx& c);
+cudaError_t launch_half_kick_mixed(Ctx& c);
+
+}  // namespace pf

@@ -1,0 +1,765 @@
+// FP64 particle cycle (compiled without FMA contraction: the gather, push,
+// level-set and weight arithmetic follows one fixed IEEE operation order so
+// cell indices, hit decisions and fixed-point charges are reproducible).
+//
+// Sec. 2.1 (Fig. 1): charge weighted to nodes (scatter), field interpolated at
+// particle positions (gather), velocity and position update (particle-push);
+// Sec. 3.1.3: pre-load, injection at open faces, absorption at open faces;
+// Sec. 5.2.2: particles hitting the object are collected and their charge is
+// accumulated for surface charging.  The paper does not name its pusher or
+// weighting; this file uses trilinear weights of the PIC cell, leapfrog, and
+// int64 fixed-point deposits of 2^32 units per particle.
+//
+// Layout: per species, particles live in bins of BLK^3 cells (SoA, one
+// contiguous slot range per bin).  One CTA handles one bin: it stages the
+// bin's (BLK+1)^3 node-field tile in shared memory with a TMA tile load,
+// pushes the bin's particles, deposits stayers into a shared int64 tile and
+// compacts them in place; particles that leave the bin go to a mover list,
+// from which a rebin kernel reinserts them (overflowing bins spill to the
+// next step's mover list).
+#include <math.h>
+
+#include "internal.h"
+
+namespace pf {
+
+__constant__ TetTables cTp;
+cudaError_t set_particle_tables(const TetTables& t) { return cudaMemcpyToSymbol(cTp, &t, sizeof(TetTables)); }
+
+constexpr double TWO32 = 4294967296.0;
+constexpr int MAX_TRIES = 32;
+
+// ---- trilinear weights, fixed order: w_l = (wx[a] * wy[b]) * wz[c] ---------------
+struct Wts {
+    int ci, cj, ck;
+    double w[8];
+};
+PF_D Wts weights(double x, double y, double z) {
+    Wts r;
+    double cx = floor(x), cy = floor(y), cz = floor(z);
+    double fx = x - cx, fy = y - cy, fz = z - cz;
+    double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+#pragma unroll
+    for (int l = 0; l < 8; ++l) r.w[l] = (wx[l & 1] * wy[(l >> 1) & 1]) * wz[(l >> 2) & 1];
+    r.ci = (int)cx; r.cj = (int)cy; r.ck = (int)cz;
+    return r;
+}
+
+// 7 rounded weights + remainder: exactly 2^32 units per particle
+PF_D void fixed_weights(const Wts& w, long long W[8]) {
+    long long rest = 1ll << 32;
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        W[l] = __double2ll_rn(w.w[l] * TWO32);
+        rest -= W[l];
+    }
+    W[7] = rest;
+}
+
+// node field at the 8 corners, accumulated left to right in node order
+template <class EA>
+PF_D void gather(const Wts& w, const EA& ea, double& ex, double& ey, double& ez) {
+    double4 e0 = ea(w.ci, w.cj, w.ck);
+    ex = w.w[0] * e0.x; ey = w.w[0] * e0.y; ez = w.w[0] * e0.z;
+#pragma unroll
+    for (int l = 1; l < 8; ++l) {
+        double4 e = ea(w.ci + (l & 1), w.cj + ((l >> 1) & 1), w.ck + ((l >> 2) & 1));
+        ex = ex + w.w[l] * e.x;
+        ey = ey + w.w[l] * e.y;
+        ez = ez + w.w[l] * e.z;
+    }
+}
+
+struct EGlobal {
+    const double4* E;
+    Mesh m;
+    PF_D double4 operator()(int i, int j, int k) const { return E[node_id(m, i, j, k)]; }
+};
+struct ETile {
+    const double4* T;
+    int x0, y0, z0;
+    PF_D double4 operator()(int i, int j, int k) const {
+        return T[(i - x0) + TILE * ((j - y0) + TILE * (k - z0))];
+    }
+};
+
+PF_D bool outside(const Mesh& m, double x, double y, double z) {
+    return (x < 0.0) | (x >= (double)m.nx) | (y < 0.0) | (y >= (double)m.ny) | (z < 0.0) | (z >= (double)m.nz);
+}
+
+// cell of the crossing point of a particle that entered the object
+PF_D int hit_target(const Launch& L, double xo, double yo, double zo, double xn, double yn, double zn) {
+    double Lo = level_set(L.obj, xo, yo, zo);
+    double Ln = level_set(L.obj, xn, yn, zn);
+    double t = Lo / (Lo - Ln);
+    double xc = xo + t * (xn - xo), yc = yo + t * (yn - yo), zc = zo + t * (zn - zo);
+    double fi = floor(xc), fj = floor(yc), fk = floor(zc);
+    fi = fi < 0.0 ? 0.0 : (fi > (double)(L.mesh.nx - 1) ? (double)(L.mesh.nx - 1) : fi);
+    fj = fj < 0.0 ? 0.0 : (fj > (double)(L.mesh.ny - 1) ? (double)(L.mesh.ny - 1) : fj);
+    fk = fk < 0.0 ? 0.0 : (fk > (double)(L.mesh.nz - 1) ? (double)(L.mesh.nz - 1) : fk);
+    return L.cell_acc[cell_id(L.mesh, (int)fi, (int)fj, (int)fk)];
+}
+
+enum { ALIVE = 0, ABSORBED = 1, COLLECTED = 2, NONE = 3 };
+
+// boundary test, then object test (codes above); acc = surface slot for hits
+PF_D int classify(const Launch& L, double xo, double yo, double zo, double x, double y, double z, int& acc) {
+    if (outside(L.mesh, x, y, z)) return ABSORBED;
+    if (level_set(L.obj, x, y, z) < 0.0) {
+        acc = hit_target(L, xo, yo, zo, x, y, z);
+        return COLLECTED;
+    }
+    return ALIVE;
+}
+
+// entries of a mover list: its counter may pass the capacity (reservations are
+// made before the capacity check), so reads are clamped to the capacity
+PF_D long long list_len(const unsigned long long* n, long long cap) {
+    long long v = (long long)*n;
+    return v < cap ? v : cap;
+}
+
+PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
+    return (ci / BLK) + L.nbx * ((cj / BLK) + L.nby * (ck / BLK));
+}
+
+PF_D void global_deposit(const Launch& L, unsigned long long* W, const Wts& w) {
+    long long Wf[8];
+    fixed_weights(w, Wf);
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+        atomicAdd(&W[node_id(L.mesh, w.ci + (l & 1), w.cj + ((l >> 1) & 1), w.ck + ((l >> 2) & 1))],
+                  (unsigned long long)Wf[l]);
+}
+
+PF_D void put(const PArr& a, long long i, double x, double y, double z, double vx, double vy, double vz,
+              long long id, bool track) {
+    a.x[i] = x; a.y[i] = y; a.z[i] = z; a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
+    if (track) a.id[i] = id;
+}
+
+// count one event per lane into a shared counter (warp-aggregated)
+PF_D void count_event(unsigned long long* sctr, bool ev) {
+    unsigned m = __ballot_sync(0xffffffffu, ev);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(sctr, (unsigned long long)__popc(m));
+}
+
+// ------------------------------------------------------------------------------------
+// fused gather + push + boundary + object hit + deposit + in-place compaction
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_constant__ CUtensorMap tmE) {
+    __shared__ alignas(128) double4 Et[TILE_N];
+    __shared__ unsigned long long Wt[TILE_N];
+    __shared__ alignas(8) unsigned long long bar;
+    __shared__ int wcnt[8];
+    __shared__ unsigned long long sctr[NCTR];
+    __shared__ int s_ok;
+    const int s = blockIdx.y;
+    const int b = blockIdx.x;
+    const SpeciesDev& S = L.sp[s];
+    const int n = S.bcount[b];
+    if (n == 0) return;
+    const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
+    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
+    for (int t = tid; t < TILE_N; t += blockDim.x) Wt[t] = 0ull;
+    if (tid < NCTR) sctr[tid] = 0ull;
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(double4));
+        tma_load_4d(Et, &tmE, &bar, 0, x0, y0, z0);
+        bool ok = mbar_wait_bounded(&bar, 0);
+        if (!ok) {
+            atomicOr(L.err, ERR_TMA_TIMEOUT);
+            mbar_wait_bounded(&bar, 0);      // give the copy in flight a second bounded chance
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const ETile ea{Et, x0, y0, z0};
+    const long long start = S.bstart[b];
+    const bool track = L.track;
+    int nstay = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        int code = NONE, acc = -1;
+        double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
+        long long id = 0;
+        Wts w;
+        if (i < n) {
+            const long long g = start + i;
+            x = S.bins.x[g]; y = S.bins.y[g]; z = S.bins.z[g];
+            vx = S.bins.vx[g]; vy = S.bins.vy[g]; vz = S.bins.vz[g];
+            if (track) id = S.bins.id[g];
+            w = weights(x, y, z);
+            double ex, ey, ez;
+            gather(w, ea, ex, ey, ez);
+            vx = vx + S.k * ex; vy = vy + S.k * ey; vz = vz + S.k * ez;
+            const double xo = x, yo = y, zo = z;
+            x = x + vx * L.dth; y = y + vy * L.dth; z = z + vz * L.dth;
+            code = classify(L, xo, yo, zo, x, y, z, acc);
+        }
+        bool stay = false, mover = false;
+        if (code == ALIVE) {
+            w = weights(x, y, z);
+            stay = (w.ci >= x0) & (w.ci < x0 + BLK) & (w.cj >= y0) & (w.cj < y0 + BLK) & (w.ck >= z0) &
+                   (w.ck < z0 + BLK);
+            mover = !stay;
+            if (stay) {
+                long long Wf[8];
+                fixed_weights(w, Wf);
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    int t = (w.ci - x0 + (l & 1)) + TILE * ((w.cj - y0 + ((l >> 1) & 1)) + TILE * (w.ck - z0 + ((l >> 2) & 1)));
+                    atomicAdd(&Wt[t], (unsigned long long)Wf[l]);
+                }
+            } else {
+                global_deposit(L, S.W, w);
+            }
+        } else if (code == COLLECTED) {
+            if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+        }
+        count_event(&sctr[C_PUSHED], code != NONE);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        // block-wide compaction of stayers (all reads of this chunk are done
+        // before the barrier, so in-place writes cannot clobber unread slots)
+        unsigned bal = __ballot_sync(0xffffffffu, stay);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) { int v = wcnt[q]; off += (q < wid) ? v : 0; tot += v; }
+        if (stay) {
+            long long dst = start + nstay + off + __popc(bal & ((1u << lane) - 1));
+            put(S.bins, dst, x, y, z, vx, vy, vz, id, track);
+        }
+        long long slot = warp_reserve(S.mov_out_n, mover);
+        if (mover) {
+            if (slot < S.mcap) put(S.mov_out, slot, x, y, z, vx, vy, vz, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+        nstay += tot;
+        __syncthreads();
+    }
+    if (tid == 0) S.bcount[b] = nstay;
+    for (int t = tid; t < TILE_N; t += blockDim.x) {
+        unsigned long long v = Wt[t];
+        if (!v) continue;
+        int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], v);
+    }
+    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
+}
+
+// particles waiting in the mover list (spilled last step): same arithmetic,
+// node field read from global memory; every survivor goes back to the list
+// of this step's movers
+__global__ void k_push_movers(Launch L) {
+    __shared__ unsigned long long sctr[NCTR];
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const long long n = list_len(S.mov_in_n, S.mcap);
+    const EGlobal ea{L.E, L.mesh};
+    const bool track = L.track;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += stride) {
+        long long i = base + threadIdx.x;
+        int code = NONE, acc = -1;
+        double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
+        long long id = 0;
+        if (i < n) {
+            x = S.mov_in.x[i]; y = S.mov_in.y[i]; z = S.mov_in.z[i];
+            vx = S.mov_in.vx[i]; vy = S.mov_in.vy[i]; vz = S.mov_in.vz[i];
+            if (track) id = S.mov_in.id[i];
+            Wts w = weights(x, y, z);
+            double ex, ey, ez;
+            gather(w, ea, ex, ey, ez);
+            vx = vx + S.k * ex; vy = vy + S.k * ey; vz = vz + S.k * ez;
+            const double xo = x, yo = y, zo = z;
+            x = x + vx * L.dth; y = y + vy * L.dth; z = z + vz * L.dth;
+            code = classify(L, xo, yo, zo, x, y, z, acc);
+            if (code == ALIVE) global_deposit(L, S.W, weights(x, y, z));
+            else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+        }
+        count_event(&sctr[C_PUSHED], code != NONE);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        bool alive = code == ALIVE;
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) put(S.mov_out, slot, x, y, z, vx, vy, vz, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------------------------
+// injection (reading of Sec. 3.1.3 / Sec. 5.2.2; see inject_one)
+// ------------------------------------------------------------------------------------
+struct InjArgs {
+    const InjectDev* st;
+    int nst;
+    int* count;            // per stream, this step
+    long long* idbase;     // per stream
+    double* carry;         // per stream
+    long long* next_id;    // per species
+    long long step;
+};
+
+// count = floor(carry + rate) per stream, ids consecutive per species in face order
+__global__ void k_inject_counts(InjArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int q = 0; q < a.nst; ++q) {
+        const InjectDev& d = a.st[q];
+        double cr = a.carry[q] + d.rate;
+        double nf = floor(cr);
+        a.carry[q] = cr - nf;
+        int cnt = (int)nf;
+        if (cnt > d.maxcnt) cnt = d.maxcnt;
+        a.count[q] = cnt;
+        a.idbase[q] = a.next_id[d.species];
+        a.next_id[d.species] += cnt;
+    }
+}
+
+PF_D void box_muller(double u1, double u2, double& z0, double& z1) {
+    double r = sqrt(-2.0 * log(u1));
+    double t = (2.0 * 3.141592653589793) * u2;
+    z0 = r * cos(t);
+    z1 = r * sin(t);
+}
+
+// flux-weighted normal speed (units of vth): proposal N(mu, 1), mu the mode of
+// v exp(-(v - s)^2 / 2), acceptance (v/mu) exp(1 - v/mu); bounded tries
+PF_D bool flux_normal(unsigned long long m, unsigned long long seed, unsigned long long key1, double s, double& v) {
+    double mu = 0.5 * (s + sqrt(s * s + 4.0));
+    for (int t = 0; t < MAX_TRIES; ++t) {
+        U64x4 r = philox4x64(m, 2 + t, 0, 0, seed, key1);
+        double z, z1;
+        box_muller(u01(r.v[0]), u01(r.v[1]), z, z1);
+        double vv = mu + z;
+        double ratio = vv / mu;
+        if (vv > 0.0 && u01(r.v[2]) < ratio * exp(1.0 - ratio)) { v = vv; return true; }
+    }
+    return false;
+}
+
+__global__ void k_inject(Launch L, InjArgs a) {
+    __shared__ unsigned long long sctr[NCTR];
+    const int q = blockIdx.y;
+    const InjectDev d = a.st[q];
+    const int s = d.species;
+    const SpeciesDev& S = L.sp[s];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int cnt = a.count[q];
+    const long long idb = a.idbase[q];
+    const int f = d.face, ax = f >> 1;
+    const double sgn = (f & 1) ? -1.0 : 1.0;
+    const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+    const double nax[3] = {(double)L.mesh.nx, (double)L.mesh.ny, (double)L.mesh.nz};
+    const unsigned long long key1 = stream_key(2, s, f, a.step);
+    const bool track = L.track;
+    for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
+        int mm = base + threadIdx.x;
+        int code = NONE, acc = -1;
+        bool rejected = false;
+        double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+        if (mm < cnt) {
+            unsigned long long m = (unsigned long long)mm;
+            U64x4 b0 = philox4x64(m, 0, 0, 0, d.seed, key1);
+            U64x4 b1 = philox4x64(m, 1, 0, 0, d.seed, key1);
+            double vn;
+            bool ok = flux_normal(m, d.seed, key1, sgn * d.drift[ax] / d.vth, vn);
+            double g1, g2;
+            box_muller(u01(b1.v[0]), u01(b1.v[1]), g1, g2);
+            double p0[3];
+            p0[ax] = sgn > 0 ? 0.0 : nax[ax];
+            p0[t1] = u01(b0.v[0]) * nax[t1];
+            p0[t2] = u01(b0.v[1]) * nax[t2];
+            double frac = u01(b0.v[2]);
+            v[ax] = sgn * (d.vth * vn);
+            v[t1] = d.drift[t1] + d.vth * g1;
+            v[t2] = d.drift[t2] + d.vth * g2;
+            double sl = frac * L.dth;
+            for (int c = 0; c < 3; ++c) p[c] = p0[c] + v[c] * sl;
+            if (!ok || level_set(L.obj, p0[0], p0[1], p0[2]) < 0.0) {
+                rejected = true;
+            } else {
+                code = classify(L, p0[0], p0[1], p0[2], p[0], p[1], p[2], acc);
+                if (code == ALIVE) global_deposit(L, S.W, weights(p[0], p[1], p[2]));
+                else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+            }
+        }
+        count_event(&sctr[C_INJECTED], code != NONE);
+        count_event(&sctr[C_REJECTED], rejected);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        bool alive = code == ALIVE;
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) put(S.mov_out, slot, p[0], p[1], p[2], v[0], v[1], v[2], idb + mm, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------------------------
+// rebin: movers -> bins; a full bin sends the particle to next step's mover list
+// ------------------------------------------------------------------------------------
+__global__ void k_rebin(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    const long long n = list_len(S.mov_out_n, S.mcap);
+    const bool track = L.track;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += stride) {
+        long long i = base + threadIdx.x;
+        bool spill = false;
+        double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
+        long long id = 0;
+        if (i < n) {
+            x = S.mov_out.x[i]; y = S.mov_out.y[i]; z = S.mov_out.z[i];
+            vx = S.mov_out.vx[i]; vy = S.mov_out.vy[i]; vz = S.mov_out.vz[i];
+            if (track) id = S.mov_out.id[i];
+            int b = block_of(L, (int)floor(x), (int)floor(y), (int)floor(z));
+            int slot = atomicAdd(&S.bcount[b], 1);
+            if (slot < S.bcap[b]) put(S.bins, S.bstart[b] + slot, x, y, z, vx, vy, vz, id, track);
+            else spill = true;
+        }
+        long long slot = warp_reserve(S.mov_in_n, spill);
+        if (spill) {
+            if (slot < S.mcap) put(S.mov_in, slot, x, y, z, vx, vy, vz, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+}
+
+__global__ void k_clamp_counts(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < L.nblocks && S.bcount[b] > S.bcap[b]) S.bcount[b] = S.bcap[b];
+    if (b == 0) {
+        unsigned long long sp = *S.mov_in_n;
+        S.ctr[C_SPILLED] = sp < (unsigned long long)S.mcap ? sp : (unsigned long long)S.mcap;
+        if (sp > (unsigned long long)S.mcap) *S.mov_in_n = S.mcap;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// loading, bin construction, flattening, deposit of everything, leapfrog start
+// ------------------------------------------------------------------------------------
+__global__ void k_load(Launch L, int s, int ppc, double vth, double dx, double dy, double dz,
+                       unsigned long long seed, PArr out, unsigned long long* nout, long long cap) {
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const Mesh& m = L.mesh;
+    if (g >= m.ncells * (long long)ppc) return;
+    long long c = g / ppc;
+    int pc = (int)(g % ppc);
+    int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
+    unsigned long long key1 = stream_key(1, s, 0, 0);
+    U64x4 b0 = philox4x64((unsigned long long)c, (unsigned long long)pc, 0, 0, seed, key1);
+    U64x4 b1 = philox4x64((unsigned long long)c, (unsigned long long)pc, 1, 0, seed, key1);
+    double x = (double)i + u01(b0.v[0]);
+    double y = (double)j + u01(b0.v[1]);
+    double z = (double)k + u01(b0.v[2]);
+    if (level_set(L.obj, x, y, z) < 0.0) return;
+    double g0, g1, g2, g3;
+    box_muller(u01(b1.v[0]), u01(b1.v[1]), g0, g1);
+    box_muller(u01(b1.v[2]), u01(b1.v[3]), g2, g3);
+    unsigned long long slot = atomicAdd(nout, 1ull);
+    if ((long long)slot >= cap) return;
+    put(out, (long long)slot, x, y, z, dx + vth * g0, dy + vth * g1, dz + vth * g2, c * ppc + pc, true);
+}
+
+__global__ void k_bin_count(Launch L, PArr a, long long n, int* cnt) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = block_of(L, (int)floor(a.x[i]), (int)floor(a.y[i]), (int)floor(a.z[i]));
+    atomicAdd(&cnt[b], 1);
+}
+
+// capacity per bin: count + 25% + 64 slack, multiple of 32
+__global__ void k_bin_caps(int nb, const int* cnt, int* cap, int* cnt_copy) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int c = cnt[b];
+    cap[b] = ((c + c / 4 + 64) + 31) & ~31;
+    cnt_copy[b] = 0;
+}
+
+__global__ void k_bin_scan(int nb, const int* cap, long long* start, long long* total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long run = 0;
+    for (int b = 0; b < nb; ++b) { start[b] = run; run += cap[b]; }
+    *total = run;
+}
+
+__global__ void k_bin_scatter(Launch L, PArr a, long long n, const long long* start, int* fill, PArr bins,
+                              bool track) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = block_of(L, (int)floor(a.x[i]), (int)floor(a.y[i]), (int)floor(a.z[i]));
+    int slot = atomicAdd(&fill[b], 1);
+    put(bins, start[b] + slot, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], track ? a.id[i] : 0, track);
+}
+
+__global__ void k_flatten(Launch L, int s, PArr out, unsigned long long* nout) {
+    const SpeciesDev& S = L.sp[s];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0) base = n ? atomicAdd(nout, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    long long st = S.bstart[b];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        long long g = st + i;
+        put(out, (long long)base + i, S.bins.x[g], S.bins.y[g], S.bins.z[g], S.bins.vx[g], S.bins.vy[g],
+            S.bins.vz[g], L.track ? S.bins.id[g] : 0, L.track);
+    }
+}
+
+__global__ void k_flatten_list(Launch L, int s, PArr out, unsigned long long* nout) {
+    const SpeciesDev& S = L.sp[s];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0 && blockIdx.x == 0) base = 0;
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) base = n ? atomicAdd(nout, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < n; i += blockDim.x)
+        put(out, (long long)base + i, S.mov_in.x[i], S.mov_in.y[i], S.mov_in.z[i], S.mov_in.vx[i], S.mov_in.vy[i],
+            S.mov_in.vz[i], L.track ? S.mov_in.id[i] : 0, L.track);
+}
+
+// scatter of every particle (bins + waiting movers) with global atomics
+__global__ void k_deposit_bins(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    long long st = S.bstart[b];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        long long g = st + i;
+        global_deposit(L, S.W, weights(S.bins.x[g], S.bins.y[g], S.bins.z[g]));
+    }
+}
+__global__ void k_deposit_list(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        global_deposit(L, S.W, weights(S.mov_in.x[i], S.mov_in.y[i], S.mov_in.z[i]));
+}
+
+// v <- v - (k/2) E(x)
+__global__ void k_half_kick_bins(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    long long st = S.bstart[b];
+    const EGlobal ea{L.E, L.mesh};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        long long g = st + i;
+        double ex, ey, ez;
+        gather(weights(S.bins.x[g], S.bins.y[g], S.bins.z[g]), ea, ex, ey, ez);
+        S.bins.vx[g] = S.bins.vx[g] - S.khalf * ex;
+        S.bins.vy[g] = S.bins.vy[g] - S.khalf * ey;
+        S.bins.vz[g] = S.bins.vz[g] - S.khalf * ez;
+    }
+}
+__global__ void k_half_kick_list(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    const EGlobal ea{L.E, L.mesh};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double ex, ey, ez;
+        gather(weights(S.mov_in.x[i], S.mov_in.y[i], S.mov_in.z[i]), ea, ex, ey, ez);
+        S.mov_in.vx[i] = S.mov_in.vx[i] - S.khalf * ex;
+        S.mov_in.vy[i] = S.mov_in.vy[i] - S.khalf * ey;
+        S.mov_in.vz[i] = S.mov_in.vz[i] - S.khalf * ez;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------
+static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+
+Launch make_launch(Ctx& c) {
+    Launch L;
+    memset(&L, 0, sizeof(L));
+    L.mesh = c.mesh; L.obj = c.obj; L.dth = c.dth;
+    L.nbx = c.nbx; L.nby = c.nby; L.nbz = c.nbz; L.nblocks = c.nblocks;
+    L.nspecies = (int)c.sp.size();
+    L.track = c.track;
+    L.cell_acc = c.cell_acc;
+    L.E = c.E; L.Ef = c.Ef;
+    L.err = c.err_word;
+    for (int s = 0; s < L.nspecies; ++s) {
+        Species& q = c.sp[s];
+        SpeciesDev& d = L.sp[s];
+        d.k = q.k; d.khalf = 0.5 * q.k;
+        d.bins = q.bins; d.binsF = q.binsF;
+        d.bstart = q.bstart; d.bcap = q.bcap; d.bcount = q.bcount;
+        d.mov_in = q.mov[0]; d.mov_out = q.mov[1];
+        d.movF_in = q.movF[0]; d.movF_out = q.movF[1];
+        d.mov_in_n = q.mov_n; d.mov_out_n = q.mov_n + 1;
+        d.mcap = q.mcap;
+        d.W = q.W; d.surf = q.surf; d.ctr = q.ctr;
+    }
+    return L;
+}
+
+static InjArgs inj_args(Ctx& c) {
+    InjArgs a;
+    a.st = c.inj_dev; a.nst = (int)c.inj.size();
+    a.count = c.inj_count; a.idbase = c.inj_base; a.carry = c.inj_carry; a.next_id = c.next_id;
+    a.step = c.step_no;
+    return a;
+}
+
+cudaError_t launch_load_maxwellian(Ctx& c, int s, int ppc, double vth, const double drift[3],
+                                   unsigned long long seed, PArr flat, unsigned long long* nflat, long long cap) {
+    Launch L = make_launch(c);
+    long long n = c.mesh.ncells * (long long)ppc;
+    k_load<<<nb(n), 256, 0, c.stream>>>(L, s, ppc, vth, drift[0], drift[1], drift[2], seed, flat, nflat, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flatten(Ctx& c, int s, PArr flat, unsigned long long* nflat) {
+    Launch L = make_launch(c);
+    if (c.sp[s].bcount) k_flatten<<<c.nblocks, 256, 0, c.stream>>>(L, s, flat, nflat);
+    if (c.sp[s].mov_n) k_flatten_list<<<1, 256, 0, c.stream>>>(L, s, flat, nflat);
+    return cudaGetLastError();
+}
+
+// (re)build the bins of species s from a flat list of n particles on the device
+cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool) {
+    Species& q = c.sp[s];
+    cudaError_t e;
+    int* cnt = nullptr;
+    long long* tot = nullptr;
+    long long total = 0;
+    e = cudaMalloc(&cnt, sizeof(int) * c.nblocks);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&tot, sizeof(long long));
+    if (e != cudaSuccess) { cudaFree(cnt); return e; }
+    cudaMemsetAsync(cnt, 0, sizeof(int) * c.nblocks, c.stream);
+    Launch L = make_launch(c);
+    if (n > 0) k_bin_count<<<nb(n), 256, 0, c.stream>>>(L, flat, n, cnt);
+    if (!q.bcap) {
+        cudaMalloc(&q.bcap, sizeof(int) * c.nblocks);
+        cudaMalloc(&q.bcount, sizeof(int) * c.nblocks);
+        cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
+    }
+    k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
+    k_bin_scan<<<1, 32, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
+    e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+    if (total > q.cap) {
+        double** arr[6] = {&q.bins.x, &q.bins.y, &q.bins.z, &q.bins.vx, &q.bins.vy, &q.bins.vz};
+        for (auto a : arr) { cudaFree(*a); *a = nullptr; }
+        cudaFree(q.bins.id); q.bins.id = nullptr;
+        for (auto a : arr) {
+            e = cudaMalloc(a, sizeof(double) * total);
+            if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+        }
+        if (c.track) {
+            e = cudaMalloc(&q.bins.id, sizeof(long long) * total);
+            if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+        }
+        q.cap = total;
+    }
+    L = make_launch(c);
+    if (n > 0) k_bin_scatter<<<nb(n), 256, 0, c.stream>>>(L, flat, n, q.bstart, q.bcount, q.bins, c.track != 0);
+    cudaMemsetAsync(q.mov_n, 0, 2 * sizeof(unsigned long long), c.stream);
+    e = cudaStreamSynchronize(c.stream);
+    cudaFree(cnt);
+    cudaFree(tot);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_all(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * c.mesh.nnodes, c.stream);
+    if (ns == 0) return cudaGetLastError();
+    k_deposit_bins<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    k_deposit_list<<<dim3(64, ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half_kick(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    if (ns == 0) return cudaSuccess;
+    k_half_kick_bins<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    k_half_kick_list<<<dim3(64, ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+// push of all bins (+ node-field tiles by TMA) and of waiting movers
+cudaError_t launch_push(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    for (int s = 0; s < ns; ++s)
+        cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
+    cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
+    k_push_bins<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, c.tmapE);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_movers(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    k_push_movers<<<dim3(152, ns), 256, 0, c.stream>>>(L);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(Ctx& c) {
+    if (c.inj.empty()) return cudaSuccess;
+    Launch L = make_launch(c);
+    InjArgs a = inj_args(c);
+    k_inject_counts<<<1, 32, 0, c.stream>>>(a);
+    int maxc = 1;
+    for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
+    unsigned gx = (unsigned)((maxc + 255) / 256);
+    if (gx > 1024) gx = 1024;
+    k_inject<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebin(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n, 0, sizeof(unsigned long long), c.stream);
+    k_rebin<<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
+    k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,529 @@
+// S0: interface and stiffness set-up on the GPU (compiled without FMA
+// contraction so the node level set and tet classification are reproducible).
+//
+// Sec. 2.1 (Eqs. 2.1-2.5) poses -div(eps grad phi) = rho with [phi] = 0 and
+// [eps d phi/dn] = q on the interface; Sec. 1 / 2.1 describe IFE functions as
+// standard linear FE functions adjusted on interface elements to satisfy those
+// conditions, with unchanged nodal degrees of freedom; Sec. 3.1.1 cuts each
+// cubic PIC cell into 5 tetrahedra.  On each interface tet this file builds
+// psi+ = a + b.x, psi- = psi+ + beta d(x) (d the signed distance to the plane
+// of the linear interpolant's zero set, beta = ((eps+ - eps-) n.b - q)/eps-),
+// fixed by the 4 nodal values through a 4x4 FP64 solve (4 basis functions +
+// the unit jump function), its exact sub-volumes, Gamma_h area, element
+// stiffness and unit-jump load.  Regular rows of the operator stay matrix-free;
+// rows touching an interface tet become explicit 19-slot patch rows.
+#include <math.h>
+
+#include "internal.h"
+
+namespace pf {
+
+__constant__ TetTables cT;
+
+cudaError_t set_tet_tables(const TetTables& t) { return cudaMemcpyToSymbol(cT, &t, sizeof(TetTables)); }
+
+static __device__ __forceinline__ void loff(int l, int& a, int& b, int& c) {
+    a = l & 1; b = (l >> 1) & 1; c = (l >> 2) & 1;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_levelset(Mesh m, Object o, double* L) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes) return;
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    L[n] = level_set(o, (double)i, (double)j, (double)k);
+}
+
+__global__ void k_classify(Mesh m, const double* L, unsigned char* mask, int* cnt) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= m.ncells) return;
+    int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
+    int p = (i + j + k) & 1;
+    bool neg[8];
+    for (int l = 0; l < 8; ++l) {
+        int a, b, cc; loff(l, a, b, cc);
+        neg[l] = L[node_id(m, i + a, j + b, k + cc)] < 0.0;
+    }
+    unsigned char mk = 0;
+    int n = 0;
+    for (int t = 0; t < 5; ++t) {
+        int nm = 0;
+        for (int v = 0; v < 4; ++v) nm += neg[cT.vert[p][t][v]];
+        if (nm > 0 && nm < 4) { mk |= (unsigned char)(1u << t); ++n; }
+    }
+    mask[c] = mk;
+    cnt[c] = n;
+}
+
+// ---- small dense helpers ------------------------------------------------------
+static __device__ double tet_vol(const double* a, const double* b, const double* c, const double* d) {
+    double u[3], v[3], w[3];
+    for (int q = 0; q < 3; ++q) { u[q] = b[q] - a[q]; v[q] = c[q] - a[q]; w[q] = d[q] - a[q]; }
+    double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                 u[2] * (v[0] * w[1] - v[1] * w[0]);
+    return fabs(det) / 6.0;
+}
+static __device__ double tri_area(const double* a, const double* b, const double* c) {
+    double u[3], v[3];
+    for (int q = 0; q < 3; ++q) { u[q] = b[q] - a[q]; v[q] = c[q] - a[q]; }
+    double x = u[1] * v[2] - u[2] * v[1], y = u[2] * v[0] - u[0] * v[2], z = u[0] * v[1] - u[1] * v[0];
+    return 0.5 * sqrt(x * x + y * y + z * z);
+}
+// Gaussian elimination with partial pivoting: A (n x n) X = R (n x m), in place
+template <int N, int M>
+static __device__ void gauss_solve(double A[N][N], double R[N][M]) {
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        double best = fabs(A[c][c]);
+        for (int r = c + 1; r < N; ++r)
+            if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); piv = r; }
+        if (piv != c) {
+            for (int q = 0; q < N; ++q) { double t = A[c][q]; A[c][q] = A[piv][q]; A[piv][q] = t; }
+            for (int q = 0; q < M; ++q) { double t = R[c][q]; R[c][q] = R[piv][q]; R[piv][q] = t; }
+        }
+        for (int r = c + 1; r < N; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int q = c; q < N; ++q) A[r][q] -= f * A[c][q];
+            for (int q = 0; q < M; ++q) R[r][q] -= f * R[c][q];
+        }
+    }
+    for (int r = N - 1; r >= 0; --r) {
+        for (int q = 0; q < M; ++q) {
+            double s = R[r][q];
+            for (int cc = r + 1; cc < N; ++cc) s -= A[r][cc] * R[cc][q];
+            R[r][q] = s / A[r][r];
+        }
+    }
+}
+
+// linear IFE local space of one interface tet -> record (layout IT_*)
+static __device__ void ife_tet(const double vx[4][3], const double Lv[4], double em, double ep, double V,
+                               double* rec) {
+    bool minus[4];
+    for (int v = 0; v < 4; ++v) minus[v] = Lv[v] < 0.0;
+    // gradient of the linear interpolant of L
+    double M3[3][3], g3[3][1];
+    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) M3[r][q] = vx[r + 1][q] - vx[0][q];
+        g3[r][0] = Lv[r + 1] - Lv[0];
+    }
+    gauss_solve<3, 1>(M3, g3);
+    double gn = sqrt(g3[0][0] * g3[0][0] + g3[1][0] * g3[1][0] + g3[2][0] * g3[2][0]);
+    double n[3] = {g3[0][0] / gn, g3[1][0] / gn, g3[2][0] / gn};
+    double dist[4];
+    for (int v = 0; v < 4; ++v) dist[v] = Lv[v] / gn;
+    double kappa = (ep - em) / em;
+    double A[4][4], R[4][5];
+    for (int v = 0; v < 4; ++v) {
+        A[v][0] = 1.0;
+        for (int q = 0; q < 3; ++q) A[v][1 + q] = vx[v][q] + (minus[v] ? dist[v] * kappa * n[q] : 0.0);
+        for (int f = 0; f < 5; ++f) R[v][f] = (f == v) ? 1.0 : 0.0;
+        R[v][4] = minus[v] ? dist[v] / em : 0.0;
+    }
+    gauss_solve<4, 5>(A, R);       // R now holds (a, b) per function
+    double gp[5][3], gm[5][3];
+    for (int f = 0; f < 5; ++f) {
+        double bn = R[1][f] * n[0] + R[2][f] * n[1] + R[3][f] * n[2];
+        double beta = kappa * bn - (f == 4 ? 1.0 / em : 0.0);
+        for (int q = 0; q < 3; ++q) { gp[f][q] = R[1 + q][f]; gm[f][q] = R[1 + q][f] + beta * n[q]; }
+    }
+    // sub-volumes and Gamma_h triangles
+    int mi[4], pl[4], nmi = 0, npl = 0;
+    for (int v = 0; v < 4; ++v) { if (minus[v]) mi[nmi++] = v; else pl[npl++] = v; }
+    double tri[2][3][3];
+    int ntri = 0;
+    double volm, volp;
+    if (nmi == 1 || nmi == 3) {
+        bool lone_minus = (nmi == 1);
+        int u = lone_minus ? mi[0] : pl[0];
+        const int* oth = lone_minus ? pl : mi;
+        double fr[3];
+        for (int e = 0; e < 3; ++e) {
+            int w = oth[e];
+            double t;
+            if (lone_minus) {
+                t = Lv[u] / (Lv[u] - Lv[w]);
+                for (int q = 0; q < 3; ++q) tri[0][e][q] = vx[u][q] + t * (vx[w][q] - vx[u][q]);
+                fr[e] = t;
+            } else {
+                t = Lv[w] / (Lv[w] - Lv[u]);
+                for (int q = 0; q < 3; ++q) tri[0][e][q] = vx[w][q] + t * (vx[u][q] - vx[w][q]);
+                fr[e] = 1.0 - t;
+            }
+        }
+        ntri = 1;
+        double vcut = V * fr[0] * fr[1] * fr[2];
+        if (lone_minus) { volm = vcut; volp = V - vcut; } else { volp = vcut; volm = V - vcut; }
+    } else {
+        int a = mi[0], b = mi[1], c = pl[0], d = pl[1];
+        double pac[3], pad[3], pbc[3], pbd[3];
+        double tac = Lv[a] / (Lv[a] - Lv[c]), tad = Lv[a] / (Lv[a] - Lv[d]);
+        double tbc = Lv[b] / (Lv[b] - Lv[c]), tbd = Lv[b] / (Lv[b] - Lv[d]);
+        for (int q = 0; q < 3; ++q) {
+            pac[q] = vx[a][q] + tac * (vx[c][q] - vx[a][q]);
+            pad[q] = vx[a][q] + tad * (vx[d][q] - vx[a][q]);
+            pbc[q] = vx[b][q] + tbc * (vx[c][q] - vx[b][q]);
+            pbd[q] = vx[b][q] + tbd * (vx[d][q] - vx[b][q]);
+        }
+        volm = tet_vol(vx[a], pac, pad, pbd) + tet_vol(vx[a], pac, pbc, pbd) + tet_vol(vx[a], vx[b], pbc, pbd);
+        volp = V - volm;
+        for (int q = 0; q < 3; ++q) {
+            tri[0][0][q] = pac[q]; tri[0][1][q] = pad[q]; tri[0][2][q] = pbd[q];
+            tri[1][0][q] = pac[q]; tri[1][1][q] = pbd[q]; tri[1][2][q] = pbc[q];
+        }
+        ntri = 2;
+    }
+    double area = 0.0, S[5] = {0, 0, 0, 0, 0};
+    for (int tr = 0; tr < ntri; ++tr) {
+        double ar = tri_area(tri[tr][0], tri[tr][1], tri[tr][2]);
+        area += ar;
+        double cen[3];
+        for (int q = 0; q < 3; ++q) cen[q] = (tri[tr][0][q] + tri[tr][1][q] + tri[tr][2][q]) / 3.0;
+        for (int f = 0; f < 5; ++f) S[f] += ar * (R[0][f] + cen[0] * R[1][f] + cen[1] * R[2][f] + cen[2] * R[3][f]);
+    }
+    rec[IT_VOLP] = volp;
+    rec[IT_VOLM] = volm;
+    rec[IT_AREA] = area;
+    for (int a = 0; a < 4; ++a) {
+        for (int b = 0; b < 4; ++b) {
+            double dp = gp[a][0] * gp[b][0] + gp[a][1] * gp[b][1] + gp[a][2] * gp[b][2];
+            double dm = gm[a][0] * gm[b][0] + gm[a][1] * gm[b][1] + gm[a][2] * gm[b][2];
+            rec[IT_K + 4 * a + b] = ep * volp * dp + em * volm * dm;
+        }
+        double dpj = gp[a][0] * gp[4][0] + gp[a][1] * gp[4][1] + gp[a][2] * gp[4][2];
+        double dmj = gm[a][0] * gm[4][0] + gm[a][1] * gm[4][1] + gm[a][2] * gm[4][2];
+        rec[IT_C + a] = -S[a] - (ep * volp * dpj + em * volm * dmj);
+        rec[IT_S + a] = S[a];
+    }
+    for (int f = 0; f < 5; ++f)
+        for (int q = 0; q < 3; ++q) { rec[IT_GP + 3 * f + q] = gp[f][q]; rec[IT_GM + 3 * f + q] = gm[f][q]; }
+    rec[IT_SJ] = S[4];
+}
+
+__global__ void k_interface(Mesh m, Object o, const double* L, const unsigned char* mask, const int* ibase,
+                            int* it_cell, int* it_t, double* it_data) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= m.ncells) return;
+    unsigned mk = mask[c];
+    if (!mk) return;
+    int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
+    int p = (i + j + k) & 1;
+    int T = ibase[c];
+    for (int t = 0; t < 5; ++t) {
+        if (!((mk >> t) & 1)) continue;
+        double vx[4][3], Lv[4];
+        for (int v = 0; v < 4; ++v) {
+            int l = cT.vert[p][t][v];
+            int a, b, cc; loff(l, a, b, cc);
+            vx[v][0] = a * m.h; vx[v][1] = b * m.h; vx[v][2] = cc * m.h;
+            Lv[v] = L[node_id(m, i + a, j + b, k + cc)];
+        }
+        double V = cT.vol[t] * m.h * m.h * m.h;
+        ife_tet(vx, Lv, o.eps_minus, o.eps_plus, V, it_data + (long long)T * IT_STRIDE);
+        it_cell[T] = (int)c;
+        it_t[T] = t;
+        ++T;
+    }
+}
+
+__global__ void k_cell_area(Mesh m, const unsigned char* mask, const int* ibase, const double* it_data,
+                            int* cutflag, double* cellarea) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= m.ncells) return;
+    unsigned mk = mask[c];
+    double a = 0.0;
+    int T = ibase[c];
+    for (int t = 0; t < 5; ++t)
+        if ((mk >> t) & 1) { a += it_data[(long long)T * IT_STRIDE + IT_AREA]; ++T; }
+    cellarea[c] = a;
+    cutflag[c] = a > 0.0 ? 1 : 0;
+}
+
+__global__ void k_cut_list(Mesh m, const int* cutflag, const long long* cutidx, const double* cellarea,
+                           int* cut_cell, double* cut_area, int* own) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= m.ncells) return;
+    if (cutflag[c]) {
+        long long q = cutidx[c];
+        cut_cell[q] = (int)c;
+        cut_area[q] = cellarea[c];
+        own[c] = (int)q;
+    } else {
+        own[c] = -1;
+    }
+}
+
+// surface-charge target of a hit cell: its own cut index, else the first cut
+// cell among the 26 neighbours ordered by L1 distance then (dz, dy, dx)
+__global__ void k_cell_acc(Mesh m, const int* own, int* acc) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= m.ncells) return;
+    int v = own[c];
+    if (v < 0) {
+        int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
+        for (int d1 = 1; d1 <= 3 && v < 0; ++d1)
+            for (int dz = -1; dz <= 1 && v < 0; ++dz)
+                for (int dy = -1; dy <= 1 && v < 0; ++dy)
+                    for (int dx = -1; dx <= 1 && v < 0; ++dx) {
+                        if (abs(dx) + abs(dy) + abs(dz) != d1) continue;
+                        int ii = i + dx, jj = j + dy, kk = k + dz;
+                        if (ii < 0 || ii >= m.nx || jj < 0 || jj >= m.ny || kk < 0 || kk >= m.nz) continue;
+                        v = own[cell_id(m, ii, jj, kk)];
+                    }
+    }
+    acc[c] = v;
+}
+
+__global__ void k_it_acc(long long nit, const int* it_cell, const int* own, int* it_acc) {
+    long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (T >= nit) return;
+    it_acc[T] = own[it_cell[T]];
+}
+
+// node kinds: Dirichlet (-3), touching an interface tet (patch, flag 1),
+// regular plus (-1) or minus (-2)
+__global__ void k_node_kind(Mesh m, const double* L, const unsigned char* mask, const int* bcdir,
+                            const double* bcval, int* ntype, int* patchflag, double* gdir) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes) return;
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    int face_on[6] = {i == 0, i == m.nx, j == 0, j == m.ny, k == 0, k == m.nz};
+    int dface = -1;
+    for (int f = 0; f < 6; ++f)
+        if (face_on[f] && bcdir[f]) { dface = f; break; }
+    patchflag[n] = 0;
+    if (dface >= 0) { ntype[n] = -3; gdir[n] = bcval[dface]; return; }
+    gdir[n] = 0.0;
+    bool touch = false;
+    for (int c8 = 0; c8 < 8 && !touch; ++c8) {
+        int a, b, cc; loff(c8, a, b, cc);
+        int ci = i - a, cj = j - b, ck = k - cc;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
+        unsigned mk = mask[cell_id(m, ci, cj, ck)];
+        if (!mk) continue;
+        int p = (ci + cj + ck) & 1;
+        for (int t = 0; t < 5; ++t) {
+            if (!((mk >> t) & 1)) continue;
+            for (int v = 0; v < 4; ++v)
+                if (cT.vert[p][t][v] == c8) touch = true;
+        }
+    }
+    if (touch) { patchflag[n] = 1; ntype[n] = 0; }
+    else ntype[n] = (L[n] < 0.0) ? -2 : -1;
+}
+
+__global__ void k_patch_rows(Mesh m, Object o, const double* L, const unsigned char* mask, const int* ibase,
+                             const double* it_data, const int* patchflag, const long long* patchidx,
+                             int* ntype, long long* patch_node, double* coef, float* coeff, double* invdiag) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes || !patchflag[n]) return;
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    long long r = patchidx[n];
+    ntype[n] = (int)r;
+    patch_node[r] = n;
+    double row[19];
+    for (int s = 0; s < 19; ++s) row[s] = 0.0;
+    for (int c8 = 0; c8 < 8; ++c8) {
+        int a, b, cc; loff(c8, a, b, cc);
+        int ci = i - a, cj = j - b, ck = k - cc;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
+        long long cell = cell_id(m, ci, cj, ck);
+        unsigned mk = mask[cell];
+        int p = (ci + cj + ck) & 1;
+        int T = ibase[cell];
+        for (int t = 0; t < 5; ++t) {
+            bool itet = (mk >> t) & 1;
+            int kk = -1;
+            for (int v = 0; v < 4; ++v)
+                if (cT.vert[p][t][v] == c8) kk = v;
+            if (kk >= 0) {
+                double e[4];
+                if (itet) {
+                    const double* rec = it_data + (long long)T * IT_STRIDE;
+                    for (int v = 0; v < 4; ++v) e[v] = rec[IT_K + 4 * kk + v];
+                } else {
+                    int l0 = cT.vert[p][t][0];
+                    int a0, b0, c0; loff(l0, a0, b0, c0);
+                    double eps = L[node_id(m, ci + a0, cj + b0, ck + c0)] < 0.0 ? o.eps_minus : o.eps_plus;
+                    double s = eps * m.h * cT.vol[t];
+                    for (int v = 0; v < 4; ++v)
+                        e[v] = s * (cT.grad[p][t][kk][0] * cT.grad[p][t][v][0] +
+                                     cT.grad[p][t][kk][1] * cT.grad[p][t][v][1] +
+                                     cT.grad[p][t][kk][2] * cT.grad[p][t][v][2]);
+                }
+                for (int v = 0; v < 4; ++v) {
+                    int l = cT.vert[p][t][v];
+                    int av, bv, cv; loff(l, av, bv, cv);
+                    int dx = av - a, dy = bv - b, dz = cv - cc;
+                    int sl = cT.slot[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+                    row[sl] += e[v];
+                }
+            }
+            if (itet) ++T;
+        }
+    }
+    for (int s = 0; s < 19; ++s) { coef[r * 19 + s] = row[s]; coeff[r * 19 + s] = (float)row[s]; }
+    invdiag[n] = 1.0 / row[0];
+}
+
+__global__ void k_invdiag_regular(Mesh m, Object o, const int* ntype, double* invdiag, float* invdiagf) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes) return;
+    int ty = ntype[n];
+    if (ty >= 0) { invdiagf[n] = (float)invdiag[n]; return; }
+    if (ty == -3) { invdiag[n] = 0.0; invdiagf[n] = 0.0f; return; }
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    int cx = (i > 0) + (i < m.nx), cy = (j > 0) + (j < m.ny), cz = (k > 0) + (k < m.nz);
+    double eps = (ty == -2) ? o.eps_minus : o.eps_plus;
+    double d = eps * (double)(cx * cy * cz) * (((i + j + k) & 1) ? 0.5 : 0.75) * m.h;
+    invdiag[n] = 1.0 / d;
+    invdiagf[n] = (float)(1.0 / d);
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int flags -> long long offsets (two-level, deterministic)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+__global__ void k_scan_tiles(const int* in, long long n, long long* out, long long* tile_sum) {
+    __shared__ long long sh[SCAN_T];
+    long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_I;
+    long long v[SCAN_I], s = 0;
+    for (int q = 0; q < SCAN_I; ++q) { v[q] = (base + q < n) ? in[base + q] : 0; s += v[q]; }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_T; off <<= 1) {
+        long long t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    long long run = sh[threadIdx.x] - s;
+    for (int q = 0; q < SCAN_I; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == SCAN_T - 1) tile_sum[blockIdx.x] = sh[SCAN_T - 1];
+}
+
+__global__ void k_scan_sums(long long* tile_sum, long long ntiles, long long* total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long run = 0;
+    for (long long t = 0; t < ntiles; ++t) { long long v = tile_sum[t]; tile_sum[t] = run; run += v; }
+    *total = run;
+}
+
+__global__ void k_scan_add(long long* out, long long n, const long long* tile_sum) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < n) out[e] += tile_sum[e / SCAN_TILE];
+}
+
+static cudaError_t exclusive_scan(const int* in, long long n, long long* out, long long* total_dev,
+                                  cudaStream_t st) {
+    long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    long long* ts = nullptr;
+    cudaError_t e = cudaMalloc(&ts, sizeof(long long) * (ntiles > 0 ? ntiles : 1));
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, n, out, ts);
+        k_scan_sums<<<1, 32, 0, st>>>(ts, ntiles, total_dev);
+        k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, ts);
+    } else {
+        cudaMemsetAsync(total_dev, 0, sizeof(long long), st);
+    }
+    e = cudaStreamSynchronize(st);
+    cudaFree(ts);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+
+__global__ void k_narrow(const long long* in, long long n, int* out) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (int)in[e];
+}
+
+#define CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) { err = _e; goto done; } } while (0)
+
+cudaError_t launch_setup(Ctx& c) {
+    cudaError_t err = cudaSuccess;
+    Mesh m = c.mesh;
+    cudaStream_t st = c.stream;
+    int* cnt = nullptr; long long* scan = nullptr; long long* tot = nullptr;
+    int* flag = nullptr; double* carea = nullptr; int* own = nullptr;
+    int* bcdir = nullptr; double* bcval = nullptr;
+    long long hv = 0;
+    long long nit_alloc = 1;
+    long long nmax = m.nnodes > m.ncells ? m.nnodes : m.ncells;
+    int hdir[6]; double hval[6];
+    CK(cudaMalloc(&cnt, sizeof(int) * nmax));
+    CK(cudaMalloc(&scan, sizeof(long long) * nmax));
+    CK(cudaMalloc(&tot, sizeof(long long)));
+    CK(cudaMalloc(&flag, sizeof(int) * m.ncells));
+    CK(cudaMalloc(&carea, sizeof(double) * m.ncells));
+    CK(cudaMalloc(&own, sizeof(int) * m.ncells));
+    CK(cudaMalloc(&bcdir, sizeof(int) * 6));
+    CK(cudaMalloc(&bcval, sizeof(double) * 6));
+
+    k_levelset<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode);
+    k_classify<<<nb(m.ncells), 256, 0, st>>>(m, c.Lnode, c.imask, cnt);
+    CK(cudaGetLastError());
+    // interface-tet offsets per cell
+    CK(exclusive_scan(cnt, m.ncells, scan, tot, st));
+    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    c.nit = hv;
+    k_narrow<<<nb(m.ncells), 256, 0, st>>>(scan, m.ncells, c.ibase);
+    nit_alloc = c.nit > 0 ? c.nit : 1;
+    CK(cudaMalloc(&c.it_cell, sizeof(int) * nit_alloc));
+    CK(cudaMalloc(&c.it_t, sizeof(int) * nit_alloc));
+    CK(cudaMalloc(&c.it_data, sizeof(double) * IT_STRIDE * nit_alloc));
+    CK(cudaMalloc(&c.it_acc, sizeof(int) * nit_alloc));
+    CK(cudaMalloc(&c.qT, sizeof(double) * nit_alloc));
+    CK(cudaMemsetAsync(c.qT, 0, sizeof(double) * nit_alloc, st));
+    k_interface<<<nb(m.ncells), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, c.ibase, c.it_cell, c.it_t, c.it_data);
+    k_cell_area<<<nb(m.ncells), 256, 0, st>>>(m, c.imask, c.ibase, c.it_data, flag, carea);
+    CK(cudaGetLastError());
+    CK(exclusive_scan(flag, m.ncells, scan, tot, st));
+    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    c.ncut = hv;
+    {
+        long long nc;
+        nc = c.ncut > 0 ? c.ncut : 1;
+        CK(cudaMalloc(&c.cut_cell, sizeof(int) * nc));
+        CK(cudaMalloc(&c.cut_area, sizeof(double) * nc));
+        CK(cudaMalloc(&c.qcut, sizeof(double) * nc));
+        CK(cudaMemsetAsync(c.qcut, 0, sizeof(double) * nc, st));
+    }
+    k_cut_list<<<nb(m.ncells), 256, 0, st>>>(m, flag, scan, carea, c.cut_cell, c.cut_area, own);
+    k_cell_acc<<<nb(m.ncells), 256, 0, st>>>(m, own, c.cell_acc);
+    if (c.nit > 0) k_it_acc<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_cell, own, c.it_acc);
+    CK(cudaGetLastError());
+    // nodes
+    for (int f = 0; f < 6; ++f) { hdir[f] = c.bc[f].kind == PIFEPIC_BC_DIRICHLET; hval[f] = c.bc[f].value; }
+    CK(cudaMemcpy(bcdir, hdir, sizeof(hdir), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(bcval, hval, sizeof(hval), cudaMemcpyHostToDevice));
+    k_node_kind<<<nb(m.nnodes), 256, 0, st>>>(m, c.Lnode, c.imask, bcdir, bcval, c.ntype, cnt, c.gdir);
+    CK(cudaGetLastError());
+    CK(exclusive_scan(cnt, m.nnodes, scan, tot, st));
+    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    c.npatch = hv;
+    {
+        long long np;
+        np = c.npatch > 0 ? c.npatch : 1;
+        CK(cudaMalloc(&c.patch_node, sizeof(long long) * np));
+        CK(cudaMalloc(&c.patch_coef, sizeof(double) * 19 * np));
+        CK(cudaMalloc(&c.patch_coeff, sizeof(float) * 19 * np));
+    }
+    k_patch_rows<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, c.ibase, c.it_data, cnt, scan,
+                                               c.ntype, c.patch_node, c.patch_coef, c.patch_coeff, c.invdiag);
+    k_invdiag_regular<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.ntype, c.invdiag, c.invdiagf);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+done:
+    cudaFree(cnt); cudaFree(scan); cudaFree(tot); cudaFree(flag); cudaFree(carea); cudaFree(own);
+    cudaFree(bcdir); cudaFree(bcval);
+    return err;
+}
+
+}  // namespace pf

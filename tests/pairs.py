@@ -1,0 +1,74 @@
+"""Paired CUDA-library / oracle instances on identical seeded inputs (test helper)."""
+import numpy as np
+
+from oracle.geometry import CapCrater, Mesh, NoObject, Plane, Sphere
+from oracle.field import FieldSystem
+from oracle.pic import Simulation as OracleSim
+from paper_2011_10214_gb300 import workloads as wl
+
+# geometry cases: ragged sizes (not multiples of the 4-cell bin), mixed boundaries
+CASES = {
+    "sphere16": dict(n=(16, 16, 16), h=0.5, obj=("sphere", (4.0, 4.0, 4.0), 2.0, 4.0, 1.0),
+                     bc=[("D", 0.0)] * 6),
+    "ragged": dict(n=(18, 13, 11), h=0.3, obj=("sphere", (2.71, 1.93, 1.64), 0.83, 6.0, 1.0),
+                   bc=[("D", 0.0), ("D", 0.25), ("N",), ("D", -0.1), ("N",), ("N",)]),
+    "crater": dict(n=(24, 22, 16), h=1.0, obj=("cap_crater", 6.0, 12.0, 11.0, 6.0, 3.0, 4.0, 1.0),
+                   bc=[("N",)] * 5 + [("D", 0.0)]),
+    "plane": dict(n=(12, 12, 12), h=0.5, obj=("plane", (0.3, -0.5, 1.0), 4.37, 10.0, 1.0),
+                  bc=[("D", 0.0)] * 6),
+}
+
+
+def oracle_object(m, o):
+    if o[0] == "sphere":
+        return Sphere(m, o[1], o[2], o[3], o[4])
+    if o[0] == "cap_crater":
+        return CapCrater(m, *o[1:])
+    if o[0] == "plane":
+        return Plane(o[1], o[2], o[3], o[4])
+    return NoObject()
+
+
+def gpu_object(sim, o):
+    from paper_2011_10214_gb300 import capi
+    if o[0] == "sphere":
+        sim.set_object(capi.OBJ_SPHERE, list(o[1]) + [o[2]], o[3], o[4])
+    elif o[0] == "cap_crater":
+        sim.set_object(capi.OBJ_CAP_CRATER, list(o[1:6]), o[6], o[7])
+    elif o[0] == "plane":
+        sim.set_object(capi.OBJ_PLANE, list(o[1]) + [o[2]], o[3], o[4])
+
+
+def make_pair(case, dt=0.05, tol=1e-12, maxit=2000, track=True, precision=0):
+    from paper_2011_10214_gb300 import capi
+    c = CASES[case]
+    m = Mesh(*c["n"], c["h"])
+    obj = oracle_object(m, c["obj"])
+    orc = OracleSim(m, obj, c["bc"], dt, tol=tol, maxit=maxit)
+    gpu = capi.Simulation(c["n"], c["h"], dt, precision=precision, pcg_tol=tol, pcg_max_iter=maxit,
+                          track_ids=track)
+    gpu.set_field_bc(c["bc"])
+    gpu_object(gpu, c["obj"])
+    return gpu, orc
+
+
+def add_species_both(gpu, orc, q, m, w):
+    a = gpu.add_species(q, m, w)
+    b = orc.add_species(q, m, w)
+    assert a == b
+    return a
+
+
+def by_id(P):
+    o = np.argsort(P["id"], kind="stable")
+    return {k: np.asarray(v)[o] for k, v in P.items()}
+
+
+def explicit_particles(gpu, orc, s, n, seed, vth, margin=0.0):
+    x, y, z, vx, vy, vz = wl.random_particles(gpu.n, n, seed, vth=vth, margin=margin)
+    keep = orc.obj.L(x, y, z) >= 0
+    arr = [a[keep] for a in (x, y, z, vx, vy, vz)]
+    ids = np.arange(len(arr[0]), dtype=np.int64) * 3 + 5
+    gpu.load_particles(s, *arr, ids)
+    orc.load_particles(s, *arr, ids)
+    return len(ids)
