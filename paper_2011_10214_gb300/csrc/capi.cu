@@ -210,16 +210,16 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.inj_base, sizeof(long long) * MAX_SPECIES * 6);
     ALLOC(c.inj_carry, sizeof(double) * MAX_SPECIES * 6);
     ALLOC(c.inj_dev, sizeof(InjectDev) * MAX_SPECIES * 6);
-    CUDA_OK(cudaMemset(c.phi, 0, sizeof(double) * N));
-    CUDA_OK(cudaMemset(c.E, 0, sizeof(double4) * N));
-    CUDA_OK(cudaMemset(c.Ef, 0, sizeof(float4) * N));
-    CUDA_OK(cudaMemset(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * N));
-    CUDA_OK(cudaMemset(c.ctrall, 0, sizeof(unsigned long long) * MAX_SPECIES * NCTR));
-    CUDA_OK(cudaMemset(c.scal, 0, sizeof(double) * 64));
-    CUDA_OK(cudaMemset(c.red_ticket, 0, sizeof(unsigned) * 4));
-    CUDA_OK(cudaMemset(c.err_word, 0, sizeof(int)));
-    CUDA_OK(cudaMemset(c.next_id, 0, sizeof(long long) * MAX_SPECIES));
-    CUDA_OK(cudaMemset(c.inj_carry, 0, sizeof(double) * MAX_SPECIES * 6));
+    CUDA_OK(szero(c.stream, c.phi, sizeof(double) * N));
+    CUDA_OK(szero(c.stream, c.E, sizeof(double4) * N));
+    CUDA_OK(szero(c.stream, c.Ef, sizeof(float4) * N));
+    CUDA_OK(szero(c.stream, c.Wall, sizeof(unsigned long long) * MAX_SPECIES * N));
+    CUDA_OK(szero(c.stream, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR));
+    CUDA_OK(szero(c.stream, c.scal, sizeof(double) * 64));
+    CUDA_OK(szero(c.stream, c.red_ticket, sizeof(unsigned) * 4));
+    CUDA_OK(szero(c.stream, c.err_word, sizeof(int)));
+    CUDA_OK(szero(c.stream, c.next_id, sizeof(long long) * MAX_SPECIES));
+    CUDA_OK(szero(c.stream, c.inj_carry, sizeof(double) * MAX_SPECIES * 6));
     TetTables t = make_tables();
     CUDA_OK(set_tet_tables(t));
     CUDA_OK(set_field_tables(t));
@@ -295,7 +295,7 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr;
     CUDA_OK(launch_setup(c));
     ALLOC(c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1));
-    CUDA_OK(cudaMemset(c.surfall, 0, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1)));
+    CUDA_OK(szero(c.stream, c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1)));
     for (size_t s = 0; s < c.sp.size(); ++s) c.sp[s].surf = c.surfall + s * (c.ncut > 0 ? c.ncut : 1);
     CUDA_OK(launch_field_lift(c));
     CUDA_OK(cudaStreamSynchronize(c.stream));
@@ -364,8 +364,8 @@ static pifepic_status upload_species_params(pifepic_ctx* ctx) {
     double co[MAX_SPECIES] = {0};
     for (size_t s = 0; s < c.sp.size(); ++s) co[s] = c.sp[s].q * c.sp[s].w;
     int ns = (int)c.sp.size();
-    CUDA_OK(cudaMemcpy(c.scal + 16, co, sizeof(co), cudaMemcpyHostToDevice));
-    CUDA_OK(cudaMemcpy((int*)(c.scal + 24), &ns, sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_OK(scopy(c.stream, c.scal + 16, co, sizeof(co), cudaMemcpyHostToDevice));
+    CUDA_OK(scopy(c.stream, (int*)(c.scal + 24), &ns, sizeof(int), cudaMemcpyHostToDevice));
     return PIFEPIC_OK;
 }
 
@@ -377,7 +377,7 @@ static pifepic_status ensure_movers(pifepic_ctx* ctx, int s, long long need) {
     long long keep = 0;
     if (q.mov_n) {
         unsigned long long n0 = 0;
-        CUDA_OK(cudaMemcpy(&n0, q.mov_n, sizeof(n0), cudaMemcpyDeviceToHost));
+        CUDA_OK(scopy(c.stream, &n0, q.mov_n, sizeof(n0), cudaMemcpyDeviceToHost));
         keep = (long long)n0;
     }
     cudaError_t e;
@@ -388,8 +388,8 @@ static pifepic_status ensure_movers(pifepic_ctx* ctx, int s, long long need) {
     if (keep > 0) {   // carry the waiting list over
         double* src[6] = {q.mov[0].x, q.mov[0].y, q.mov[0].z, q.mov[0].vx, q.mov[0].vy, q.mov[0].vz};
         double* dst[6] = {a0.x, a0.y, a0.z, a0.vx, a0.vy, a0.vz};
-        for (int d = 0; d < 6; ++d) CUDA_OK(cudaMemcpy(dst[d], src[d], sizeof(double) * keep, cudaMemcpyDeviceToDevice));
-        if (c.track) CUDA_OK(cudaMemcpy(a0.id, q.mov[0].id, sizeof(long long) * keep, cudaMemcpyDeviceToDevice));
+        for (int d = 0; d < 6; ++d) CUDA_OK(scopy(c.stream, dst[d], src[d], sizeof(double) * keep, cudaMemcpyDeviceToDevice));
+        if (c.track) CUDA_OK(scopy(c.stream, a0.id, q.mov[0].id, sizeof(long long) * keep, cudaMemcpyDeviceToDevice));
     }
     free_parr(q.mov[0]); free_parr(q.mov[1]);
     q.mov[0] = a0; q.mov[1] = a1;
@@ -413,7 +413,7 @@ pifepic_status pifepic_add_species(pifepic_ctx* ctx, double qq, double mm, doubl
     q.surf = c.surfall + (long long)idx * (c.ncut > 0 ? c.ncut : 1);
     q.ctr = c.ctrall + idx * NCTR;
     ALLOC(q.mov_n, 2 * sizeof(unsigned long long));
-    CUDA_OK(cudaMemset(q.mov_n, 0, 2 * sizeof(unsigned long long)));
+    CUDA_OK(szero(c.stream, q.mov_n, 2 * sizeof(unsigned long long)));
     pifepic_status st = ensure_movers(ctx, idx, 1 << 16);
     if (st) return st;
     // empty bins
@@ -437,7 +437,7 @@ static pifepic_status flatten(pifepic_ctx* ctx, int s, long long extra, PArr* fl
     *flat = alloc_parr_raw(n0 + extra, true, &e);
     if (e != cudaSuccess) { free_parr(*flat); FAIL(PIFEPIC_ENOMEM, "flat particle buffer allocation failed"); }
     ALLOC(*nflat, sizeof(unsigned long long));
-    CUDA_OK(cudaMemset(*nflat, 0, sizeof(unsigned long long)));
+    CUDA_OK(szero(c.stream, *nflat, sizeof(unsigned long long)));
     if (!c.track) {   // without ids the flat copy still carries an id array: fill it later
     }
     CUDA_OK(launch_flatten(c, s, *flat, *nflat));
@@ -449,11 +449,11 @@ static pifepic_status flatten(pifepic_ctx* ctx, int s, long long extra, PArr* fl
 static long long count_particles(Ctx& c, int s) {
     Species& q = c.sp[s];
     std::vector<int> cnt(c.nblocks);
-    if (cudaMemcpy(cnt.data(), q.bcount, sizeof(int) * c.nblocks, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (scopy(c.stream, cnt.data(), q.bcount, sizeof(int) * c.nblocks, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
     long long n = 0;
     for (int v : cnt) n += v;
     unsigned long long w = 0;
-    if (cudaMemcpy(&w, q.mov_n, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (scopy(c.stream, &w, q.mov_n, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
     return n + (long long)w;
 }
 
@@ -479,13 +479,13 @@ pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double 
     if (st) return st;
     CUDA_OK(launch_load_maxwellian(c, s, ppc, vth, drift, seed, flat, nflat, n0 + add));
     unsigned long long nt = 0;
-    CUDA_OK(cudaMemcpy(&nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
+    CUDA_OK(scopy(c.stream, &nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
     st = rebuild(ctx, s, flat, (long long)nt);
     free_parr(flat); cudaFree(nflat);
     if (st) return st;
     Species& q = c.sp[s];
     q.next_id = std::max<long long>(q.next_id, c.mesh.ncells * (long long)ppc);
-    CUDA_OK(cudaMemcpy(c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
+    CUDA_OK(scopy(c.stream, c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
     return PIFEPIC_OK;
 }
 
@@ -500,30 +500,30 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int s, size_t n, const d
     pifepic_status st = flatten(ctx, s, (long long)n, &flat, &nflat, &n0);
     if (st) return st;
     unsigned long long cur = 0;
-    CUDA_OK(cudaMemcpy(&cur, nflat, sizeof(cur), cudaMemcpyDeviceToHost));
+    CUDA_OK(scopy(c.stream, &cur, nflat, sizeof(cur), cudaMemcpyDeviceToHost));
     cudaMemcpyKind k = mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const double* src[6] = {x, y, z, vx, vy, vz};
     double* dst[6] = {flat.x, flat.y, flat.z, flat.vx, flat.vy, flat.vz};
     Species& q = c.sp[s];
     if (n > 0) {
-        for (int d = 0; d < 6; ++d) CUDA_OK(cudaMemcpy(dst[d] + cur, src[d], sizeof(double) * n, k));
+        for (int d = 0; d < 6; ++d) CUDA_OK(scopy(c.stream, dst[d] + cur, src[d], sizeof(double) * n, k));
         long long newmax = q.next_id + (long long)n - 1;
         if (ids) {
-            CUDA_OK(cudaMemcpy(flat.id + cur, ids, sizeof(long long) * n, k));
+            CUDA_OK(scopy(c.stream, flat.id + cur, ids, sizeof(long long) * n, k));
             unsigned long long* mx = nullptr;
             ALLOC(mx, sizeof(unsigned long long));
-            CUDA_OK(cudaMemset(mx, 0, sizeof(unsigned long long)));
-            k_max_id<<<nb256((long long)n), 256>>>((long long)n, (const long long*)flat.id + cur, mx);
+            CUDA_OK(szero(c.stream, mx, sizeof(unsigned long long)));
+            k_max_id<<<nb256((long long)n), 256, 0, c.stream>>>((long long)n, (const long long*)flat.id + cur, mx);
             unsigned long long hm = 0;
-            CUDA_OK(cudaMemcpy(&hm, mx, sizeof(hm), cudaMemcpyDeviceToHost));
+            CUDA_OK(scopy(c.stream, &hm, mx, sizeof(hm), cudaMemcpyDeviceToHost));
             cudaFree(mx);
             newmax = (long long)hm;
         } else {
-            k_seq_id<<<nb256((long long)n), 256>>>((long long)n, q.next_id, flat.id + cur);
+            k_seq_id<<<nb256((long long)n), 256, 0, c.stream>>>((long long)n, q.next_id, flat.id + cur);
         }
         CUDA_OK(cudaGetLastError());
         q.next_id = std::max<long long>(q.next_id, newmax + 1);
-        CUDA_OK(cudaMemcpy(c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
+        CUDA_OK(scopy(c.stream, c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
     }
     st = rebuild(ctx, s, flat, (long long)cur + (long long)n);
     free_parr(flat); cudaFree(nflat);
@@ -559,7 +559,7 @@ pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, dou
     // rebuild the stream list in (species, face) order; keep carries of unchanged streams
     std::vector<double> oldcarry(MAX_SPECIES * 6, 0.0), hc(c.inj.size());
     if (!c.inj.empty()) {
-        CUDA_OK(cudaMemcpy(hc.data(), c.inj_carry, sizeof(double) * c.inj.size(), cudaMemcpyDeviceToHost));
+        CUDA_OK(scopy(c.stream, hc.data(), c.inj_carry, sizeof(double) * c.inj.size(), cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < c.inj.size(); ++i) oldcarry[c.inj[i].species * 6 + c.inj[i].face] = hc[i];
     }
     for (int f = 0; f < 6; ++f) oldcarry[s * 6 + f] = 0.0;
@@ -579,8 +579,8 @@ pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, dou
         }
     }
     if (!c.inj.empty()) {
-        CUDA_OK(cudaMemcpy(c.inj_dev, c.inj.data(), sizeof(InjectDev) * c.inj.size(), cudaMemcpyHostToDevice));
-        CUDA_OK(cudaMemcpy(c.inj_carry, carry.data(), sizeof(double) * carry.size(), cudaMemcpyHostToDevice));
+        CUDA_OK(scopy(c.stream, c.inj_dev, c.inj.data(), sizeof(InjectDev) * c.inj.size(), cudaMemcpyHostToDevice));
+        CUDA_OK(scopy(c.stream, c.inj_carry, carry.data(), sizeof(double) * carry.size(), cudaMemcpyHostToDevice));
     }
     long long n = count_particles(c, s);
     long long need = std::max<long long>(1 << 16, n / 8 + 4096);
@@ -603,7 +603,7 @@ pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem
     long long N = c.mesh.nnodes;
     double* tmp = nullptr;
     ALLOC(tmp, sizeof(double) * 3 * N);
-    CUDA_OK(cudaMemcpy(tmp, E, sizeof(double) * 3 * N,
+    CUDA_OK(scopy(c.stream, tmp, E, sizeof(double) * 3 * N,
                        mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     k_pack_E<<<nb256(N), 256, 0, c.stream>>>(N, tmp, c.E, c.Ef);
     CUDA_OK(cudaGetLastError());
@@ -614,12 +614,12 @@ pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem
 }
 
 static void read_counters(Ctx& c, unsigned long long* out) {
-    cudaMemcpy(out, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR, cudaMemcpyDeviceToHost);
+    scopy(c.stream, out, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR, cudaMemcpyDeviceToHost);
 }
 
 static long long iters_total(Ctx& c) {
     long long v = 0;
-    cudaMemcpy(&v, (long long*)(c.scal + 40), sizeof(v), cudaMemcpyDeviceToHost);
+    scopy(c.stream, &v, (long long*)(c.scal + 40), sizeof(v), cudaMemcpyDeviceToHost);
     return v;
 }
 
@@ -660,7 +660,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     s.surface_potential = d2[1];
     if (phase_ms) for (int k = 0; k < 8; ++k) s.phase_ms[k] = phase_ms[k];
     int herr = 0;
-    cudaMemcpy(&herr, c.err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    scopy(c.stream, &herr, c.err_word, sizeof(int), cudaMemcpyDeviceToHost);
     c.stats = s;
     if (st) *st = s;
     if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
@@ -750,7 +750,7 @@ pifepic_status pifepic_get_potential(pifepic_ctx* ctx, double* phi, int mem_kind
     NEED(ctx); NEED(phi);
     Ctx& c = ctx->c;
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    CUDA_OK(cudaMemcpy(phi, c.phi, sizeof(double) * c.mesh.nnodes, out_kind(mem_kind)));
+    CUDA_OK(scopy(c.stream, phi, c.phi, sizeof(double) * c.mesh.nnodes, out_kind(mem_kind)));
     return PIFEPIC_OK;
 }
 
@@ -762,7 +762,7 @@ pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind) {
     ALLOC(tmp, sizeof(double) * 3 * N);
     k_unpack_E<<<nb256(N), 256, 0, c.stream>>>(N, c.E, tmp);
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    CUDA_OK(cudaMemcpy(E, tmp, sizeof(double) * 3 * N, out_kind(mem_kind)));
+    CUDA_OK(scopy(c.stream, E, tmp, sizeof(double) * 3 * N, out_kind(mem_kind)));
     cudaFree(tmp);
     return PIFEPIC_OK;
 }
@@ -772,7 +772,7 @@ pifepic_status pifepic_get_node_charge(pifepic_ctx* ctx, int s, int64_t* W, int 
     Ctx& c = ctx->c;
     if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    CUDA_OK(cudaMemcpy(W, c.sp[s].W, sizeof(int64_t) * c.mesh.nnodes, out_kind(mem_kind)));
+    CUDA_OK(scopy(c.stream, W, c.sp[s].W, sizeof(int64_t) * c.mesh.nnodes, out_kind(mem_kind)));
     return PIFEPIC_OK;
 }
 
@@ -781,7 +781,7 @@ pifepic_status pifepic_get_surface_charge(pifepic_ctx* ctx, int s, int64_t* cnt,
     Ctx& c = ctx->c;
     if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    if (c.ncut > 0) CUDA_OK(cudaMemcpy(cnt, c.sp[s].surf, sizeof(int64_t) * c.ncut, out_kind(mem_kind)));
+    if (c.ncut > 0) CUDA_OK(scopy(c.stream, cnt, c.sp[s].surf, sizeof(int64_t) * c.ncut, out_kind(mem_kind)));
     return PIFEPIC_OK;
 }
 
@@ -789,15 +789,15 @@ pifepic_status pifepic_get_cut_cells(pifepic_ctx* ctx, int32_t* cells, double* a
     NEED(ctx);
     Ctx& c = ctx->c;
     if (c.ncut == 0) return PIFEPIC_OK;
-    if (cells) CUDA_OK(cudaMemcpy(cells, c.cut_cell, sizeof(int32_t) * c.ncut, cudaMemcpyDeviceToHost));
-    if (area) CUDA_OK(cudaMemcpy(area, c.cut_area, sizeof(double) * c.ncut, cudaMemcpyDeviceToHost));
+    if (cells) CUDA_OK(scopy(c.stream, cells, c.cut_cell, sizeof(int32_t) * c.ncut, cudaMemcpyDeviceToHost));
+    if (area) CUDA_OK(scopy(c.stream, area, c.cut_area, sizeof(double) * c.ncut, cudaMemcpyDeviceToHost));
     return PIFEPIC_OK;
 }
 
 pifepic_status pifepic_get_cell_target(pifepic_ctx* ctx, int32_t* target) {
     NEED(ctx); NEED(target);
     Ctx& c = ctx->c;
-    CUDA_OK(cudaMemcpy(target, c.cell_acc, sizeof(int32_t) * c.mesh.ncells, cudaMemcpyDeviceToHost));
+    CUDA_OK(scopy(c.stream, target, c.cell_acc, sizeof(int32_t) * c.mesh.ncells, cudaMemcpyDeviceToHost));
     return PIFEPIC_OK;
 }
 
@@ -806,10 +806,10 @@ pifepic_status pifepic_get_interface(pifepic_ctx* ctx, int32_t* cell, int32_t* t
     NEED(ctx);
     Ctx& c = ctx->c;
     if (c.nit == 0) return PIFEPIC_OK;
-    if (cell) CUDA_OK(cudaMemcpy(cell, c.it_cell, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
-    if (tet) CUDA_OK(cudaMemcpy(tet, c.it_t, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
+    if (cell) CUDA_OK(scopy(c.stream, cell, c.it_cell, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
+    if (tet) CUDA_OK(scopy(c.stream, tet, c.it_t, sizeof(int32_t) * c.nit, cudaMemcpyDeviceToHost));
     std::vector<double> rec((size_t)c.nit * IT_STRIDE);
-    CUDA_OK(cudaMemcpy(rec.data(), c.it_data, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
+    CUDA_OK(scopy(c.stream, rec.data(), c.it_data, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
     for (long long T = 0; T < c.nit; ++T) {
         const double* r = rec.data() + T * IT_STRIDE;
         if (vp) vp[T] = r[IT_VOLP];
@@ -845,7 +845,7 @@ pifepic_status pifepic_get_particles(pifepic_ctx* ctx, int s, int64_t cap, doubl
         flat = alloc_parr_raw(cnt, true, &e);
         if (e != cudaSuccess) { free_parr(flat); FAIL(PIFEPIC_ENOMEM, "flat buffer"); }
         ALLOC(nflat, sizeof(unsigned long long));
-        CUDA_OK(cudaMemset(nflat, 0, sizeof(unsigned long long)));
+        CUDA_OK(szero(c.stream, nflat, sizeof(unsigned long long)));
         CUDA_OK(launch_flatten_mixed_to_f64(c, s, flat, nflat));
         CUDA_OK(cudaStreamSynchronize(c.stream));
         n0 = cnt;
@@ -858,8 +858,8 @@ pifepic_status pifepic_get_particles(pifepic_ctx* ctx, int s, int64_t cap, doubl
     double* dst[6] = {x, y, z, vx, vy, vz};
     double* src[6] = {flat.x, flat.y, flat.z, flat.vx, flat.vy, flat.vz};
     for (int d = 0; d < 6; ++d)
-        if (dst[d] && m > 0) CUDA_OK(cudaMemcpy(dst[d], src[d], sizeof(double) * m, k));
-    if (ids && m > 0) CUDA_OK(cudaMemcpy(ids, flat.id, sizeof(int64_t) * m, k));
+        if (dst[d] && m > 0) CUDA_OK(scopy(c.stream, dst[d], src[d], sizeof(double) * m, k));
+    if (ids && m > 0) CUDA_OK(scopy(c.stream, ids, flat.id, sizeof(int64_t) * m, k));
     *n = m;
     free_parr(flat); cudaFree(nflat);
     return PIFEPIC_OK;
@@ -880,10 +880,10 @@ pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const doub
     double* Fd = nullptr;
     ALLOC(Fd, sizeof(double) * N);
     cudaMemcpyKind k = mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CUDA_OK(cudaMemcpy(Fd, F, sizeof(double) * N, k));
+    CUDA_OK(scopy(c.stream, Fd, F, sizeof(double) * N, k));
     if (c.nit > 0) {
-        if (q) CUDA_OK(cudaMemcpy(c.qT, q, sizeof(double) * c.nit, k));
-        else CUDA_OK(cudaMemset(c.qT, 0, sizeof(double) * c.nit));
+        if (q) CUDA_OK(scopy(c.stream, c.qT, q, sizeof(double) * c.nit, k));
+        else CUDA_OK(szero(c.stream, c.qT, sizeof(double) * c.nit));
     }
     cudaError_t e = launch_solve_external(c, Fd, iters, relres);
     cudaFree(Fd);

@@ -652,7 +652,7 @@ cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double
     cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(&hs, S, sizeof(PcgState), cudaMemcpyDeviceToHost);
+    e = scopy(c.stream, &hs, S, sizeof(PcgState), cudaMemcpyDeviceToHost);
     if (iters) *iters = hs.it;
     if (relres) *relres = hs.relres;
     c.last_iters = hs.it; c.last_relres = hs.relres; c.last_conv = hs.converged;

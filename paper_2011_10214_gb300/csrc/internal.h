@@ -173,6 +173,23 @@ struct Ctx {
     int last_conv = 1;
 };
 
+// Stream-ordered copies and fills on the context's stream.  The caller's
+// stream may be non-blocking with respect to the legacy default stream (as
+// PyTorch streams are), so the library never uses the synchronous
+// cudaMemcpy / cudaMemset, which run on the legacy stream.
+inline cudaError_t scopy(cudaStream_t st, void* dst, const void* src, size_t n, cudaMemcpyKind k) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, k, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+inline cudaError_t szero(cudaStream_t st, void* p, size_t n) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p, 0, n, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
 // interface-tet record layout (doubles)
 enum {
     IT_VOLP = 0, IT_VOLM = 1, IT_AREA = 2,

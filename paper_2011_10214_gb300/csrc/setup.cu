@@ -471,7 +471,7 @@ cudaError_t launch_setup(Ctx& c) {
     CK(cudaGetLastError());
     // interface-tet offsets per cell
     CK(exclusive_scan(cnt, m.ncells, scan, tot, st));
-    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(scopy(st, &hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
     c.nit = hv;
     k_narrow<<<nb(m.ncells), 256, 0, st>>>(scan, m.ncells, c.ibase);
     nit_alloc = c.nit > 0 ? c.nit : 1;
@@ -485,7 +485,7 @@ cudaError_t launch_setup(Ctx& c) {
     k_cell_area<<<nb(m.ncells), 256, 0, st>>>(m, c.imask, c.ibase, c.it_data, flag, carea);
     CK(cudaGetLastError());
     CK(exclusive_scan(flag, m.ncells, scan, tot, st));
-    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(scopy(st, &hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
     c.ncut = hv;
     {
         long long nc;
@@ -501,12 +501,12 @@ cudaError_t launch_setup(Ctx& c) {
     CK(cudaGetLastError());
     // nodes
     for (int f = 0; f < 6; ++f) { hdir[f] = c.bc[f].kind == PIFEPIC_BC_DIRICHLET; hval[f] = c.bc[f].value; }
-    CK(cudaMemcpy(bcdir, hdir, sizeof(hdir), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(bcval, hval, sizeof(hval), cudaMemcpyHostToDevice));
+    CK(scopy(st, bcdir, hdir, sizeof(hdir), cudaMemcpyHostToDevice));
+    CK(scopy(st, bcval, hval, sizeof(hval), cudaMemcpyHostToDevice));
     k_node_kind<<<nb(m.nnodes), 256, 0, st>>>(m, c.Lnode, c.imask, bcdir, bcval, c.ntype, cnt, c.gdir);
     CK(cudaGetLastError());
     CK(exclusive_scan(cnt, m.nnodes, scan, tot, st));
-    CK(cudaMemcpy(&hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(scopy(st, &hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
     c.npatch = hv;
     {
         long long np;
