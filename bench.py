@@ -81,7 +81,8 @@ class Clocks:
 
 def workload(name):
     from paper_2011_10214_gb300 import workloads as wl
-    return {"sphere64": wl.SPHERE64, "sphere16": wl.SPHERE16}[name]
+    return {"sphere64": wl.SPHERE64, "sphere16": wl.SPHERE16,
+            "sphere32": wl.sphere_config(32, 3.0, 64, 100, seed_offset=6)}[name]
 
 
 def cfg_desc(cfg, precision, extra=None):
@@ -305,7 +306,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="sphere64", choices=["sphere64", "sphere16"])
+    ap.add_argument("--workload", default="sphere64", choices=["sphere64", "sphere32", "sphere16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--as-baseline", action="store_true")
