@@ -213,6 +213,31 @@ pifepic_status pifepic_get_stats(pifepic_ctx* ctx, pifepic_stats* stats);
 pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const double* q, int mem_kind,
                                    int* iters, double* relres);
 
+/* Field solve that allocates nothing.  (The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory once they are
+ * running -- a serving loop whose memory comes from a pool it does not own,
+ * code that issues work while a stream is being captured into a CUDA graph,
+ * or a host application that forbids allocation after start-up.
+ * pifepic_solve_field allocates a staging buffer and builds a CUDA graph on
+ * every call; this variant does neither.)
+ *
+ * Same system and stopping rule as pifepic_solve_field, on the context's
+ * operator, tolerance and iteration cap; the context's own potential, node
+ * field and solver state are left untouched.  F (nnodes), q
+ * (n_interface_tets, may be NULL for no flux jump) and phi (nnodes, output)
+ * are caller-owned DEVICE arrays.  The PCG work vectors live in one fixed
+ * __device__ array of the library, 5.3 MB, which every GPU that loads the
+ * library holds until the process exits; meshes with more than
+ * PIFEPIC_NOALLOC_MAX_NODES nodes are rejected with EINVAL.  The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress), so make
+ * it before any stream capture.  Every call shares the array and it keeps the
+ * previous call's contents: calls that overlap on the GPU (other streams,
+ * other contexts on the same device) race.  Synchronises the context's stream
+ * to return iters and relres. */
+#define PIFEPIC_NOALLOC_MAX_NODES 131072
+pifepic_status pifepic_solve_field_noalloc(pifepic_ctx* ctx, const double* F, const double* q, double* phi,
+                                           int* iters, double* relres);
+
 #ifdef __cplusplus
 }
 #endif

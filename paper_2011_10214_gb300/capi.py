@@ -92,6 +92,7 @@ _sigs = {
     "pifepic_get_particles": [_ctx, C.c_int, C.c_int64] + [_dp] * 7 + [C.POINTER(C.c_int64), C.c_int],
     "pifepic_get_stats": [_ctx, C.POINTER(Stats)],
     "pifepic_solve_field": [_ctx, _dp, _dp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "pifepic_solve_field_noalloc": [_ctx, _dp, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
 }
 for _n, _a in _sigs.items():
     _f = getattr(lib, _n)
@@ -231,6 +232,15 @@ class Simulation:
             q = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
         self._ok(lib.pifepic_solve_field(self._c, _addr(F), _addr(q), DEVICE if dev else HOST, C.byref(it),
                                          C.byref(rr)), "solve_field")
+        return it.value, rr.value
+
+    def solve_field_noalloc(self, F, q, phi):
+        """Field solve into phi without any device allocation; F, q, phi are
+        CUDA tensors (q may be None).  See pifepic_solve_field_noalloc."""
+        it = C.c_int()
+        rr = C.c_double()
+        self._ok(lib.pifepic_solve_field_noalloc(self._c, _addr(F), _addr(q), _addr(phi), C.byref(it),
+                                                 C.byref(rr)), "solve_field_noalloc")
         return it.value, rr.value
 
     # -- read-back ----------------------------------------------------------------------

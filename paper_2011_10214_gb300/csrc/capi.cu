@@ -20,6 +20,8 @@ cudaError_t read_pcg_state(Ctx& c);
 int solve_graph_fixed_kernels(const Ctx& c);
 cudaError_t build_pcg_graph_mixed(Ctx& c);
 cudaError_t launch_pcg_mixed(Ctx& c);
+pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
+                                   double* relres);
 
 // 5-tet split tables, computed from the definition (reading of Sec. 3.1.1)
 static TetTables make_tables() {
@@ -889,6 +891,13 @@ pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const doub
     cudaFree(Fd);
     if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "field solve: %s", cudaGetErrorString(e));
     return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_solve_field_noalloc(pifepic_ctx* ctx, const double* F, const double* q, double* phi,
+                                           int* iters, double* relres) {
+    NEED(ctx); NEED(F); NEED(phi);
+    if (!ctx->c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
+    return solve_field_noalloc(ctx->c, F, q, phi, iters, relres);
 }
 
 }  // extern "C"

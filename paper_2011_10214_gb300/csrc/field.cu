@@ -15,6 +15,7 @@
 // on the device; no host round trip.  Reductions are deterministic: per-block
 // partials, summed in a fixed order by the last block to finish.
 #include <math.h>
+#include <stdio.h>
 
 #include "internal.h"
 
@@ -699,6 +700,172 @@ cudaError_t launch_qtets(Ctx& c) {
     if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, c.stream>>>(a, c.cut_area, c.qcut);
     if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, c.stream>>>(c.nit, c.it_acc, c.qcut, c.qT);
     return cudaGetLastError();
+}
+
+// ======================================================================================
+// Field solve that allocates nothing (pifepic_solve_field_noalloc).
+//
+// Some callers cannot call cudaMalloc once their run is under way: a serving
+// loop whose device memory is handed out by a pool it does not own, code that
+// runs while a stream is being captured into a CUDA graph, or an embedding
+// that forbids allocation after start-up.  pifepic_solve_field allocates a
+// staging buffer and builds a CUDA graph on every call, so those callers need
+// this variant.  It reuses the context's operator (read only), takes the load
+// F, the flux jumps q and the output phi as caller-owned device arrays, and
+// keeps every work vector of the PCG in one file-scope device array of fixed
+// size, found once per device with cudaGetSymbolAddress.
+// ======================================================================================
+constexpr long long NOALLOC_MAX_NODES = 131072;                  // 2^17 mesh nodes
+constexpr long long NOALLOC_PARTIALS = 4 * (NOALLOC_MAX_NODES / 256 + 1);
+constexpr long long NOALLOC_DOUBLES = 5 * NOALLOC_MAX_NODES + NOALLOC_PARTIALS + 32;
+// layout: u, b, r, p, q (NOALLOC_MAX_NODES each) | partials | PcgState + ticket
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+// the PCG steps of the graph version without the conditional handle; every
+// launch after convergence returns at once, so the host can queue the
+// iteration cap without waiting for the device
+__global__ void k_na_init(FieldArgs f, const double* b, const double* q, double* r, double* p, double* partial,
+                          unsigned* ticket, PcgState* S) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[3] = {0, 0, 0};
+    if (n < f.m.nnodes) {
+        double bn = b[n];
+        double rn = (f.ntype[n] == -3) ? 0.0 : bn - q[n];
+        double zn = f.invdiag[n] * rn;
+        r[n] = rn;
+        p[n] = zn;
+        v[0] = bn * bn; v[1] = rn * rn; v[2] = rn * zn;
+    }
+    double tot[3];
+    if (grid_sum<3>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        S->bb = tot[0]; S->rr = tot[1]; S->rz = tot[2];
+        S->it = 0;
+        S->converged = (tot[0] == 0.0) || (tot[1] <= S->tol2 * tot[0]);
+        S->done = S->converged || (S->maxit <= 0);
+        S->relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+    }
+}
+
+__global__ void k_na_spmv(FieldArgs f, const double* p, double* q, double* partial, unsigned* ticket, PcgState* S) {
+    if (S->done) return;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (n < f.m.nnodes) {
+        int i, j, k;
+        node_ijk(f.m, n, i, j, k);
+        double y = apply_row<double>(f, n, i, j, k, p, f.coef);
+        q[n] = y;
+        v[0] = p[n] * y;
+    }
+    double tot[1];
+    if (grid_sum<1>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        S->pq = tot[0];
+        S->alpha = S->rz / tot[0];
+    }
+}
+
+__global__ void k_na_update(FieldArgs f, double* u, double* r, const double* p, const double* q, double* partial,
+                            unsigned* ticket, PcgState* S) {
+    if (S->done) return;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double alpha = S->alpha;
+    double v[2] = {0, 0};
+    if (n < f.m.nnodes) {
+        double rn = r[n] - alpha * q[n];
+        u[n] = u[n] + alpha * p[n];
+        r[n] = rn;
+        v[0] = rn * rn; v[1] = rn * f.invdiag[n] * rn;
+    }
+    double tot[2];
+    if (grid_sum<2>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        S->rr = tot[0];
+        S->beta = tot[1] / S->rz;
+        S->rz = tot[1];
+        S->it = S->it + 1;
+        S->converged = tot[0] <= S->tol2 * S->bb;
+        S->relres = sqrt(tot[0] / S->bb);
+        S->done = S->converged || (S->it >= S->maxit);
+    }
+}
+
+__global__ void k_na_dir(FieldArgs f, const double* r, double* p, const PcgState* S) {
+    if (S->done) return;
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n < f.m.nnodes) p[n] = f.invdiag[n] * r[n] + S->beta * p[n];
+}
+
+__global__ void k_na_state(PcgState* S, unsigned* ticket, double tol2, int maxit) {
+    PcgState s = {};
+    s.tol2 = tol2;
+    s.maxit = maxit;
+    *S = s;
+    *ticket = 0u;
+}
+
+// set-up once per device (with that device current): in host code the name of
+// a __device__ array is a host-side stand-in, not a device address, so the
+// address is looked up with cudaGetSymbolAddress and cached per device.  Two
+// threads doing the first call on one device at once both store the same value.
+static void* g_noalloc_dev[64];
+static int g_noalloc_ready[64];
+
+pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
+                                   double* relres) {
+    long long N = c.mesh.nnodes;
+    if (N > NOALLOC_MAX_NODES) {
+        char b[256];
+        snprintf(b, sizeof(b), "solve_field_noalloc: mesh has %lld nodes; the fixed scratch holds at most %lld",
+                 N, NOALLOC_MAX_NODES);
+        c.err = b;
+        return PIFEPIC_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { c.err = "solve_field_noalloc: no device"; return PIFEPIC_ECUDA; }
+    if (!g_noalloc_ready[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            c.err = std::string("solve_field_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            return PIFEPIC_ECUDA;
+        }
+        g_noalloc_dev[dev] = ptr;
+        g_noalloc_ready[dev] = 1;
+    }
+    double* base = (double*)g_noalloc_dev[dev];
+    double* u = base;
+    double* bvec = base + NOALLOC_MAX_NODES;
+    double* r = base + 2 * NOALLOC_MAX_NODES;
+    double* p = base + 3 * NOALLOC_MAX_NODES;
+    double* qv = base + 4 * NOALLOC_MAX_NODES;
+    double* partial = base + 5 * NOALLOC_MAX_NODES;
+    PcgState* S = (PcgState*)(partial + NOALLOC_PARTIALS);
+    unsigned* ticket = (unsigned*)(partial + NOALLOC_PARTIALS + 24);
+    FieldArgs f = fargs(c);
+    RhsArgs a = rargs(c);
+    unsigned gb = nb(N);
+    cudaStream_t st = c.stream;
+    k_na_state<<<1, 1, 0, st>>>(S, ticket, c.tol * c.tol, c.maxit);
+    k_rhs<<<gb, 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, q, c.lift, bvec, F);
+    cudaMemsetAsync(u, 0, sizeof(double) * N, st);
+    k_matvec<<<gb, 256, 0, st>>>(f, u, qv);
+    k_na_init<<<gb, 256, 0, st>>>(f, bvec, qv, r, p, partial, ticket, S);
+    for (int it = 0; it < c.maxit; ++it) {
+        k_na_spmv<<<gb, 256, 0, st>>>(f, p, qv, partial, ticket, S);
+        k_na_update<<<gb, 256, 0, st>>>(f, u, r, p, qv, partial, ticket, S);
+        k_na_dir<<<gb, 256, 0, st>>>(f, r, p, S);
+    }
+    k_phi_from_u<<<gb, 256, 0, st>>>(N, u, c.gdir, phi, S);
+    cudaError_t e = cudaGetLastError();
+    PcgState hs;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, S, sizeof(PcgState), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        c.err = std::string("solve_field_noalloc: ") + cudaGetErrorString(e);
+        return PIFEPIC_ECUDA;
+    }
+    if (iters) *iters = hs.it;
+    if (relres) *relres = hs.relres;
+    return PIFEPIC_OK;
 }
 
 }  // namespace pf
