@@ -20,6 +20,8 @@ cudaError_t read_pcg_state(Ctx& c);
 int solve_graph_fixed_kernels(const Ctx& c);
 cudaError_t build_pcg_graph_mixed(Ctx& c);
 cudaError_t launch_pcg_mixed(Ctx& c);
+cudaError_t alloc_parrf(PArrF& a, long long n, bool id);
+void free_parrf(PArrF& a);
 pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
                                    double* relres);
 
@@ -383,6 +385,25 @@ static pifepic_status ensure_movers(pifepic_ctx* ctx, int s, long long need) {
         keep = (long long)n0;
     }
     cudaError_t e;
+    if (c.precision == PIFEPIC_MIXED) {
+        PArrF f0{}, f1{};
+        e = alloc_parrf(f0, need, c.track != 0);
+        if (e == cudaSuccess) e = alloc_parrf(f1, need, c.track != 0);
+        if (e != cudaSuccess) FAIL(PIFEPIC_ENOMEM, "mover list allocation failed");
+        if (keep > 0) {
+            CUDA_OK(scopy(c.stream, f0.cell, q.movF[0].cell, sizeof(int) * keep, cudaMemcpyDeviceToDevice));
+            float* src[6] = {q.movF[0].fx, q.movF[0].fy, q.movF[0].fz, q.movF[0].vx, q.movF[0].vy, q.movF[0].vz};
+            float* dst[6] = {f0.fx, f0.fy, f0.fz, f0.vx, f0.vy, f0.vz};
+            for (int d = 0; d < 6; ++d)
+                CUDA_OK(scopy(c.stream, dst[d], src[d], sizeof(float) * keep, cudaMemcpyDeviceToDevice));
+            if (c.track) CUDA_OK(scopy(c.stream, f0.id, q.movF[0].id, sizeof(long long) * keep, cudaMemcpyDeviceToDevice));
+        }
+        PArrF old0 = q.movF[0], old1 = q.movF[1];
+        q.movF[0] = f0; q.movF[1] = f1;
+        free_parrf(old0); free_parrf(old1);
+        q.mcap = need;
+        return PIFEPIC_OK;
+    }
     PArr a0 = alloc_parr_raw(need, c.track != 0, &e);
     if (e != cudaSuccess) { free_parr(a0); FAIL(PIFEPIC_ENOMEM, "mover list allocation failed"); }
     PArr a1 = alloc_parr_raw(need, c.track != 0, &e);
@@ -420,7 +441,8 @@ pifepic_status pifepic_add_species(pifepic_ctx* ctx, double qq, double mm, doubl
     if (st) return st;
     // empty bins
     PArr none{};
-    CUDA_OK(launch_build_bins(c, idx, none, 0, true));
+    CUDA_OK(c.precision == PIFEPIC_MIXED ? launch_build_bins_mixed(c, idx, none, 0, true)
+                                         : launch_build_bins(c, idx, none, 0, true));
     st = upload_species_params(ctx);
     if (st) return st;
     if (id) *id = idx;
@@ -442,7 +464,8 @@ static pifepic_status flatten(pifepic_ctx* ctx, int s, long long extra, PArr* fl
     CUDA_OK(szero(c.stream, *nflat, sizeof(unsigned long long)));
     if (!c.track) {   // without ids the flat copy still carries an id array: fill it later
     }
-    CUDA_OK(launch_flatten(c, s, *flat, *nflat));
+    CUDA_OK(c.precision == PIFEPIC_MIXED ? launch_flatten_mixed_to_f64(c, s, *flat, *nflat)
+                                         : launch_flatten(c, s, *flat, *nflat));
     CUDA_OK(cudaStreamSynchronize(c.stream));
     *nexist = n0;
     return PIFEPIC_OK;
@@ -465,7 +488,8 @@ static pifepic_status rebuild(pifepic_ctx* ctx, int s, PArr flat, long long n) {
     for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
     pifepic_status st = ensure_movers(ctx, s, need);
     if (st) return st;
-    CUDA_OK(launch_build_bins(c, s, flat, n, true));
+    CUDA_OK(c.precision == PIFEPIC_MIXED ? launch_build_bins_mixed(c, s, flat, n, true)
+                                         : launch_build_bins(c, s, flat, n, true));
     return PIFEPIC_OK;
 }
 
@@ -624,9 +648,15 @@ static long long iters_total(Ctx& c) {
     scopy(c.stream, &v, (long long*)(c.scal + 40), sizeof(v), cudaMemcpyDeviceToHost);
     return v;
 }
+static long long outer_total(Ctx& c) {
+    long long v = 0;
+    scopy(c.stream, &v, (long long*)(c.scal + 41), sizeof(v), cudaMemcpyDeviceToHost);
+    return v;
+}
 
 static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* before, pifepic_stats* st,
-                                 const float* phase_ms, long long it0, long long l0, long long nsolves) {
+                                 const float* phase_ms, long long it0, long long l0, long long nsolves,
+                                 long long ot0) {
     Ctx& c = ctx->c;
     unsigned long long now[MAX_SPECIES * NCTR];
     read_counters(c, now);
@@ -649,7 +679,9 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     cudaError_t e = read_pcg_state(c);
     if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "pcg state: %s", cudaGetErrorString(e));
     s.pcg_iters_total = iters_total(c) - it0;
-    s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c) + 3 * s.pcg_iters_total;
+    // solve graph: fixed kernels + 3 per PCG iteration (+ 2 per refinement step in MIXED mode)
+    s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c) + 3 * s.pcg_iters_total +
+                        2 * (outer_total(c) - ot0);
     s.pcg_iters = c.last_iters;
     s.pcg_relres = c.last_relres;
     s.pcg_converged = c.last_conv;
@@ -683,12 +715,12 @@ pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
     if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
     unsigned long long before[MAX_SPECIES * NCTR];
     read_counters(c, before);
-    long long it0 = iters_total(c), l0 = c.launches;
+    long long it0 = iters_total(c), l0 = c.launches, ot0 = outer_total(c);
     if (c.precision == PIFEPIC_MIXED) CUDA_OK(launch_deposit_all_mixed(c));
     else CUDA_OK(launch_deposit_all(c));
     if (!c.external_E) CUDA_OK(run_solve(c));
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    return fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1);
+    return fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1, ot0);
 }
 
 pifepic_status pifepic_leapfrog_init(pifepic_ctx* ctx) {
@@ -707,7 +739,7 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
     if (nsteps < 0) FAIL(PIFEPIC_EINVAL, "nsteps < 0");
     unsigned long long before[MAX_SPECIES * NCTR];
     read_counters(c, before);
-    long long it0 = iters_total(c), l0 = c.launches;
+    long long it0 = iters_total(c), l0 = c.launches, ot0 = outer_total(c);
     float ph[8] = {0};
     bool mixed = c.precision == PIFEPIC_MIXED;
     for (int it = 0; it < nsteps; ++it) {
@@ -731,7 +763,7 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
             ph[map[k]] += t;
         }
     }
-    return fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps);
+    return fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps, ot0);
 }
 
 pifepic_status pifepic_get_sizes(pifepic_ctx* ctx, int64_t* nn, int64_t* nc, int64_t* nit, int64_t* ncut) {

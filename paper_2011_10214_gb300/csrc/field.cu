@@ -26,9 +26,9 @@ __constant__ TetTables cTf;
 struct PcgState {
     double bb, rz, rr, pq, alpha, beta, tol2, relres;
     int it, maxit, done, converged;
-    // mixed mode
+    // mixed mode: FP32 inner PCG inside FP64 refinement
     double rr64, inner_tol2, inner_bb;
-    int inner_it, outer_it, inner_max;
+    int inner_it, outer_it, inner_max, done_in;
 };
 
 struct FieldArgs {
@@ -700,6 +700,206 @@ cudaError_t launch_qtets(Ctx& c) {
     if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, c.stream>>>(a, c.cut_area, c.qcut);
     if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, c.stream>>>(c.nit, c.it_acc, c.qcut, c.qT);
     return cudaGetLastError();
+}
+
+// ======================================================================================
+// MIXED solve: FP32 PCG inside FP64 iterative refinement.  Each outer step forms
+// the FP64 residual r = b - A u (FP64 operator, FP64 norms), solves A d = r in
+// FP32 (FP32 vectors and operator, FP64 dot products) to a relative 1e-3, and
+// adds d to u in FP64.  The outer test is the FP64 relative residual, so the
+// result meets the same ||r|| <= tol ||b|| as the FP64 solve.
+// ======================================================================================
+constexpr double MIXED_INNER_TOL = 1e-3;
+constexpr int MIXED_MAX_OUTER = 12;
+
+__global__ void k_ref_res(FieldArgs f, const double* b, const double* u, double* r64, float* rf, float* uf, float* pf,
+                          double* partial, unsigned* ticket, PcgState* S, cudaGraphConditionalHandle h_out,
+                          cudaGraphConditionalHandle h_in, long long* outer_total) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[3] = {0, 0, 0};
+    if (n < f.m.nnodes) {
+        int i, j, k;
+        node_ijk(f.m, n, i, j, k);
+        double bn = b[n];
+        double rn = (f.ntype[n] == -3) ? 0.0 : bn - apply_row<double>(f, n, i, j, k, u, f.coef);
+        r64[n] = rn;
+        float rfn = (float)rn;
+        float zn = f.invdiagf[n] * rfn;
+        rf[n] = rfn;
+        uf[n] = 0.0f;
+        pf[n] = zn;
+        v[0] = bn * bn; v[1] = rn * rn; v[2] = (double)rfn * (double)zn;
+    }
+    double tot[3];
+    if (grid_sum<3>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        if (S->outer_it == 0) S->bb = tot[0];
+        double bb = S->bb;
+        S->rr64 = tot[1];
+        S->relres = bb > 0.0 ? sqrt(tot[1] / bb) : 0.0;
+        bool conv = (bb == 0.0) || (tot[1] <= S->tol2 * bb);
+        bool stop = conv || (S->outer_it >= MIXED_MAX_OUTER) || (S->it >= S->maxit);
+        S->converged = conv;
+        S->done = stop;
+        S->rz = tot[2];
+        S->inner_bb = tot[1];
+        S->inner_it = 0;
+        S->done_in = stop;
+        S->outer_it = S->outer_it + 1;
+        *outer_total += 1;
+        cudaGraphSetConditional(h_out, stop ? 0u : 1u);
+        cudaGraphSetConditional(h_in, stop ? 0u : 1u);
+    }
+}
+
+__global__ void k_in_spmv(FieldArgs f, const float* p, float* q, double* partial, unsigned* ticket, PcgState* S,
+                          cudaGraphConditionalHandle h_in) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_in, 0u);
+    double v[1] = {0.0};
+    if (n < f.m.nnodes) {
+        int i, j, k;
+        node_ijk(f.m, n, i, j, k);
+        float y = apply_row<float>(f, n, i, j, k, p, f.coeff);
+        q[n] = y;
+        v[0] = (double)p[n] * (double)y;
+    }
+    double tot[1];
+    if (grid_sum<1>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        S->pq = tot[0];
+        S->alpha = S->rz / tot[0];
+    }
+}
+
+__global__ void k_in_update(FieldArgs f, float* u, float* r, const float* p, const float* q, double* partial,
+                            unsigned* ticket, PcgState* S, cudaGraphConditionalHandle h_in, long long* it_total) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float alpha = (float)S->alpha;
+    double v[2] = {0, 0};
+    if (n < f.m.nnodes) {
+        float rn = r[n] - alpha * q[n];
+        u[n] = u[n] + alpha * p[n];
+        r[n] = rn;
+        float zn = f.invdiagf[n] * rn;
+        v[0] = (double)rn * (double)rn; v[1] = (double)rn * (double)zn;
+    }
+    double tot[2];
+    if (grid_sum<2>(v, partial, ticket, tot) && threadIdx.x == 0) {
+        S->beta = tot[1] / S->rz;
+        S->rz = tot[1];
+        S->inner_it = S->inner_it + 1;
+        S->it = S->it + 1;
+        *it_total += 1;
+        bool stop = (tot[0] <= S->inner_tol2 * S->inner_bb) || (S->it >= S->maxit) || (S->inner_it >= S->inner_max);
+        S->done_in = stop;
+        if (!stop) cudaGraphSetConditional(h_in, 1u);
+    }
+}
+
+__global__ void k_in_dir(FieldArgs f, const float* r, float* p, const PcgState* S) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= f.m.nnodes || S->done_in) return;
+    p[n] = f.invdiagf[n] * r[n] + (float)S->beta * p[n];
+}
+
+__global__ void k_ref_add(long long N, double* u, const float* d) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n < N) u[n] = u[n] + (double)d[n];
+}
+
+cudaError_t build_pcg_graph_mixed(Ctx& c) {
+    if (c.pcg_exec) { cudaGraphExecDestroy(c.pcg_exec); c.pcg_exec = nullptr; }
+    if (c.pcg_graph) { cudaGraphDestroy(c.pcg_graph); c.pcg_graph = nullptr; }
+    cudaError_t e;
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g;
+    e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return e; }
+    long long N = c.mesh.nnodes;
+    unsigned gb = nb(N);
+    FieldArgs f = fargs(c);
+    PcgState* S = pcg_state(c);
+    long long* it_total = (long long*)(c.scal + 40);
+    long long* outer_total = (long long*)(c.scal + 41);
+    cudaStream_t keep = c.stream;
+    cudaGraphConditionalHandle h_out, h_in;
+    cudaGraphNode_t sink, cond_out, sink_b, cond_in;
+    cudaGraphNodeParams po = {}, pi = {};
+    cudaGraph_t body_out, body_in;
+    e = cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) goto fail;
+    c.stream = cs;
+    e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) goto fail;
+    solve_prefix(c, nullptr);
+    e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) goto fail;
+    e = find_sink(g, &sink);
+    if (e != cudaSuccess) goto fail;
+    po.type = cudaGraphNodeTypeConditional;
+    po.conditional.handle = h_out;
+    po.conditional.type = cudaGraphCondTypeWhile;
+    po.conditional.size = 1;
+    e = cudaGraphAddNode(&cond_out, g, &sink, nullptr, 1, &po);
+    if (e != cudaSuccess) goto fail;
+    body_out = po.conditional.phGraph_out[0];
+    e = cudaGraphConditionalHandleCreate(&h_in, body_out, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) goto fail;
+    e = cudaStreamBeginCaptureToGraph(cs, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) goto fail;
+    k_ref_res<<<gb, 256, 0, cs>>>(f, c.b, c.u, c.r, c.rf, c.uf, c.pf, c.red, c.red_ticket, S, h_out, h_in, outer_total);
+    e = cudaStreamEndCapture(cs, &body_out);
+    if (e != cudaSuccess) goto fail;
+    e = find_sink(body_out, &sink_b);
+    if (e != cudaSuccess) goto fail;
+    pi.type = cudaGraphNodeTypeConditional;
+    pi.conditional.handle = h_in;
+    pi.conditional.type = cudaGraphCondTypeWhile;
+    pi.conditional.size = 1;
+    e = cudaGraphAddNode(&cond_in, body_out, &sink_b, nullptr, 1, &pi);
+    if (e != cudaSuccess) goto fail;
+    body_in = pi.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) goto fail;
+    k_in_spmv<<<gb, 256, 0, cs>>>(f, c.pf, c.qf, c.red, c.red_ticket, S, h_in);
+    k_in_update<<<gb, 256, 0, cs>>>(f, c.uf, c.rf, c.pf, c.qf, c.red, c.red_ticket, S, h_in, it_total);
+    k_in_dir<<<gb, 256, 0, cs>>>(f, c.rf, c.pf, S);
+    e = cudaStreamEndCapture(cs, &body_in);
+    if (e != cudaSuccess) goto fail;
+    e = cudaStreamBeginCaptureToGraph(cs, body_out, &cond_in, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) goto fail;
+    k_ref_add<<<gb, 256, 0, cs>>>(N, c.u, c.uf);
+    e = cudaStreamEndCapture(cs, &body_out);
+    if (e != cudaSuccess) goto fail;
+    e = cudaStreamBeginCaptureToGraph(cs, g, &cond_out, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) goto fail;
+    k_phi_from_u<<<gb, 256, 0, cs>>>(N, c.u, c.gdir, c.phi, S);
+    k_node_E<<<gb, 256, 0, cs>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) goto fail;
+    e = cudaGraphInstantiate(&c.pcg_exec, g, 0);
+    if (e != cudaSuccess) goto fail;
+    c.pcg_graph = g;
+    c.stream = keep;
+    cudaStreamDestroy(cs);
+    return cudaSuccess;
+fail:
+    c.stream = keep;
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+cudaError_t launch_pcg_mixed(Ctx& c) {
+    PcgState h = {};
+    h.tol2 = c.tol * c.tol;
+    h.maxit = c.maxit;
+    h.inner_tol2 = MIXED_INNER_TOL * MIXED_INNER_TOL;
+    h.inner_max = c.maxit;
+    cudaError_t e = cudaMemcpyAsync(c.scal, &h, sizeof(PcgState), cudaMemcpyHostToDevice, c.stream);
+    if (e != cudaSuccess) return e;
+    return cudaGraphLaunch(c.pcg_exec, c.stream);
 }
 
 // ======================================================================================

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "sampling.cuh"
 
 namespace pf {
 
@@ -27,7 +28,6 @@ __constant__ TetTables cTp;
 cudaError_t set_particle_tables(const TetTables& t) { return cudaMemcpyToSymbol(cTp, &t, sizeof(TetTables)); }
 
 constexpr double TWO32 = 4294967296.0;
-constexpr int MAX_TRIES = 32;
 
 // ---- trilinear weights, fixed order: w_l = (wx[a] * wy[b]) * wz[c] ---------------
 struct Wts {
@@ -305,16 +305,6 @@ __global__ void k_push_movers(Launch L) {
 // ------------------------------------------------------------------------------------
 // injection (reading of Sec. 3.1.3 / Sec. 5.2.2; see inject_one)
 // ------------------------------------------------------------------------------------
-struct InjArgs {
-    const InjectDev* st;
-    int nst;
-    int* count;            // per stream, this step
-    long long* idbase;     // per stream
-    double* carry;         // per stream
-    long long* next_id;    // per species
-    long long step;
-};
-
 // count = floor(carry + rate) per stream, ids consecutive per species in face order
 __global__ void k_inject_counts(InjArgs a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -331,28 +321,6 @@ __global__ void k_inject_counts(InjArgs a) {
     }
 }
 
-PF_D void box_muller(double u1, double u2, double& z0, double& z1) {
-    double r = sqrt(-2.0 * log(u1));
-    double t = (2.0 * 3.141592653589793) * u2;
-    z0 = r * cos(t);
-    z1 = r * sin(t);
-}
-
-// flux-weighted normal speed (units of vth): proposal N(mu, 1), mu the mode of
-// v exp(-(v - s)^2 / 2), acceptance (v/mu) exp(1 - v/mu); bounded tries
-PF_D bool flux_normal(unsigned long long m, unsigned long long seed, unsigned long long key1, double s, double& v) {
-    double mu = 0.5 * (s + sqrt(s * s + 4.0));
-    for (int t = 0; t < MAX_TRIES; ++t) {
-        U64x4 r = philox4x64(m, 2 + t, 0, 0, seed, key1);
-        double z, z1;
-        box_muller(u01(r.v[0]), u01(r.v[1]), z, z1);
-        double vv = mu + z;
-        double ratio = vv / mu;
-        if (vv > 0.0 && u01(r.v[2]) < ratio * exp(1.0 - ratio)) { v = vv; return true; }
-    }
-    return false;
-}
-
 __global__ void k_inject(Launch L, InjArgs a) {
     __shared__ unsigned long long sctr[NCTR];
     const int q = blockIdx.y;
@@ -363,11 +331,6 @@ __global__ void k_inject(Launch L, InjArgs a) {
     __syncthreads();
     const int cnt = a.count[q];
     const long long idb = a.idbase[q];
-    const int f = d.face, ax = f >> 1;
-    const double sgn = (f & 1) ? -1.0 : 1.0;
-    const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-    const double nax[3] = {(double)L.mesh.nx, (double)L.mesh.ny, (double)L.mesh.nz};
-    const unsigned long long key1 = stream_key(2, s, f, a.step);
     const bool track = L.track;
     for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
         int mm = base + threadIdx.x;
@@ -375,23 +338,10 @@ __global__ void k_inject(Launch L, InjArgs a) {
         bool rejected = false;
         double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
         if (mm < cnt) {
-            unsigned long long m = (unsigned long long)mm;
-            U64x4 b0 = philox4x64(m, 0, 0, 0, d.seed, key1);
-            U64x4 b1 = philox4x64(m, 1, 0, 0, d.seed, key1);
-            double vn;
-            bool ok = flux_normal(m, d.seed, key1, sgn * d.drift[ax] / d.vth, vn);
-            double g1, g2;
-            box_muller(u01(b1.v[0]), u01(b1.v[1]), g1, g2);
-            double p0[3];
-            p0[ax] = sgn > 0 ? 0.0 : nax[ax];
-            p0[t1] = u01(b0.v[0]) * nax[t1];
-            p0[t2] = u01(b0.v[1]) * nax[t2];
-            double frac = u01(b0.v[2]);
-            v[ax] = sgn * (d.vth * vn);
-            v[t1] = d.drift[t1] + d.vth * g1;
-            v[t2] = d.drift[t2] + d.vth * g2;
-            double sl = frac * L.dth;
-            for (int c = 0; c < 3; ++c) p[c] = p0[c] + v[c] * sl;
+            InjSample sm = inject_sample(d, mm, a.step, s, L.mesh, L.dth);
+            double p0[3] = {sm.p0[0], sm.p0[1], sm.p0[2]};
+            bool ok = sm.ok;
+            for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
             if (!ok || level_set(L.obj, p0[0], p0[1], p0[2]) < 0.0) {
                 rejected = true;
             } else {

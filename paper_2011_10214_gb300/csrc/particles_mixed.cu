@@ -1,18 +1,657 @@
-// MIXED-precision particle cycle and FP32/FP64-refined PCG (in progress):
-// until these kernels land, contexts created with PIFEPIC_MIXED report
-// cudaErrorNotSupported from every mixed launcher.
+// MIXED-precision particle cycle: the same steps as particles.cu (Sec. 2.1
+// gather / push / scatter, Sec. 3.1.3 and Sec. 5.2.2 injection, absorption and
+// collection) with the state a particle carries cut to 28 bytes: a packed
+// int32 cell (i | j<<11 | k<<22), the FP32 offset inside the cell and the
+// FP32 velocity.  Positions never lose precision far from the origin because
+// the offset is relative to the cell.  Fixed-point deposits stay int64 (exact
+// 2^32 units per particle); the weights are FP32.  Injection samples in FP64
+// (shared sampler) and converts.
+#include <math.h>
+
 #include "internal.h"
+#include "sampling.cuh"
 
 namespace pf {
+
+// kernels defined in particles.cu (bin construction and count clamping do not
+// depend on the particle representation)
+__global__ void k_bin_count(Launch L, PArr a, long long n, int* cnt);
+__global__ void k_bin_caps(int nb, const int* cnt, int* cap, int* cnt_copy);
+__global__ void k_bin_scan(int nb, const int* cap, long long* start, long long* total);
+__global__ void k_clamp_counts(Launch L);
+
+struct ObjF {
+    int kind;
+    float a0, a1, a2, a3, a4, a5;
+};
+
+static ObjF obj_f(const Object& o) {
+    ObjF f;
+    f.kind = o.kind;
+    f.a0 = (float)o.a0; f.a1 = (float)o.a1; f.a2 = (float)o.a2;
+    f.a3 = (float)o.a3; f.a4 = (float)o.a4; f.a5 = (float)o.a5;
+    return f;
+}
+
+PF_D float level_set_f(const ObjF& o, float x, float y, float z) {
+    if (o.kind == 1) {
+        float dx = x - o.a0, dy = y - o.a1, dz = z - o.a2;
+        return (dx * dx + dy * dy + dz * dz) - o.a3;
+    } else if (o.kind == 2) {
+        float dx = x - o.a1, dy = y - o.a2;
+        float r2 = dx * dx + dy * dy;
+        float zs = (r2 < o.a3) ? o.a5 - sqrtf(o.a4 - r2) : o.a0;
+        return z - zs;
+    } else if (o.kind == 3) {
+        return o.a0 * x + o.a1 * y + o.a2 * z - o.a3;
+    }
+    return 1.0f;
+}
+
+PF_D int pack_cell(int i, int j, int k) { return i | (j << 11) | (k << 22); }
+PF_D void unpack_cell(int c, int& i, int& j, int& k) {
+    unsigned u = (unsigned)c;
+    i = (int)(u & 2047u);
+    j = (int)((u >> 11) & 2047u);
+    k = (int)(u >> 22);
+}
+
+struct WF {
+    float w[8];
+};
+PF_D WF weights_f(float fx, float fy, float fz) {
+    WF r;
+    float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
+#pragma unroll
+    for (int l = 0; l < 8; ++l) r.w[l] = (wx[l & 1] * wy[(l >> 1) & 1]) * wz[(l >> 2) & 1];
+    return r;
+}
+
+PF_D void fixed_weights_f(const WF& w, long long W[8]) {
+    long long rest = 1ll << 32;
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        W[l] = __float2ll_rn(w.w[l] * 4294967296.0f);
+        rest -= W[l];
+    }
+    W[7] = rest;
+}
+
+struct EGlobalF {
+    const float4* E;
+    Mesh m;
+    PF_D float4 operator()(int i, int j, int k) const { return E[node_id(m, i, j, k)]; }
+};
+struct ETileF {
+    const float4* T;
+    int x0, y0, z0;
+    PF_D float4 operator()(int i, int j, int k) const { return T[(i - x0) + TILE * ((j - y0) + TILE * (k - z0))]; }
+};
+
+template <class EA>
+PF_D void gather_f(int i, int j, int k, const WF& w, const EA& ea, float& ex, float& ey, float& ez) {
+    ex = 0.f; ey = 0.f; ez = 0.f;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        float4 e = ea(i + (l & 1), j + ((l >> 1) & 1), k + ((l >> 2) & 1));
+        ex += w.w[l] * e.x;
+        ey += w.w[l] * e.y;
+        ez += w.w[l] * e.z;
+    }
+}
+
+// one particle: kick, drift in cell-relative coordinates, cell change,
+// boundary test, object test (codes as in particles.cu)
+enum { ALIVE = 0, ABSORBED = 1, COLLECTED = 2, NONE = 3 };
+
+struct PF32 {
+    int i, j, k;
+    float fx, fy, fz, vx, vy, vz;
+};
+
+PF_D void advance_axis(float& f, int& c) {
+    float s = floorf(f);
+    f -= s;
+    c += (int)s;
+    if (f >= 1.0f) { f = 0.0f; c += 1; }   // -tiny - (-1) rounded up to 1
+}
+
+PF_D int hit_cell_f(const Launch& L, const ObjF& of, float xo, float yo, float zo, float xn, float yn, float zn) {
+    float Lo = level_set_f(of, xo, yo, zo), Ln = level_set_f(of, xn, yn, zn);
+    float t = Lo / (Lo - Ln);
+    float xc = xo + t * (xn - xo), yc = yo + t * (yn - yo), zc = zo + t * (zn - zo);
+    int ci = min(max((int)floorf(xc), 0), L.mesh.nx - 1);
+    int cj = min(max((int)floorf(yc), 0), L.mesh.ny - 1);
+    int ck = min(max((int)floorf(zc), 0), L.mesh.nz - 1);
+    return L.cell_acc[cell_id(L.mesh, ci, cj, ck)];
+}
+
+template <class EA>
+PF_D int push_one(const Launch& L, const ObjF& of, float kf, float dthf, PF32& p, const EA& ea, int& acc) {
+    WF w = weights_f(p.fx, p.fy, p.fz);
+    float ex, ey, ez;
+    gather_f(p.i, p.j, p.k, w, ea, ex, ey, ez);
+    p.vx += kf * ex; p.vy += kf * ey; p.vz += kf * ez;
+    float xo = (float)p.i + p.fx, yo = (float)p.j + p.fy, zo = (float)p.k + p.fz;
+    p.fx += p.vx * dthf; p.fy += p.vy * dthf; p.fz += p.vz * dthf;
+    advance_axis(p.fx, p.i); advance_axis(p.fy, p.j); advance_axis(p.fz, p.k);
+    if (p.i < 0 || p.i >= L.mesh.nx || p.j < 0 || p.j >= L.mesh.ny || p.k < 0 || p.k >= L.mesh.nz) return ABSORBED;
+    float xn = (float)p.i + p.fx, yn = (float)p.j + p.fy, zn = (float)p.k + p.fz;
+    if (level_set_f(of, xn, yn, zn) < 0.0f) {
+        acc = hit_cell_f(L, of, xo, yo, zo, xn, yn, zn);
+        return COLLECTED;
+    }
+    return ALIVE;
+}
+
+PF_D void global_deposit_f(const Launch& L, unsigned long long* W, const PF32& p) {
+    long long Wf[8];
+    fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+        atomicAdd(&W[node_id(L.mesh, p.i + (l & 1), p.j + ((l >> 1) & 1), p.k + ((l >> 2) & 1))],
+                  (unsigned long long)Wf[l]);
+}
+
+PF_D void load_p(const PArrF& a, long long g, PF32& p) {
+    unpack_cell(a.cell[g], p.i, p.j, p.k);
+    p.fx = a.fx[g]; p.fy = a.fy[g]; p.fz = a.fz[g];
+    p.vx = a.vx[g]; p.vy = a.vy[g]; p.vz = a.vz[g];
+}
+PF_D void store_p(const PArrF& a, long long g, const PF32& p, long long id, bool track) {
+    a.cell[g] = pack_cell(p.i, p.j, p.k);
+    a.fx[g] = p.fx; a.fy[g] = p.fy; a.fz[g] = p.fz;
+    a.vx[g] = p.vx; a.vy[g] = p.vy; a.vz[g] = p.vz;
+    if (track) a.id[g] = id;
+}
+
+PF_D void count_event(unsigned long long* sctr, bool ev) {
+    unsigned m = __ballot_sync(0xffffffffu, ev);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(sctr, (unsigned long long)__popc(m));
+}
+
+PF_D long long list_len(const unsigned long long* n, long long cap) {
+    long long v = (long long)*n;
+    return v < cap ? v : cap;
+}
+
+PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
+    return (ci / BLK) + L.nbx * ((cj / BLK) + L.nby * (ck / BLK));
+}
+
+// ------------------------------------------------------------------------------------
+// fused gather + push + boundary + collection + deposit + compaction (one bin per CTA)
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
+                                                     const __grid_constant__ CUtensorMap tmE) {
+    __shared__ alignas(128) float4 Et[TILE_N];
+    __shared__ unsigned long long Wt[TILE_N];
+    __shared__ alignas(8) unsigned long long bar;
+    __shared__ int wcnt[8];
+    __shared__ unsigned long long sctr[NCTR];
+    __shared__ int s_ok;
+    const int s = blockIdx.y;
+    const int b = blockIdx.x;
+    const SpeciesDev& S = L.sp[s];
+    const int n = S.bcount[b];
+    if (n == 0) return;
+    const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
+    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
+    for (int t = tid; t < TILE_N; t += blockDim.x) Wt[t] = 0ull;
+    if (tid < NCTR) sctr[tid] = 0ull;
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(float4));
+        tma_load_4d(Et, &tmE, &bar, 0, x0, y0, z0);
+        bool ok = mbar_wait_bounded(&bar, 0);
+        if (!ok) {
+            atomicOr(L.err, ERR_TMA_TIMEOUT);
+            mbar_wait_bounded(&bar, 0);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const ETileF ea{Et, x0, y0, z0};
+    const long long start = S.bstart[b];
+    const bool track = L.track;
+    const float kf = (float)S.k;
+    int nstay = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        int code = NONE, acc = -1;
+        PF32 p;
+        long long id = 0;
+        if (i < n) {
+            load_p(S.binsF, start + i, p);
+            if (track) id = S.binsF.id[start + i];
+            code = push_one(L, of, kf, dthf, p, ea, acc);
+        }
+        bool stay = false, mover = false;
+        if (code == ALIVE) {
+            stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
+            mover = !stay;
+            if (stay) {
+                long long Wf[8];
+                fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
+                    atomicAdd(&Wt[t], (unsigned long long)Wf[l]);
+                }
+            } else {
+                global_deposit_f(L, S.W, p);
+            }
+        } else if (code == COLLECTED) {
+            if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+        }
+        count_event(&sctr[C_PUSHED], code != NONE);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        unsigned bal = __ballot_sync(0xffffffffu, stay);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) { int v = wcnt[q]; off += (q < wid) ? v : 0; tot += v; }
+        if (stay) store_p(S.binsF, start + nstay + off + __popc(bal & ((1u << lane) - 1)), p, id, track);
+        long long slot = warp_reserve(S.mov_out_n, mover);
+        if (mover) {
+            if (slot < S.mcap) store_p(S.movF_out, slot, p, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+        nstay += tot;
+        __syncthreads();
+    }
+    if (tid == 0) S.bcount[b] = nstay;
+    for (int t = tid; t < TILE_N; t += blockDim.x) {
+        unsigned long long v = Wt[t];
+        if (!v) continue;
+        int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], v);
+    }
+    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
+}
+
+__global__ void k_push_movers_m(Launch L, ObjF of, float dthf) {
+    __shared__ unsigned long long sctr[NCTR];
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const long long n = list_len(S.mov_in_n, S.mcap);
+    const EGlobalF ea{L.Ef, L.mesh};
+    const bool track = L.track;
+    const float kf = (float)S.k;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += stride) {
+        long long i = base + threadIdx.x;
+        int code = NONE, acc = -1;
+        PF32 p;
+        long long id = 0;
+        if (i < n) {
+            load_p(S.movF_in, i, p);
+            if (track) id = S.movF_in.id[i];
+            code = push_one(L, of, kf, dthf, p, ea, acc);
+            if (code == ALIVE) global_deposit_f(L, S.W, p);
+            else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+        }
+        count_event(&sctr[C_PUSHED], code != NONE);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        bool alive = code == ALIVE;
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) store_p(S.movF_out, slot, p, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+// injection: FP64 sampling and tests (as the FP64 path), stored as cell + FP32 offset
+PF_D bool outside_d(const Mesh& m, double x, double y, double z) {
+    return (x < 0.0) | (x >= (double)m.nx) | (y < 0.0) | (y >= (double)m.ny) | (z < 0.0) | (z >= (double)m.nz);
+}
+
+__global__ void k_inject_m(Launch L, InjArgs a) {
+    __shared__ unsigned long long sctr[NCTR];
+    const int q = blockIdx.y;
+    const InjectDev d = a.st[q];
+    const int s = d.species;
+    const SpeciesDev& S = L.sp[s];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int cnt = a.count[q];
+    const long long idb = a.idbase[q];
+    const bool track = L.track;
+    for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
+        int mm = base + threadIdx.x;
+        int code = NONE, acc = -1;
+        bool rejected = false;
+        PF32 p;
+        if (mm < cnt) {
+            InjSample sm = inject_sample(d, mm, a.step, s, L.mesh, L.dth);
+            if (!sm.ok || level_set(L.obj, sm.p0[0], sm.p0[1], sm.p0[2]) < 0.0) {
+                rejected = true;
+            } else if (outside_d(L.mesh, sm.p[0], sm.p[1], sm.p[2])) {
+                code = ABSORBED;
+            } else {
+                double fi = floor(sm.p[0]), fj = floor(sm.p[1]), fk = floor(sm.p[2]);
+                p.i = (int)fi; p.j = (int)fj; p.k = (int)fk;
+                p.fx = (float)(sm.p[0] - fi); p.fy = (float)(sm.p[1] - fj); p.fz = (float)(sm.p[2] - fk);
+                if (p.fx >= 1.0f) p.fx = 0.99999994f;
+                if (p.fy >= 1.0f) p.fy = 0.99999994f;
+                if (p.fz >= 1.0f) p.fz = 0.99999994f;
+                p.vx = (float)sm.v[0]; p.vy = (float)sm.v[1]; p.vz = (float)sm.v[2];
+                if (level_set(L.obj, sm.p[0], sm.p[1], sm.p[2]) < 0.0) {
+                    ObjF of = {L.obj.kind, (float)L.obj.a0, (float)L.obj.a1, (float)L.obj.a2, (float)L.obj.a3,
+                               (float)L.obj.a4, (float)L.obj.a5};
+                    acc = hit_cell_f(L, of, (float)sm.p0[0], (float)sm.p0[1], (float)sm.p0[2], (float)sm.p[0],
+                                     (float)sm.p[1], (float)sm.p[2]);
+                    code = COLLECTED;
+                    if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+                } else {
+                    code = ALIVE;
+                    global_deposit_f(L, S.W, p);
+                }
+            }
+        }
+        count_event(&sctr[C_INJECTED], code != NONE);
+        count_event(&sctr[C_REJECTED], rejected);
+        count_event(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        bool alive = code == ALIVE;
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) store_p(S.movF_out, slot, p, idb + mm, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+__global__ void k_rebin_m(Launch L) {
+    const int s = blockIdx.y;
+    const SpeciesDev& S = L.sp[s];
+    const long long n = list_len(S.mov_out_n, S.mcap);
+    const bool track = L.track;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += stride) {
+        long long i = base + threadIdx.x;
+        bool spill = false;
+        PF32 p;
+        long long id = 0;
+        if (i < n) {
+            load_p(S.movF_out, i, p);
+            if (track) id = S.movF_out.id[i];
+            int b = block_of(L, p.i, p.j, p.k);
+            int slot = atomicAdd(&S.bcount[b], 1);
+            if (slot < S.bcap[b]) store_p(S.binsF, S.bstart[b] + slot, p, id, track);
+            else spill = true;
+        }
+        long long slot = warp_reserve(S.mov_in_n, spill);
+        if (spill) {
+            if (slot < S.mcap) store_p(S.movF_in, slot, p, id, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+}
+
+// FP64 flat list -> MIXED bins (load, explicit particles, rebuild)
+__global__ void k_bin_scatter_m(Launch L, PArr a, long long n, const long long* start, int* fill, PArrF bins,
+                                bool track) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double fi = floor(a.x[i]), fj = floor(a.y[i]), fk = floor(a.z[i]);
+    PF32 p;
+    p.i = (int)fi; p.j = (int)fj; p.k = (int)fk;
+    p.fx = (float)(a.x[i] - fi); p.fy = (float)(a.y[i] - fj); p.fz = (float)(a.z[i] - fk);
+    if (p.fx >= 1.0f) p.fx = 0.99999994f;
+    if (p.fy >= 1.0f) p.fy = 0.99999994f;
+    if (p.fz >= 1.0f) p.fz = 0.99999994f;
+    p.vx = (float)a.vx[i]; p.vy = (float)a.vy[i]; p.vz = (float)a.vz[i];
+    int b = block_of(L, p.i, p.j, p.k);
+    int slot = atomicAdd(&fill[b], 1);
+    store_p(bins, start[b] + slot, p, track ? a.id[i] : 0, track);
+}
+
+PF_D void put_d(const PArr& o, long long g, const PF32& p, long long id, bool track) {
+    o.x[g] = (double)p.i + (double)p.fx; o.y[g] = (double)p.j + (double)p.fy; o.z[g] = (double)p.k + (double)p.fz;
+    o.vx[g] = p.vx; o.vy[g] = p.vy; o.vz[g] = p.vz;
+    if (track) o.id[g] = id;
+}
+
+__global__ void k_flatten_m(Launch L, int s, PArr out, unsigned long long* nout) {
+    const SpeciesDev& S = L.sp[s];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0) base = n ? atomicAdd(nout, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    long long st = S.bstart[b];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        PF32 p;
+        load_p(S.binsF, st + i, p);
+        put_d(out, (long long)base + i, p, L.track ? S.binsF.id[st + i] : 0, true);
+    }
+}
+
+__global__ void k_flatten_list_m(Launch L, int s, PArr out, unsigned long long* nout) {
+    const SpeciesDev& S = L.sp[s];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    __shared__ unsigned long long base;
+    if (threadIdx.x == 0) base = n ? atomicAdd(nout, (unsigned long long)n) : 0ull;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        PF32 p;
+        load_p(S.movF_in, i, p);
+        put_d(out, (long long)base + i, p, L.track ? S.movF_in.id[i] : 0, true);
+    }
+}
+
+__global__ void k_deposit_bins_m(Launch L) {
+    const SpeciesDev& S = L.sp[blockIdx.y];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    long long st = S.bstart[b];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        PF32 p;
+        load_p(S.binsF, st + i, p);
+        global_deposit_f(L, S.W, p);
+    }
+}
+__global__ void k_deposit_list_m(Launch L) {
+    const SpeciesDev& S = L.sp[blockIdx.y];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        PF32 p;
+        load_p(S.movF_in, i, p);
+        global_deposit_f(L, S.W, p);
+    }
+}
+
+__global__ void k_half_kick_bins_m(Launch L) {
+    const SpeciesDev& S = L.sp[blockIdx.y];
+    int b = blockIdx.x;
+    int n = S.bcount[b];
+    long long st = S.bstart[b];
+    const EGlobalF ea{L.Ef, L.mesh};
+    const float kh = (float)S.khalf;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        PF32 p;
+        load_p(S.binsF, st + i, p);
+        float ex, ey, ez;
+        gather_f(p.i, p.j, p.k, weights_f(p.fx, p.fy, p.fz), ea, ex, ey, ez);
+        S.binsF.vx[st + i] = p.vx - kh * ex;
+        S.binsF.vy[st + i] = p.vy - kh * ey;
+        S.binsF.vz[st + i] = p.vz - kh * ez;
+    }
+}
+__global__ void k_half_kick_list_m(Launch L) {
+    const SpeciesDev& S = L.sp[blockIdx.y];
+    long long n = list_len(S.mov_in_n, S.mcap);
+    const EGlobalF ea{L.Ef, L.mesh};
+    const float kh = (float)S.khalf;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        PF32 p;
+        load_p(S.movF_in, i, p);
+        float ex, ey, ez;
+        gather_f(p.i, p.j, p.k, weights_f(p.fx, p.fy, p.fz), ea, ex, ey, ez);
+        S.movF_in.vx[i] = p.vx - kh * ex;
+        S.movF_in.vy[i] = p.vy - kh * ey;
+        S.movF_in.vz[i] = p.vz - kh * ez;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------
+static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+
 cudaError_t set_mixed_tables(const TetTables&) { return cudaSuccess; }
-cudaError_t build_pcg_graph_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_pcg_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_flatten_mixed_to_f64(Ctx&, int, PArr, unsigned long long*) { return cudaErrorNotSupported; }
-cudaError_t launch_build_bins_mixed(Ctx&, int, PArr, long long, bool) { return cudaErrorNotSupported; }
-cudaError_t launch_push_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_movers_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_inject_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_rebin_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_deposit_all_mixed(Ctx&) { return cudaErrorNotSupported; }
-cudaError_t launch_half_kick_mixed(Ctx&) { return cudaErrorNotSupported; }
+
+static InjArgs inj_args_m(Ctx& c) {
+    InjArgs a;
+    a.st = c.inj_dev; a.nst = (int)c.inj.size();
+    a.count = c.inj_count; a.idbase = c.inj_base; a.carry = c.inj_carry; a.next_id = c.next_id;
+    a.step = c.step_no;
+    return a;
+}
+
+__global__ void k_inject_counts(InjArgs a);   // particles.cu
+
+cudaError_t launch_push_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
+    cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
+    k_push_bins_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_movers_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    k_push_movers_m<<<dim3(152, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_mixed(Ctx& c) {
+    if (c.inj.empty()) return cudaSuccess;
+    Launch L = make_launch(c);
+    InjArgs a = inj_args_m(c);
+    k_inject_counts<<<1, 32, 0, c.stream>>>(a);
+    int maxc = 1;
+    for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
+    unsigned gx = (unsigned)((maxc + 255) / 256);
+    if (gx > 1024) gx = 1024;
+    k_inject_m<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebin_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n, 0, sizeof(unsigned long long), c.stream);
+    k_rebin_m<<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
+    k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_all_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * c.mesh.nnodes, c.stream);
+    if (ns == 0) return cudaGetLastError();
+    k_deposit_bins_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    k_deposit_list_m<<<dim3(64, ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half_kick_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
+    if (ns == 0) return cudaSuccess;
+    k_half_kick_bins_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    k_half_kick_list_m<<<dim3(64, ns), 256, 0, c.stream>>>(L);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flatten_mixed_to_f64(Ctx& c, int s, PArr flat, unsigned long long* nflat) {
+    Launch L = make_launch(c);
+    if (c.sp[s].bcount) k_flatten_m<<<c.nblocks, 256, 0, c.stream>>>(L, s, flat, nflat);
+    if (c.sp[s].mov_n) k_flatten_list_m<<<1, 256, 0, c.stream>>>(L, s, flat, nflat);
+    return cudaGetLastError();
+}
+
+void free_parrf(PArrF& a) {
+    cudaFree(a.cell); cudaFree(a.fx); cudaFree(a.fy); cudaFree(a.fz); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz);
+    cudaFree(a.id);
+    a = PArrF{};
+}
+
+cudaError_t alloc_parrf(PArrF& a, long long n, bool id) {
+    free_parrf(a);
+    long long m = n > 0 ? n : 1;
+    cudaError_t e = cudaMalloc(&a.cell, sizeof(int) * m);
+    float** f[6] = {&a.fx, &a.fy, &a.fz, &a.vx, &a.vy, &a.vz};
+    for (auto p : f)
+        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * m);
+    if (e == cudaSuccess && id) e = cudaMalloc(&a.id, sizeof(long long) * m);
+    return e;
+}
+
+// (re)build MIXED bins of species s from a flat FP64 list of n particles
+cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool) {
+    Species& q = c.sp[s];
+    cudaError_t e;
+    int* cnt = nullptr;
+    long long* tot = nullptr;
+    long long total = 0;
+    e = cudaMalloc(&cnt, sizeof(int) * c.nblocks);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&tot, sizeof(long long));
+    if (e != cudaSuccess) { cudaFree(cnt); return e; }
+    cudaMemsetAsync(cnt, 0, sizeof(int) * c.nblocks, c.stream);
+    Launch L = make_launch(c);
+    if (n > 0) k_bin_count<<<nb(n), 256, 0, c.stream>>>(L, flat, n, cnt);
+    if (!q.bcap) {
+        cudaMalloc(&q.bcap, sizeof(int) * c.nblocks);
+        cudaMalloc(&q.bcount, sizeof(int) * c.nblocks);
+        cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
+    }
+    k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
+    k_bin_scan<<<1, 32, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
+    e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+    if (total > q.cap) {
+        e = alloc_parrf(q.binsF, total, c.track != 0);
+        if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+        q.cap = total;
+    }
+    L = make_launch(c);
+    if (n > 0) k_bin_scatter_m<<<nb(n), 256, 0, c.stream>>>(L, flat, n, q.bstart, q.bcount, q.binsF, c.track != 0);
+    cudaMemsetAsync(q.mov_n, 0, 2 * sizeof(unsigned long long), c.stream);
+    e = cudaStreamSynchronize(c.stream);
+    cudaFree(cnt);
+    cudaFree(tot);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 }  // namespace pf

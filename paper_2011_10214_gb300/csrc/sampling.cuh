@@ -1,0 +1,78 @@
+// Injection sampling shared by the FP64 and MIXED particle kernels
+// (reading of Sec. 3.1.3 / Sec. 5.2.2; the paper gives no sampler):
+// uniform position on the face, flux-weighted normal speed by rejection,
+// Gaussian tangential speeds plus drift, then a uniform fraction of one step.
+#pragma once
+#include "internal.h"
+
+namespace pf {
+
+constexpr int MAX_TRIES = 32;
+
+struct InjArgs {
+    const InjectDev* st;
+    int nst;
+    int* count;            // per stream, this step
+    long long* idbase;     // per stream
+    double* carry;         // per stream
+    long long* next_id;    // per species
+    long long step;
+};
+
+PF_D void box_muller(double u1, double u2, double& z0, double& z1) {
+    double r = sqrt(-2.0 * log(u1));
+    double t = (2.0 * 3.141592653589793) * u2;
+    z0 = r * cos(t);
+    z1 = r * sin(t);
+}
+
+// flux-weighted normal speed (units of vth): proposal N(mu, 1), mu the mode of
+// v exp(-(v - s)^2 / 2), acceptance (v/mu) exp(1 - v/mu); bounded tries
+PF_D bool flux_normal(unsigned long long m, unsigned long long seed, unsigned long long key1, double s, double& v) {
+    double mu = 0.5 * (s + sqrt(s * s + 4.0));
+    for (int t = 0; t < MAX_TRIES; ++t) {
+        U64x4 r = philox4x64(m, 2 + t, 0, 0, seed, key1);
+        double z, z1;
+        box_muller(u01(r.v[0]), u01(r.v[1]), z, z1);
+        double vv = mu + z;
+        double ratio = vv / mu;
+        if (vv > 0.0 && u01(r.v[2]) < ratio * exp(1.0 - ratio)) { v = vv; return true; }
+    }
+    return false;
+}
+
+struct InjSample {
+    double p0[3], p[3], v[3];
+    bool ok;
+};
+
+// particle mm of stream d in step `step`: start point p0 on the face, velocity
+// v, position p after the partial first step; ok = false if every rejection
+// try failed.  Counter (mm, block, 0, 0), key (seed, purpose 2 | species | face | step).
+PF_D InjSample inject_sample(const InjectDev& d, int mm, long long step, int s, const Mesh& mesh, double dth) {
+    const int f = d.face, ax = f >> 1;
+    const double sgn = (f & 1) ? -1.0 : 1.0;
+    const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+    const double nax[3] = {(double)mesh.nx, (double)mesh.ny, (double)mesh.nz};
+    const unsigned long long key1 = stream_key(2, s, f, step);
+    unsigned long long m = (unsigned long long)mm;
+    U64x4 b0 = philox4x64(m, 0, 0, 0, d.seed, key1);
+    U64x4 b1 = philox4x64(m, 1, 0, 0, d.seed, key1);
+    InjSample r;
+    double vn = 0.0;
+    r.ok = flux_normal(m, d.seed, key1, sgn * d.drift[ax] / d.vth, vn);
+    double g1, g2;
+    box_muller(u01(b1.v[0]), u01(b1.v[1]), g1, g2);
+    r.p0[ax] = sgn > 0 ? 0.0 : nax[ax];
+    r.p0[t1] = u01(b0.v[0]) * nax[t1];
+    r.p0[t2] = u01(b0.v[1]) * nax[t2];
+    double frac = u01(b0.v[2]);
+    r.v[ax] = sgn * (d.vth * vn);
+    r.v[t1] = d.drift[t1] + d.vth * g1;
+    r.v[t2] = d.drift[t2] + d.vth * g2;
+    double sl = frac * dth;
+    for (int c = 0; c < 3; ++c) r.p[c] = r.p0[c] + r.v[c] * sl;
+    return r;
+}
+
+}  // namespace pf

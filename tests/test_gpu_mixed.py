@@ -1,0 +1,89 @@
+"""MIXED mode (FP32 push with int32 cell + FP32 offset; FP32 PCG inside FP64
+refinement) against the FP64 oracle.
+
+Bar (FP32 modes): positions and velocities within 1e-4 relative per step
+(10 steps, frozen field), potential within 1e-4 relative at the paper's
+tolerance and within 1e-8 at tol 1e-12 (the refinement residual is FP64).
+Cell-index and absorb/collect mismatches are reported as rates and must stay
+rare; fixed-point charge is still exact in total (2^32 units per particle)."""
+import numpy as np
+import pytest
+
+from paper_2011_10214_gb300 import workloads as wl
+from tests.pairs import CASES, add_species_both, by_id, explicit_particles, make_pair
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+TOL32 = 1e-4
+
+
+@pytest.mark.parametrize("case,vth,npart", [("sphere16", 1.0, 30000), ("ragged", 3.0, 20000),
+                                            ("crater", 2.0, 40000)])
+def test_mixed_frozen_field_ten_steps(case, vth, npart):
+    gpu, orc = make_pair(case, dt=0.2, precision=MIXED)
+    E = wl.random_node_field(orc.mesh.nnodes, 3, scale=0.7)
+    for s, (q, m) in enumerate(((-1.0, 1.0), (1.0, 25.0))):
+        add_species_both(gpu, orc, q, m, 0.01)
+        explicit_particles(gpu, orc, s, npart, 100 + s, vth / (1 + 4 * s))
+    gpu.set_external_E(E)
+    orc.set_external_E(E)
+    for _ in range(10):
+        gpu.step(1)
+        orc.step()
+    for s in range(2):
+        g, o = by_id(gpu.particles(s)), by_id(orc.P[s])
+        common, gi, oi = np.intersect1d(g["id"], o["id"], return_indices=True)
+        n = len(o["id"])
+        mismatch = (len(g["id"]) - len(common)) + (n - len(common))
+        assert mismatch <= max(2, 1e-3 * n), f"absorb/collect mismatch {mismatch} of {n}"
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            d = np.abs(g[k][gi] - o[k][oi]) / np.maximum(np.abs(o[k][oi]), 1.0)
+            assert d.max() <= TOL32, (k, d.max())
+        cell_rate = np.mean(np.any([np.floor(g[k][gi]) != np.floor(o[k][oi]) for k in ("x", "y", "z")], axis=0))
+        assert cell_rate <= 1e-3, cell_rate
+        W = gpu.node_charge(s)
+        assert W.sum() == 2 ** 32 * len(g["id"])
+        assert np.abs(W - orc.W[s]).max() <= TOL32 * 2 ** 32 * 8
+    gpu.close()
+
+
+@pytest.mark.parametrize("case", ["sphere16", "crater"])
+def test_mixed_field_solve_reaches_fp64_accuracy(case):
+    gpu, orc = make_pair(case, precision=MIXED)
+    fs = orc.fs
+    add_species_both(gpu, orc, -1.0, 1.0, 0.01)
+    explicit_particles(gpu, orc, 0, 5000, 7, 1.0)
+    gpu.solve()
+    orc.solve()
+    rel = np.abs(gpu.potential() - orc.phi).max() / np.abs(orc.phi).max()
+    assert rel <= 1e-8, rel
+    E_rel = np.abs(gpu.node_E() - orc.E).max() / np.abs(orc.E).max()
+    assert E_rel <= 1e-8, E_rel
+    gpu.close()
+
+
+def test_mixed_pic_steps_track_oracle():
+    from paper_2011_10214_gb300 import capi
+    from oracle.geometry import Mesh, Sphere
+    from oracle.pic import Simulation as OracleSim
+    cfg = wl.SPHERE16
+    gpu = capi.from_config(cfg, precision=MIXED, track_ids=True, pcg_tol=1e-12, pcg_max_iter=5000)
+    m = Mesh(*cfg["n"], cfg["h"])
+    ob = cfg["object"]
+    orc = OracleSim(m, Sphere(m, ob["center"], ob["radius"], ob["eps_in"], ob["eps_out"]), cfg["face_bc"], cfg["dt"],
+                    tol=1e-12, maxit=5000)
+    for s, sp in enumerate(cfg["species"]):
+        orc.add_species(sp["q"], sp["m"], wl.macro_weight(cfg, sp))
+        orc.load_maxwellian(s, sp["ppc"], sp["vth"], sp["drift"], cfg["seed"])
+        orc.set_injection(s, cfg["inject_faces"], sp["density"], sp["vth"], sp["drift"], cfg["seed"])
+    gpu.solve(); orc.solve()
+    gpu.leapfrog_init(); orc.leapfrog_init()
+    for _ in range(5):
+        sg, so = gpu.step(1), orc.step()
+        assert sg["pcg_converged"] == 1
+        for s in range(2):
+            assert sg["injected"][s] == so["injected"][s]
+        rel = np.abs(gpu.potential() - orc.phi).max() / np.abs(orc.phi).max()
+        assert rel <= TOL32, rel
+    gpu.close()
