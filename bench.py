@@ -101,6 +101,69 @@ def cfg_desc(cfg, precision, extra=None):
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
+FP64_FLOPS_PER_PARTICLE_STEP = 80     # trilinear weights 19, gather 45, kick and drift 12, cell test 4
+NSM, DFMA_PER_CLK_SM = 152, 2          # GB300: 2 FP64 FMA per SM per clock
+
+
+def measure(cfg, precision, steps, warmup, stream, dist, local):
+    """Set up one instance, warm up, time `steps` PIC steps with CUDA events."""
+    import torch
+    from paper_2011_10214_gb300 import capi
+    prec = capi.MIXED if precision == "mixed" else capi.FP64
+    sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream)
+    sim.solve()
+    sim.leapfrog_init()
+    if warmup > 0:
+        sim.step(warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    barrier()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = sim.step(steps)
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    pushed = sum(st["pushed"])
+    t = torch.tensor([ms / 1e3, float(pushed)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        t = torch.stack([tmax[0], t[1]])
+    return sim, st, float(t[0]), float(t[1]), pushed, ck
+
+
+def roofline(precision, st, steps, ck):
+    """Dominant kernel: the fused gather/push/collect/deposit launch (phase 0)."""
+    push_ms = st["phase_ms"][0] / steps
+    per_launch = sum(st["pushed"]) / steps
+    peaks, src = _peaks()
+    if precision == "mixed":
+        alg = per_launch * BYTES_PER_PARTICLE_STEP["mixed"]
+        ach = alg / (push_ms / 1e3) / 1e9
+        return {"kernel": "k_push_bins_m (fused gather+push+collect+deposit, FP32 state)", "bound": "hbm",
+                "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
+                "alg_bytes_per_launch": alg, "avg_launch_ms": push_ms}
+    flops = per_launch * FP64_FLOPS_PER_PARTICLE_STEP
+    ach = flops / (push_ms / 1e3) / 1e9
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = NSM * DFMA_PER_CLK_SM * 2 * mhz / 1e3
+    return {"kernel": "k_push_bins (FP64, no FMA contraction)", "bound": "alu", "achieved": round(ach, 1),
+            "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+            "alg_flops_per_launch": flops, "avg_launch_ms": push_ms,
+            "hbm_view": {"achieved_gbs": round(per_launch * 96 / (push_ms / 1e3) / 1e9, 1),
+                         "peak_gbs": peaks["hbm_gbs"]}}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -115,48 +178,12 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     cfg = workload(args.workload)
-    prec = capi.MIXED if args.precision == "mixed" else capi.FP64
     stream = torch.cuda.Stream()
-    sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream)
-    sim.solve()
-    sim.leapfrog_init()
-    if args.warmup > 0:
-        sim.step(args.warmup)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-
-    barrier()
-    clocks = Clocks(local)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    st = sim.step(args.steps)
-    ev1.record(stream)
-    barrier()
-    ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    pushed = sum(st["pushed"])
-    t = torch.tensor([ms / 1e3, float(pushed)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tmax = t.clone(); dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        t = torch.stack([tmax[0], t[1]])
-    secs, total = float(t[0]), float(t[1])
+    main = args.precision
+    other = "fp64" if main == "mixed" else "mixed"
+    sim, st, secs, total, pushed, ck = measure(cfg, main, args.steps, args.warmup, stream, dist, local)
     value = total / secs
-
-    # dominant kernel: the fused gather/push/collect/deposit launch (phase 0)
-    push_ms = st["phase_ms"][0] / args.steps
-    per_launch_particles = pushed / args.steps
-    bpp = BYTES_PER_PARTICLE_STEP[args.precision]
-    alg_bytes = per_launch_particles * bpp
-    peaks, src = _peaks()
-    achieved = alg_bytes / (push_ms / 1e3) / 1e9
-    roof = {"kernel": "k_push_bins (fused gather+push+collect+deposit)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-            "peak_source": src, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": push_ms}
+    roof = roofline(main, st, args.steps, ck)
 
     # end to end through the C ABI from host buffers: the initial particle state
     # is copied host -> device (pinned) inside the timed region, and every step
@@ -164,6 +191,7 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         state = [sim.particles(s) for s in range(len(cfg["species"]))]
+        prec = capi.MIXED if main == "mixed" else capi.FP64
         sim2 = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream, load=False)
         pinned = []
         for P in state:
@@ -171,7 +199,9 @@ def run_gpu(args):
                            for k in ("x", "y", "z", "vx", "vy", "vz")})
         nn = sim2.sizes()["nnodes"]
         phi_host = torch.empty(nn, dtype=torch.float64).pin_memory().numpy()
-        barrier()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         for s, P in enumerate(pinned):
             sim2.load_particles(s, P["x"], P["y"], P["z"], P["vx"], P["vy"], P["vz"])
@@ -181,7 +211,7 @@ def run_gpu(args):
             st2 = sim2.step(1)
             pushed2 += sum(st2["pushed"])
             capi.lib.pifepic_get_potential(sim2._c, phi_host.ctypes.data, capi.HOST)
-        barrier()
+        torch.cuda.synchronize()
         t1 = time.perf_counter()
         h2d = sum(P[k].nbytes for P in pinned for k in P)
         e2e = {"value": pushed2 / (t1 - t0), "unit": "particle-steps/s",
@@ -189,28 +219,41 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(phi_host.nbytes + 512),
                "note": "initial particle state h2d (amortised over the steps) + per-step phi and stats d2h"}
         sim2.close()
+    sim.close()
+
+    # the other precision on the same workload, for the FP32-refined vs plain FP64 comparison
+    alt = None
+    if not args.no_compare:
+        sim_b, st_b, secs_b, total_b, _, ck_b = measure(cfg, other, args.steps, args.warmup, stream, dist, local)
+        alt = {"precision": other, "value": total_b / secs_b, "ms_per_step": secs_b * 1e3 / args.steps,
+               "roofline": roofline(other, st_b, args.steps, ck_b),
+               "pcg_iters_per_step": st_b["pcg_iters_total"] / args.steps,
+               "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st_b["phase_ms"]) if v}}
+        sim_b.close()
 
     out = {
         "metric": "particle-steps/s incl. IFE solve", "value": value, "unit": "particle-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if main == "fp64" else "f32+f64",
         "data": "synthetic (seeded Philox load and injection)",
-        "config": cfg_desc(cfg, args.precision, {"particles": int(per_launch_particles),
-                                                  "parallelism": f"replicas x{world}"}),
+        "config": cfg_desc(cfg, main, {"particles": int(pushed / args.steps),
+                                       "parallelism": f"replicas x{world}"}),
         "roofline": roof, "clocks": ck, "e2e": e2e,
         "gpu_launches": int(st["kernel_launches"]),
         "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
-        "phase_ms_per_step": {k: v / args.steps for k, v in zip(("push", "movers", "inject", "rebin", "rhs", "solve",
-                                                                  "node_E", "other"), st["phase_ms"]) if v},
+        "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st["phase_ms"]) if v},
+        "compare": alt,
     }
-    sim.close()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+PHASES = ("push", "movers", "inject", "rebin", "rhs", "solve", "node_E", "other")
 
 
 # ---------------------------------------------------------------------------------
@@ -305,10 +348,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="sphere64", choices=["sphere64", "sphere32", "sphere16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")
     ap.add_argument("--as-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -23,6 +23,7 @@ UNITS = [
     ("particles.cu", ["--fmad=false"]),
     ("particles_mixed.cu", []),
     ("field.cu", []),
+    ("pcg_coop.cu", []),
     ("capi.cu", ["--fmad=false"]),
 ]
 

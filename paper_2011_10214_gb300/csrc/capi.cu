@@ -206,6 +206,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.ibase, sizeof(int) * C);
     ALLOC(c.cell_acc, sizeof(int) * C);
     ALLOC(c.red, sizeof(double) * 4 * (N / 128 + 1024));
+    ALLOC(c.coop_partial, sizeof(double) * 8 * 2048);
     ALLOC(c.scal, sizeof(double) * 64);
     ALLOC(c.red_ticket, sizeof(unsigned) * 4);
     ALLOC(c.err_word, sizeof(int));
@@ -240,7 +241,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     void* ptrs[] = {c.Lnode, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
-                    c.patch_coef, c.patch_coeff, c.red, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,
+                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
     for (auto& s : c.sp) {
@@ -679,9 +680,9 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     cudaError_t e = read_pcg_state(c);
     if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "pcg state: %s", cudaGetErrorString(e));
     s.pcg_iters_total = iters_total(c) - it0;
-    // solve graph: fixed kernels + 3 per PCG iteration (+ 2 per refinement step in MIXED mode)
-    s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c) + 3 * s.pcg_iters_total +
-                        2 * (outer_total(c) - ot0);
+    // host-launched kernels + the solve graph's kernels (the PCG is one persistent launch)
+    s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c);
+    (void)ot0;
     s.pcg_iters = c.last_iters;
     s.pcg_relres = c.last_relres;
     s.pcg_converged = c.last_conv;
@@ -698,6 +699,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     c.stats = s;
     if (st) *st = s;
     if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
+    if (herr & ERR_BARRIER_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a grid barrier of the PCG solve timed out");
     for (size_t q = 0; q < c.sp.size(); ++q)
         if (s.dropped[q]) FAIL(PIFEPIC_ENOMEM, "species %zu: %lld particles dropped (mover list full)", q,
                                (long long)s.dropped[q]);

@@ -1,0 +1,168 @@
+// Shared by the field-solve translation units: PCG scalar state, the operator
+// arguments, the matrix-free row of the IFE operator (regular 7/19-point rows of
+// the 5-tet P1 stencil, explicit 19-slot rows where a node touches an interface
+// tet) and deterministic block / grid reductions.
+#pragma once
+#include "internal.h"
+
+namespace pf {
+
+struct PcgState {
+    double bb, rz, rr, pq, alpha, beta, tol2, relres;
+    int it, maxit, done, converged;
+    // mixed mode: FP32 inner PCG inside FP64 refinement
+    double rr64, inner_tol2, inner_bb;
+    int inner_it, outer_it, inner_max, done_in;
+};
+
+struct FieldArgs {
+    Mesh m;
+    Object o;
+    const int* ntype;
+    const double* coef;       // patch rows [npatch][19]
+    const float* coeff;
+    const double* invdiag;
+    const float* invdiagf;
+};
+
+static __device__ __forceinline__ void loff(int l, int& a, int& b, int& c) {
+    a = l & 1; b = (l >> 1) & 1; c = (l >> 2) & 1;
+}
+
+// load of a vector entry; CG = true reads through L2 only (bypassing L1), as a
+// persistent kernel must for entries other blocks wrote since its last barrier
+template <bool CG, typename T>
+static __device__ __forceinline__ T ldx(const T* x, long long i) {
+    if constexpr (CG) return __ldcg(x + i);
+    else return x[i];
+}
+
+// y_n = (A x)_n for the IFE operator; Dirichlet rows give 0 (x is 0 there)
+template <typename T, bool CG = false>
+static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, int i, int j, int k, const T* x,
+                                              const T* coef) {
+    const Mesh& m = f.m;
+    int ty = f.ntype[n];
+    if (ty == -3) return (T)0;
+    const long long sx = 1, sy = m.NX, sz = (long long)m.NX * m.NY;
+    bool xm = i > 0, xp = i < m.nx, ym = j > 0, yp = j < m.ny, zm = k > 0, zp = k < m.nz;
+    if (ty >= 0) {
+        const T* c = coef + (long long)ty * 19;
+        T y = c[0] * ldx<CG>(x, n);
+        if (xm) y += c[1] * ldx<CG>(x, n - sx);
+        if (xp) y += c[2] * ldx<CG>(x, n + sx);
+        if (ym) y += c[3] * ldx<CG>(x, n - sy);
+        if (yp) y += c[4] * ldx<CG>(x, n + sy);
+        if (zm) y += c[5] * ldx<CG>(x, n - sz);
+        if (zp) y += c[6] * ldx<CG>(x, n + sz);
+        if ((i + j + k) & 1) return y;
+        if (xm && ym) y += c[7] * ldx<CG>(x, n - sx - sy);
+        if (xp && ym) y += c[8] * ldx<CG>(x, n + sx - sy);
+        if (xm && yp) y += c[9] * ldx<CG>(x, n - sx + sy);
+        if (xp && yp) y += c[10] * ldx<CG>(x, n + sx + sy);
+        if (xm && zm) y += c[11] * ldx<CG>(x, n - sx - sz);
+        if (xp && zm) y += c[12] * ldx<CG>(x, n + sx - sz);
+        if (xm && zp) y += c[13] * ldx<CG>(x, n - sx + sz);
+        if (xp && zp) y += c[14] * ldx<CG>(x, n + sx + sz);
+        if (ym && zm) y += c[15] * ldx<CG>(x, n - sy - sz);
+        if (yp && zm) y += c[16] * ldx<CG>(x, n + sy - sz);
+        if (ym && zp) y += c[17] * ldx<CG>(x, n - sy + sz);
+        if (yp && zp) y += c[18] * ldx<CG>(x, n + sy + sz);
+        return y;
+    }
+    // regular row: assembled P1 stencil of the 5-tet split with eps of the region;
+    // each coefficient = (cubes sharing the edge) x (per-cube element integral)
+    T eps = (T)(ty == -2 ? f.o.eps_minus : f.o.eps_plus);
+    T h = (T)m.h;
+    int cx = (int)xm + (int)xp, cy = (int)ym + (int)yp, cz = (int)zm + (int)zp;
+    bool odd = (i + j + k) & 1;
+    T y = (T)(cx * cy * cz) * (odd ? (T)0.5 : (T)0.75) * h * ldx<CG>(x, n);
+    T ax = (T)0, ay = (T)0, az = (T)0;
+    if (xm) ax += ldx<CG>(x, n - sx);
+    if (xp) ax += ldx<CG>(x, n + sx);
+    if (ym) ay += ldx<CG>(x, n - sy);
+    if (yp) ay += ldx<CG>(x, n + sy);
+    if (zm) az += ldx<CG>(x, n - sz);
+    if (zp) az += ldx<CG>(x, n + sz);
+    T h6 = h / (T)6;
+    y -= h6 * ((T)(cy * cz) * ax + (T)(cx * cz) * ay + (T)(cx * cy) * az);
+    if (!odd) {
+        T dxy = (T)0, dxz = (T)0, dyz = (T)0;
+        if (xm && ym) dxy += ldx<CG>(x, n - sx - sy);
+        if (xp && ym) dxy += ldx<CG>(x, n + sx - sy);
+        if (xm && yp) dxy += ldx<CG>(x, n - sx + sy);
+        if (xp && yp) dxy += ldx<CG>(x, n + sx + sy);
+        if (xm && zm) dxz += ldx<CG>(x, n - sx - sz);
+        if (xp && zm) dxz += ldx<CG>(x, n + sx - sz);
+        if (xm && zp) dxz += ldx<CG>(x, n - sx + sz);
+        if (xp && zp) dxz += ldx<CG>(x, n + sx + sz);
+        if (ym && zm) dyz += ldx<CG>(x, n - sy - sz);
+        if (yp && zm) dyz += ldx<CG>(x, n + sy - sz);
+        if (ym && zp) dyz += ldx<CG>(x, n - sy + sz);
+        if (yp && zp) dyz += ldx<CG>(x, n + sy + sz);
+        T h12 = h / (T)12;
+        y -= h12 * ((T)cz * dxy + (T)cy * dxz + (T)cx * dyz);
+    }
+    return eps * y;
+}
+
+static __device__ __forceinline__ void node_ijk(const Mesh& m, long long n, int& i, int& j, int& k) {
+    i = (int)(n % m.NX);
+    j = (int)((n / m.NX) % m.NY);
+    k = (int)(n / ((long long)m.NX * m.NY));
+}
+
+// ---- deterministic block reduction of NV doubles -----------------------------
+template <int NV>
+static __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+    // sh: [NV][32]
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = v[q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[q * 32 + w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < nw ? sh[q * 32 + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// writes block partials; returns true in the one block that arrives last,
+// which then holds the grid totals in tot[]
+template <int NV>
+static __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partial, unsigned* ticket, double (&tot)[NV]) {
+    __shared__ double sh[NV * 32];
+    __shared__ bool last;
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NV; ++q) partial[(long long)q * gridDim.x + blockIdx.x] = v[q];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[NV];
+    for (int q = 0; q < NV; ++q) {
+        s[q] = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s[q] += ((volatile double*)partial)[(long long)q * gridDim.x + b];
+    }
+    block_sum<NV>(s, sh);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NV; ++q) tot[q] = s[q];
+        *ticket = 0;
+    }
+    return true;
+}
+
+}  // namespace pf

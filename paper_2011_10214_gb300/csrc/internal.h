@@ -144,6 +144,7 @@ struct Ctx {
     float* patch_coeff = nullptr;
     // reductions / PCG scalars
     double* red = nullptr;         // partial sums
+    double* coop_partial = nullptr; // [8][2048] block partials of the persistent PCG
     double* scal = nullptr;        // PCG scalars
     unsigned int* red_ticket = nullptr;
     int* err_word = nullptr;
