@@ -194,6 +194,8 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.r, sizeof(double) * N);
     ALLOC(c.p, sizeof(double) * N);
     ALLOC(c.q, sizeof(double) * N);
+    ALLOC(c.z, sizeof(double) * N);
+    ALLOC(c.zf, sizeof(float) * N);
     ALLOC(c.rf, sizeof(float) * N);
     ALLOC(c.pf, sizeof(float) * N);
     ALLOC(c.qf, sizeof(float) * N);
@@ -238,7 +240,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (!ctx) return;
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
-    void* ptrs[] = {c.Lnode, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q,
+    void* ptrs[] = {c.Lnode, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,

@@ -128,6 +128,16 @@ PF_D long long warp_reserve(unsigned long long* counter, bool want) {
     return (long long)(base + __popc(mask & ((1u << lane) - 1)));
 }
 
+// Shared-memory fixed-point tile accumulation with native 32-bit atomics: a
+// weight W <= 2^32 is added as its low 16 bits and the rest (W >> 16) to two
+// uint32 counters.  Exact while a bin holds at most 65535 particles (bins are
+// capped there): each counter then stays below 65535 * 65536 < 2^32.
+PF_D void tile_add(unsigned* lo, unsigned* hi, int t, long long W) {
+    atomicAdd(&lo[t], (unsigned)(W & 0xFFFF));
+    atomicAdd(&hi[t], (unsigned)(W >> 16));
+}
+constexpr int BIN_MAX = 65535;
+
 // ---------------------------------------------------------------------------
 // mbarrier + TMA (cp.async.bulk.tensor) helpers
 // ---------------------------------------------------------------------------

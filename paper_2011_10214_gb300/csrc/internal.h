@@ -114,7 +114,8 @@ struct Ctx {
     double* phi = nullptr;
     double* u = nullptr;           // unknown (phi - g)
     double* b = nullptr;           // right-hand side
-    double *r = nullptr, *p = nullptr, *q = nullptr;
+    double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+    float* zf = nullptr;
     float *rf = nullptr, *pf = nullptr, *qf = nullptr, *uf = nullptr, *invdiagf = nullptr;
     double4* E = nullptr;          // node field (x, y, z, 0)
     float4* Ef = nullptr;          // FP32 copy for the MIXED push

@@ -149,7 +149,7 @@ PF_D void count_event(unsigned long long* sctr, bool ev) {
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) double4 Et[TILE_N];
-    __shared__ unsigned long long Wt[TILE_N];
+    __shared__ unsigned Wlo[TILE_N], Whi[TILE_N];   // fixed-point tile: low 16 bits / rest
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < TILE_N; t += blockDim.x) Wt[t] = 0ull;
+    for (int t = tid; t < TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
     if (tid < NCTR) sctr[tid] = 0ull;
     __syncthreads();
     if (tid == 0) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
                     int t = (w.ci - x0 + (l & 1)) + TILE * ((w.cj - y0 + ((l >> 1) & 1)) + TILE * (w.ck - z0 + ((l >> 2) & 1)));
-                    atomicAdd(&Wt[t], (unsigned long long)Wf[l]);
+                    tile_add(Wlo, Whi, t, Wf[l]);
                 }
             } else {
                 global_deposit(L, S.W, w);
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
-        unsigned long long v = Wt[t];
+        unsigned long long v = (unsigned long long)Wlo[t] + ((unsigned long long)Whi[t] << 16);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
@@ -447,7 +447,8 @@ __global__ void k_bin_caps(int nb, const int* cnt, int* cap, int* cnt_copy) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     int c = cnt[b];
-    cap[b] = ((c + c / 4 + 64) + 31) & ~31;
+    int cp = ((c + c / 4 + 64) + 31) & ~31;
+    cap[b] = cp < BIN_MAX ? cp : BIN_MAX;   // larger loads wait in the mover list
     cnt_copy[b] = 0;
 }
 
@@ -458,13 +459,21 @@ __global__ void k_bin_scan(int nb, const int* cap, long long* start, long long* 
     *total = run;
 }
 
-__global__ void k_bin_scatter(Launch L, PArr a, long long n, const long long* start, int* fill, PArr bins,
-                              bool track) {
+// a bin already at capacity sends the particle to the waiting (mover) list
+__global__ void k_bin_scatter(Launch L, int s, PArr a, long long n, bool track) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SpeciesDev& S = L.sp[s];
     int b = block_of(L, (int)floor(a.x[i]), (int)floor(a.y[i]), (int)floor(a.z[i]));
-    int slot = atomicAdd(&fill[b], 1);
-    put(bins, start[b] + slot, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], track ? a.id[i] : 0, track);
+    int slot = atomicAdd(&S.bcount[b], 1);
+    long long id = track ? a.id[i] : 0;
+    if (slot < S.bcap[b]) {
+        put(S.bins, S.bstart[b] + slot, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], id, track);
+    } else {
+        unsigned long long q = atomicAdd(S.mov_in_n, 1ull);
+        if ((long long)q < S.mcap) put(S.mov_in, (long long)q, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], id, track);
+        else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+    }
 }
 
 __global__ void k_flatten(Launch L, int s, PArr out, unsigned long long* nout) {
@@ -638,8 +647,9 @@ cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool) {
         q.cap = total;
     }
     L = make_launch(c);
-    if (n > 0) k_bin_scatter<<<nb(n), 256, 0, c.stream>>>(L, flat, n, q.bstart, q.bcount, q.bins, c.track != 0);
     cudaMemsetAsync(q.mov_n, 0, 2 * sizeof(unsigned long long), c.stream);
+    if (n > 0) k_bin_scatter<<<nb(n), 256, 0, c.stream>>>(L, s, flat, n, c.track != 0);
+    k_clamp_counts<<<dim3(nb(c.nblocks), (unsigned)c.sp.size()), 256, 0, c.stream>>>(L);
     e = cudaStreamSynchronize(c.stream);
     cudaFree(cnt);
     cudaFree(tot);

@@ -71,7 +71,9 @@ PF_D void fixed_weights_f(const WF& w, long long W[8]) {
     long long rest = 1ll << 32;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
-        W[l] = __float2ll_rn(w.w[l] * 4294967296.0f);
+        // w < 1 except at a cell corner; 2^32 saturates to 2^32 - 1 and the
+        // remainder weight below restores the exact total
+        W[l] = (long long)__float2uint_rn(w.w[l] * 4294967296.0f);
         rest -= W[l];
     }
     W[7] = rest;
@@ -185,7 +187,7 @@ PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
 __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
-    __shared__ unsigned long long Wt[TILE_N];
+    __shared__ unsigned Wlo[TILE_N], Whi[TILE_N];   // fixed-point tile: low 16 bits / rest
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < TILE_N; t += blockDim.x) Wt[t] = 0ull;
+    for (int t = tid; t < TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
     if (tid < NCTR) sctr[tid] = 0ull;
     __syncthreads();
     if (tid == 0) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
                     int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
-                    atomicAdd(&Wt[t], (unsigned long long)Wf[l]);
+                    tile_add(Wlo, Whi, t, Wf[l]);
                 }
             } else {
                 global_deposit_f(L, S.W, p);
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
-        unsigned long long v = Wt[t];
+        unsigned long long v = (unsigned long long)Wlo[t] + ((unsigned long long)Whi[t] << 16);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
@@ -406,10 +408,10 @@ __global__ void k_rebin_m(Launch L) {
 }
 
 // FP64 flat list -> MIXED bins (load, explicit particles, rebuild)
-__global__ void k_bin_scatter_m(Launch L, PArr a, long long n, const long long* start, int* fill, PArrF bins,
-                                bool track) {
+__global__ void k_bin_scatter_m(Launch L, int s, PArr a, long long n, bool track) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SpeciesDev& S = L.sp[s];
     double fi = floor(a.x[i]), fj = floor(a.y[i]), fk = floor(a.z[i]);
     PF32 p;
     p.i = (int)fi; p.j = (int)fj; p.k = (int)fk;
@@ -419,8 +421,15 @@ __global__ void k_bin_scatter_m(Launch L, PArr a, long long n, const long long* 
     if (p.fz >= 1.0f) p.fz = 0.99999994f;
     p.vx = (float)a.vx[i]; p.vy = (float)a.vy[i]; p.vz = (float)a.vz[i];
     int b = block_of(L, p.i, p.j, p.k);
-    int slot = atomicAdd(&fill[b], 1);
-    store_p(bins, start[b] + slot, p, track ? a.id[i] : 0, track);
+    int slot = atomicAdd(&S.bcount[b], 1);
+    long long id = track ? a.id[i] : 0;
+    if (slot < S.bcap[b]) {
+        store_p(S.binsF, S.bstart[b] + slot, p, id, track);
+    } else {   // a full bin: the particle waits in the mover list
+        unsigned long long q = atomicAdd(S.mov_in_n, 1ull);
+        if ((long long)q < S.mcap) store_p(S.movF_in, (long long)q, p, id, track);
+        else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+    }
 }
 
 PF_D void put_d(const PArr& o, long long g, const PF32& p, long long id, bool track) {
@@ -645,8 +654,9 @@ cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool)
         q.cap = total;
     }
     L = make_launch(c);
-    if (n > 0) k_bin_scatter_m<<<nb(n), 256, 0, c.stream>>>(L, flat, n, q.bstart, q.bcount, q.binsF, c.track != 0);
     cudaMemsetAsync(q.mov_n, 0, 2 * sizeof(unsigned long long), c.stream);
+    if (n > 0) k_bin_scatter_m<<<nb(n), 256, 0, c.stream>>>(L, s, flat, n, c.track != 0);
+    k_clamp_counts<<<dim3(nb(c.nblocks), (unsigned)c.sp.size()), 256, 0, c.stream>>>(L);
     e = cudaStreamSynchronize(c.stream);
     cudaFree(cnt);
     cudaFree(tot);

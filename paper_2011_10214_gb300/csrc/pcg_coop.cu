@@ -15,23 +15,27 @@
 // bounded (about a second); a timeout raises an error bit and ends the solve.
 #include <math.h>
 
+#include <type_traits>
+
 #include "field_common.cuh"
 #include "internal.h"
 
 namespace pf {
 
-constexpr double COOP_INNER_TOL = 1e-3;   // MIXED: relative reduction per refinement step
+constexpr double COOP_INNER_TOL = 1e-4;   // MIXED: least relative reduction per refinement step
 constexpr int COOP_MAX_OUTER = 12;
-constexpr int COOP_THREADS = 256;
+constexpr int COOP_THREADS = 512;
 
 struct CoopArgs {
     FieldArgs f;
     const double* b;
     double* u;
-    double* r;        // FP64 residual (both modes)
+    double* r;        // FP64 mode vectors
+    double* z;
     double* p;
     double* q;
-    float* rf;        // MIXED inner vectors
+    float* rf;        // MIXED inner vectors (df: the correction)
+    float* zf;
     float* pf;
     float* qf;
     float* df;
@@ -99,16 +103,27 @@ static __device__ __forceinline__ void get_total(const CoopArgs& a, int slot, do
     __syncthreads();
 }
 
+// Jacobi PCG with the direction product carried by recurrence: after the
+// residual update every block writes z = D^-1 r; then p = z + beta p and
+// q = A z + beta q (= A p) need only that one barrier, so an iteration costs
+// two grid barriers (one per reduction).
 template <bool MIXED>
-__global__ void __launch_bounds__(COOP_THREADS) k_pcg_coop(CoopArgs a) {
+__global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
+    using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ double sh[3 * 32];
     __shared__ double bc[4];
     __shared__ int s_ok;
     const FieldArgs& f = a.f;
     const Mesh& m = f.m;
     const long long N = m.nnodes;
-    const long long T = (long long)gridDim.x * blockDim.x;
+    const long long TT = (long long)gridDim.x * blockDim.x;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    T* r = MIXED ? (T*)a.rf : (T*)a.r;
+    T* z = MIXED ? (T*)a.zf : (T*)a.z;
+    T* p = MIXED ? (T*)a.pf : (T*)a.p;
+    T* q = MIXED ? (T*)a.qf : (T*)a.q;
+    const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
+    const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
     PcgState* S = a.S;
     const double tol2 = S->tol2;
     const int maxit = S->maxit;
@@ -116,25 +131,20 @@ __global__ void __launch_bounds__(COOP_THREADS) k_pcg_coop(CoopArgs a) {
     double bb = 0.0, rr = 0.0;
     bool conv = false, alive = true;
 
-    for (;;) {   // refinement loop (one pass in FP64 mode)
-        // residual r = b - A u in FP64 (u read through L2: other blocks wrote it)
+    for (;;) {   // refinement loop (a single pass in FP64 mode)
+        // r = b - A u (FP64; u read through L2), z = D^-1 r, p = z
         double v[3] = {0, 0, 0};
-        for (long long n = t0; n < N; n += T) {
+        for (long long n = t0; n < N; n += TT) {
             int i, j, k;
             node_ijk(m, n, i, j, k);
             double bn = a.b[n];
             double rn = (f.ntype[n] == -3) ? 0.0 : bn - apply_row<double, true>(f, n, i, j, k, a.u, f.coef);
+            T rt = (T)rn, zt = dinv[n] * rt;
+            r[n] = rt; z[n] = zt; p[n] = zt;
+            if (MIXED) a.df[n] = 0.0f;
             v[0] += bn * bn;
             v[1] += rn * rn;
-            if (MIXED) {
-                float rfn = (float)rn, zn = f.invdiagf[n] * rfn;
-                a.rf[n] = rfn; a.df[n] = 0.0f; a.pf[n] = zn;
-                v[2] += (double)rfn * (double)zn;
-            } else {
-                double zn = f.invdiag[n] * rn;
-                a.r[n] = rn; a.p[n] = zn;
-                v[2] += rn * zn;
-            }
+            v[2] += (double)rt * (double)zt;
         }
         put_partial<3>(a, v, 0, sh);
         if (!(alive = grid_barrier(a, &s_ok))) break;
@@ -143,49 +153,37 @@ __global__ void __launch_bounds__(COOP_THREADS) k_pcg_coop(CoopArgs a) {
         if (outer == 0) bb = tot[0];
         rr = tot[1];
         double rz = tot[2];
-        const double rr_outer = rr;
+        // inner target: the final tolerance, or a 1e-4 reduction of this residual
+        const double rr_stop = MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * tot[1]) : tol2 * bb;
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
         ++outer;
-        // (inner) PCG iterations
+        // q = A p (p = z here)
+        double w[1] = {0.0};
+        for (long long n = t0; n < N; n += TT) {
+            int i, j, k;
+            node_ijk(m, n, i, j, k);
+            T y = apply_row<T, true>(f, n, i, j, k, z, coef);
+            q[n] = y;
+            w[0] += (double)p[n] * (double)y;
+        }
+        put_partial<1>(a, w, 3, sh);
+        if (!(alive = grid_barrier(a, &s_ok))) break;
+        double pq[1];
+        get_total<1>(a, 3, pq, sh, bc);
+        double alpha = rz / pq[0];
         for (;;) {
-            double w[1] = {0.0};
-            for (long long n = t0; n < N; n += T) {
-                int i, j, k;
-                node_ijk(m, n, i, j, k);
-                if (MIXED) {
-                    float y = apply_row<float, true>(f, n, i, j, k, a.pf, f.coeff);
-                    a.qf[n] = y;
-                    w[0] += (double)a.pf[n] * (double)y;
-                } else {
-                    double y = apply_row<double, true>(f, n, i, j, k, a.p, f.coef);
-                    a.q[n] = y;
-                    w[0] += a.p[n] * y;
-                }
-            }
-            put_partial<1>(a, w, 3, sh);
-            if (!(alive = grid_barrier(a, &s_ok))) break;
-            double pq[1];
-            get_total<1>(a, 3, pq, sh, bc);
-            const double alpha = rz / pq[0];
+            // u += alpha p, r -= alpha q, z = D^-1 r
             double x2[2] = {0, 0};
-            for (long long n = t0; n < N; n += T) {
-                if (MIXED) {
-                    float al = (float)alpha;
-                    float rn = a.rf[n] - al * a.qf[n];
-                    a.df[n] = a.df[n] + al * a.pf[n];
-                    a.rf[n] = rn;
-                    float zn = f.invdiagf[n] * rn;
-                    x2[0] += (double)rn * (double)rn;
-                    x2[1] += (double)rn * (double)zn;
-                } else {
-                    double rn = a.r[n] - alpha * a.q[n];
-                    a.u[n] = a.u[n] + alpha * a.p[n];
-                    a.r[n] = rn;
-                    double zn = f.invdiag[n] * rn;
-                    x2[0] += rn * rn;
-                    x2[1] += rn * zn;
-                }
+            const T al = (T)alpha;
+            for (long long n = t0; n < N; n += TT) {
+                T rn = r[n] - al * q[n];
+                if (MIXED) a.df[n] = a.df[n] + (float)al * (float)p[n];
+                else a.u[n] = a.u[n] + alpha * (double)p[n];
+                T zn = dinv[n] * rn;
+                r[n] = rn; z[n] = zn;
+                x2[0] += (double)rn * (double)rn;
+                x2[1] += (double)rn * (double)zn;
             }
             put_partial<2>(a, x2, 4, sh);
             if (!(alive = grid_barrier(a, &s_ok))) break;
@@ -195,23 +193,31 @@ __global__ void __launch_bounds__(COOP_THREADS) k_pcg_coop(CoopArgs a) {
             rz = t2[1];
             rr = t2[0];
             ++it;
-            bool stop;
-            if (MIXED) stop = (rr <= COOP_INNER_TOL * COOP_INNER_TOL * rr_outer) || (it >= maxit);
-            else { conv = rr <= tol2 * bb; stop = conv || (it >= maxit); }
-            if (stop) break;
-            for (long long n = t0; n < N; n += T) {
-                if (MIXED) a.pf[n] = f.invdiagf[n] * a.rf[n] + (float)beta * a.pf[n];
-                else a.p[n] = f.invdiag[n] * a.r[n] + beta * a.p[n];
+            if (!MIXED) conv = rr <= tol2 * bb;
+            if (rr <= rr_stop || it >= maxit) break;
+            // p = z + beta p, q = A z + beta q (z of neighbours through L2)
+            double w2[1] = {0.0};
+            const T bt = (T)beta;
+            for (long long n = t0; n < N; n += TT) {
+                int i, j, k;
+                node_ijk(m, n, i, j, k);
+                T pn = z[n] + bt * p[n];
+                T qn = apply_row<T, true>(f, n, i, j, k, z, coef) + bt * q[n];
+                p[n] = pn; q[n] = qn;
+                w2[0] += (double)pn * (double)qn;
             }
+            put_partial<1>(a, w2, 3, sh);
             if (!(alive = grid_barrier(a, &s_ok))) break;
+            double pq2[1];
+            get_total<1>(a, 3, pq2, sh, bc);
+            alpha = rz / pq2[0];
         }
         if (!alive || !MIXED) break;
         // refinement: u += d, then a barrier before the next residual reads u
-        for (long long n = t0; n < N; n += T) a.u[n] = a.u[n] + (double)a.df[n];
+        for (long long n = t0; n < N; n += TT) a.u[n] = a.u[n] + (double)a.df[n];
         if (!(alive = grid_barrier(a, &s_ok))) break;
     }
-    // phi = u + g (the lift alone when the right-hand side vanishes)
-    for (long long n = t0; n < N; n += T) a.phi[n] = (bb == 0.0) ? a.g[n] : a.u[n] + a.g[n];
+    for (long long n = t0; n < N; n += TT) a.phi[n] = (bb == 0.0) ? a.g[n] : a.u[n] + a.g[n];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         S->bb = bb;
         S->rr = rr;
@@ -242,8 +248,8 @@ cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     CoopArgs a;
     a.f.m = c.mesh; a.f.o = c.obj; a.f.ntype = c.ntype; a.f.coef = c.patch_coef; a.f.coeff = c.patch_coeff;
     a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;
-    a.b = c.b; a.u = c.u; a.r = c.r; a.p = c.p; a.q = c.q;
-    a.rf = c.rf; a.pf = c.pf; a.qf = c.qf; a.df = c.uf;
+    a.b = c.b; a.u = c.u; a.r = c.r; a.z = c.z; a.p = c.p; a.q = c.q;
+    a.rf = c.rf; a.zf = c.zf; a.pf = c.pf; a.qf = c.qf; a.df = c.uf;
     a.g = c.gdir; a.phi = c.phi;
     a.partial = c.coop_partial;
     a.bar_count = c.red_ticket + 1;
