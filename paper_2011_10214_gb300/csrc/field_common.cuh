@@ -107,9 +107,13 @@ static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, i
 }
 
 static __device__ __forceinline__ void node_ijk(const Mesh& m, long long n, int& i, int& j, int& k) {
-    i = (int)(n % m.NX);
-    j = (int)((n / m.NX) % m.NY);
-    k = (int)(n / ((long long)m.NX * m.NY));
+    // node counts stay below 2^31 (mesh limits 2047 x 2047 x 1023 cells): 32-bit division
+    unsigned u = (unsigned)n, NX = (unsigned)m.NX, NXY = (unsigned)m.NX * (unsigned)m.NY;
+    unsigned kk = u / NXY, rem = u - kk * NXY;
+    unsigned jj = rem / NX;
+    i = (int)(rem - jj * NX);
+    j = (int)jj;
+    k = (int)kk;
 }
 
 // ---- deterministic block reduction of NV doubles -----------------------------

@@ -159,14 +159,15 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
         ++outer;
         // q = A p (p = z here)
-        double w[1] = {0.0};
+        T wt = (T)0;
         for (long long n = t0; n < N; n += TT) {
             int i, j, k;
             node_ijk(m, n, i, j, k);
             T y = apply_row<T, true>(f, n, i, j, k, z, coef);
             q[n] = y;
-            w[0] += (double)p[n] * (double)y;
+            wt += p[n] * y;
         }
+        double w[1] = {(double)wt};
         put_partial<1>(a, w, 3, sh);
         if (!(alive = grid_barrier(a, &s_ok))) break;
         double pq[1];
@@ -174,7 +175,9 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
         double alpha = rz / pq[0];
         for (;;) {
             // u += alpha p, r -= alpha q, z = D^-1 r
-            double x2[2] = {0, 0};
+            // per-thread partials in the working precision (a thread owns a few
+            // nodes), widened once; block and grid sums are FP64
+            T s0 = (T)0, s1 = (T)0;
             const T al = (T)alpha;
             for (long long n = t0; n < N; n += TT) {
                 T rn = r[n] - al * q[n];
@@ -182,9 +185,10 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
                 else a.u[n] = a.u[n] + alpha * (double)p[n];
                 T zn = dinv[n] * rn;
                 r[n] = rn; z[n] = zn;
-                x2[0] += (double)rn * (double)rn;
-                x2[1] += (double)rn * (double)zn;
+                s0 += rn * rn;
+                s1 += rn * zn;
             }
+            double x2[2] = {(double)s0, (double)s1};
             put_partial<2>(a, x2, 4, sh);
             if (!(alive = grid_barrier(a, &s_ok))) break;
             double t2[2];
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
             if (!MIXED) conv = rr <= tol2 * bb;
             if (rr <= rr_stop || it >= maxit) break;
             // p = z + beta p, q = A z + beta q (z of neighbours through L2)
-            double w2[1] = {0.0};
+            T s2 = (T)0;
             const T bt = (T)beta;
             for (long long n = t0; n < N; n += TT) {
                 int i, j, k;
@@ -204,8 +208,9 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
                 T pn = z[n] + bt * p[n];
                 T qn = apply_row<T, true>(f, n, i, j, k, z, coef) + bt * q[n];
                 p[n] = pn; q[n] = qn;
-                w2[0] += (double)pn * (double)qn;
+                s2 += pn * qn;
             }
+            double w2[1] = {(double)s2};
             put_partial<1>(a, w2, 3, sh);
             if (!(alive = grid_barrier(a, &s_ok))) break;
             double pq2[1];
