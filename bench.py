@@ -342,6 +342,79 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """64 independent sphere-charging instances (16^3..48^3 cells, R 1..8,
+    eps 2..10, 16..64 ppc/species), MIXED, one graph launch per step."""
+    import numpy as np
+    import torch
+    from paper_2011_10214_gb300 import capi, serve
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(2011102144)
+    cfgs = serve.request_distribution(rng, args.instances, big_fraction=0.0)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    sims = []
+    for c in cfgs:
+        s = capi.from_config(c, precision=capi.MIXED, stream=stream.cuda_stream)
+        s.solve(); s.leapfrog_init()
+        sims.append(s)
+    setup_s = time.perf_counter() - t0
+    batch = capi.Batch(sims, stream=stream.cuda_stream)
+    best, _ = serve.autotune_batch(batch)
+    batch.step(args.warmup, stats=False)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = batch.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    pushed = sum(sum(x["pushed"]) for x in st)
+    out = {"metric": "particle-steps/s incl. IFE solve (batched)", "value": pushed / (ms / 1e3),
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32+f64",
+           "data": "synthetic (seeded Philox load and injection)",
+           "config": {"workload": f"{len(cfgs)} independent sphere-charging instances, n ~ U{{16..48}}^3, "
+                                  "R ~ U[1,8], eps ~ U[2,10], ppc ~ U{16..64}, MIXED",
+                      "particles": int(pushed / args.steps), "batched_pcg_threads": best,
+                      "setup_s": setup_s},
+           "gpu_launches": int(sum(x["kernel_launches"] for x in st)), "graph_launches": args.steps,
+           "pcg_iters_per_step_max": max(x["pcg_iters_total"] for x in st) / args.steps, "clocks": ck}
+    batch.close()
+    for s in sims:
+        s.close()
+    print(json.dumps(out))
+
+
+def run_serve(args):
+    """Poisson arrivals of sphere-charging requests (batched distribution plus
+    5 % at 96^3 with 64 ppc), admitted by HBM budget into one running batch."""
+    import numpy as np
+    import torch
+    from paper_2011_10214_gb300 import capi, serve
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(2011102145)
+    arr = serve.poisson_arrivals(rng, args.rate, args.horizon)
+    reqs = serve.request_distribution(rng, len(arr), big_fraction=0.05)
+    stream = torch.cuda.Stream()
+    budget = int(args.hbm_budget_gb * 2**30)
+    srv = serve.Server(budget, precision=capi.MIXED, steps_per_round=10, max_steps=args.max_steps,
+                       stream=stream.cuda_stream)
+    res = srv.run(reqs, arr, time_limit=args.time_limit)
+    srv.close()
+    out = {"metric": "served latency p50/p99 and aggregate particle-steps/s", "unit": "s",
+           "p50_s": res["p50_s"], "p99_s": res["p99_s"], "completed": res["completed"], "requests": len(arr),
+           "particle_steps_per_s": res["particle_steps_per_s"], "wall_s": res["wall_s"],
+           "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic (seeded Poisson arrivals)",
+           "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.horizon}s; sphere-charging requests "
+                                  "n ~ U{16..48}^3 (+5% 96^3 at 64 ppc), stop at "
+                                  f"{args.max_steps} steps or <1% change of the surface potential over 50 steps",
+                      "hbm_budget_gb": args.hbm_budget_gb}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,10 +426,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--horizon", type=float, default=10.0)
+    ap.add_argument("--max-steps", type=int, default=500)
+    ap.add_argument("--time-limit", type=float, default=240.0)
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--as-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

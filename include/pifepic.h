@@ -213,6 +213,27 @@ pifepic_status pifepic_get_stats(pifepic_ctx* ctx, pifepic_stats* stats);
 pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const double* q, int mem_kind,
                                    int* iters, double* relres);
 
+/* Batched steps over many independent contexts (serving many charging
+ * problems at once; the paper runs one problem per job, Sec. 3 and Sec. 5).
+ * One CUDA graph launch per step advances every member: each member's particle
+ * phases and right-hand side are independent branches (they overlap on the
+ * device), one batched PCG kernel solves every member's field with one CTA per
+ * member, then each member's node field is formed.  Members must share one
+ * precision; their own streams are synchronised before the batch stream (given
+ * at creation) takes over.  A member's results do not depend on the other
+ * members.  The graph is rebuilt on the next step after add / remove /
+ * set_threads.  stats (if not NULL) receives one entry per member, in member
+ * order.  The batch borrows the contexts: destroy the batch first. */
+typedef struct pifepic_batch pifepic_batch;
+pifepic_status pifepic_batch_create(pifepic_ctx** ctxs, int n, void* stream, pifepic_batch** out);
+pifepic_status pifepic_batch_add(pifepic_batch* batch, pifepic_ctx* ctx);
+pifepic_status pifepic_batch_remove(pifepic_batch* batch, pifepic_ctx* ctx);
+/* CTA size of the batched PCG (256, 512 or 1024); the serving loop's tuner sets it. */
+pifepic_status pifepic_batch_set_threads(pifepic_batch* batch, int threads);
+pifepic_status pifepic_batch_step(pifepic_batch* batch, int nsteps, pifepic_stats* stats);
+const char* pifepic_batch_last_error(const pifepic_batch* batch);
+void pifepic_batch_destroy(pifepic_batch* batch);
+
 /* Field solve that allocates nothing.  (The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory once they are
  * running -- a serving loop whose memory comes from a pool it does not own,

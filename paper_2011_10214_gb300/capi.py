@@ -93,6 +93,11 @@ _sigs = {
     "pifepic_get_stats": [_ctx, C.POINTER(Stats)],
     "pifepic_solve_field": [_ctx, _dp, _dp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "pifepic_solve_field_noalloc": [_ctx, _dp, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "pifepic_batch_create": [C.POINTER(_ctx), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)],
+    "pifepic_batch_add": [C.c_void_p, _ctx],
+    "pifepic_batch_remove": [C.c_void_p, _ctx],
+    "pifepic_batch_set_threads": [C.c_void_p, C.c_int],
+    "pifepic_batch_step": [C.c_void_p, C.c_int, C.c_void_p],
 }
 for _n, _a in _sigs.items():
     _f = getattr(lib, _n)
@@ -102,8 +107,13 @@ lib.pifepic_destroy.argtypes = [_ctx]
 lib.pifepic_destroy.restype = None
 lib.pifepic_last_error.argtypes = [_ctx]
 lib.pifepic_last_error.restype = C.c_char_p
+lib.pifepic_batch_destroy.argtypes = [C.c_void_p]
+lib.pifepic_batch_destroy.restype = None
+lib.pifepic_batch_last_error.argtypes = [C.c_void_p]
+lib.pifepic_batch_last_error.restype = C.c_char_p
 
-EXPORTED = sorted(list(_sigs) + ["pifepic_destroy", "pifepic_last_error"])
+EXPORTED = sorted(list(_sigs) + ["pifepic_destroy", "pifepic_last_error", "pifepic_batch_destroy",
+                                 "pifepic_batch_last_error"])
 
 
 class PifepicError(RuntimeError):
@@ -329,3 +339,53 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
         if inject:
             sim.set_injection(s, cfg["inject_faces"], sp["density"], sp["vth"], sp["drift"], cfg["seed"])
     return sim
+
+
+class Batch:
+    """Many Simulations advanced together, one CUDA graph launch per step
+    (pifepic_batch_*).  Members keep their own state; results of a member do
+    not depend on the others."""
+
+    def __init__(self, sims=(), stream=None):
+        self._b = C.c_void_p()
+        self.members = []
+        st = lib.pifepic_batch_create(None, 0, C.c_void_p(stream or 0), C.byref(self._b))
+        if st != 0:
+            raise PifepicError(f"pifepic_batch_create: {STATUS.get(st, st)}")
+        for s in sims:
+            self.add(s)
+
+    def _ok(self, st, what):
+        if st != 0:
+            raise PifepicError(f"{what}: {STATUS.get(st, st)}: {lib.pifepic_batch_last_error(self._b).decode()}")
+
+    def add(self, sim):
+        self._ok(lib.pifepic_batch_add(self._b, sim._c), "batch_add")
+        self.members.append(sim)
+
+    def remove(self, sim):
+        self._ok(lib.pifepic_batch_remove(self._b, sim._c), "batch_remove")
+        self.members.remove(sim)
+
+    def set_threads(self, threads):
+        self._ok(lib.pifepic_batch_set_threads(self._b, int(threads)), "batch_set_threads")
+
+    def step(self, nsteps=1, stats=True):
+        n = len(self.members)
+        arr = (Stats * max(n, 1))() if stats else None
+        self._ok(lib.pifepic_batch_step(self._b, int(nsteps), C.cast(arr, C.c_void_p) if arr is not None else None),
+                 "batch_step")
+        if not stats:
+            return None
+        return [arr[i].as_dict(m.nspecies) for i, m in enumerate(self.members)]
+
+    def close(self):
+        if self._b is not None and self._b.value:
+            lib.pifepic_batch_destroy(self._b)
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

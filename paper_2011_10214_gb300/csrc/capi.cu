@@ -104,9 +104,6 @@ __global__ void k_seq_id(long long n, long long base, long long* id) {
 
 using namespace pf;
 
-struct pifepic_ctx {
-    Ctx c;
-};
 
 #define FAIL(code, ...)                                                              \
     do {                                                                             \
@@ -656,6 +653,29 @@ static long long outer_total(Ctx& c) {
     scopy(c.stream, &v, (long long*)(c.scal + 41), sizeof(v), cudaMemcpyDeviceToHost);
     return v;
 }
+
+static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* before, pifepic_stats* st,
+                                 const float* phase_ms, long long it0, long long l0, long long nsolves,
+                                 long long ot0);
+
+}  // extern "C"
+
+namespace pf {
+// counters before a batched call, and the statistics after it (batch.cu)
+void snapshot_counters(pifepic_ctx* ctx, unsigned long long* before, long long* it0, long long* ot0, long long* l0) {
+    read_counters(ctx->c, before);
+    *it0 = iters_total(ctx->c);
+    *ot0 = outer_total(ctx->c);
+    *l0 = ctx->c.launches;
+}
+pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, long long it0, long long ot0,
+                            long long nsteps, long long kernels, pifepic_stats* st) {
+    long long l0 = ctx->c.launches - kernels;
+    return fill_stats(ctx, before, st, nullptr, it0, l0, 0, ot0);
+}
+}  // namespace pf
+
+extern "C" {
 
 static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* before, pifepic_stats* st,
                                  const float* phase_ms, long long it0, long long l0, long long nsolves,

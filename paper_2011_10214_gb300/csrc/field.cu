@@ -267,6 +267,23 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
     return cudaGetLastError();
 }
 
+// the solve's pieces around the PCG, for the batched step (batch.cu)
+cudaError_t launch_solve_prefix(Ctx& c, cudaStream_t st) {
+    FieldArgs f = fargs(c);
+    RhsArgs a = rargs(c);
+    long long N = c.mesh.nnodes;
+    if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
+    if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
+    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr);
+    k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.gdir, c.u);
+    return cudaGetLastError();
+}
+cudaError_t launch_solve_suffix(Ctx& c, cudaStream_t st) {
+    FieldArgs f = fargs(c);
+    k_node_E<<<nb(c.mesh.nnodes), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    return cudaGetLastError();
+}
+
 // kernels launched per solve
 int solve_graph_fixed_kernels(const Ctx& c) { return (c.ncut > 0) + (c.nit > 0) + 4; }
 

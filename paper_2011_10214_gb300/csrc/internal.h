@@ -238,3 +238,7 @@ cudaError_t launch_deposit_all_mixed(Ctx& c);
 cudaError_t launch_half_kick_mixed(Ctx& c);
 
 }  // namespace pf
+
+struct pifepic_ctx {
+    pf::Ctx c;
+};

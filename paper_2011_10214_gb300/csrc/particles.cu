@@ -338,7 +338,7 @@ __global__ void k_inject(Launch L, InjArgs a) {
         bool rejected = false;
         double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
         if (mm < cnt) {
-            InjSample sm = inject_sample(d, mm, a.step, s, L.mesh, L.dth);
+            InjSample sm = inject_sample(d, mm, *a.step, s, L.mesh, L.dth);
             double p0[3] = {sm.p0[0], sm.p0[1], sm.p0[2]};
             bool ok = sm.ok;
             for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
@@ -396,6 +396,8 @@ __global__ void k_rebin(Launch L) {
         }
     }
 }
+
+__global__ void k_step_advance(long long* step) { *step += 1; }
 
 __global__ void k_clamp_counts(Launch L) {
     const int s = blockIdx.y;
@@ -589,7 +591,7 @@ static InjArgs inj_args(Ctx& c) {
     InjArgs a;
     a.st = c.inj_dev; a.nst = (int)c.inj.size();
     a.count = c.inj_count; a.idbase = c.inj_base; a.carry = c.inj_carry; a.next_id = c.next_id;
-    a.step = c.step_no;
+    a.step = (const long long*)(c.scal + 42);
     return a;
 }
 
@@ -718,7 +720,8 @@ cudaError_t launch_rebin(Ctx& c) {
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n, 0, sizeof(unsigned long long), c.stream);
     k_rebin<<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
     k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
-    c.launches += 2;
+    k_step_advance<<<1, 1, 0, c.stream>>>((long long*)(c.scal + 42));
+    c.launches += 3;
     return cudaGetLastError();
 }
 

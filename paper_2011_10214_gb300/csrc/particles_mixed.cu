@@ -338,7 +338,7 @@ __global__ void k_inject_m(Launch L, InjArgs a) {
         bool rejected = false;
         PF32 p;
         if (mm < cnt) {
-            InjSample sm = inject_sample(d, mm, a.step, s, L.mesh, L.dth);
+            InjSample sm = inject_sample(d, mm, *a.step, s, L.mesh, L.dth);
             if (!sm.ok || level_set(L.obj, sm.p0[0], sm.p0[1], sm.p0[2]) < 0.0) {
                 rejected = true;
             } else if (outside_d(L.mesh, sm.p[0], sm.p[1], sm.p[2])) {
@@ -531,11 +531,12 @@ static InjArgs inj_args_m(Ctx& c) {
     InjArgs a;
     a.st = c.inj_dev; a.nst = (int)c.inj.size();
     a.count = c.inj_count; a.idbase = c.inj_base; a.carry = c.inj_carry; a.next_id = c.next_id;
-    a.step = c.step_no;
+    a.step = (const long long*)(c.scal + 42);
     return a;
 }
 
 __global__ void k_inject_counts(InjArgs a);   // particles.cu
+__global__ void k_step_advance(long long* step);
 
 cudaError_t launch_push_mixed(Ctx& c) {
     Launch L = make_launch(c);
@@ -575,7 +576,8 @@ cudaError_t launch_rebin_mixed(Ctx& c) {
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n, 0, sizeof(unsigned long long), c.stream);
     k_rebin_m<<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
     k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
-    c.launches += 2;
+    k_step_advance<<<1, 1, 0, c.stream>>>((long long*)(c.scal + 42));
+    c.launches += 3;
     return cudaGetLastError();
 }
 

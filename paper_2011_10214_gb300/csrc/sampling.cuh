@@ -16,7 +16,7 @@ struct InjArgs {
     long long* idbase;     // per stream
     double* carry;         // per stream
     long long* next_id;    // per species
-    long long step;
+    const long long* step; // steps completed so far (device; advanced at the end of each step)
 };
 
 PF_D void box_muller(double u1, double u2, double& z0, double& z1) {

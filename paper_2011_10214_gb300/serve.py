@@ -1,0 +1,185 @@
+"""Continuous-batching server for independent charging simulations.
+
+Requests (one sphere-charging problem each) arrive over time.  The server
+admits a request as soon as its estimated device memory fits the HBM budget
+next to the running ones, sets it up (load, initial field solve, leapfrog
+start) and adds it to one pifepic batch; every round advances all running
+members with one CUDA graph launch per step, so requests that arrive while
+others run share the device.  A member finishes after `max_steps` steps or
+once its area-mean surface potential changed by less than `rel_change` over
+the last `window` steps (the charging has reached its floating potential,
+Sec. 3.1.2).  Latency = finish time - arrival time.
+
+Host-side orchestration only (admission, batch membership, stop tests); every
+step of every member runs in libpifepic's kernels.
+"""
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import capi
+from . import workloads as wl
+
+
+def estimate_bytes(cfg, precision=capi.MIXED):
+    """Device memory of one instance: particle bins with slack, mover lists,
+    mesh, field and solver arrays (a conservative estimate)."""
+    n = cfg["n"]
+    cells = n[0] * n[1] * n[2]
+    nodes = (n[0] + 1) * (n[1] + 1) * (n[2] + 1)
+    per_p = 28 if precision == capi.MIXED else 48
+    parts = sum(sp["ppc"] for sp in cfg["species"]) * cells
+    bins = parts * per_p * 1.25 + len(cfg["species"]) * (cells // 64 + 1) * 64 * per_p
+    movers = len(cfg["species"]) * 2 * max(1 << 16, parts // len(cfg["species"]) // 8 + 4096) * per_p
+    mesh = nodes * (8 * 20 + 4 * 12 + 8 * 8 * 8) + cells * 16
+    return int(bins + movers + mesh + (4 << 20))
+
+
+def request_distribution(rng, count, big_fraction=0.05):
+    """Sphere-charging requests: n ~ U{16..48} cells per side (h = 0.5),
+    R ~ U[1, 8] Debye lengths clamped to fit the box, eps_in ~ U[2, 10],
+    ppc ~ U{16..64}; a fraction at 96^3 cells with 64 ppc."""
+    out = []
+    for _ in range(count):
+        if rng.random() < big_fraction:
+            n, ppc = 96, 64
+        else:
+            n, ppc = int(rng.integers(16, 49)), int(rng.integers(16, 65))
+        box = n * 0.5
+        R = float(min(rng.uniform(1.0, 8.0), 0.3 * box))
+        eps = float(rng.uniform(2.0, 10.0))
+        out.append(wl.sphere_config(n, R, ppc, 500, eps_in=eps, seed_offset=int(rng.integers(100, 10**6))))
+    return out
+
+
+@dataclass
+class Member:
+    rid: int
+    cfg: dict
+    arrival: float
+    sim: object
+    admitted: float
+    steps: int = 0
+    pushed: int = 0
+    history: list = field(default_factory=list)   # (step, surface potential)
+
+
+class Server:
+    def __init__(self, hbm_budget, precision=capi.MIXED, steps_per_round=10, max_steps=500, window=50,
+                 rel_change=0.01, pcg_tol=1e-6, threads=512, stream=None, keep_phi=False):
+        self.budget = int(hbm_budget)
+        self.precision = precision
+        self.k = int(steps_per_round)
+        self.max_steps = int(max_steps)
+        self.window = int(window)
+        self.rel = float(rel_change)
+        self.pcg_tol = pcg_tol
+        self.batch = capi.Batch(stream=stream)
+        self.batch.set_threads(threads)
+        self.stream = stream
+        self.running = []
+        self.used = 0
+        self.results = []
+        self.keep_phi = keep_phi
+
+    def _admit(self, rid, cfg, arrival):
+        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=self.stream)
+        sim.solve()
+        sim.leapfrog_init()
+        self.batch.add(sim)
+        m = Member(rid, cfg, arrival, sim, time.perf_counter())
+        self.running.append(m)
+        self.used += estimate_bytes(cfg, self.precision)
+        return m
+
+    def _done(self, m):
+        if m.steps >= self.max_steps:
+            return True
+        past = [v for s, v in m.history if s <= m.steps - self.window]
+        if not past or not m.history:
+            return False
+        v0, v1 = past[-1], m.history[-1][1]
+        return abs(v1 - v0) <= self.rel * max(abs(v0), 1e-30)
+
+    def run(self, requests, arrivals, time_limit=None):
+        """requests: list of workload dicts; arrivals: seconds after start.
+        Returns per-request results and aggregate throughput."""
+        t_start = time.perf_counter()
+        pending = sorted(zip(arrivals, range(len(requests)), requests))
+        queue = []
+        pushed_total = 0
+        while pending or queue or self.running:
+            now = time.perf_counter() - t_start
+            if time_limit is not None and now > time_limit:
+                break
+            while pending and pending[0][0] <= now:
+                queue.append(pending.pop(0))
+            # admission by HBM budget, first come first served
+            while queue:
+                arr, rid, cfg = queue[0]
+                need = estimate_bytes(cfg, self.precision)
+                if self.running and self.used + need > self.budget:
+                    break
+                queue.pop(0)
+                self._admit(rid, cfg, t_start + arr)
+            if not self.running:
+                if pending:
+                    time.sleep(max(0.0, min(0.05, pending[0][0] - (time.perf_counter() - t_start))))
+                continue
+            stats = self.batch.step(self.k)
+            for m, st in zip(list(self.running), stats):
+                m.steps += self.k
+                pushed = int(sum(st["pushed"]))
+                m.pushed += pushed
+                pushed_total += pushed
+                m.history.append((m.steps, st["surface_potential"]))
+            for m in [m for m in self.running if self._done(m)]:
+                t = time.perf_counter()
+                self.batch.remove(m.sim)
+                self.results.append(dict(rid=m.rid, n=m.cfg["n"][0], steps=m.steps, latency=t - m.arrival,
+                                         queue_wait=m.admitted - m.arrival, pushed=m.pushed,
+                                         surface_potential=m.history[-1][1],
+                                         phi=m.sim.potential() if self.keep_phi else None))
+                m.sim.close()
+                self.running.remove(m)
+                self.used -= estimate_bytes(m.cfg, self.precision)
+        wall = time.perf_counter() - t_start
+        lat = np.array([r["latency"] for r in self.results]) if self.results else np.zeros(1)
+        return dict(completed=len(self.results), wall_s=wall, particle_steps=pushed_total,
+                    particle_steps_per_s=pushed_total / wall if wall > 0 else 0.0,
+                    p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                    results=self.results)
+
+    def close(self):
+        for m in self.running:
+            self.batch.remove(m.sim)
+            m.sim.close()
+        self.running = []
+        self.batch.close()
+
+
+def autotune_batch(batch, trial_steps=2, candidates=(256, 512, 1024)):
+    """Pick the batched-PCG CTA size by timing real steps of the batch (the
+    trial steps advance the members like any other step)."""
+    best, best_t = None, math.inf
+    for th in candidates:
+        batch.set_threads(th)
+        batch.step(1, stats=False)            # graph rebuild + warm-up
+        t0 = time.perf_counter()
+        batch.step(trial_steps, stats=False)
+        t = time.perf_counter() - t0
+        if t < best_t:
+            best, best_t = th, t
+    batch.set_threads(best)
+    return best, best_t / trial_steps
+
+
+def poisson_arrivals(rng, rate, horizon):
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > horizon:
+            return out
+        out.append(t)
