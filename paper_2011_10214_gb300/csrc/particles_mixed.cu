@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     __shared__ alignas(128) float4 Et[TILE_N];
     __shared__ unsigned Wlo[TILE_N], Whi[TILE_N];   // fixed-point tile: low 16 bits / rest
     __shared__ alignas(8) unsigned long long bar;
-    __shared__ int hist[64], hoff[65];   // per-chunk counting sort of stayers by cell
+    __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
     __shared__ int s_ok;
     const int s = blockIdx.y;
@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
     for (int t = tid; t < TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
     if (tid < NCTR) sctr[tid] = 0ull;
-    if (tid < 64) hist[tid] = 0;
     __syncthreads();
     if (tid == 0) {
         mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(float4));
@@ -233,68 +232,40 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
             code = push_one(L, of, kf, dthf, p, ea, acc);
         }
         bool stay = false, mover = false;
-        int lc = 0;   // cell inside the bin (0..63) of a particle that stays
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
             mover = !stay;
-            if (stay) lc = (p.i - x0) + BLK * ((p.j - y0) + BLK * (p.k - z0));
-            else global_deposit_f(L, S.W, p);
+            if (stay) {
+                long long Wf[8];
+                fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
+                    tile_add(Wlo, Whi, t, Wf[l]);
+                }
+            } else {
+                global_deposit_f(L, S.W, p);
+            }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
-        }
-        // warp-aggregated deposit of stayers into the shared fixed-point tile:
-        // lanes in the same cell add their weights with one hardware reduction
-        // per corner and half, and the group's first lane issues the atomics
-        // (particles are kept cell-sorted, so a warp holds few distinct cells)
-        {
-            unsigned grp = __match_any_sync(0xffffffffu, stay ? lc : 64 + lane);
-            bool lead = stay && (lane == __ffs(grp) - 1);
-            long long Wf[8];
-            fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
-#pragma unroll
-            for (int l = 0; l < 8; ++l) {
-                unsigned lo = stay ? (unsigned)(Wf[l] & 0xFFFF) : 0u;
-                unsigned hi = stay ? (unsigned)(Wf[l] >> 16) : 0u;
-                lo = __reduce_add_sync(grp, lo);
-                hi = __reduce_add_sync(grp, hi);
-                if (lead) {
-                    int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
-                    atomicAdd(&Wlo[t], lo);
-                    atomicAdd(&Whi[t], hi);
-                }
-            }
         }
         count_event(&sctr[C_PUSHED], code != NONE);
         count_event(&sctr[C_ABSORBED], code == ABSORBED);
         count_event(&sctr[C_COLLECTED], code == COLLECTED);
         count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
-        // stayers are written back in-place, ordered by their new cell (a block
-        // counting sort of the chunk): the bin stays cell-sorted chunk by chunk
-        int rank = 0;
-        if (stay) rank = atomicAdd(&hist[lc], 1);
+        unsigned bal = __ballot_sync(0xffffffffu, stay);
+        if (lane == 0) wcnt[wid] = __popc(bal);
         __syncthreads();
-        if (wid == 0) {   // exclusive scan of the 64 cell counts (2 per lane)
-            int a0 = hist[2 * lane], a1 = hist[2 * lane + 1];
-            int s = a0 + a1, incl = s;
-            for (int o = 1; o < 32; o <<= 1) {
-                int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            int excl = incl - s;
-            hoff[2 * lane] = excl;
-            hoff[2 * lane + 1] = excl + a0;
-            if (lane == 31) hoff[64] = incl;
-        }
-        __syncthreads();
-        if (stay) store_p(S.binsF, start + nstay + hoff[lc] + rank, p, id, track);
+        int off = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) { int v = wcnt[q]; off += (q < wid) ? v : 0; tot += v; }
+        if (stay) store_p(S.binsF, start + nstay + off + __popc(bal & ((1u << lane) - 1)), p, id, track);
         long long slot = warp_reserve(S.mov_out_n, mover);
         if (mover) {
             if (slot < S.mcap) store_p(S.movF_out, slot, p, id, track);
             else atomicAdd(&S.ctr[C_DROPPED], 1ull);
         }
-        nstay += hoff[64];
+        nstay += tot;
         __syncthreads();
-        if (tid < 64) hist[tid] = 0;
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
