@@ -187,7 +187,8 @@ PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
 __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
-    __shared__ unsigned Wlo[TILE_N], Whi[TILE_N];   // fixed-point tile: low 16 bits / rest
+    // fixed-point tiles, one per warp (no cross-warp contention): low 16 bits / rest
+    __shared__ unsigned Wlo[8 * TILE_N], Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
     if (tid < NCTR) sctr[tid] = 0ull;
     __syncthreads();
     if (tid == 0) {
@@ -221,16 +222,25 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const bool track = L.track;
     const float kf = (float)S.k;
     int nstay = 0;
+    // the next chunk is loaded into registers while this one is processed
+    // (its slots lie beyond every slot this chunk's in-place writes can reach)
+    PF32 pn;
+    long long idn = 0;
+    if (tid < n) {
+        load_p(S.binsF, start + tid, pn);
+        if (track) idn = S.binsF.id[start + tid];
+    }
     for (int base = 0; base < n; base += blockDim.x) {
         const int i = base + tid;
         int code = NONE, acc = -1;
-        PF32 p;
-        long long id = 0;
-        if (i < n) {
-            load_p(S.binsF, start + i, p);
-            if (track) id = S.binsF.id[start + i];
-            code = push_one(L, of, kf, dthf, p, ea, acc);
+        PF32 p = pn;
+        long long id = idn;
+        const int inext = i + blockDim.x;
+        if (inext < n) {
+            load_p(S.binsF, start + inext, pn);
+            if (track) idn = S.binsF.id[start + inext];
         }
+        if (i < n) code = push_one(L, of, kf, dthf, p, ea, acc);
         bool stay = false, mover = false;
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
                     int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
-                    tile_add(Wlo, Whi, t, Wf[l]);
+                    tile_add(Wlo + wid * TILE_N, Whi + wid * TILE_N, t, Wf[l]);
                 }
             } else {
                 global_deposit_f(L, S.W, p);
@@ -269,7 +279,9 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
-        unsigned long long v = (unsigned long long)Wlo[t] + ((unsigned long long)Whi[t] << 16);
+        unsigned long long lo = 0, hi = 0;
+        for (int w = 0; w < nw; ++w) { lo += Wlo[w * TILE_N + t]; hi += Whi[w * TILE_N + t]; }
+        unsigned long long v = lo + (hi << 16);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
