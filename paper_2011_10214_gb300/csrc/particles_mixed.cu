@@ -187,7 +187,9 @@ PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
 __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
-    // fixed-point tiles, one per warp (no cross-warp contention): low 16 bits / rest
+    // fixed-point tile, low 16 bits / rest, with 8 interleaved copies per node
+    // (copy = lane & 7): the lanes of one atomic instruction spread over the
+    // banks instead of colliding on the few nodes of a 4^3-cell bin
     __shared__ unsigned Wlo[8 * TILE_N], Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
                     int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
-                    tile_add(Wlo + wid * TILE_N, Whi + wid * TILE_N, t, Wf[l]);
+                    tile_add(Wlo, Whi, t * 8 + (lane & 7), Wf[l]);
                 }
             } else {
                 global_deposit_f(L, S.W, p);
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
         unsigned long long lo = 0, hi = 0;
-        for (int w = 0; w < nw; ++w) { lo += Wlo[w * TILE_N + t]; hi += Whi[w * TILE_N + t]; }
+        for (int c = 0; c < 8; ++c) { lo += Wlo[t * 8 + c]; hi += Whi[t * 8 + c]; }
         unsigned long long v = lo + (hi << 16);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
