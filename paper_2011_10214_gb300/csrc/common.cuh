@@ -128,15 +128,20 @@ PF_D long long warp_reserve(unsigned long long* counter, bool want) {
     return (long long)(base + __popc(mask & ((1u << lane) - 1)));
 }
 
-// Shared-memory fixed-point tile accumulation with native 32-bit atomics: a
-// weight W <= 2^32 is added as its low 16 bits and the rest (W >> 16) to two
-// uint32 counters.  Exact while a bin holds at most 65535 particles (bins are
-// capped there): each counter then stays below 65535 * 65536 < 2^32.
-PF_D void tile_add(unsigned* lo, unsigned* hi, int t, long long W) {
+// Shared-memory fixed-point tile accumulation with native 32-bit atomics.  A
+// weight W (-2^16 < W <= 2^32: the remainder weight can dip a few units below
+// zero when the other seven round up) is added as its low 16 bits (0..65535)
+// and its arithmetic high part W >> 16 (-1..65536, a signed counter).  A bin
+// holds at most BIN_MAX particles, so |low sum| and |high sum| stay below 2^31
+// and tile_value() restores the exact int64 total.
+PF_D void tile_add(unsigned* lo, int* hi, int t, long long W) {
     atomicAdd(&lo[t], (unsigned)(W & 0xFFFF));
-    atomicAdd(&hi[t], (unsigned)(W >> 16));
+    atomicAdd(&hi[t], (int)(W >> 16));
 }
-constexpr int BIN_MAX = 65535;
+PF_D long long tile_value(unsigned lo, int hi) { return (long long)lo + ((long long)hi << 16); }
+constexpr int BIN_MAX = 32767;
+// corner offsets in a (BLK+1)^3 tile, node order 000,100,010,110,001,101,011,111
+PF_D int tile_corner(int l) { return (l & 1) + TILE * ((l >> 1) & 1) + TILE * TILE * ((l >> 2) & 1); }
 
 // ---------------------------------------------------------------------------
 // mbarrier + TMA (cp.async.bulk.tensor) helpers

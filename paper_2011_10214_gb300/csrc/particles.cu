@@ -149,7 +149,10 @@ PF_D void count_event(unsigned long long* sctr, bool ev) {
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) double4 Et[TILE_N];
-    __shared__ unsigned Wlo[TILE_N], Whi[TILE_N];   // fixed-point tile: low 16 bits / rest
+    // fixed-point tile (low 16 bits / signed high part) with 8 interleaved
+    // copies per node, copy = lane & 7, to spread the atomics over the banks
+    __shared__ unsigned Wlo[8 * TILE_N];
+    __shared__ int Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0; }
     if (tid < NCTR) sctr[tid] = 0ull;
     __syncthreads();
     if (tid == 0) {
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
                     int t = (w.ci - x0 + (l & 1)) + TILE * ((w.cj - y0 + ((l >> 1) & 1)) + TILE * (w.ck - z0 + ((l >> 2) & 1)));
-                    tile_add(Wlo, Whi, t, Wf[l]);
+                    tile_add(Wlo, Whi, t * 8 + (lane & 7), Wf[l]);
                 }
             } else {
                 global_deposit(L, S.W, w);
@@ -246,11 +249,12 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
-        unsigned long long v = (unsigned long long)Wlo[t] + ((unsigned long long)Whi[t] << 16);
+        long long v = 0;
+        for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
-        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], v);
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
     }
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
 }

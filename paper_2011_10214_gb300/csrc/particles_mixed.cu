@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     // fixed-point tile, low 16 bits / rest, with 8 interleaved copies per node
     // (copy = lane & 7): the lanes of one atomic instruction spread over the
     // banks instead of colliding on the few nodes of a 4^3-cell bin
-    __shared__ unsigned Wlo[8 * TILE_N], Whi[8 * TILE_N];
+    __shared__ unsigned Wlo[8 * TILE_N];
+    __shared__ int Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
     __shared__ unsigned long long sctr[NCTR];
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0u; }
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0; }
     if (tid < NCTR) sctr[tid] = 0ull;
     __syncthreads();
     if (tid == 0) {
@@ -281,13 +282,12 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     }
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
-        unsigned long long lo = 0, hi = 0;
-        for (int c = 0; c < 8; ++c) { lo += Wlo[t * 8 + c]; hi += Whi[t * 8 + c]; }
-        unsigned long long v = lo + (hi << 16);
+        long long v = 0;
+        for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
-        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], v);
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
     }
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
 }

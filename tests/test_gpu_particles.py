@@ -104,3 +104,30 @@ def test_injection_matches_oracle():
         for k in ("x", "y", "z", "vx", "vy", "vz"):
             assert np.allclose(g[k], o[k], rtol=1e-12, atol=1e-12), k
     gpu.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_deposit_with_negative_remainder_weight(precision):
+    """Particles a hair above a cell face: the seven rounded weights can sum past
+    2^32, so the remainder weight is negative; node sums must stay exact."""
+    gpu, orc = make_pair("sphere16", dt=0.05, precision=precision)
+    add_species_both(gpu, orc, -1.0, 1.0, 0.01)
+    g = np.random.default_rng(17)
+    n = 4000
+    x = 3.0 + g.uniform(0, 1, n)
+    y = 2.0 + g.uniform(0, 1, n)
+    z = 1.0 + g.choice([1e-13, 1e-12, 2.0 ** -40, 3e-14], n)
+    zero = np.zeros(n)
+    ids = np.arange(n, dtype=np.int64)
+    gpu.load_particles(0, x, y, z, zero, zero, zero, ids)
+    orc.load_particles(0, x, y, z, zero, zero, zero, ids)
+    E = np.zeros((orc.mesh.nnodes, 3))
+    gpu.set_external_E(E); orc.set_external_E(E)
+    gpu.step(1); orc.step()
+    W = gpu.node_charge(0)
+    assert W.sum() == 2 ** 32 * n
+    if precision == 0:
+        assert np.array_equal(W, orc.W[0])
+    else:
+        assert np.abs(W - orc.W[0]).max() <= 1e-4 * 2 ** 32 * 8
+    gpu.close()
