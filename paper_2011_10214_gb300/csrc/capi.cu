@@ -18,7 +18,6 @@ cudaError_t set_mixed_tables(const TetTables& t);
 cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double* relres);
 cudaError_t read_pcg_state(Ctx& c);
 int solve_graph_fixed_kernels(const Ctx& c);
-cudaError_t build_pcg_graph_mixed(Ctx& c);
 cudaError_t launch_pcg_mixed(Ctx& c);
 cudaError_t alloc_parrf(PArrF& a, long long n, bool id);
 void free_parrf(PArrF& a);
@@ -191,8 +190,11 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.r, sizeof(double) * N);
     ALLOC(c.p, sizeof(double) * N);
     ALLOC(c.q, sizeof(double) * N);
-    ALLOC(c.z, sizeof(double) * N);
-    ALLOC(c.zf, sizeof(float) * N);
+    // z / zf: the persistent PCG reads them in 16-byte vectors, up to 16 entries past N
+    ALLOC(c.z, sizeof(double) * (N + 16));
+    ALLOC(c.zf, sizeof(float) * (N + 16));
+    CUDA_OK(szero(c.stream, c.z, sizeof(double) * (N + 16)));
+    CUDA_OK(szero(c.stream, c.zf, sizeof(float) * (N + 16)));
     ALLOC(c.rf, sizeof(float) * N);
     ALLOC(c.pf, sizeof(float) * N);
     ALLOC(c.qf, sizeof(float) * N);
@@ -304,7 +306,6 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     CUDA_OK(launch_field_lift(c));
     CUDA_OK(cudaStreamSynchronize(c.stream));
     CUDA_OK(build_pcg_graph(c));
-    if (c.precision == PIFEPIC_MIXED) CUDA_OK(build_pcg_graph_mixed(c));
     pifepic_status st = encode_tmaps(ctx);
     if (st) return st;
     c.have_object = true;

@@ -290,6 +290,7 @@ int solve_graph_fixed_kernels(const Ctx& c) { return (c.ncut > 0) + (c.nit > 0) 
 // The solve as one CUDA graph (both precisions): q_T -> RHS -> warm start ->
 // persistent PCG -> node field
 cudaError_t build_pcg_graph(Ctx& c) {
+    plan_pcg(c);
     if (c.pcg_exec) { cudaGraphExecDestroy(c.pcg_exec); c.pcg_exec = nullptr; }
     if (c.pcg_graph) { cudaGraphDestroy(c.pcg_graph); c.pcg_graph = nullptr; }
     cudaStream_t cs;
@@ -308,7 +309,6 @@ cudaError_t build_pcg_graph(Ctx& c) {
     cudaStreamDestroy(cs);
     return e;
 }
-cudaError_t build_pcg_graph_mixed(Ctx& c) { return build_pcg_graph(c); }
 
 static cudaError_t set_pcg_state(Ctx& c) {
     PcgState h = {};

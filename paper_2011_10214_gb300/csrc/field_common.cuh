@@ -37,10 +37,11 @@ static __device__ __forceinline__ T ldx(const T* x, long long i) {
     else return x[i];
 }
 
-// y_n = (A x)_n for the IFE operator; Dirichlet rows give 0 (x is 0 there)
-template <typename T, bool CG = false>
-static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, int i, int j, int k, const T* x,
-                                              const T* coef) {
+// y_n = (A x)_n for the IFE operator; Dirichlet rows give 0 (x is 0 there).
+// ld(m) returns x_m (from global memory or from a shared-memory window).
+template <typename T, typename LD>
+static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n, int i, int j, int k, LD ld,
+                                                 const T* coef) {
     const Mesh& m = f.m;
     int ty = f.ntype[n];
     if (ty == -3) return (T)0;
@@ -48,26 +49,26 @@ static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, i
     bool xm = i > 0, xp = i < m.nx, ym = j > 0, yp = j < m.ny, zm = k > 0, zp = k < m.nz;
     if (ty >= 0) {
         const T* c = coef + (long long)ty * 19;
-        T y = c[0] * ldx<CG>(x, n);
-        if (xm) y += c[1] * ldx<CG>(x, n - sx);
-        if (xp) y += c[2] * ldx<CG>(x, n + sx);
-        if (ym) y += c[3] * ldx<CG>(x, n - sy);
-        if (yp) y += c[4] * ldx<CG>(x, n + sy);
-        if (zm) y += c[5] * ldx<CG>(x, n - sz);
-        if (zp) y += c[6] * ldx<CG>(x, n + sz);
+        T y = c[0] * ld(n);
+        if (xm) y += c[1] * ld(n - sx);
+        if (xp) y += c[2] * ld(n + sx);
+        if (ym) y += c[3] * ld(n - sy);
+        if (yp) y += c[4] * ld(n + sy);
+        if (zm) y += c[5] * ld(n - sz);
+        if (zp) y += c[6] * ld(n + sz);
         if ((i + j + k) & 1) return y;
-        if (xm && ym) y += c[7] * ldx<CG>(x, n - sx - sy);
-        if (xp && ym) y += c[8] * ldx<CG>(x, n + sx - sy);
-        if (xm && yp) y += c[9] * ldx<CG>(x, n - sx + sy);
-        if (xp && yp) y += c[10] * ldx<CG>(x, n + sx + sy);
-        if (xm && zm) y += c[11] * ldx<CG>(x, n - sx - sz);
-        if (xp && zm) y += c[12] * ldx<CG>(x, n + sx - sz);
-        if (xm && zp) y += c[13] * ldx<CG>(x, n - sx + sz);
-        if (xp && zp) y += c[14] * ldx<CG>(x, n + sx + sz);
-        if (ym && zm) y += c[15] * ldx<CG>(x, n - sy - sz);
-        if (yp && zm) y += c[16] * ldx<CG>(x, n + sy - sz);
-        if (ym && zp) y += c[17] * ldx<CG>(x, n - sy + sz);
-        if (yp && zp) y += c[18] * ldx<CG>(x, n + sy + sz);
+        if (xm && ym) y += c[7] * ld(n - sx - sy);
+        if (xp && ym) y += c[8] * ld(n + sx - sy);
+        if (xm && yp) y += c[9] * ld(n - sx + sy);
+        if (xp && yp) y += c[10] * ld(n + sx + sy);
+        if (xm && zm) y += c[11] * ld(n - sx - sz);
+        if (xp && zm) y += c[12] * ld(n + sx - sz);
+        if (xm && zp) y += c[13] * ld(n - sx + sz);
+        if (xp && zp) y += c[14] * ld(n + sx + sz);
+        if (ym && zm) y += c[15] * ld(n - sy - sz);
+        if (yp && zm) y += c[16] * ld(n + sy - sz);
+        if (ym && zp) y += c[17] * ld(n - sy + sz);
+        if (yp && zp) y += c[18] * ld(n + sy + sz);
         return y;
     }
     // regular row: assembled P1 stencil of the 5-tet split with eps of the region;
@@ -76,34 +77,40 @@ static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, i
     T h = (T)m.h;
     int cx = (int)xm + (int)xp, cy = (int)ym + (int)yp, cz = (int)zm + (int)zp;
     bool odd = (i + j + k) & 1;
-    T y = (T)(cx * cy * cz) * (odd ? (T)0.5 : (T)0.75) * h * ldx<CG>(x, n);
+    T y = (T)(cx * cy * cz) * (odd ? (T)0.5 : (T)0.75) * h * ld(n);
     T ax = (T)0, ay = (T)0, az = (T)0;
-    if (xm) ax += ldx<CG>(x, n - sx);
-    if (xp) ax += ldx<CG>(x, n + sx);
-    if (ym) ay += ldx<CG>(x, n - sy);
-    if (yp) ay += ldx<CG>(x, n + sy);
-    if (zm) az += ldx<CG>(x, n - sz);
-    if (zp) az += ldx<CG>(x, n + sz);
+    if (xm) ax += ld(n - sx);
+    if (xp) ax += ld(n + sx);
+    if (ym) ay += ld(n - sy);
+    if (yp) ay += ld(n + sy);
+    if (zm) az += ld(n - sz);
+    if (zp) az += ld(n + sz);
     T h6 = h / (T)6;
     y -= h6 * ((T)(cy * cz) * ax + (T)(cx * cz) * ay + (T)(cx * cy) * az);
     if (!odd) {
         T dxy = (T)0, dxz = (T)0, dyz = (T)0;
-        if (xm && ym) dxy += ldx<CG>(x, n - sx - sy);
-        if (xp && ym) dxy += ldx<CG>(x, n + sx - sy);
-        if (xm && yp) dxy += ldx<CG>(x, n - sx + sy);
-        if (xp && yp) dxy += ldx<CG>(x, n + sx + sy);
-        if (xm && zm) dxz += ldx<CG>(x, n - sx - sz);
-        if (xp && zm) dxz += ldx<CG>(x, n + sx - sz);
-        if (xm && zp) dxz += ldx<CG>(x, n - sx + sz);
-        if (xp && zp) dxz += ldx<CG>(x, n + sx + sz);
-        if (ym && zm) dyz += ldx<CG>(x, n - sy - sz);
-        if (yp && zm) dyz += ldx<CG>(x, n + sy - sz);
-        if (ym && zp) dyz += ldx<CG>(x, n - sy + sz);
-        if (yp && zp) dyz += ldx<CG>(x, n + sy + sz);
+        if (xm && ym) dxy += ld(n - sx - sy);
+        if (xp && ym) dxy += ld(n + sx - sy);
+        if (xm && yp) dxy += ld(n - sx + sy);
+        if (xp && yp) dxy += ld(n + sx + sy);
+        if (xm && zm) dxz += ld(n - sx - sz);
+        if (xp && zm) dxz += ld(n + sx - sz);
+        if (xm && zp) dxz += ld(n - sx + sz);
+        if (xp && zp) dxz += ld(n + sx + sz);
+        if (ym && zm) dyz += ld(n - sy - sz);
+        if (yp && zm) dyz += ld(n + sy - sz);
+        if (ym && zp) dyz += ld(n - sy + sz);
+        if (yp && zp) dyz += ld(n + sy + sz);
         T h12 = h / (T)12;
         y -= h12 * ((T)cz * dxy + (T)cy * dxz + (T)cx * dyz);
     }
     return eps * y;
+}
+
+template <typename T, bool CG = false>
+static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, int i, int j, int k, const T* x,
+                                              const T* coef) {
+    return apply_row_ld<T>(f, n, i, j, k, [&](long long m) { return ldx<CG>(x, m); }, coef);
 }
 
 static __device__ __forceinline__ void node_ijk(const Mesh& m, long long n, int& i, int& j, int& k) {

@@ -148,6 +148,12 @@ struct Ctx {
     double* coop_partial = nullptr; // [8][2048] block partials of the persistent PCG
     double* scal = nullptr;        // PCG scalars
     unsigned int* red_ticket = nullptr;
+    // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
+    // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
+    int pcg_npt = -1;
+    int pcg_G = 1;
+    long long pcg_M = 0;
+    size_t pcg_smem = 0;
     int* err_word = nullptr;
     // graphs
     cudaGraphExec_t pcg_exec = nullptr;
@@ -209,6 +215,7 @@ cudaError_t set_tet_tables(const TetTables& t);
 cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
 cudaError_t launch_field_lift(Ctx& c);
 cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
+void plan_pcg(Ctx& c);                                 // pcg_coop.cu
 cudaError_t launch_rhs(Ctx& c);
 cudaError_t launch_pcg(Ctx& c);
 cudaError_t launch_node_E(Ctx& c);

@@ -235,6 +235,277 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
     }
 }
 
+// ---- register-resident PCG --------------------------------------------------
+//
+// When a full-occupancy grid gives every thread at most 8 nodes, block b owns
+// the contiguous nodes [b*M, (b+1)*M) and its thread t the nodes
+// b*M + t + s*REG_THREADS (s < NPT); all PCG vectors of those nodes live in
+// registers.  Only z = D^-1 r, which the operator reads at neighbouring nodes,
+// goes through global memory (it stays in L2): before each matrix product a
+// block copies the window of z its rows touch -- its own range plus one
+// z-plane, one row and one node on each side, contiguous in node order -- into
+// shared memory with 16-byte loads, one round trip instead of one per node.
+//
+// Both modes run Jacobi PCG with the q recurrence: two grid exchanges per
+// iteration, one per reduction.  An exchange is the counter barrier above with
+// the block partials in one of two slots by exchange parity, so a block that
+// races ahead into the next exchange never overwrites partials a slower block
+// is still summing.  MIXED wraps FP32 inner solves in FP64 refinement as the
+// global-memory kernel does.  (The pipelined form of PCG would need one
+// exchange per iteration, but its recurrences stagnated on meshes with mostly
+// Neumann faces, in FP32 and with FP64 recurrences alike, so it is not used.)
+
+constexpr int REG_THREADS = 512;
+
+struct RegArgs {
+    FieldArgs f;
+    const double* b;
+    double* u;                 // FP64 unknown (warm start in, solution out)
+    const double* g;           // Dirichlet values
+    double* phi;
+    void* zg;                  // exchanged vector z (T), padded by 16 entries
+    long long M;               // nodes per block
+    double* val;               // [2][4][G] block partials
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    PcgState* S;
+    long long* it_total;
+    long long* outer_total;
+    int* err;
+};
+
+struct ExchShared {
+    double sh[4 * 32];
+    double bc[4];
+    int ok;
+};
+
+// grid exchange number e: publish this block's NV partials, wait for every
+// block, return the grid totals (same in every block); false after a timeout
+template <int NV>
+static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, double (&v)[NV], double (&tot)[NV],
+                                                ExchShared& xs) {
+    block_sum<NV>(v, xs.sh);                  // ends with __syncthreads: the block's z stores are issued
+    const unsigned G = gridDim.x;
+    double* val = a.val + (size_t)(e & 1) * 4 * G;
+    ++e;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) __stcg(val + (size_t)q * G + blockIdx.x, v[q]);
+        volatile unsigned* gen = a.bar_gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(a.bar_count, 1u);
+        int ok = 1;
+        if (arrived == G - 1) {
+            *a.bar_count = 0u;
+            __threadfence();
+            atomicAdd(a.bar_gen, 1u);
+        } else {
+            const long long c0 = clock64();
+            while (*gen == g0)
+                if (clock64() - c0 > (1ll << 31)) { ok = 0; atomicOr(a.err, ERR_BARRIER_TIMEOUT); break; }
+        }
+        __threadfence();
+        xs.ok = ok;
+    }
+    __syncthreads();
+    if (!xs.ok) return false;
+    double s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) s[q] = threadIdx.x < G ? __ldcg(val + (size_t)q * G + threadIdx.x) : 0.0;
+    block_sum<NV>(s, xs.sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) xs.bc[q] = s[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = xs.bc[q];
+    return true;
+}
+
+static __device__ __forceinline__ unsigned pack_ijk(int i, int j, int k) {
+    return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22);
+}
+template <typename T, typename LD>
+static __device__ __forceinline__ T row_at(const FieldArgs& f, long long n, unsigned pk, LD ld, const T* coef) {
+    return apply_row_ld<T>(f, n, (int)(pk & 2047u), (int)((pk >> 11) & 2047u), (int)(pk >> 22), ld, coef);
+}
+
+// the window of z a block's rows read: [ws, we), both multiples of the 16-byte
+// vector, we <= N rounded up (inside the padded allocation)
+template <typename T>
+static __host__ __device__ __forceinline__ void z_window(long long N, long long NX, long long NXY, long long b0,
+                                                         long long b1, long long& ws, long long& we) {
+    constexpr long long VEC = 16 / sizeof(T);
+    const long long halo = NXY + NX + 1;
+    ws = b0 - halo;
+    if (ws < 0) ws = 0;
+    ws -= ws % VEC;
+    we = b1 + halo;
+    if (we > N) we = N;
+    we = (we + VEC - 1) / VEC * VEC;
+}
+
+// Jacobi PCG, vectors in registers.  FP64 mode: one pass in FP64.  MIXED: FP64
+// refinement (true residual of u in FP64) around FP32 inner solves for x.
+template <bool MIXED, int NPT>
+__global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    using V = typename std::conditional<MIXED, float4, double2>::type;
+    constexpr int VEC = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char win_raw[];
+    T* win = (T*)win_raw;
+    __shared__ ExchShared xs;
+    const FieldArgs& f = a.f;
+    const long long N = f.m.nnodes;
+    const long long b0 = (long long)blockIdx.x * a.M;
+    const long long b1 = b0 + a.M < N ? b0 + a.M : N;
+    long long ws, we;
+    z_window<T>(N, f.m.NX, (long long)f.m.NX * f.m.NY, b0, b1, ws, we);
+    const int nvec = (int)((we - ws) / VEC);
+    T* zg = (T*)a.zg;
+    const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
+    const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
+    const double tol2 = a.S->tol2;
+    const int maxit = a.S->maxit;
+    auto ldw = [&](long long m) { return win[m - ws]; };
+    auto ldu = [&](long long m) { return __ldcg(a.u + m); };
+    int e = 0;
+    unsigned pk[NPT];
+    T dv[NPT];
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+        const long long n = b0 + threadIdx.x + s * REG_THREADS;
+        pk[s] = 0;
+        dv[s] = (T)0;
+        if (n < b1) {
+            int i, j, kk;
+            node_ijk(f.m, n, i, j, kk);
+            pk[s] = pack_ijk(i, j, kk);
+            dv[s] = dinv[n];
+        }
+    }
+    int it = 0, outer = 0;
+    double bb = 0.0, rr = 0.0;
+    bool conv = false, alive = true;
+    for (;;) {
+        // true residual of u in FP64 (neighbours of u through L2); z = D^-1 r, p = z
+        T x[NPT], r[NPT], z[NPT], p[NPT], q[NPT];
+        double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int s = 0; s < NPT; ++s) {
+            const long long n = b0 + threadIdx.x + s * REG_THREADS;
+            x[s] = r[s] = z[s] = p[s] = q[s] = (T)0;
+            if (n < b1) {
+                const double bn = a.b[n];
+                const double rn = (f.ntype[n] == -3) ? 0.0 : bn - row_at<double>(f, n, pk[s], ldu, f.coef);
+                r[s] = (T)rn;
+                z[s] = dv[s] * r[s];
+                p[s] = z[s];
+                zg[n] = z[s];
+                v3[0] += bn * bn;
+                v3[1] += rn * rn;
+                v3[2] += (double)r[s] * (double)z[s];
+            }
+        }
+        double t3[3];
+        if (!(alive = exchange<3>(a, e, v3, t3, xs))) break;
+        if (outer == 0) bb = t3[0];
+        rr = t3[1];
+        double rz = t3[2];
+        conv = (bb == 0.0) || (rr <= tol2 * bb);
+        if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
+        // inner target: the final tolerance, or (MIXED) a 1e-4 reduction of this residual
+        const double rr_stop = MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb;
+        ++outer;
+        double beta = 0.0, rr_in = rr;
+        bool first = true;
+        for (;;) {
+            // stage the z window (the last exchange ordered every block's z stores
+            // and every read of the previous window)
+            {
+                const V* src = (const V*)(zg + ws);
+                V* dst = (V*)win;
+                for (int c = threadIdx.x; c < nvec; c += REG_THREADS) dst[c] = __ldcg(src + c);
+            }
+            __syncthreads();
+            // p = z + beta p, q = A z + beta q (= A p); first pass: q = A z
+            double v1[1] = {0.0};
+            const T bt = (T)beta;
+#pragma unroll
+            for (int s = 0; s < NPT; ++s) {
+                const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                if (n < b1) {
+                    const T az = row_at<T>(f, n, pk[s], ldw, coef);
+                    if (first) {
+                        q[s] = az;
+                    } else {
+                        p[s] = z[s] + bt * p[s];
+                        q[s] = az + bt * q[s];
+                    }
+                    v1[0] += (double)p[s] * (double)q[s];
+                }
+            }
+            first = false;
+            double pq[1];
+            if (!(alive = exchange<1>(a, e, v1, pq, xs))) break;
+            const double alpha = rz / pq[0];
+            const T al = (T)alpha;
+            double v2[2] = {0.0, 0.0};
+#pragma unroll
+            for (int s = 0; s < NPT; ++s) {
+                const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                if (n < b1) {
+                    x[s] = x[s] + al * p[s];
+                    r[s] = r[s] - al * q[s];
+                    z[s] = dv[s] * r[s];
+                    zg[n] = z[s];
+                    v2[0] += (double)r[s] * (double)r[s];
+                    v2[1] += (double)r[s] * (double)z[s];
+                }
+            }
+            double t2[2];
+            if (!(alive = exchange<2>(a, e, v2, t2, xs))) break;
+            beta = t2[1] / rz;
+            rz = t2[1];
+            rr_in = t2[0];
+            ++it;
+            if (rr_in <= rr_stop || it >= maxit) break;
+        }
+        if (!alive) break;
+        // u += x; MIXED: an exchange so that the next residual sees the new u
+#pragma unroll
+        for (int s = 0; s < NPT; ++s) {
+            const long long n = b0 + threadIdx.x + s * REG_THREADS;
+            if (n < b1) a.u[n] = a.u[n] + (double)x[s];
+        }
+        if (!MIXED) {
+            rr = rr_in;
+            conv = rr <= tol2 * bb;
+            break;
+        }
+        double v0[1] = {0.0}, t0s[1];
+        if (!(alive = exchange<1>(a, e, v0, t0s, xs))) break;
+    }
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+        const long long n = b0 + threadIdx.x + s * REG_THREADS;
+        if (n < b1) a.phi[n] = (bb == 0.0) ? a.g[n] : a.u[n] + a.g[n];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        PcgState* S = a.S;
+        S->bb = bb;
+        S->rr = rr;
+        S->it = it;
+        S->outer_it = outer;
+        S->converged = alive && conv;
+        S->relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        *a.it_total += it;
+        *a.outer_total += MIXED ? outer : 0;
+    }
+}
+
 static int coop_grid(Ctx& c, bool mixed) {
     int dev = c.device, nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -247,9 +518,98 @@ static int coop_grid(Ctx& c, bool mixed) {
     return (int)(g > 0 ? g : 1);
 }
 
+template <bool MIXED, int NPT>
+static void* reg_kernel() { return (void*)k_pcg_reg<MIXED, NPT>; }
+
+static void* reg_kernel(bool mixed, int npt) {
+    switch (npt) {
+        case 1: return mixed ? reg_kernel<true, 1>() : reg_kernel<false, 1>();
+        case 2: return mixed ? reg_kernel<true, 2>() : reg_kernel<false, 2>();
+        case 4: return mixed ? reg_kernel<true, 4>() : reg_kernel<false, 4>();
+        case 8: return mixed ? reg_kernel<true, 8>() : reg_kernel<false, 8>();
+        default: return nullptr;
+    }
+}
+
+// nodes per thread, grid and shared memory of the register-resident kernel for
+// this mesh (stored in the context; called before any capture of the solve);
+// npt = 0 if it needs more than 8 nodes per thread or a z window larger than
+// shared memory
+void plan_pcg(Ctx& c) {
+    const bool mixed = c.precision == PIFEPIC_MIXED;
+    c.pcg_npt = 0;
+    int dev = c.device, nsm = 0, smem_max = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const long long N = c.mesh.nnodes;
+    const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+    long long G = (N + REG_THREADS - 1) / REG_THREADS;
+    if (G > nsm) G = nsm;          // one 512-thread block per SM (registers allow no more)
+    if (G > REG_THREADS) G = REG_THREADS;   // exchange totals: one partial per thread
+    if (G < 1) G = 1;
+    const long long M = (N + G - 1) / G;
+    const long long npt = (M + REG_THREADS - 1) / REG_THREADS;
+    int pick = npt <= 1 ? 1 : npt <= 2 ? 2 : npt <= 4 ? 4 : npt <= 8 ? 8 : 0;
+    if (!pick) return;
+    // largest window over the blocks, plus one vector of slack
+    const long long NX = c.mesh.NX, NXY = (long long)c.mesh.NX * c.mesh.NY;
+    long long wmax = 0;
+    for (long long bl = 0; bl < G; ++bl) {
+        long long ws, we, b0 = bl * M, b1 = b0 + M < N ? b0 + M : N;
+        if (mixed) z_window<float>(N, NX, NXY, b0, b1, ws, we);
+        else z_window<double>(N, NX, NXY, b0, b1, ws, we);
+        if (we - ws > wmax) wmax = we - ws;
+    }
+    const size_t smem = (size_t)wmax * tsz;
+    const size_t static_smem = sizeof(ExchShared) + 64;
+    if (smem + static_smem > (size_t)smem_max) return;
+    void* kern = reg_kernel(mixed, pick);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, REG_THREADS, smem);
+    if (per < 1) return;
+    c.pcg_npt = pick;
+    c.pcg_G = (int)G;
+    c.pcg_M = M;
+    c.pcg_smem = smem;
+}
+
+static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
+    RegArgs a;
+    a.f.m = c.mesh; a.f.o = c.obj; a.f.ntype = c.ntype; a.f.coef = c.patch_coef; a.f.coeff = c.patch_coeff;
+    a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;
+    a.b = c.b; a.u = c.u; a.g = c.gdir; a.phi = c.phi;
+    a.zg = mixed ? (void*)c.zf : (void*)c.z;
+    a.M = c.pcg_M;
+    a.val = c.coop_partial;
+    a.bar_count = c.red_ticket + 1;
+    a.bar_gen = c.red_ticket + 2;
+    a.S = (PcgState*)c.scal;
+    a.it_total = (long long*)(c.scal + 40);
+    a.outer_total = (long long*)(c.scal + 41);
+    a.err = c.err_word;
+    void* args[] = {&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.pcg_G);
+    cfg.blockDim = dim3(REG_THREADS);
+    cfg.dynamicSmemBytes = c.pcg_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, reg_kernel(mixed, c.pcg_npt), args);
+}
+
 // the PCG state must already hold tol2 and maxit; writes phi
 cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     bool mixed = c.precision == PIFEPIC_MIXED;
+    if (c.pcg_npt < 0) plan_pcg(c);
+    if (c.pcg_npt > 0) return launch_reg(c, st, mixed);
     CoopArgs a;
     a.f.m = c.mesh; a.f.o = c.obj; a.f.ntype = c.ntype; a.f.coef = c.patch_coef; a.f.coeff = c.patch_coeff;
     a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;

@@ -78,3 +78,34 @@ def test_manufactured_sphere_on_gpu():
         phi_o, _, _ = fs.solve(F, np.full(nit, ep * gamma / R ** 2), tol=1e-12, maxit=5000)
         assert _rel(sim.potential(), phi_o) <= TOL_PHI
         sim.close()
+
+
+@pytest.mark.parametrize("n", [48, 64, 80])
+def test_solve_sizes_of_every_nodes_per_thread_variant(n):
+    """Meshes whose node count puts 2, 4 and 8 nodes on each thread of the
+    register-resident PCG (one 512-thread block per SM): both precisions reach
+    the oracle's FP64 solution at tol 1e-12."""
+    from oracle.field import FieldSystem
+    from oracle.geometry import Mesh, Sphere
+    from paper_2011_10214_gb300 import capi
+    m = Mesh(n, n, n, 0.5)
+    c = n * 0.25
+    R = n * 0.1
+    fs = FieldSystem(m, Sphere(m, (c, c, c), R, 4.0, 1.0), [("D", 0.0)] * 6)
+    g = np.random.default_rng(3)
+    F = g.normal(size=m.nnodes) * m.h ** 3
+    q = g.normal(size=len(fs.it_cell))
+    phi_o, it_o, _ = fs.solve(F, q, tol=1e-12, maxit=5000)
+    for precision in (capi.FP64, capi.MIXED):
+        sim = capi.Simulation((n, n, n), 0.5, 0.05, precision=precision, pcg_tol=1e-12, pcg_max_iter=5000)
+        sim.set_field_bc([("D", 0.0)] * 6)
+        sim.set_object(capi.OBJ_SPHERE, [c, c, c, R], 4.0, 1.0)
+        it, rr = sim.solve_field(F, q)
+        assert rr <= 1e-12, (precision, rr)
+        assert _rel(sim.potential(), phi_o) <= TOL_PHI, precision
+        if precision == capi.FP64:
+            assert abs(it - it_o) <= max(3, 0.05 * it_o), (it, it_o)
+        # a second solve from the converged state (warm start) stops at once
+        it2, rr2 = sim.solve_field(F, q)
+        assert rr2 <= 1e-12 and it2 <= 2, (precision, it2)
+        sim.close()
