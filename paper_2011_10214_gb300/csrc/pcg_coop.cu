@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
 // shared memory with 16-byte loads, one round trip instead of one per node.
 //
 // Both modes run Jacobi PCG with the q recurrence: two grid exchanges per
-// iteration, one per reduction.  An exchange is the counter barrier above with
+// iteration, one per reduction.  Inner-loop dot products, block sums and the
+// scalars alpha and beta are in the working precision (FP32 in MIXED mode; the
+// outer FP64 residual corrects what FP32 inner products lose).  An exchange is the counter barrier above with
 // the block partials in one of two slots by exchange parity, so a block that
 // races ahead into the next exchange never overwrites partials a slower block
 // is still summing.  MIXED wraps FP32 inner solves in FP64 refinement as the
@@ -280,14 +282,40 @@ struct ExchShared {
     int ok;
 };
 
+// deterministic block sum of NV values of type A (thread 0 gets the totals);
+// A = float keeps the MIXED inner loop off the FP64 pipe, which issues a warp
+// instruction only every few dozen cycles on this part
+template <typename A, int NV>
+static __device__ __forceinline__ void block_sum_t(A (&v)[NV], A* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        A s = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[q * 32 + w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            A s = lane < nw ? sh[q * 32 + lane] : (A)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
 // grid exchange number e: publish this block's NV partials, wait for every
 // block, return the grid totals (same in every block); false after a timeout
-template <int NV>
-static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, double (&v)[NV], double (&tot)[NV],
-                                                ExchShared& xs) {
-    block_sum<NV>(v, xs.sh);                  // ends with __syncthreads: the block's z stores are issued
+template <typename A, int NV>
+static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, A (&v)[NV], A (&tot)[NV], ExchShared& xs) {
+    A* sh = (A*)xs.sh;
+    block_sum_t<A, NV>(v, sh);                // ends with __syncthreads: the block's z stores are issued
     const unsigned G = gridDim.x;
-    double* val = a.val + (size_t)(e & 1) * 4 * G;
+    A* val = (A*)a.val + (size_t)(e & 1) * 4 * G;
     ++e;
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -311,16 +339,17 @@ static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, double
     }
     __syncthreads();
     if (!xs.ok) return false;
-    double s[NV];
+    A s[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) s[q] = threadIdx.x < G ? __ldcg(val + (size_t)q * G + threadIdx.x) : 0.0;
-    block_sum<NV>(s, xs.sh);
+    for (int q = 0; q < NV; ++q) s[q] = threadIdx.x < G ? __ldcg(val + (size_t)q * G + threadIdx.x) : (A)0;
+    block_sum_t<A, NV>(s, sh);
+    A* bc = (A*)xs.bc;
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) xs.bc[q] = s[q];
+        for (int q = 0; q < NV; ++q) bc[q] = s[q];
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NV; ++q) tot[q] = xs.bc[q];
+    for (int q = 0; q < NV; ++q) tot[q] = bc[q];
     return true;
 }
 
@@ -410,16 +439,16 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             }
         }
         double t3[3];
-        if (!(alive = exchange<3>(a, e, v3, t3, xs))) break;
+        if (!(alive = exchange<double, 3>(a, e, v3, t3, xs))) break;
         if (outer == 0) bb = t3[0];
         rr = t3[1];
-        double rz = t3[2];
+        T rz = (T)t3[2];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
         // inner target: the final tolerance, or (MIXED) a 1e-4 reduction of this residual
-        const double rr_stop = MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb;
+        const T rr_stop = (T)(MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb);
         ++outer;
-        double beta = 0.0, rr_in = rr;
+        T beta = (T)0, rr_in = (T)rr;
         bool first = true;
         for (;;) {
             // stage the z window (the last exchange ordered every block's z stores
@@ -431,8 +460,8 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             }
             __syncthreads();
             // p = z + beta p, q = A z + beta q (= A p); first pass: q = A z
-            double v1[1] = {0.0};
-            const T bt = (T)beta;
+            T v1[1] = {(T)0};
+            const T bt = beta;
 #pragma unroll
             for (int s = 0; s < NPT; ++s) {
                 const long long n = b0 + threadIdx.x + s * REG_THREADS;
@@ -444,15 +473,14 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
                         p[s] = z[s] + bt * p[s];
                         q[s] = az + bt * q[s];
                     }
-                    v1[0] += (double)p[s] * (double)q[s];
+                    v1[0] += p[s] * q[s];
                 }
             }
             first = false;
-            double pq[1];
-            if (!(alive = exchange<1>(a, e, v1, pq, xs))) break;
-            const double alpha = rz / pq[0];
-            const T al = (T)alpha;
-            double v2[2] = {0.0, 0.0};
+            T pq[1];
+            if (!(alive = exchange<T, 1>(a, e, v1, pq, xs))) break;
+            const T al = rz / pq[0];
+            T v2[2] = {(T)0, (T)0};
 #pragma unroll
             for (int s = 0; s < NPT; ++s) {
                 const long long n = b0 + threadIdx.x + s * REG_THREADS;
@@ -461,12 +489,12 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
                     r[s] = r[s] - al * q[s];
                     z[s] = dv[s] * r[s];
                     zg[n] = z[s];
-                    v2[0] += (double)r[s] * (double)r[s];
-                    v2[1] += (double)r[s] * (double)z[s];
+                    v2[0] += r[s] * r[s];
+                    v2[1] += r[s] * z[s];
                 }
             }
-            double t2[2];
-            if (!(alive = exchange<2>(a, e, v2, t2, xs))) break;
+            T t2[2];
+            if (!(alive = exchange<T, 2>(a, e, v2, t2, xs))) break;
             beta = t2[1] / rz;
             rz = t2[1];
             rr_in = t2[0];
@@ -481,12 +509,12 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             if (n < b1) a.u[n] = a.u[n] + (double)x[s];
         }
         if (!MIXED) {
-            rr = rr_in;
+            rr = (double)rr_in;
             conv = rr <= tol2 * bb;
             break;
         }
-        double v0[1] = {0.0}, t0s[1];
-        if (!(alive = exchange<1>(a, e, v0, t0s, xs))) break;
+        T v0[1] = {(T)0}, t0s[1];
+        if (!(alive = exchange<T, 1>(a, e, v0, t0s, xs))) break;
     }
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
