@@ -179,6 +179,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     for (int f = 0; f < 6; ++f) { c.bc[f].kind = PIFEPIC_BC_DIRICHLET; c.bc[f].value = 0.0; }
     long long N = m.nnodes, C = m.ncells;
     ALLOC(c.Lnode, sizeof(double) * N);
+    ALLOC(c.Lpos, N);
     ALLOC(c.ntype, sizeof(int) * N);
     ALLOC(c.gdir, sizeof(double) * N);
     ALLOC(c.lift, sizeof(double) * N);
@@ -239,7 +240,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (!ctx) return;
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
-    void* ptrs[] = {c.Lnode, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
+    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,
@@ -294,12 +295,14 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     Ctx& c = ctx->c;
     // free a previous interface set-up
     void* old[] = {c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut,
-                   c.patch_node, c.patch_coef, c.patch_coeff, c.surfall};
+                   c.patch_node, c.patch_coef, c.patch_coeff, c.surfall, c.it_dataf};
     for (void* p : old) cudaFree(p);
     c.it_cell = c.it_t = c.it_acc = c.cut_cell = nullptr;
     c.it_data = c.qT = c.cut_area = c.qcut = c.patch_coef = nullptr;
-    c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr;
+    c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr; c.it_dataf = nullptr;
     CUDA_OK(launch_setup(c));
+    ALLOC(c.it_dataf, sizeof(float) * 32 * (c.nit > 0 ? c.nit : 1));
+    CUDA_OK(launch_node_E_tables(c));
     ALLOC(c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1));
     CUDA_OK(szero(c.stream, c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1)));
     for (size_t s = 0; s < c.sp.size(); ++s) c.sp[s].surf = c.surfall + s * (c.ncut > 0 ? c.ncut : 1);
@@ -817,6 +820,8 @@ pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind) {
     NEED(ctx); NEED(E);
     Ctx& c = ctx->c;
     long long N = c.mesh.nnodes;
+    // MIXED steps keep only the FP32 node field; the FP64 one is made here from phi
+    if (c.precision == PIFEPIC_MIXED && !c.external_E && c.have_object) CUDA_OK(launch_node_E64(c));
     double* tmp = nullptr;
     ALLOC(tmp, sizeof(double) * 3 * N);
     k_unpack_E<<<nb256(N), 256, 0, c.stream>>>(N, c.E, tmp);

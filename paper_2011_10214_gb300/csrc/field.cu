@@ -23,6 +23,8 @@
 namespace pf {
 
 __constant__ TetTables cTf;
+__constant__ float cGradF[2][5][4][3];   // cTf.grad in FP32
+__constant__ float cVolF[5];
 
 // ---- right-hand side ----------------------------------------------------------
 struct RhsArgs {
@@ -180,6 +182,116 @@ __global__ void k_node_E(FieldArgs f, const double* L, const unsigned char* imas
     if (Ef) Ef[n] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.0f);
 }
 
+// FP32 copies of what the node field reads, made once per set-up
+__global__ void k_node_E_tables(long long nit, const double* it_data, float* itf, long long N, const double* L,
+                                unsigned char* Lpos) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < nit) {
+        const double* rec = it_data + t * IT_STRIDE;
+        float* o = itf + t * 32;
+        for (int q = 0; q < 15; ++q) o[q] = (float)rec[IT_GP + q];
+        for (int q = 0; q < 15; ++q) o[15 + q] = (float)rec[IT_GM + q];
+        o[30] = (float)rec[IT_VOLP];
+        o[31] = (float)rec[IT_VOLM];
+    }
+    if (t < N) Lpos[t] = L[t] >= 0.0 ? 1 : 0;
+}
+
+// Node field in FP32 (MIXED steps; the push reads only this copy).  Same
+// reading as k_node_E: minus the volume-weighted mean of the element
+// gradients around the node, plasma-side pieces preferred.  A block covers a
+// 32 x 4 x 2 brick of nodes and stages phi of the brick and a one-node halo
+// (34 x 6 x 4) in shared memory, converted to FP32 once.
+constexpr int NE_BX = 32, NE_BY = 4, NE_BZ = 2;
+constexpr int NE_TX = NE_BX + 2, NE_TY = NE_BY + 2, NE_TZ = NE_BZ + 2;
+__global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, const unsigned char* Lpos,
+                                                                    const unsigned char* imask, const int* ibase,
+                                                                    const float* itf, const double* qT,
+                                                                    const double* phi, float4* Ef) {
+    __shared__ float ph[NE_TX * NE_TY * NE_TZ];
+    const int i0 = blockIdx.x * NE_BX, j0 = blockIdx.y * NE_BY, k0 = blockIdx.z * NE_BZ;
+    const int tid = threadIdx.x + NE_BX * (threadIdx.y + NE_BY * threadIdx.z);
+    for (int q = tid; q < NE_TX * NE_TY * NE_TZ; q += NE_BX * NE_BY * NE_BZ) {
+        const int gi = i0 - 1 + q % NE_TX, gj = j0 - 1 + (q / NE_TX) % NE_TY, gk = k0 - 1 + q / (NE_TX * NE_TY);
+        const bool in = gi >= 0 && gj >= 0 && gk >= 0 && gi < m.NX && gj < m.NY && gk < m.NZ;
+        ph[q] = in ? (float)phi[node_id(m, gi, gj, gk)] : 0.0f;
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y, k = k0 + threadIdx.z;
+    if (i >= m.NX || j >= m.NY || k >= m.NZ) return;
+    float apl[3] = {0.f, 0.f, 0.f}, vpl = 0.f, aal[3] = {0.f, 0.f, 0.f}, val = 0.f;
+    const float ih = 1.0f / (float)m.h, V3 = (float)m.h * (float)m.h * (float)m.h;
+    for (int c8 = 0; c8 < 8; ++c8) {
+        const int a = c8 & 1, b = (c8 >> 1) & 1, c = (c8 >> 2) & 1;
+        const int ci = i - a, cj = j - b, ck = k - c;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
+        const long long cell = cell_id(m, ci, cj, ck);
+        const unsigned mk = imask[cell];
+        const int p = (ci + cj + ck) & 1;
+        int T = ibase[cell];
+        // the cube's corner (ci, cj, ck) in the staged brick
+        const int tb = (ci - i0 + 1) + NE_TX * ((cj - j0 + 1) + NE_TY * (ck - k0 + 1));
+        for (int t = 0; t < 5; ++t) {
+            const bool itet = (mk >> t) & 1;
+            bool has = false;
+            for (int v = 0; v < 4; ++v) has |= (cTf.vert[p][t][v] == c8);
+            if (has) {
+                float pv[4];
+                int lv0 = 0;
+                for (int v = 0; v < 4; ++v) {
+                    const int lv = cTf.vert[p][t][v];
+                    if (v == 0) lv0 = lv;
+                    pv[v] = ph[tb + (lv & 1) + NE_TX * (((lv >> 1) & 1) + NE_TY * ((lv >> 2) & 1))];
+                }
+                if (itet) {
+                    const float* rec = itf + (long long)T * 32;
+                    const float qt = (float)qT[T];
+                    float gp[3], gm[3];
+                    for (int d = 0; d < 3; ++d) {
+                        gp[d] = pv[0] * rec[d] + pv[1] * rec[3 + d] + pv[2] * rec[6 + d] + pv[3] * rec[9 + d] +
+                                qt * rec[12 + d];
+                        gm[d] = pv[0] * rec[15 + d] + pv[1] * rec[18 + d] + pv[2] * rec[21 + d] +
+                                pv[3] * rec[24 + d] + qt * rec[27 + d];
+                    }
+                    const float vp = rec[30], vm = rec[31];
+                    if (vp > 0.f) {
+                        for (int d = 0; d < 3; ++d) apl[d] += vp * gp[d];
+                        vpl += vp;
+                    }
+                    for (int d = 0; d < 3; ++d) aal[d] += vp * gp[d] + vm * gm[d];
+                    val += vp + vm;
+                } else {
+                    float g[3];
+                    for (int d = 0; d < 3; ++d)
+                        g[d] = (pv[0] * cGradF[p][t][0][d] + pv[1] * cGradF[p][t][1][d] +
+                                pv[2] * cGradF[p][t][2][d] + pv[3] * cGradF[p][t][3][d]) * ih;
+                    const float V = cVolF[t] * V3;
+                    const int a0 = lv0 & 1, b0 = (lv0 >> 1) & 1, c0 = (lv0 >> 2) & 1;
+                    if (Lpos[node_id(m, ci + a0, cj + b0, ck + c0)]) {
+                        for (int d = 0; d < 3; ++d) apl[d] += V * g[d];
+                        vpl += V;
+                    }
+                    for (int d = 0; d < 3; ++d) aal[d] += V * g[d];
+                    val += V;
+                }
+            }
+            if (itet) ++T;
+        }
+    }
+    float4 e;
+    if (vpl > 0.f) e = make_float4(-apl[0] / vpl, -apl[1] / vpl, -apl[2] / vpl, 0.f);
+    else e = make_float4(-aal[0] / val, -aal[1] / val, -aal[2] / val, 0.f);
+    Ef[node_id(m, i, j, k)] = e;
+}
+
+static void launch_node_E_f(const Ctx& c, cudaStream_t st) {
+    const Mesh& m = c.mesh;
+    dim3 grid((m.NX + NE_BX - 1) / NE_BX, (m.NY + NE_BY - 1) / NE_BY, (m.NZ + NE_BZ - 1) / NE_BZ);
+    k_node_E_f<<<grid, dim3(NE_BX, NE_BY, NE_BZ), 0, st>>>(m, c.Lpos, c.imask, c.ibase, c.it_dataf, c.qT, c.phi,
+                                                          c.Ef);
+}
+
+
 // ---- surface diagnostics: total collected charge, area-mean potential on Gamma_h ----
 __global__ void k_surface_diag(Mesh m, long long nit, const int* it_cell, const int* it_t, const double* it_data,
                                const double* qT, const double* phi, double* partial, unsigned* ticket,
@@ -263,7 +375,8 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
     if (e != cudaSuccess) return e;
     e = launch_pcg_coop(c, st);
     if (e != cudaSuccess) return e;
-    k_node_E<<<nb(N), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
+    else k_node_E<<<nb(N), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
     return cudaGetLastError();
 }
 
@@ -280,7 +393,8 @@ cudaError_t launch_solve_prefix(Ctx& c, cudaStream_t st) {
 }
 cudaError_t launch_solve_suffix(Ctx& c, cudaStream_t st) {
     FieldArgs f = fargs(c);
-    k_node_E<<<nb(c.mesh.nnodes), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
+    else k_node_E<<<nb(c.mesh.nnodes), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
     return cudaGetLastError();
 }
 
@@ -366,14 +480,33 @@ cudaError_t launch_surface_diag(Ctx& c, double* out2) {
     return cudaStreamSynchronize(c.stream);
 }
 
-cudaError_t launch_node_E(Ctx& c) {
-    FieldArgs f = fargs(c);
-    k_node_E<<<nb(c.mesh.nnodes), 256, 0, c.stream>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E,
-                                                      c.Ef);
+cudaError_t launch_node_E_tables(Ctx& c) {
+    long long n = c.nit > c.mesh.nnodes ? c.nit : c.mesh.nnodes;
+    k_node_E_tables<<<nb(n), 256, 0, c.stream>>>(c.nit, c.it_data, c.it_dataf, c.mesh.nnodes, c.Lnode, c.Lpos);
     return cudaGetLastError();
 }
 
-cudaError_t set_field_tables(const TetTables& t) { return cudaMemcpyToSymbol(cTf, &t, sizeof(TetTables)); }
+// FP64 node field from the current phi into E only (the FP32 copy the MIXED
+// push reads is left as the step made it)
+cudaError_t launch_node_E64(Ctx& c) {
+    FieldArgs f = fargs(c);
+    k_node_E<<<nb(c.mesh.nnodes), 256, 0, c.stream>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E,
+                                                      nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t set_field_tables(const TetTables& t) {
+    float g[2][5][4][3], v[5];
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 5; ++q)
+            for (int a = 0; a < 4; ++a)
+                for (int d = 0; d < 3; ++d) g[p][q][a][d] = (float)t.grad[p][q][a][d];
+    for (int q = 0; q < 5; ++q) v[q] = (float)t.vol[q];
+    cudaError_t e = cudaMemcpyToSymbol(cTf, &t, sizeof(TetTables));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGradF, g, sizeof(g));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cVolF, v, sizeof(v));
+    return e;
+}
 
 cudaError_t launch_qtets(Ctx& c) {
     RhsArgs a = rargs(c);

@@ -131,6 +131,8 @@ struct Ctx {
     int* it_cell = nullptr;
     int* it_t = nullptr;
     double* it_data = nullptr;     // IT_STRIDE doubles per tet
+    float* it_dataf = nullptr;     // [nit][32] FP32 node-field subset: GP(15), GM(15), VOLP, VOLM
+    unsigned char* Lpos = nullptr; // per node: level set >= 0 (plasma side)
     int* it_acc = nullptr;
     double* qT = nullptr;
     // cut cells
@@ -213,12 +215,13 @@ enum {
 // ---- launchers ---------------------------------------------------------------
 cudaError_t set_tet_tables(const TetTables& t);
 cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
+cudaError_t launch_node_E_tables(Ctx& c);              // field.cu: it_dataf, Lpos
+cudaError_t launch_node_E64(Ctx& c);                   // field.cu: FP64 E from phi (E only)
 cudaError_t launch_field_lift(Ctx& c);
 cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
 void plan_pcg(Ctx& c);                                 // pcg_coop.cu
 cudaError_t launch_rhs(Ctx& c);
 cudaError_t launch_pcg(Ctx& c);
-cudaError_t launch_node_E(Ctx& c);
 cudaError_t launch_surface_diag(Ctx& c, double* out2);   // [charge, potential]
 cudaError_t launch_qtets(Ctx& c);
 
