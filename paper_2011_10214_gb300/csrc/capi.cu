@@ -211,6 +211,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.coop_partial, sizeof(double) * 8 * 2048);
     ALLOC(c.scal, sizeof(double) * 64);
     ALLOC(c.red_ticket, sizeof(unsigned) * 4);
+    ALLOC(c.bar64, sizeof(unsigned long long) * 4);
     ALLOC(c.err_word, sizeof(int));
     ALLOC(c.next_id, sizeof(long long) * MAX_SPECIES);
     ALLOC(c.inj_count, sizeof(int) * MAX_SPECIES * 6);
@@ -224,6 +225,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     CUDA_OK(szero(c.stream, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR));
     CUDA_OK(szero(c.stream, c.scal, sizeof(double) * 64));
     CUDA_OK(szero(c.stream, c.red_ticket, sizeof(unsigned) * 4));
+    CUDA_OK(szero(c.stream, c.bar64, sizeof(unsigned long long) * 4));
     CUDA_OK(szero(c.stream, c.err_word, sizeof(int)));
     CUDA_OK(szero(c.stream, c.next_id, sizeof(long long) * MAX_SPECIES));
     CUDA_OK(szero(c.stream, c.inj_carry, sizeof(double) * MAX_SPECIES * 6));
@@ -243,7 +245,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
-                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.err_word, c.inj_dev, c.inj_count,
+                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
     for (auto& s : c.sp) {
@@ -725,7 +727,15 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     c.stats = s;
     if (st) *st = s;
     if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
-    if (herr & ERR_BARRIER_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a grid barrier of the PCG solve timed out");
+    if (herr & ERR_BARRIER_TIMEOUT) {
+        // the barrier counters are left mid-count: clear them and the flag so
+        // that a later solve starts from a clean state
+        szero(c.stream, c.red_ticket, sizeof(unsigned) * 4);
+        szero(c.stream, c.bar64, sizeof(unsigned long long) * 4);
+        szero(c.stream, c.err_word, sizeof(int));
+        cudaStreamSynchronize(c.stream);
+        FAIL(PIFEPIC_ETIMEOUT, "a grid barrier of the PCG solve timed out");
+    }
     for (size_t q = 0; q < c.sp.size(); ++q)
         if (s.dropped[q]) FAIL(PIFEPIC_ENOMEM, "species %zu: %lld particles dropped (mover list full)", q,
                                (long long)s.dropped[q]);

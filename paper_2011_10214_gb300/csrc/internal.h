@@ -150,6 +150,7 @@ struct Ctx {
     double* coop_partial = nullptr; // [8][2048] block partials of the persistent PCG
     double* scal = nullptr;        // PCG scalars
     unsigned int* red_ticket = nullptr;
+    unsigned long long* bar64 = nullptr;  // arrival counter of the register-resident PCG (multiple of its grid between launches)
     // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;

@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) k_pcg_coop(CoopArgs a) {
 // Both modes run Jacobi PCG with the q recurrence: two grid exchanges per
 // iteration, one per reduction.  Inner-loop dot products, block sums and the
 // scalars alpha and beta are in the working precision (FP32 in MIXED mode; the
-// outer FP64 residual corrects what FP32 inner products lose).  An exchange is the counter barrier above with
-// the block partials in one of two slots by exchange parity, so a block that
-// races ahead into the next exchange never overwrites partials a slower block
-// is still summing.  MIXED wraps FP32 inner solves in FP64 refinement as the
+// outer FP64 residual corrects what FP32 inner products lose).  An exchange
+// is a monotonic arrival counter (below) with the block partials in one of two
+// slots by exchange parity, so a block that races ahead into the next exchange
+// never overwrites partials a slower block is still summing.  MIXED wraps FP32 inner solves in FP64 refinement as the
 // global-memory kernel does.  (The pipelined form of PCG would need one
 // exchange per iteration, but its recurrences stagnated on meshes with mostly
 // Neumann faces, in FP32 and with FP64 recurrences alike, so it is not used.)
@@ -268,8 +268,7 @@ struct RegArgs {
     void* zg;                  // exchanged vector z (T), padded by 16 entries
     long long M;               // nodes per block
     double* val;               // [2][4][G] block partials
-    unsigned* bar_count;
-    unsigned* bar_gen;
+    unsigned long long* arrivals;  // grows by G per exchange
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -308,8 +307,22 @@ static __device__ __forceinline__ void block_sum_t(A (&v)[NV], A* sh) {
     __syncthreads();
 }
 
+static __device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+static __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // grid exchange number e: publish this block's NV partials, wait for every
-// block, return the grid totals (same in every block); false after a timeout
+// block, return the grid totals (same in every block); false after a timeout.
+// The barrier is one monotonic counter: each block adds 1 with release
+// semantics and waits (acquire) until the count reaches the next multiple of
+// the grid size -- no generation word, no reset, one atomic per block.
 template <typename A, int NV>
 static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, A (&v)[NV], A (&tot)[NV], ExchShared& xs) {
     A* sh = (A*)xs.sh;
@@ -320,21 +333,14 @@ static __device__ __forceinline__ bool exchange(const RegArgs& a, int& e, A (&v)
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) __stcg(val + (size_t)q * G + blockIdx.x, v[q]);
-        volatile unsigned* gen = a.bar_gen;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(a.bar_count, 1u);
+        const unsigned long long t = atom_add_release(a.arrivals, 1ull);
+        const unsigned long long target = (t / G + 1) * G;
         int ok = 1;
-        if (arrived == G - 1) {
-            *a.bar_count = 0u;
-            __threadfence();
-            atomicAdd(a.bar_gen, 1u);
-        } else {
+        if (ld_acquire(a.arrivals) < target) {
             const long long c0 = clock64();
-            while (*gen == g0)
+            while (ld_acquire(a.arrivals) < target)
                 if (clock64() - c0 > (1ll << 31)) { ok = 0; atomicOr(a.err, ERR_BARRIER_TIMEOUT); break; }
         }
-        __threadfence();
         xs.ok = ok;
     }
     __syncthreads();
@@ -613,8 +619,7 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     a.zg = mixed ? (void*)c.zf : (void*)c.z;
     a.M = c.pcg_M;
     a.val = c.coop_partial;
-    a.bar_count = c.red_ticket + 1;
-    a.bar_gen = c.red_ticket + 2;
+    a.arrivals = c.bar64;
     a.S = (PcgState*)c.scal;
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
