@@ -107,6 +107,46 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
     return eps * y;
 }
 
+// The 19 coefficients of row n of the same operator, in the slot order of
+// apply_row_ld (centre, -x, +x, -y, +y, -z, +z, then -x-y, +x-y, -x+y, +x+y,
+// -x-z, +x-z, -x+z, +x+z, -y-z, +y-z, -y+z, +y+z); slots apply_row_ld skips
+// (a neighbour outside the mesh, a diagonal of an odd node, a Dirichlet row)
+// are zero.
+template <typename T>
+static __device__ __forceinline__ void row_coeffs(const FieldArgs& f, long long n, int i, int j, int k,
+                                                  const T* coef, T (&c)[19]) {
+    const Mesh& m = f.m;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) c[q] = (T)0;
+    const int ty = f.ntype[n];
+    if (ty == -3) return;
+    const bool xm = i > 0, xp = i < m.nx, ym = j > 0, yp = j < m.ny, zm = k > 0, zp = k < m.nz;
+    const bool odd = (i + j + k) & 1;
+    const bool has[19] = {true, xm, xp, ym, yp, zm, zp, xm && ym, xp && ym, xm && yp, xp && yp,
+                          xm && zm, xp && zm, xm && zp, xp && zp, ym && zm, yp && zm, ym && zp, yp && zp};
+    if (ty >= 0) {
+        const T* r = coef + (long long)ty * 19;
+#pragma unroll
+        for (int q = 0; q < 19; ++q)
+            if (has[q] && (q < 7 || !odd)) c[q] = r[q];
+        return;
+    }
+    const T eps = (T)(ty == -2 ? f.o.eps_minus : f.o.eps_plus);
+    const T h = (T)m.h;
+    const int cx = (int)xm + (int)xp, cy = (int)ym + (int)yp, cz = (int)zm + (int)zp;
+    c[0] = eps * ((T)(cx * cy * cz) * (odd ? (T)0.5 : (T)0.75) * h);
+    const T a6 = eps * (h / (T)6);
+    const T ax = -a6 * (T)(cy * cz), ay = -a6 * (T)(cx * cz), az = -a6 * (T)(cx * cy);
+    const T axis[6] = {ax, ax, ay, ay, az, az};
+#pragma unroll
+    for (int q = 1; q < 7; ++q) c[q] = has[q] ? axis[q - 1] : (T)0;
+    if (odd) return;
+    const T a12 = eps * (h / (T)12);
+    const T dxy = -a12 * (T)cz, dxz = -a12 * (T)cy, dyz = -a12 * (T)cx;
+#pragma unroll
+    for (int q = 7; q < 19; ++q) c[q] = has[q] ? (q < 11 ? dxy : q < 15 ? dxz : dyz) : (T)0;
+}
+
 template <typename T, bool CG = false>
 static __device__ __forceinline__ T apply_row(const FieldArgs& f, long long n, int i, int j, int k, const T* x,
                                               const T* coef) {

@@ -154,6 +154,7 @@ struct Ctx {
     // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;
+    bool pcg_rows = false;            // operator rows staged in shared memory
     int pcg_G = 1;
     long long pcg_M = 0;
     size_t pcg_smem = 0;

@@ -267,6 +267,7 @@ struct RegArgs {
     double* phi;
     void* zg;                  // exchanged vector z (T), padded by 16 entries
     long long M;               // nodes per block
+    int woff[19];              // staged rows: window offset of each stencil slot
     double* val;               // [2][4][G] block partials
     unsigned long long* arrivals;  // grows by G per exchange
     PcgState* S;
@@ -382,23 +383,46 @@ static __host__ __device__ __forceinline__ void z_window(long long N, long long 
     we = (we + VEC - 1) / VEC * VEC;
 }
 
+// the zero-padded window of the staged-rows variant: [ws, we) around the
+// block's range without clamping to the mesh, so that every stencil slot of
+// every owned node indexes inside it; entries outside [0, N) read as zero
+template <typename T>
+static __host__ __device__ __forceinline__ void z_window_padded(long long NX, long long NXY, long long b0,
+                                                                long long b1, long long& ws, long long& we) {
+    constexpr long long VEC = 16 / sizeof(T);
+    const long long halo = NXY + NX + 1;
+    ws = b0 - halo;
+    ws = (ws >= 0) ? ws - ws % VEC : -(((-ws) + VEC - 1) / VEC) * VEC;
+    we = (b1 + halo + VEC - 1) / VEC * VEC;
+}
+
 // Jacobi PCG, vectors in registers.  FP64 mode: one pass in FP64.  MIXED: FP64
 // refinement (true residual of u in FP64) around FP32 inner solves for x.
-template <bool MIXED, int NPT>
+// ROWS: the block's operator rows are built once into shared memory ([node][19]
+// coefficients) and every matrix product is a branch-free 19-term sum over a
+// zero-padded window; otherwise rows are evaluated from the mesh each time.
+template <bool MIXED, int NPT, bool ROWS>
 __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     using V = typename std::conditional<MIXED, float4, double2>::type;
     constexpr int VEC = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char win_raw[];
-    T* win = (T*)win_raw;
     __shared__ ExchShared xs;
     const FieldArgs& f = a.f;
     const long long N = f.m.nnodes;
+    const long long NXY = (long long)f.m.NX * f.m.NY;
     const long long b0 = (long long)blockIdx.x * a.M;
     const long long b1 = b0 + a.M < N ? b0 + a.M : N;
+    const int nown = (int)(b1 - b0);
+    // staged rows come first (19 T per owned node, rounded to 16 bytes), then the window
+    const size_t rows_bytes = ROWS ? ((size_t)a.M * 19 * sizeof(T) + 15) / 16 * 16 : 0;
+    T* rows = (T*)win_raw;
+    T* win = (T*)(win_raw + rows_bytes);
     long long ws, we;
-    z_window<T>(N, f.m.NX, (long long)f.m.NX * f.m.NY, b0, b1, ws, we);
+    if (ROWS) z_window_padded<T>(f.m.NX, NXY, b0, b1, ws, we);
+    else z_window<T>(N, f.m.NX, NXY, b0, b1, ws, we);
     const int nvec = (int)((we - ws) / VEC);
+    const long long nvec_in = (N + VEC - 1) / VEC;   // vectors of z inside the padded allocation
     T* zg = (T*)a.zg;
     const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
     const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
@@ -407,6 +431,18 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
     auto ldw = [&](long long m) { return win[m - ws]; };
     auto ldu = [&](long long m) { return __ldcg(a.u + m); };
     int e = 0;
+    if (ROWS) {
+        for (int li = threadIdx.x; li < nown; li += REG_THREADS) {
+            const long long n = b0 + li;
+            int i, j, kk;
+            node_ijk(f.m, n, i, j, kk);
+            T c[19];
+            row_coeffs<T>(f, n, i, j, kk, coef, c);
+#pragma unroll
+            for (int q = 0; q < 19; ++q) rows[li * 19 + q] = c[q];
+        }
+        // rows are read only after the first exchange's __syncthreads
+    }
     unsigned pk[NPT];
     T dv[NPT];
 #pragma unroll
@@ -460,9 +496,19 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             // stage the z window (the last exchange ordered every block's z stores
             // and every read of the previous window)
             {
-                const V* src = (const V*)(zg + ws);
                 V* dst = (V*)win;
-                for (int c = threadIdx.x; c < nvec; c += REG_THREADS) dst[c] = __ldcg(src + c);
+                if (ROWS) {
+                    const long long v0 = ws / VEC;   // exact: ws is a multiple of VEC
+                    for (int c = threadIdx.x; c < nvec; c += REG_THREADS) {
+                        const long long gv = v0 + c;
+                        V val = {};
+                        if (gv >= 0 && gv < nvec_in) val = __ldcg((const V*)zg + gv);
+                        dst[c] = val;
+                    }
+                } else {
+                    const V* src = (const V*)(zg + ws);
+                    for (int c = threadIdx.x; c < nvec; c += REG_THREADS) dst[c] = __ldcg(src + c);
+                }
             }
             __syncthreads();
             // p = z + beta p, q = A z + beta q (= A p); first pass: q = A z
@@ -472,7 +518,17 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             for (int s = 0; s < NPT; ++s) {
                 const long long n = b0 + threadIdx.x + s * REG_THREADS;
                 if (n < b1) {
-                    const T az = row_at<T>(f, n, pk[s], ldw, coef);
+                    T az;
+                    if (ROWS) {
+                        const int li = threadIdx.x + s * REG_THREADS;
+                        const T* rw = rows + li * 19;
+                        const T* wc = win + (n - ws);
+                        az = rw[0] * wc[0];
+#pragma unroll
+                        for (int q = 1; q < 19; ++q) az += rw[q] * wc[a.woff[q]];
+                    } else {
+                        az = row_at<T>(f, n, pk[s], ldw, coef);
+                    }
                     if (first) {
                         q[s] = az;
                     } else {
@@ -552,15 +608,23 @@ static int coop_grid(Ctx& c, bool mixed) {
     return (int)(g > 0 ? g : 1);
 }
 
-template <bool MIXED, int NPT>
-static void* reg_kernel() { return (void*)k_pcg_reg<MIXED, NPT>; }
-
-static void* reg_kernel(bool mixed, int npt) {
+// staged rows only in MIXED mode (19 FP64 coefficients per node do not fit
+// next to an FP64 window)
+static void* reg_kernel(bool mixed, int npt, bool rows) {
+    if (mixed && rows) {
+        switch (npt) {
+            case 1: return (void*)k_pcg_reg<true, 1, true>;
+            case 2: return (void*)k_pcg_reg<true, 2, true>;
+            case 4: return (void*)k_pcg_reg<true, 4, true>;
+            case 8: return (void*)k_pcg_reg<true, 8, true>;
+            default: return nullptr;
+        }
+    }
     switch (npt) {
-        case 1: return mixed ? reg_kernel<true, 1>() : reg_kernel<false, 1>();
-        case 2: return mixed ? reg_kernel<true, 2>() : reg_kernel<false, 2>();
-        case 4: return mixed ? reg_kernel<true, 4>() : reg_kernel<false, 4>();
-        case 8: return mixed ? reg_kernel<true, 8>() : reg_kernel<false, 8>();
+        case 1: return mixed ? (void*)k_pcg_reg<true, 1, false> : (void*)k_pcg_reg<false, 1, false>;
+        case 2: return mixed ? (void*)k_pcg_reg<true, 2, false> : (void*)k_pcg_reg<false, 2, false>;
+        case 4: return mixed ? (void*)k_pcg_reg<true, 4, false> : (void*)k_pcg_reg<false, 4, false>;
+        case 8: return mixed ? (void*)k_pcg_reg<true, 8, false> : (void*)k_pcg_reg<false, 8, false>;
         default: return nullptr;
     }
 }
@@ -594,21 +658,35 @@ void plan_pcg(Ctx& c) {
         else z_window<double>(N, NX, NXY, b0, b1, ws, we);
         if (we - ws > wmax) wmax = we - ws;
     }
-    const size_t smem = (size_t)wmax * tsz;
     const size_t static_smem = sizeof(ExchShared) + 64;
-    if (smem + static_smem > (size_t)smem_max) return;
-    void* kern = reg_kernel(mixed, pick);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return;
+    auto try_plan = [&](bool rows, size_t smem) {
+        if (smem + static_smem > (size_t)smem_max) return false;
+        void* kern = reg_kernel(mixed, pick, rows);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, REG_THREADS, smem);
+        if (per < 1) return false;
+        c.pcg_npt = pick;
+        c.pcg_rows = rows;
+        c.pcg_G = (int)G;
+        c.pcg_M = M;
+        c.pcg_smem = smem;
+        return true;
+    };
+    if (mixed) {
+        long long wpad = 0;   // longest zero-padded window over the blocks
+        for (long long bl = 0; bl < G; ++bl) {
+            long long ws, we, b0 = bl * M, b1 = b0 + M < N ? b0 + M : N;
+            z_window_padded<float>(NX, NXY, b0, b1, ws, we);
+            if (we - ws > wpad) wpad = we - ws;
+        }
+        const size_t rows_bytes = ((size_t)M * 19 * sizeof(float) + 15) / 16 * 16;
+        if (try_plan(true, rows_bytes + (size_t)wpad * sizeof(float))) return;
     }
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, REG_THREADS, smem);
-    if (per < 1) return;
-    c.pcg_npt = pick;
-    c.pcg_G = (int)G;
-    c.pcg_M = M;
-    c.pcg_smem = smem;
+    try_plan(false, (size_t)wmax * tsz);
 }
 
 static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
@@ -618,6 +696,13 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     a.b = c.b; a.u = c.u; a.g = c.gdir; a.phi = c.phi;
     a.zg = mixed ? (void*)c.zf : (void*)c.z;
     a.M = c.pcg_M;
+    {
+        const int NX = c.mesh.NX, NXY = c.mesh.NX * c.mesh.NY;
+        const int d[19][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1},
+                              {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}, {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {1, 0, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+        for (int q = 0; q < 19; ++q) a.woff[q] = d[q][0] + d[q][1] * NX + d[q][2] * NXY;
+    }
     a.val = c.coop_partial;
     a.arrivals = c.bar64;
     a.S = (PcgState*)c.scal;
@@ -635,7 +720,7 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, reg_kernel(mixed, c.pcg_npt), args);
+    return cudaLaunchKernelExC(&cfg, reg_kernel(mixed, c.pcg_npt, c.pcg_rows), args);
 }
 
 // the PCG state must already hold tol2 and maxit; writes phi
