@@ -128,20 +128,43 @@ PF_D long long warp_reserve(unsigned long long* counter, bool want) {
     return (long long)(base + __popc(mask & ((1u << lane) - 1)));
 }
 
-// Shared-memory fixed-point tile accumulation with native 32-bit atomics.  A
-// weight W (-2^16 < W <= 2^32: the remainder weight can dip a few units below
-// zero when the other seven round up) is added as its low 16 bits (0..65535)
-// and its arithmetic high part W >> 16 (-1..65536, a signed counter).  A bin
-// holds at most BIN_MAX particles, so |low sum| and |high sum| stay below 2^31
-// and tile_value() restores the exact int64 total.
-PF_D void tile_add(unsigned* lo, int* hi, int t, long long W) {
-    atomicAdd(&lo[t], (unsigned)(W & 0xFFFF));
-    atomicAdd(&hi[t], (int)(W >> 16));
-}
-PF_D long long tile_value(unsigned lo, int hi) { return (long long)lo + ((long long)hi << 16); }
 constexpr int BIN_MAX = 32767;
 // corner offsets in a (BLK+1)^3 tile, node order 000,100,010,110,001,101,011,111
-PF_D int tile_corner(int l) { return (l & 1) + TILE * ((l >> 1) & 1) + TILE * TILE * ((l >> 2) & 1); }
+PF_HD constexpr int tile_corner(int l) {
+    return (l & 1) + TILE * ((l >> 1) & 1) + TILE * TILE * ((l >> 2) & 1);
+}
+
+// Shared-memory fixed-point deposit of one particle with native 32-bit atomics.
+// The tile keeps 8 interleaved copies per node (index 8 * node + copy; base =
+// 8 * corner-0 node + copy).  W[l] (l < 7, 0 <= W[l] <= 2^32) are the rounded
+// weights of corners 0..6; each goes in as its low 16 bits and its high part
+// W >> 16 (two signed counters).  Corner 7 receives minus the low parts and
+// 2^16 minus the high parts of the other seven: exactly 2^32 - sum W[l], the
+// remainder weight, so the particle adds exactly 2^32 and every node the same
+// integer as an int64 deposit.  Per copy at most BIN_MAX / 8 + 1 particles
+// reach a node, each moving a counter by less than 7 * 2^16, so both counters
+// stay inside 32 bits and tile_value() is exact.
+template <typename WT>
+PF_D void tile_deposit(int* lo, int* hi, int base, const WT (&W)[7]) {
+    int slo = 0, shi = 0;
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        const int a = (int)(W[l] & 0xFFFF), b = (int)(W[l] >> 16);
+        atomicAdd(&lo[base + 8 * tile_corner(l)], a);
+        atomicAdd(&hi[base + 8 * tile_corner(l)], b);
+        slo += a;
+        shi += b;
+    }
+    atomicAdd(&lo[base + 8 * tile_corner(7)], -slo);
+    atomicAdd(&hi[base + 8 * tile_corner(7)], 65536 - shi);
+}
+PF_D long long tile_value(int lo, int hi) { return (long long)lo + ((long long)hi << 16); }
+
+// warp-aggregated event count into a 32-bit shared counter
+PF_D void count_event32(unsigned* c, bool ev) {
+    const unsigned m = __ballot_sync(0xffffffffu, ev);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(c, (unsigned)__popc(m));
+}
 
 // ---------------------------------------------------------------------------
 // mbarrier + TMA (cp.async.bulk.tensor) helpers

@@ -151,11 +151,11 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     __shared__ alignas(128) double4 Et[TILE_N];
     // fixed-point tile (low 16 bits / signed high part) with 8 interleaved
     // copies per node, copy = lane & 7, to spread the atomics over the banks
-    __shared__ unsigned Wlo[8 * TILE_N];
+    __shared__ int Wlo[8 * TILE_N];
     __shared__ int Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ int wcnt[8];
-    __shared__ unsigned long long sctr[NCTR];
+    __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
     const int s = blockIdx.y;
     const int b = blockIdx.x;
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0; }
-    if (tid < NCTR) sctr[tid] = 0ull;
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    if (tid < NCTR) sctr[tid] = 0u;
     __syncthreads();
     if (tid == 0) {
         mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(double4));
@@ -213,21 +213,19 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
             if (stay) {
                 long long Wf[8];
                 fixed_weights(w, Wf);
-#pragma unroll
-                for (int l = 0; l < 8; ++l) {
-                    int t = (w.ci - x0 + (l & 1)) + TILE * ((w.cj - y0 + ((l >> 1) & 1)) + TILE * (w.ck - z0 + ((l >> 2) & 1)));
-                    tile_add(Wlo, Whi, t * 8 + (lane & 7), Wf[l]);
-                }
+                const long long W7[7] = {Wf[0], Wf[1], Wf[2], Wf[3], Wf[4], Wf[5], Wf[6]};
+                const int t0 = (w.ci - x0) + TILE * ((w.cj - y0) + TILE * (w.ck - z0));
+                tile_deposit(Wlo, Whi, 8 * t0 + (lane & 7), W7);
             } else {
                 global_deposit(L, S.W, w);
             }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
-        count_event(&sctr[C_PUSHED], code != NONE);
-        count_event(&sctr[C_ABSORBED], code == ABSORBED);
-        count_event(&sctr[C_COLLECTED], code == COLLECTED);
-        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        count_event32(&sctr[C_PUSHED], code != NONE);
+        count_event32(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event32(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event32(&sctr[C_LOST], code == COLLECTED && acc < 0);
         // block-wide compaction of stayers (all reads of this chunk are done
         // before the barrier, so in-place writes cannot clobber unread slots)
         unsigned bal = __ballot_sync(0xffffffffu, stay);
@@ -256,7 +254,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
         if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
     }
-    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
+    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
 
 // particles waiting in the mover list (spilled last step): same arithmetic,

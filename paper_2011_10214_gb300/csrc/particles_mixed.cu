@@ -84,11 +84,6 @@ struct EGlobalF {
     Mesh m;
     PF_D float4 operator()(int i, int j, int k) const { return E[node_id(m, i, j, k)]; }
 };
-struct ETileF {
-    const float4* T;
-    int x0, y0, z0;
-    PF_D float4 operator()(int i, int j, int k) const { return T[(i - x0) + TILE * ((j - y0) + TILE * (k - z0))]; }
-};
 
 template <class EA>
 PF_D void gather_f(int i, int j, int k, const WF& w, const EA& ea, float& ex, float& ey, float& ez) {
@@ -184,17 +179,33 @@ PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
 // ------------------------------------------------------------------------------------
 // fused gather + push + boundary + collection + deposit + compaction (one bin per CTA)
 // ------------------------------------------------------------------------------------
+// gather from the staged node-field tile; t0 = tile index of the cell's corner 0
+PF_D void gather_tile(const float4* Et, int t0, const WF& w, float& ex, float& ey, float& ez) {
+    ex = 0.f; ey = 0.f; ez = 0.f;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const float4 e = Et[t0 + tile_corner(l)];
+        ex += w.w[l] * e.x;
+        ey += w.w[l] * e.y;
+        ez += w.w[l] * e.z;
+    }
+}
+
+PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
+    return (i - x0) + TILE * ((j - y0) + TILE * (k - z0));
+}
+
 __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
-    // fixed-point tile, low 16 bits / rest, with 8 interleaved copies per node
-    // (copy = lane & 7): the lanes of one atomic instruction spread over the
-    // banks instead of colliding on the few nodes of a 4^3-cell bin
-    __shared__ unsigned Wlo[8 * TILE_N];
+    // fixed-point tile, low 16 bits / high part, with 8 interleaved copies per
+    // node (copy = lane & 7): the lanes of one atomic instruction spread over
+    // the banks instead of colliding on the few nodes of a 4^3-cell bin
+    __shared__ int Wlo[8 * TILE_N];
     __shared__ int Whi[8 * TILE_N];
     __shared__ alignas(8) unsigned long long bar;
-    __shared__ int wcnt[8];
-    __shared__ unsigned long long sctr[NCTR];
+    __shared__ int wcnt[2][8];        // stayers per warp, by chunk parity
+    __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
     const int s = blockIdx.y;
     const int b = blockIdx.x;
@@ -205,8 +216,8 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0u; Whi[t] = 0; }
-    if (tid < NCTR) sctr[tid] = 0ull;
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    if (tid < NCTR) sctr[tid] = 0u;
     __syncthreads();
     if (tid == 0) {
         mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(float4));
@@ -220,10 +231,10 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     }
     __syncthreads();
     if (!s_ok) return;
-    const ETileF ea{Et, x0, y0, z0};
     const long long start = S.bstart[b];
     const bool track = L.track;
     const float kf = (float)S.k;
+    const int copy = lane & 7;
     int nstay = 0;
     // the next chunk is loaded into registers while this one is processed
     // (its slots lie beyond every slot this chunk's in-place writes can reach)
@@ -233,7 +244,8 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
         load_p(S.binsF, start + tid, pn);
         if (track) idn = S.binsF.id[start + tid];
     }
-    for (int base = 0; base < n; base += blockDim.x) {
+    int par = 0;
+    for (int base = 0; base < n; base += blockDim.x, par ^= 1) {
         const int i = base + tid;
         int code = NONE, acc = -1;
         PF32 p = pn;
@@ -243,34 +255,60 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
             load_p(S.binsF, start + inext, pn);
             if (track) idn = S.binsF.id[start + inext];
         }
-        if (i < n) code = push_one(L, of, kf, dthf, p, ea, acc);
+        if (i < n) {
+            // kick with the field gathered at the old position, then drift
+            const WF w = weights_f(p.fx, p.fy, p.fz);
+            float ex, ey, ez;
+            gather_tile(Et, tile_index(p.i, p.j, p.k, x0, y0, z0), w, ex, ey, ez);
+            p.vx += kf * ex; p.vy += kf * ey; p.vz += kf * ez;
+            const float xo = (float)p.i + p.fx, yo = (float)p.j + p.fy, zo = (float)p.k + p.fz;
+            p.fx += p.vx * dthf; p.fy += p.vy * dthf; p.fz += p.vz * dthf;
+            advance_axis(p.fx, p.i); advance_axis(p.fy, p.j); advance_axis(p.fz, p.k);
+            if (p.i < 0 || p.i >= L.mesh.nx || p.j < 0 || p.j >= L.mesh.ny || p.k < 0 || p.k >= L.mesh.nz) {
+                code = ABSORBED;
+            } else {
+                const float xn = (float)p.i + p.fx, yn = (float)p.j + p.fy, zn = (float)p.k + p.fz;
+                if (level_set_f(of, xn, yn, zn) < 0.0f) {
+                    acc = hit_cell_f(L, of, xo, yo, zo, xn, yn, zn);
+                    code = COLLECTED;
+                } else {
+                    code = ALIVE;
+                }
+            }
+        }
         bool stay = false, mover = false;
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
             mover = !stay;
             if (stay) {
-                long long Wf[8];
-                fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+                const WF w = weights_f(p.fx, p.fy, p.fz);
+                unsigned W[7];
 #pragma unroll
-                for (int l = 0; l < 8; ++l) {
-                    int t = (p.i - x0 + (l & 1)) + TILE * ((p.j - y0 + ((l >> 1) & 1)) + TILE * (p.k - z0 + ((l >> 2) & 1)));
-                    tile_add(Wlo, Whi, t * 8 + (lane & 7), Wf[l]);
-                }
+                for (int l = 0; l < 7; ++l) W[l] = __float2uint_rn(w.w[l] * 4294967296.0f);
+                tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W);
             } else {
                 global_deposit_f(L, S.W, p);
             }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
-        count_event(&sctr[C_PUSHED], code != NONE);
-        count_event(&sctr[C_ABSORBED], code == ABSORBED);
-        count_event(&sctr[C_COLLECTED], code == COLLECTED);
-        count_event(&sctr[C_LOST], code == COLLECTED && acc < 0);
-        unsigned bal = __ballot_sync(0xffffffffu, stay);
-        if (lane == 0) wcnt[wid] = __popc(bal);
+        count_event32(&sctr[C_PUSHED], code != NONE);
+        count_event32(&sctr[C_ABSORBED], code == ABSORBED);
+        count_event32(&sctr[C_COLLECTED], code == COLLECTED);
+        count_event32(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        const unsigned bal = __ballot_sync(0xffffffffu, stay);
+        if (lane == 0) wcnt[par][wid] = __popc(bal);
         __syncthreads();
-        int off = 0, tot = 0;
-        for (int q = 0; q < nw; ++q) { int v = wcnt[q]; off += (q < wid) ? v : 0; tot += v; }
+        // this warp's offset among the chunk's stayers: scan of the warp counts
+        const int v = lane < nw ? wcnt[par][lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, nw - 1);
+        const int off = __shfl_sync(0xffffffffu, incl - v, wid);
         if (stay) store_p(S.binsF, start + nstay + off + __popc(bal & ((1u << lane) - 1)), p, id, track);
         long long slot = warp_reserve(S.mov_out_n, mover);
         if (mover) {
@@ -278,8 +316,11 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
             else atomicAdd(&S.ctr[C_DROPPED], 1ull);
         }
         nstay += tot;
-        __syncthreads();
+        // one barrier per chunk: wcnt alternates with the chunk parity, and a
+        // warp one chunk ahead writes only slots whose particles every warp
+        // loaded before the barrier it has already passed
     }
+    __syncthreads();
     if (tid == 0) S.bcount[b] = nstay;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
         long long v = 0;
@@ -287,9 +328,10 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
-        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz) atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
+            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
     }
-    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], sctr[tid]);
+    if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
 
 __global__ void k_push_movers_m(Launch L, ObjF of, float dthf) {
