@@ -187,6 +187,8 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.invdiagf, sizeof(float) * N);
     ALLOC(c.phi, sizeof(double) * N);
     ALLOC(c.u, sizeof(double) * N);
+    ALLOC(c.phi_prev, sizeof(double) * N);
+    CUDA_OK(szero(c.stream, c.phi_prev, sizeof(double) * N));
     ALLOC(c.b, sizeof(double) * N);
     ALLOC(c.r, sizeof(double) * N);
     ALLOC(c.p, sizeof(double) * N);
@@ -242,7 +244,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (!ctx) return;
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
-    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
+    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,

@@ -52,9 +52,12 @@ __global__ void k_qtets(long long nit, const int* it_acc, const double* qcut, do
 }
 
 __global__ void k_rhs(FieldArgs f, RhsArgs a, const unsigned char* imask, const int* ibase, const double* it_data,
-                      const double* qT, const double* lift, double* b, const double* Fext) {
+                      const double* qT, const double* lift, double* b, const double* Fext, long long* hist) {
     const Mesh& m = f.m;
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // solves so far, this one included (capped at 3): the start-vector kernel
+    // that follows extrapolates only once two earlier solves exist
+    if (hist && n == 0 && *hist < 3) *hist += 1;
     if (n >= m.nnodes) return;
     int ty = f.ntype[n];
     if (ty == -3) { b[n] = 0.0; return; }
@@ -103,9 +106,18 @@ __global__ void k_phi_from_u(long long N, const double* u, const double* g, doub
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n < N) phi[n] = S->bb == 0.0 ? g[n] : u[n] + g[n];
 }
-__global__ void k_u_from_phi(long long N, const int* ntype, const double* phi, const double* g, double* u) {
+// PCG start vector: the last potential, or once two earlier solves exist its
+// linear extrapolation 2 phi_{n-1} - phi_{n-2} (particles move the charge
+// smoothly from step to step, so this start is closer); phi_prev <- phi.  The
+// solve still stops on the same relative residual.
+__global__ void k_u_from_phi(long long N, const int* ntype, const double* phi, double* phi_prev, const double* g,
+                             double* u, const long long* hist) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n < N) u[n] = ntype[n] == -3 ? 0.0 : phi[n] - g[n];
+    if (n >= N) return;
+    const double p = phi[n];
+    const double start = (*hist >= 3) ? 2.0 * p - phi_prev[n] : p;
+    u[n] = ntype[n] == -3 ? 0.0 : start - g[n];
+    phi_prev[n] = p;
 }
 
 // ---- node field ---------------------------------------------------------------------
@@ -327,6 +339,8 @@ __global__ void k_surface_charge(RhsArgs a, double* partial, unsigned* ticket, d
 
 // ------------------------------------------------------------------------------------
 static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+// device count of solves (PCG start extrapolation), scalar slot 43
+static long long* solve_hist(Ctx& c) { return (long long*)(c.scal + 43); }
 
 static FieldArgs fargs(Ctx& c) {
     FieldArgs f;
@@ -369,8 +383,8 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
         if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
         if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
     }
-    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, Fext);
-    k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.gdir, c.u);
+    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, Fext, solve_hist(c));
+    k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_pcg_coop(c, st);
@@ -387,8 +401,8 @@ cudaError_t launch_solve_prefix(Ctx& c, cudaStream_t st) {
     long long N = c.mesh.nnodes;
     if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
     if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
-    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr);
-    k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.gdir, c.u);
+    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr, solve_hist(c));
+    k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     return cudaGetLastError();
 }
 cudaError_t launch_solve_suffix(Ctx& c, cudaStream_t st) {
@@ -658,7 +672,7 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
     unsigned gb = nb(N);
     cudaStream_t st = c.stream;
     k_na_state<<<1, 1, 0, st>>>(S, ticket, c.tol * c.tol, c.maxit);
-    k_rhs<<<gb, 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, q, c.lift, bvec, F);
+    k_rhs<<<gb, 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, q, c.lift, bvec, F, nullptr);
     cudaMemsetAsync(u, 0, sizeof(double) * N, st);
     k_matvec<<<gb, 256, 0, st>>>(f, u, qv);
     k_na_init<<<gb, 256, 0, st>>>(f, bvec, qv, r, p, partial, ticket, S);

@@ -112,7 +112,8 @@ struct Ctx {
     double* lift = nullptr;        // (A g) restricted to free nodes
     double* invdiag = nullptr;
     double* phi = nullptr;
-    double* u = nullptr;           // unknown (phi - g)
+    double* u = nullptr;
+    double* phi_prev = nullptr;    // potential before the last solve (start extrapolation)           // unknown (phi - g)
     double* b = nullptr;           // right-hand side
     double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
     float* zf = nullptr;
