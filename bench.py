@@ -102,6 +102,12 @@ def cfg_desc(cfg, precision, extra=None):
 # GPU arm
 # ---------------------------------------------------------------------------------
 FP64_FLOPS_PER_PARTICLE_STEP = 80     # trilinear weights 19, gather 45, kick and drift 12, cell test 4
+# PCG: 7 node-vector passes per iteration (p, x, r, z updates, the operator's read of p and write of q)
+SOLVE_BYTES_PER_NODE_ITER = {"mixed": 7 * 4, "fp64": 7 * 8}
+# DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 32^3 sphere
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launch's particles); None when not measured
+# for the current kernel
+PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (115809024 + 57204992) / 4074576, "fp64": None}
 NSM, DFMA_PER_CLK_SM = 152, 2          # GB300: 2 FP64 FMA per SM per clock
 
 
@@ -148,10 +154,13 @@ def roofline(precision, st, steps, ck):
     if precision == "mixed":
         alg = per_launch * BYTES_PER_PARTICLE_STEP["mixed"]
         ach = alg / (push_ms / 1e3) / 1e9
+        tpp = PUSH_TRAFFIC_PER_PARTICLE["mixed"]
         return {"kernel": "k_push_bins_m (fused gather+push+collect+deposit, FP32 state)", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
-                "alg_bytes_per_launch": alg, "avg_launch_ms": push_ms}
+                "frac": round(ach / peaks["hbm_gbs"], 4),
+                "traffic": None if tpp is None else round(tpp * per_launch),
+                "traffic_note": "ncu DRAM bytes per particle of a 32^3 launch, scaled to this launch's particles",
+                "peak_source": src, "alg_bytes_per_launch": alg, "avg_launch_ms": push_ms}
     flops = per_launch * FP64_FLOPS_PER_PARTICLE_STEP
     ach = flops / (push_ms / 1e3) / 1e9
     mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -162,6 +171,21 @@ def roofline(precision, st, steps, ck):
             "alg_flops_per_launch": flops, "avg_launch_ms": push_ms,
             "hbm_view": {"achieved_gbs": round(per_launch * 96 / (push_ms / 1e3) / 1e9, 1),
                          "peak_gbs": peaks["hbm_gbs"]}}
+
+
+def roofline_solve(precision, st, steps, nnodes):
+    """The field solve: algorithmic node-vector bytes of the PCG iterations over the solve graph's time
+    (the persistent PCG kernel plus the short RHS, start-vector and node-field kernels around it)."""
+    solve_ms = st["phase_ms"][5] / steps
+    iters = st["pcg_iters_total"] / steps
+    alg = nnodes * SOLVE_BYTES_PER_NODE_ITER[precision] * iters
+    ach = alg / (solve_ms / 1e3) / 1e9
+    peaks, src = _peaks()
+    return {"kernel": "k_pcg_reg (persistent PCG, one launch per solve) in the solve graph", "bound": "hbm",
+            "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
+            "alg_bytes_per_launch": alg, "avg_launch_ms": solve_ms, "iters_per_solve": iters,
+            "note": "latency-bound: two grid exchanges per iteration, vectors in registers and L2"}
 
 
 def run_gpu(args):
@@ -183,7 +207,14 @@ def run_gpu(args):
     other = "fp64" if main == "mixed" else "mixed"
     sim, st, secs, total, pushed, ck = measure(cfg, main, args.steps, args.warmup, stream, dist, local)
     value = total / secs
-    roof = roofline(main, st, args.steps, ck)
+    nnodes = sim.sizes()["nnodes"]
+    roof_push = roofline(main, st, args.steps, ck)
+    roof_solve = roofline_solve(main, st, args.steps, nnodes)
+    # the longer of the two phases is the dominant kernel; the other is reported beside it
+    if roof_solve["avg_launch_ms"] > roof_push["avg_launch_ms"]:
+        roof, roof_other = roof_solve, roof_push
+    else:
+        roof, roof_other = roof_push, roof_solve
 
     # end to end through the C ABI from host buffers: the initial particle state
     # is copied host -> device (pinned) inside the timed region, and every step
@@ -239,7 +270,7 @@ def run_gpu(args):
         "data": "synthetic (seeded Philox load and injection)",
         "config": cfg_desc(cfg, main, {"particles": int(pushed / args.steps),
                                        "parallelism": f"replicas x{world}"}),
-        "roofline": roof, "clocks": ck, "e2e": e2e,
+        "roofline": roof, "roofline_other": roof_other, "clocks": ck, "e2e": e2e,
         "gpu_launches": int(st["kernel_launches"]),
         "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
         "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st["phase_ms"]) if v},
