@@ -1,10 +1,10 @@
 // Batched IFE-PIC steps: many independent instances advanced by ONE CUDA graph
 // launch per step.  Each instance's particle phases (push, movers, injection,
 // rebin) and right-hand side are independent branches of the graph, so small
-// instances overlap on the device; one batched PCG kernel then solves every
-// instance's field at once with one CTA per instance (block-level
-// synchronisation only, no grid barrier shared between instances); the node
-// fields follow as branches again.  The paper runs one problem per job (Sec. 3,
+// instances overlap on the device; the field solves run on thread-block
+// clusters, one cluster per instance (pcg_cluster.cu), with a one-CTA-per-
+// instance kernel for instances too large for a cluster; the node fields
+// follow as branches again.  The paper runs one problem per job (Sec. 3,
 // Sec. 5); batching and serving many charging problems is this build's addition
 // on top of the same per-instance method.
 #include <math.h>
@@ -25,20 +25,6 @@ void snapshot_counters(pifepic_ctx* ctx, unsigned long long* before, long long* 
 pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, long long it0, long long ot0,
                             long long nsteps, long long kernels, pifepic_stats* st);
 
-struct BatchItem {
-    FieldArgs f;
-    const double* b;
-    double* u;
-    double *r, *z, *p, *q;
-    float *rf, *zf, *pf, *qf, *df;
-    const double* g;
-    double* phi;
-    PcgState* S;
-    long long* it_total;
-    long long* outer_total;
-    double tol2;
-    int maxit;
-};
 
 constexpr double BATCH_INNER_TOL = 1e-4;
 constexpr int BATCH_MAX_OUTER = 12;
@@ -158,6 +144,9 @@ __global__ void __launch_bounds__(THREADS) k_pcg_batch(const BatchItem* items) {
     }
 }
 
+int cluster_size_for(long long N, long long H, bool mixed);                      // pcg_cluster.cu
+size_t cluster_smem_for(long long N, long long H, int C, bool mixed);
+cudaError_t launch_pcg_cluster(const BatchItem* items, int count, int C, size_t smem, bool mixed, cudaStream_t st);
 cudaError_t launch_push(Ctx& c);
 cudaError_t launch_movers(Ctx& c);
 cudaError_t launch_inject(Ctx& c);
@@ -227,6 +216,13 @@ static pifepic_status batch_fail(pifepic_batch* b, pifepic_status st, const std:
     return st;
 }
 
+static long long node_halo(const Mesh& m) { return (long long)m.NX * m.NY + m.NX + 1; }
+
+// The batch step as one graph: per instance a branch with its particle
+// phases and right-hand side; then the field solves, grouped by cluster size
+// (one launch per group, each waiting only for its own members' branches;
+// instances too large for a cluster share the one-CTA-per-instance kernel);
+// then per instance the node field.
 static cudaError_t build_batch_graph(pifepic_batch* b) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -239,18 +235,30 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
         if (e != cudaSuccess) return e;
         b->items_cap = n;
     }
-    std::vector<BatchItem> h(n);
-    for (int i = 0; i < n; ++i) h[i] = make_item(b->ctx[i]->c);
-    cudaError_t e = cudaMemcpyAsync(b->items, h.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return e;
+    // solve groups: cluster size per instance (0: the one-CTA kernel), items in group order
+    std::vector<int> csize(n, -1);
+    for (int i = 0; i < n; ++i) {
+        const Ctx& c = b->ctx[i]->c;
+        if (!c.external_E) csize[i] = cluster_size_for(c.mesh.nnodes, node_halo(c.mesh), mixed);
+    }
+    const int groups[6] = {16, 8, 4, 2, 1, 0};
+    std::vector<int> order;
+    std::vector<BatchItem> h;
+    for (int g : groups)
+        for (int i = 0; i < n; ++i)
+            if (csize[i] == g) { order.push_back(i); h.push_back(make_item(b->ctx[i]->c)); }
+    cudaError_t e = cudaSuccess;
+    if (!h.empty()) {
+        e = cudaMemcpyAsync(b->items, h.data(), sizeof(BatchItem) * h.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return e;
+    }
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     cudaGraph_t g;
     e = cudaGraphCreate(&g, 0);
-    std::vector<cudaGraphNode_t> pre(n), post(n);
-    cudaGraphNode_t solve = nullptr;
+    std::vector<cudaGraphNode_t> pre(n), post(n), solve_of(n, nullptr);
     b->kernels.assign(n, 0);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         Ctx& c = b->ctx[i]->c;
@@ -266,32 +274,50 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
         }, &sub);
         if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&pre[i], g, nullptr, 0, sub);
         if (sub) cudaGraphDestroy(sub);
-        // captured particle kernels, the solve prefix and suffix, and one CTA of the batched PCG
+        // captured particle kernels, the solve prefix and suffix, and its share of one solve launch
         b->kernels[i] = (c.launches - l0) + (c.external_E ? 0 : (solve_graph_fixed_kernels(c) - 1));
         c.launches = l0;
     }
-    // one batched PCG for every instance whose field is not frozen
-    bool any_solve = false;
-    for (auto* x : b->ctx) any_solve |= !x->c.external_E;
-    if (e == cudaSuccess && any_solve) {
+    // one solve launch per group
+    size_t off = 0;
+    for (int gsz : groups) {
+        if (e != cudaSuccess) break;
+        std::vector<int> mem;
+        for (int i : order)
+            if (csize[i] == gsz) mem.push_back(i);
+        if (mem.empty()) continue;
+        const BatchItem* items = b->items + off;
+        const int count = (int)mem.size();
+        off += mem.size();
+        size_t smem = 0;
+        for (int i : mem) {
+            const Ctx& c = b->ctx[i]->c;
+            if (gsz > 0) smem = std::max(smem, cluster_smem_for(c.mesh.nnodes, node_halo(c.mesh), gsz, mixed));
+        }
+        std::vector<cudaGraphNode_t> deps;
+        for (int i : mem) deps.push_back(pre[i]);
         cudaGraph_t sub = nullptr;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = mixed ? launch_batch_pcg<true>(b->items, n, b->threads, cs)
-                                   : launch_batch_pcg<false>(b->items, n, b->threads, cs);
+            cudaError_t e2;
+            if (gsz > 0) e2 = launch_pcg_cluster(items, count, gsz, smem, mixed, cs);
+            else e2 = mixed ? launch_batch_pcg<true>(items, count, b->threads, cs)
+                            : launch_batch_pcg<false>(items, count, b->threads, cs);
             e = cudaStreamEndCapture(cs, &sub);
             if (e == cudaSuccess) e = e2;
         }
-        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&solve, g, pre.data(), n, sub);
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, g, deps.data(), deps.size(), sub);
         if (sub) cudaGraphDestroy(sub);
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
-            Ctx& c = b->ctx[i]->c;
-            if (c.external_E) continue;
-            cudaGraph_t s2 = nullptr;
-            e = capture(c, cs, [](Ctx& cc) -> cudaError_t { return launch_solve_suffix(cc, cc.stream); }, &s2);
-            if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&post[i], g, &solve, 1, s2);
-            if (s2) cudaGraphDestroy(s2);
-        }
+        for (int i : mem) solve_of[i] = node;
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        Ctx& c = b->ctx[i]->c;
+        if (c.external_E) continue;
+        cudaGraph_t s2 = nullptr;
+        e = capture(c, cs, [](Ctx& cc) -> cudaError_t { return launch_solve_suffix(cc, cc.stream); }, &s2);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&post[i], g, &solve_of[i], 1, s2);
+        if (s2) cudaGraphDestroy(s2);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
     if (e == cudaSuccess) { b->graph = g; b->dirty = false; }

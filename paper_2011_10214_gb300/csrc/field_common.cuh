@@ -25,6 +25,22 @@ struct FieldArgs {
     const float* invdiagf;
 };
 
+// one instance of a batched solve (batch.cu, pcg_cluster.cu)
+struct BatchItem {
+    FieldArgs f;
+    const double* b;
+    double* u;
+    double *r, *z, *p, *q;
+    float *rf, *zf, *pf, *qf, *df;
+    const double* g;
+    double* phi;
+    PcgState* S;
+    long long* it_total;
+    long long* outer_total;
+    double tol2;
+    int maxit;
+};
+
 static __device__ __forceinline__ void loff(int l, int& a, int& b, int& c) {
     a = l & 1; b = (l >> 1) & 1; c = (l >> 2) & 1;
 }
@@ -184,6 +200,43 @@ static __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
         }
     }
     __syncthreads();
+}
+
+// deterministic block sum of NV values of type A (thread 0 gets the totals);
+// A = float keeps the MIXED inner loop off the FP64 pipe, which issues a warp
+// instruction only every few dozen cycles on this part
+template <typename A, int NV>
+static __device__ __forceinline__ void block_sum_t(A (&v)[NV], A* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        A s = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[q * 32 + w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            A s = lane < nw ? sh[q * 32 + lane] : (A)0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+static __device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+static __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // writes block partials; returns true in the one block that arrives last,

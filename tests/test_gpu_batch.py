@@ -102,3 +102,34 @@ def test_served_results_equal_alone():
     for i, a in enumerate(alone):
         assert by[i]["steps"] == a["steps"]
         assert np.array_equal(by[i]["phi"], a["phi"])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_solves_match_single_instance_solves(precision):
+    """Members of 20^3..48^3 cells put the batched solve on clusters of 2, 4,
+    8 and 16 CTAs (FP64: the largest goes to the one-CTA kernel).  After one
+    step from the same state, each member's potential equals the same instance
+    stepped alone (persistent single-instance solver) to the solver tolerance."""
+    from paper_2011_10214_gb300 import capi
+    cfgs = [wl.sphere_config(n, 0.2 * n * 0.5, 4, 1, eps_in=3.0, seed_offset=30 + n) for n in (20, 24, 28, 36, 48)]
+
+    def fresh(cfg):
+        s = capi.from_config(cfg, precision=precision, pcg_tol=1e-12, pcg_max_iter=5000)
+        s.solve(); s.leapfrog_init()
+        return s
+    alone = []
+    for cfg in cfgs:
+        s = fresh(cfg)
+        s.step(1)
+        alone.append(s.potential())
+        s.close()
+    sims = [fresh(cfg) for cfg in cfgs]
+    b = capi.Batch(sims)
+    st = b.step(1)
+    for k, (s, phi) in enumerate(zip(sims, alone)):
+        assert st[k]["pcg_converged"] == 1, k
+        rel = np.abs(s.potential() - phi).max() / np.abs(phi).max()
+        assert rel <= 1e-8, (cfgs[k]["n"], rel)
+    b.close()
+    for s in sims:
+        s.close()
