@@ -391,7 +391,7 @@ def run_batch(args):
         sims.append(s)
     setup_s = time.perf_counter() - t0
     batch = capi.Batch(sims, stream=stream.cuda_stream)
-    best, _ = serve.autotune_batch(batch)
+    best = None if args.no_autotune else serve.autotune_batch(batch)[0]
     batch.step(args.warmup, stats=False)
     torch.cuda.synchronize()
     clocks = Clocks(0)
@@ -459,6 +459,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default PCG block size")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--horizon", type=float, default=10.0)
     ap.add_argument("--max-steps", type=int, default=500)

@@ -218,11 +218,10 @@ static pifepic_status batch_fail(pifepic_batch* b, pifepic_status st, const std:
 
 static long long node_halo(const Mesh& m) { return (long long)m.NX * m.NY + m.NX + 1; }
 
-// The batch step as one graph: per instance a branch with its particle
-// phases and right-hand side; then the field solves, grouped by cluster size
-// (one launch per group, each waiting only for its own members' branches;
-// instances too large for a cluster share the one-CTA-per-instance kernel);
-// then per instance the node field.
+// The batch step as one graph: per instance a chain of its particle phases,
+// right-hand side, field solve (one cluster launch; instances too large for a
+// cluster share one launch of the one-CTA-per-instance kernel) and node field,
+// so every instance advances as soon as its own work allows.
 static cudaError_t build_batch_graph(pifepic_batch* b) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -278,38 +277,46 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
         b->kernels[i] = (c.launches - l0) + (c.external_E ? 0 : (solve_graph_fixed_kernels(c) - 1));
         c.launches = l0;
     }
-    // one solve launch per group
+    // one solve launch per instance, waiting only for that instance's branch
+    // (instances too large for a cluster share the one-CTA-per-instance kernel)
     size_t off = 0;
+    std::vector<int> fallback;
     for (int gsz : groups) {
-        if (e != cudaSuccess) break;
-        std::vector<int> mem;
-        for (int i : order)
-            if (csize[i] == gsz) mem.push_back(i);
-        if (mem.empty()) continue;
-        const BatchItem* items = b->items + off;
-        const int count = (int)mem.size();
-        off += mem.size();
-        size_t smem = 0;
-        for (int i : mem) {
+        for (int i : order) {
+            if (csize[i] != gsz) continue;
+            const BatchItem* items = b->items + off;
+            ++off;
+            if (gsz == 0) { fallback.push_back(i); continue; }
+            if (e != cudaSuccess) break;
             const Ctx& c = b->ctx[i]->c;
-            if (gsz > 0) smem = std::max(smem, cluster_smem_for(c.mesh.nnodes, node_halo(c.mesh), gsz, mixed));
+            const size_t smem = cluster_smem_for(c.mesh.nnodes, node_halo(c.mesh), gsz, mixed);
+            cudaGraph_t sub = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = launch_pcg_cluster(items, 1, gsz, smem, mixed, cs);
+                e = cudaStreamEndCapture(cs, &sub);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&solve_of[i], g, &pre[i], 1, sub);
+            if (sub) cudaGraphDestroy(sub);
         }
+    }
+    if (e == cudaSuccess && !fallback.empty()) {
+        const BatchItem* items = b->items + (off - fallback.size());
         std::vector<cudaGraphNode_t> deps;
-        for (int i : mem) deps.push_back(pre[i]);
+        for (int i : fallback) deps.push_back(pre[i]);
         cudaGraph_t sub = nullptr;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2;
-            if (gsz > 0) e2 = launch_pcg_cluster(items, count, gsz, smem, mixed, cs);
-            else e2 = mixed ? launch_batch_pcg<true>(items, count, b->threads, cs)
-                            : launch_batch_pcg<false>(items, count, b->threads, cs);
+            cudaError_t e2 = mixed ? launch_batch_pcg<true>(items, (int)fallback.size(), b->threads, cs)
+                                   : launch_batch_pcg<false>(items, (int)fallback.size(), b->threads, cs);
             e = cudaStreamEndCapture(cs, &sub);
             if (e == cudaSuccess) e = e2;
         }
         cudaGraphNode_t node = nullptr;
         if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, g, deps.data(), deps.size(), sub);
         if (sub) cudaGraphDestroy(sub);
-        for (int i : mem) solve_of[i] = node;
+        for (int i : fallback) solve_of[i] = node;
     }
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         Ctx& c = b->ctx[i]->c;

@@ -123,6 +123,62 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
     return eps * y;
 }
 
+// Row kinds for the masked regular stencil: the six neighbour-presence flags,
+// the node parity, the region, and whether the row is general (an interface
+// patch row) or Dirichlet (zero).
+enum : unsigned short {
+    RK_XM = 1, RK_XP = 2, RK_YM = 4, RK_YP = 8, RK_ZM = 16, RK_ZP = 32, RK_ODD = 64, RK_INNER = 128,
+    RK_GENERAL = 256, RK_DIRICHLET = 512
+};
+
+static __device__ __forceinline__ unsigned short row_kind(const FieldArgs& f, long long n, int i, int j, int k) {
+    const Mesh& m = f.m;
+    const int ty = f.ntype[n];
+    if (ty == -3) return RK_DIRICHLET;
+    if (ty >= 0) return RK_GENERAL;
+    unsigned short kd = 0;
+    if (i > 0) kd |= RK_XM;
+    if (i < m.nx) kd |= RK_XP;
+    if (j > 0) kd |= RK_YM;
+    if (j < m.ny) kd |= RK_YP;
+    if (k > 0) kd |= RK_ZM;
+    if (k < m.nz) kd |= RK_ZP;
+    if ((i + j + k) & 1) kd |= RK_ODD;
+    if (ty == -2) kd |= RK_INNER;
+    return kd;
+}
+
+// A regular row (kind without RK_GENERAL / RK_DIRICHLET) of the operator of
+// apply_row_ld, branch-free: absent neighbours are read from the window (any
+// finite value) and multiplied by zero.  wc points at the node's own entry;
+// NX, NXY are the window strides.  Same closed form as the regular branch of
+// apply_row_ld (summation order differs).
+template <typename T>
+static __device__ __forceinline__ T regular_row_masked(const T* wc, int NX, int NXY, unsigned kd, T h, T eps_plus,
+                                                       T eps_minus) {
+    const T mxm = (kd & RK_XM) ? (T)1 : (T)0, mxp = (kd & RK_XP) ? (T)1 : (T)0;
+    const T mym = (kd & RK_YM) ? (T)1 : (T)0, myp = (kd & RK_YP) ? (T)1 : (T)0;
+    const T mzm = (kd & RK_ZM) ? (T)1 : (T)0, mzp = (kd & RK_ZP) ? (T)1 : (T)0;
+    const bool odd = kd & RK_ODD;
+    const T eps = (kd & RK_INNER) ? eps_minus : eps_plus;
+    const T cx = mxm + mxp, cy = mym + myp, cz = mzm + mzp;
+    const T ax = mxm * wc[-1] + mxp * wc[1];
+    const T ay = mym * wc[-NX] + myp * wc[NX];
+    const T az = mzm * wc[-NXY] + mzp * wc[NXY];
+    T y = cx * cy * cz * (odd ? (T)0.5 : (T)0.75) * h * wc[0];
+    y -= (h / (T)6) * (cy * cz * ax + cx * cz * ay + cx * cy * az);
+    if (!odd) {
+        const T dxy = (mxm * mym) * wc[-1 - NX] + (mxp * mym) * wc[1 - NX] + (mxm * myp) * wc[-1 + NX] +
+                      (mxp * myp) * wc[1 + NX];
+        const T dxz = (mxm * mzm) * wc[-1 - NXY] + (mxp * mzm) * wc[1 - NXY] + (mxm * mzp) * wc[-1 + NXY] +
+                      (mxp * mzp) * wc[1 + NXY];
+        const T dyz = (mym * mzm) * wc[-NX - NXY] + (myp * mzm) * wc[NX - NXY] + (mym * mzp) * wc[-NX + NXY] +
+                      (myp * mzp) * wc[NX + NXY];
+        y -= (h / (T)12) * (cz * dxy + cy * dxz + cx * dyz);
+    }
+    return eps * y;
+}
+
 // The 19 coefficients of row n of the same operator, in the slot order of
 // apply_row_ld (centre, -x, +x, -y, +y, -z, +z, then -x-y, +x-y, -x+y, +x+y,
 // -x-z, +x-z, -x+z, +x+z, -y-z, +y-z, -y+z, +y+z); slots apply_row_ld skips

@@ -372,12 +372,9 @@ __global__ void k_push_movers_m(Launch L, ObjF of, float dthf) {
     if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
 }
 
-// injection: FP64 sampling and tests (as the FP64 path), stored as cell + FP32 offset
-PF_D bool outside_d(const Mesh& m, double x, double y, double z) {
-    return (x < 0.0) | (x >= (double)m.nx) | (y < 0.0) | (y >= (double)m.ny) | (z < 0.0) | (z >= (double)m.nz);
-}
-
-__global__ void k_inject_m(Launch L, InjArgs a) {
+// injection: FP32 sampling (same random streams as the FP64 path) and FP32
+// tests, stored as cell + FP32 offset
+__global__ void k_inject_m(Launch L, InjArgs a, ObjF of, float dthf) {
     __shared__ unsigned long long sctr[NCTR];
     const int q = blockIdx.y;
     const InjectDev d = a.st[q];
@@ -388,30 +385,30 @@ __global__ void k_inject_m(Launch L, InjArgs a) {
     const int cnt = a.count[q];
     const long long idb = a.idbase[q];
     const bool track = L.track;
+    const float nxf = (float)L.mesh.nx, nyf = (float)L.mesh.ny, nzf = (float)L.mesh.nz;
     for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
         int mm = base + threadIdx.x;
         int code = NONE, acc = -1;
         bool rejected = false;
         PF32 p;
         if (mm < cnt) {
-            InjSample sm = inject_sample(d, mm, *a.step, s, L.mesh, L.dth);
-            if (!sm.ok || level_set(L.obj, sm.p0[0], sm.p0[1], sm.p0[2]) < 0.0) {
+            // FP32 sample (the MIXED state is FP32); tests on the FP32 level set
+            const InjSampleF sm = inject_sample_f(d, mm, *a.step, s, L.mesh, dthf);
+            if (!sm.ok || level_set_f(of, sm.p0[0], sm.p0[1], sm.p0[2]) < 0.0f) {
                 rejected = true;
-            } else if (outside_d(L.mesh, sm.p[0], sm.p[1], sm.p[2])) {
+            } else if (sm.p[0] < 0.0f || sm.p[0] >= nxf || sm.p[1] < 0.0f || sm.p[1] >= nyf || sm.p[2] < 0.0f ||
+                       sm.p[2] >= nzf) {
                 code = ABSORBED;
             } else {
-                double fi = floor(sm.p[0]), fj = floor(sm.p[1]), fk = floor(sm.p[2]);
+                const float fi = floorf(sm.p[0]), fj = floorf(sm.p[1]), fk = floorf(sm.p[2]);
                 p.i = (int)fi; p.j = (int)fj; p.k = (int)fk;
-                p.fx = (float)(sm.p[0] - fi); p.fy = (float)(sm.p[1] - fj); p.fz = (float)(sm.p[2] - fk);
+                p.fx = sm.p[0] - fi; p.fy = sm.p[1] - fj; p.fz = sm.p[2] - fk;
                 if (p.fx >= 1.0f) p.fx = 0.99999994f;
                 if (p.fy >= 1.0f) p.fy = 0.99999994f;
                 if (p.fz >= 1.0f) p.fz = 0.99999994f;
-                p.vx = (float)sm.v[0]; p.vy = (float)sm.v[1]; p.vz = (float)sm.v[2];
-                if (level_set(L.obj, sm.p[0], sm.p[1], sm.p[2]) < 0.0) {
-                    ObjF of = {L.obj.kind, (float)L.obj.a0, (float)L.obj.a1, (float)L.obj.a2, (float)L.obj.a3,
-                               (float)L.obj.a4, (float)L.obj.a5};
-                    acc = hit_cell_f(L, of, (float)sm.p0[0], (float)sm.p0[1], (float)sm.p0[2], (float)sm.p[0],
-                                     (float)sm.p[1], (float)sm.p[2]);
+                p.vx = sm.v[0]; p.vy = sm.v[1]; p.vz = sm.v[2];
+                if (level_set_f(of, sm.p[0], sm.p[1], sm.p[2]) < 0.0f) {
+                    acc = hit_cell_f(L, of, sm.p0[0], sm.p0[1], sm.p0[2], sm.p[0], sm.p[1], sm.p[2]);
                     code = COLLECTED;
                     if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
                 } else {
@@ -621,7 +618,7 @@ cudaError_t launch_inject_mixed(Ctx& c) {
     for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
     unsigned gx = (unsigned)((maxc + 255) / 256);
     if (gx > 1024) gx = 1024;
-    k_inject_m<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a);
+    k_inject_m<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a, obj_f(c.obj), (float)c.dth);
     c.launches += 2;
     return cudaGetLastError();
 }

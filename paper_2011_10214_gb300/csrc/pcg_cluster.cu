@@ -48,11 +48,11 @@ struct ClusterShared {
 };
 
 // shared-memory layout of one CTA (T = working precision): r, p, q, x [M] T,
-// window [M + 2H] T, then pk [M] unsigned -- the 4-byte array last, so every T
-// array starts on a multiple of sizeof(T) for any M
+// window [M + 2H] T, pk [M] unsigned, kind [M] unsigned short -- narrower
+// arrays after wider ones, so each starts aligned for any M
 template <typename T>
 static __host__ __device__ __forceinline__ size_t cl_smem_bytes(long long M, long long H) {
-    return (size_t)M * (4 * sizeof(T) + sizeof(unsigned)) + (size_t)(M + 2 * H) * sizeof(T);
+    return (size_t)M * (4 * sizeof(T) + sizeof(unsigned) + sizeof(unsigned short)) + (size_t)(M + 2 * H) * sizeof(T);
 }
 
 // reduction across the cluster: every CTA gets the same NV totals
@@ -113,6 +113,9 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
     T* x = q + M;
     T* win = x + M;                 // node n at win[H + n - b0]
     unsigned* pk = (unsigned*)(win + M + 2 * H);
+    unsigned short* kind = (unsigned short*)(pk + M);
+    const int NXw = m.NX, NXYw = m.NX * m.NY;
+    const T hT = (T)m.h, epsP = (T)f.o.eps_plus, epsM = (T)f.o.eps_minus;
     const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
     const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
     const double tol2 = a.tol2;
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
         int i, j, k;
         node_ijk(m, b0 + li, i, j, k);
         pk[li] = cl_pack(i, j, k);
+        kind[li] = row_kind(f, b0 + li, i, j, k);
     }
     // window halves outside the instance's nodes stay zero (never read with a
     // non-zero coefficient, but inside the buffer)
@@ -179,8 +183,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
             __syncthreads();
             T v1[1] = {(T)0};
             for (int li = threadIdx.x; li < nown; li += CL_THREADS) {
-                const T az = row(li, ldw, coef);
-                const T zl = win[H + li];
+                const unsigned kd = kind[li];
+                const T* wc = win + ((int)H + li);
+                T az;
+                if (kd & RK_DIRICHLET) az = (T)0;
+                else if (kd & RK_GENERAL) az = row(li, ldw, coef);
+                else az = regular_row_masked<T>(wc, NXw, NXYw, kd, hT, epsP, epsM);
+                const T zl = wc[0];
                 T pl, ql;
                 if (first) {
                     pl = zl;
@@ -256,7 +265,7 @@ int cluster_size_for(long long N, long long H, bool mixed) {
         if (M > cap) continue;
         if (C > 1 && M < H) return 0;        // the halo would reach past the adjacent CTA
         const size_t bytes = mixed ? cl_smem_bytes<float>(M, H) : cl_smem_bytes<double>(M, H);
-        if (bytes + sizeof(ClusterShared) + 1024 > (size_t)smem_max) return 0;
+        if (bytes + sizeof(ClusterShared) + 1024 > (size_t)smem_max) continue;   // a larger cluster, smaller M
         return C;
     }
     return 0;

@@ -75,4 +75,63 @@ PF_D InjSample inject_sample(const InjectDev& d, int mm, long long step, int s, 
     return r;
 }
 
+// ---- FP32 sampling for the MIXED path -----------------------------------------
+// The same Philox counters and keys as above; uniforms from the top 24 bits,
+// ((x >> 40) + 0.5) 2^-24, strictly inside (0, 1) and exact in FP32, so an
+// injected particle is the FP64 sample to FP32 precision.
+PF_D float u01f(unsigned long long x) { return ((float)(x >> 40) + 0.5f) * 5.9604644775390625e-8f; }
+
+PF_D void box_muller_f(float u1, float u2, float& z0, float& z1) {
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+}
+
+PF_D bool flux_normal_f(unsigned long long m, unsigned long long seed, unsigned long long key1, float s, float& v) {
+    const float mu = 0.5f * (s + sqrtf(s * s + 4.0f));
+    for (int t = 0; t < MAX_TRIES; ++t) {
+        U64x4 r = philox4x64(m, 2 + t, 0, 0, seed, key1);
+        float z, z1;
+        box_muller_f(u01f(r.v[0]), u01f(r.v[1]), z, z1);
+        const float vv = mu + z;
+        const float ratio = vv / mu;
+        if (vv > 0.0f && u01f(r.v[2]) < ratio * expf(1.0f - ratio)) { v = vv; return true; }
+    }
+    return false;
+}
+
+struct InjSampleF {
+    float p0[3], p[3], v[3];
+    bool ok;
+};
+
+PF_D InjSampleF inject_sample_f(const InjectDev& d, int mm, long long step, int s, const Mesh& mesh, float dth) {
+    const int f = d.face, ax = f >> 1;
+    const float sgn = (f & 1) ? -1.0f : 1.0f;
+    const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+    const float nax[3] = {(float)mesh.nx, (float)mesh.ny, (float)mesh.nz};
+    const unsigned long long key1 = stream_key(2, s, f, step);
+    const unsigned long long m = (unsigned long long)mm;
+    U64x4 b0 = philox4x64(m, 0, 0, 0, d.seed, key1);
+    U64x4 b1 = philox4x64(m, 1, 0, 0, d.seed, key1);
+    InjSampleF r;
+    float vn = 0.0f;
+    const float vth = (float)d.vth;
+    r.ok = flux_normal_f(m, d.seed, key1, sgn * (float)d.drift[ax] / vth, vn);
+    float g1, g2;
+    box_muller_f(u01f(b1.v[0]), u01f(b1.v[1]), g1, g2);
+    r.p0[ax] = sgn > 0.0f ? 0.0f : nax[ax];
+    r.p0[t1] = u01f(b0.v[0]) * nax[t1];
+    r.p0[t2] = u01f(b0.v[1]) * nax[t2];
+    const float frac = u01f(b0.v[2]);
+    r.v[ax] = sgn * (vth * vn);
+    r.v[t1] = (float)d.drift[t1] + vth * g1;
+    r.v[t2] = (float)d.drift[t2] + vth * g2;
+    const float sl = frac * dth;
+    for (int c = 0; c < 3; ++c) r.p[c] = r.p0[c] + r.v[c] * sl;
+    return r;
+}
+
 }  // namespace pf
