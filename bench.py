@@ -409,7 +409,7 @@ def run_batch(args):
            "data": "synthetic (seeded Philox load and injection)",
            "config": {"workload": f"{len(cfgs)} independent sphere-charging instances, n ~ U{{16..48}}^3, "
                                   "R ~ U[1,8], eps ~ U[2,10], ppc ~ U{16..64}, MIXED",
-                      "particles": int(pushed / args.steps), "batched_pcg_threads": best,
+                      "particles": int(pushed / args.steps), "cta_nodes": best,
                       "setup_s": setup_s},
            "gpu_launches": int(sum(x["kernel_launches"] for x in st)), "graph_launches": args.steps,
            "pcg_iters_per_step_max": max(x["pcg_iters_total"] for x in st) / args.steps, "clocks": ck}
@@ -459,7 +459,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
     ap.add_argument("--instances", type=int, default=64)
-    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default PCG block size")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default nodes per CTA of the clustered solves")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--horizon", type=float, default=10.0)
     ap.add_argument("--max-steps", type=int, default=500)

@@ -215,21 +215,26 @@ pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const doub
 
 /* Batched steps over many independent contexts (serving many charging
  * problems at once; the paper runs one problem per job, Sec. 3 and Sec. 5).
- * One CUDA graph launch per step advances every member: each member's particle
- * phases and right-hand side are independent branches (they overlap on the
- * device), one batched PCG kernel solves every member's field with one CTA per
- * member, then each member's node field is formed.  Members must share one
- * precision; their own streams are synchronised before the batch stream (given
- * at creation) takes over.  A member's results do not depend on the other
- * members.  The graph is rebuilt on the next step after add / remove /
- * set_threads.  stats (if not NULL) receives one entry per member, in member
- * order.  The batch borrows the contexts: destroy the batch first. */
+ * One CUDA graph launch per step advances every member: each member is its own
+ * chain of particle phases, right-hand side, field solve and node field, and
+ * the chains overlap on the device.  A member's field solve runs on one
+ * thread-block cluster (1 to 16 CTAs of at most cta_nodes nodes each); a member
+ * too large for a cluster uses the single-member persistent solver.  Members
+ * must share one precision; their own streams are synchronised before the
+ * batch stream (given at creation) takes over.  A member's results do not
+ * depend on the other members.  The graph is rebuilt on the next step after
+ * add / remove / set_cta_nodes.  stats (if not NULL) receives one entry per
+ * member, in member order.  The batch borrows the contexts: destroy the batch
+ * first. */
 typedef struct pifepic_batch pifepic_batch;
 pifepic_status pifepic_batch_create(pifepic_ctx** ctxs, int n, void* stream, pifepic_batch** out);
 pifepic_status pifepic_batch_add(pifepic_batch* batch, pifepic_ctx* ctx);
 pifepic_status pifepic_batch_remove(pifepic_batch* batch, pifepic_ctx* ctx);
-/* CTA size of the batched PCG (256, 512 or 1024); the serving loop's tuner sets it. */
-pifepic_status pifepic_batch_set_threads(pifepic_batch* batch, int threads);
+/* Preferred nodes per CTA of the clustered solves (2048, 4096 or 8192, the
+ * default): a member gets the smallest cluster that keeps each CTA at or under
+ * it.  Fewer nodes per CTA is less work per iteration and more synchronisation;
+ * the serving loop's tuner picks by timing steps.  EINVAL for other values. */
+pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* batch, int cta_nodes);
 pifepic_status pifepic_batch_step(pifepic_batch* batch, int nsteps, pifepic_stats* stats);
 const char* pifepic_batch_last_error(const pifepic_batch* batch);
 void pifepic_batch_destroy(pifepic_batch* batch);

@@ -96,7 +96,7 @@ _sigs = {
     "pifepic_batch_create": [C.POINTER(_ctx), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)],
     "pifepic_batch_add": [C.c_void_p, _ctx],
     "pifepic_batch_remove": [C.c_void_p, _ctx],
-    "pifepic_batch_set_threads": [C.c_void_p, C.c_int],
+    "pifepic_batch_set_cta_nodes": [C.c_void_p, C.c_int],
     "pifepic_batch_step": [C.c_void_p, C.c_int, C.c_void_p],
 }
 for _n, _a in _sigs.items():
@@ -367,8 +367,9 @@ class Batch:
         self._ok(lib.pifepic_batch_remove(self._b, sim._c), "batch_remove")
         self.members.remove(sim)
 
-    def set_threads(self, threads):
-        self._ok(lib.pifepic_batch_set_threads(self._b, int(threads)), "batch_set_threads")
+    def set_cta_nodes(self, cta_nodes):
+        """Preferred nodes per CTA of the clustered field solves (2048, 4096, 8192)."""
+        self._ok(lib.pifepic_batch_set_cta_nodes(self._b, int(cta_nodes)), "batch_set_cta_nodes")
 
     def step(self, nsteps=1, stats=True):
         n = len(self.members)

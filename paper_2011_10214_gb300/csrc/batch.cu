@@ -26,127 +26,10 @@ pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, 
                             long long nsteps, long long kernels, pifepic_stats* st);
 
 
-constexpr double BATCH_INNER_TOL = 1e-4;
-constexpr int BATCH_MAX_OUTER = 12;
-
-// block-wide sums of NV doubles, the result broadcast to every thread
-template <int NV>
-static __device__ __forceinline__ void bsum(double (&v)[NV], double* sh, double* bc) {
-    block_sum<NV>(v, sh);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < NV; ++q) bc[q] = v[q];
-    __syncthreads();
-    for (int q = 0; q < NV; ++q) v[q] = bc[q];
-    __syncthreads();
-}
-
-// The same Jacobi PCG (and MIXED refinement) as the persistent kernel, run by
-// one CTA on one instance.
-template <bool MIXED, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_pcg_batch(const BatchItem* items) {
-    using T = typename std::conditional<MIXED, float, double>::type;
-    __shared__ double sh[3 * 32];
-    __shared__ double bc[4];
-    const BatchItem& a = items[blockIdx.x];
-    const FieldArgs& f = a.f;
-    const Mesh& m = f.m;
-    const long long N = m.nnodes;
-    T* r = MIXED ? (T*)a.rf : (T*)a.r;
-    T* z = MIXED ? (T*)a.zf : (T*)a.z;
-    T* p = MIXED ? (T*)a.pf : (T*)a.p;
-    T* q = MIXED ? (T*)a.qf : (T*)a.q;
-    const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
-    const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
-    const double tol2 = a.tol2;
-    const int maxit = a.maxit;
-    int it = 0, outer = 0;
-    double bb = 0.0, rr = 0.0;
-    bool conv = false;
-    for (;;) {
-        double v[3] = {0, 0, 0};
-        for (long long n = threadIdx.x; n < N; n += THREADS) {
-            int i, j, k;
-            node_ijk(m, n, i, j, k);
-            double bn = a.b[n];
-            double rn = (f.ntype[n] == -3) ? 0.0 : bn - apply_row<double>(f, n, i, j, k, a.u, f.coef);
-            T rt = (T)rn, zt = dinv[n] * rt;
-            r[n] = rt; z[n] = zt; p[n] = zt;
-            if (MIXED) a.df[n] = 0.0f;
-            v[0] += bn * bn;
-            v[1] += rn * rn;
-            v[2] += (double)rt * (double)zt;
-        }
-        bsum<3>(v, sh, bc);
-        if (outer == 0) bb = v[0];
-        rr = v[1];
-        double rz = v[2];
-        const double rr_stop = MIXED ? fmax(0.25 * tol2 * bb, BATCH_INNER_TOL * BATCH_INNER_TOL * v[1]) : tol2 * bb;
-        conv = (bb == 0.0) || (rr <= tol2 * bb);
-        if (conv || it >= maxit || (MIXED && outer >= BATCH_MAX_OUTER)) break;
-        ++outer;
-        T wt = (T)0;
-        for (long long n = threadIdx.x; n < N; n += THREADS) {
-            int i, j, k;
-            node_ijk(m, n, i, j, k);
-            T y = apply_row<T>(f, n, i, j, k, z, coef);
-            q[n] = y;
-            wt += p[n] * y;
-        }
-        double w[1] = {(double)wt};
-        bsum<1>(w, sh, bc);
-        double alpha = rz / w[0];
-        for (;;) {
-            T s0 = (T)0, s1 = (T)0;
-            const T al = (T)alpha;
-            for (long long n = threadIdx.x; n < N; n += THREADS) {
-                T rn = r[n] - al * q[n];
-                if (MIXED) a.df[n] = a.df[n] + (float)al * (float)p[n];
-                else a.u[n] = a.u[n] + alpha * (double)p[n];
-                T zn = dinv[n] * rn;
-                r[n] = rn; z[n] = zn;
-                s0 += rn * rn;
-                s1 += rn * zn;
-            }
-            double x2[2] = {(double)s0, (double)s1};
-            bsum<2>(x2, sh, bc);
-            const double beta = x2[1] / rz;
-            rz = x2[1];
-            rr = x2[0];
-            ++it;
-            if (!MIXED) conv = rr <= tol2 * bb;
-            if (rr <= rr_stop || it >= maxit) break;
-            T s2 = (T)0;
-            const T bt = (T)beta;
-            for (long long n = threadIdx.x; n < N; n += THREADS) {
-                int i, j, k;
-                node_ijk(m, n, i, j, k);
-                T pn = z[n] + bt * p[n];
-                T qn = apply_row<T>(f, n, i, j, k, z, coef) + bt * q[n];
-                p[n] = pn; q[n] = qn;
-                s2 += pn * qn;
-            }
-            double w2[1] = {(double)s2};
-            bsum<1>(w2, sh, bc);
-            alpha = rz / w2[0];
-        }
-        if (!MIXED) break;
-        for (long long n = threadIdx.x; n < N; n += THREADS) a.u[n] = a.u[n] + (double)a.df[n];
-        __syncthreads();
-    }
-    for (long long n = threadIdx.x; n < N; n += THREADS) a.phi[n] = (bb == 0.0) ? a.g[n] : a.u[n] + a.g[n];
-    if (threadIdx.x == 0) {
-        PcgState* S = a.S;
-        S->bb = bb; S->rr = rr; S->it = it; S->outer_it = outer;
-        S->converged = conv;
-        S->relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-        *a.it_total += it;
-        *a.outer_total += MIXED ? outer : 0;
-    }
-}
-
-int cluster_size_for(long long N, long long H, bool mixed);                      // pcg_cluster.cu
+int cluster_size_for(long long N, long long H, bool mixed, long long cta_nodes);   // pcg_cluster.cu
 size_t cluster_smem_for(long long N, long long H, int C, bool mixed);
 cudaError_t launch_pcg_cluster(const BatchItem* items, int count, int C, size_t smem, bool mixed, cudaStream_t st);
+cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st);                               // pcg_coop.cu
 cudaError_t launch_push(Ctx& c);
 cudaError_t launch_movers(Ctx& c);
 cudaError_t launch_inject(Ctx& c);
@@ -186,14 +69,6 @@ static cudaError_t capture(Ctx& c, cudaStream_t cs, F fn, cudaGraph_t* out) {
     return e;
 }
 
-template <bool MIXED>
-static cudaError_t launch_batch_pcg(const BatchItem* items, int n, int threads, cudaStream_t st) {
-    if (threads == 256) k_pcg_batch<MIXED, 256><<<n, 256, 0, st>>>(items);
-    else if (threads == 512) k_pcg_batch<MIXED, 512><<<n, 512, 0, st>>>(items);
-    else k_pcg_batch<MIXED, 1024><<<n, 1024, 0, st>>>(items);
-    return cudaGetLastError();
-}
-
 }  // namespace pf
 
 using namespace pf;
@@ -203,7 +78,7 @@ struct pifepic_batch {
     cudaStream_t stream = nullptr;
     BatchItem* items = nullptr;
     int items_cap = 0;
-    int threads = 512;
+    int cta_nodes = 8192;
     bool dirty = true;
     std::vector<long long> kernels;   // kernels per step of each instance (its share of the batch graph)
     cudaGraph_t graph = nullptr;
@@ -219,9 +94,9 @@ static pifepic_status batch_fail(pifepic_batch* b, pifepic_status st, const std:
 static long long node_halo(const Mesh& m) { return (long long)m.NX * m.NY + m.NX + 1; }
 
 // The batch step as one graph: per instance a chain of its particle phases,
-// right-hand side, field solve (one cluster launch; instances too large for a
-// cluster share one launch of the one-CTA-per-instance kernel) and node field,
-// so every instance advances as soon as its own work allows.
+// right-hand side, field solve (one cluster launch; an instance too large for
+// a cluster uses the single-instance persistent solver) and node field, so
+// every instance advances as soon as its own work allows.
 static cudaError_t build_batch_graph(pifepic_batch* b) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -238,7 +113,7 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     std::vector<int> csize(n, -1);
     for (int i = 0; i < n; ++i) {
         const Ctx& c = b->ctx[i]->c;
-        if (!c.external_E) csize[i] = cluster_size_for(c.mesh.nnodes, node_halo(c.mesh), mixed);
+        if (!c.external_E) csize[i] = cluster_size_for(c.mesh.nnodes, node_halo(c.mesh), mixed, b->cta_nodes);
     }
     const int groups[6] = {16, 8, 4, 2, 1, 0};
     std::vector<int> order;
@@ -278,7 +153,6 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
         c.launches = l0;
     }
     // one solve launch per instance, waiting only for that instance's branch
-    // (instances too large for a cluster share the one-CTA-per-instance kernel)
     size_t off = 0;
     std::vector<int> fallback;
     for (int gsz : groups) {
@@ -301,22 +175,19 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
             if (sub) cudaGraphDestroy(sub);
         }
     }
-    if (e == cudaSuccess && !fallback.empty()) {
-        const BatchItem* items = b->items + (off - fallback.size());
-        std::vector<cudaGraphNode_t> deps;
-        for (int i : fallback) deps.push_back(pre[i]);
+    // instances too large for a cluster: the single-instance persistent solver
+    // (one cooperative launch over the device), one after another -- two
+    // cooperative grids spinning on halves of the device could wait on each other
+    cudaGraphNode_t last_big = nullptr;
+    for (int i : fallback) {
+        if (e != cudaSuccess) break;
+        Ctx& c = b->ctx[i]->c;
         cudaGraph_t sub = nullptr;
-        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e2 = mixed ? launch_batch_pcg<true>(items, (int)fallback.size(), b->threads, cs)
-                                   : launch_batch_pcg<false>(items, (int)fallback.size(), b->threads, cs);
-            e = cudaStreamEndCapture(cs, &sub);
-            if (e == cudaSuccess) e = e2;
-        }
-        cudaGraphNode_t node = nullptr;
-        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, g, deps.data(), deps.size(), sub);
+        e = capture(c, cs, [](Ctx& cc) -> cudaError_t { return launch_pcg_coop(cc, cc.stream); }, &sub);
+        cudaGraphNode_t deps[2] = {pre[i], last_big};
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&solve_of[i], g, deps, last_big ? 2 : 1, sub);
         if (sub) cudaGraphDestroy(sub);
-        for (int i : fallback) solve_of[i] = node;
+        last_big = solve_of[i];
     }
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         Ctx& c = b->ctx[i]->c;
@@ -369,9 +240,9 @@ pifepic_status pifepic_batch_remove(pifepic_batch* b, pifepic_ctx* ctx) {
     return PIFEPIC_OK;
 }
 
-pifepic_status pifepic_batch_set_threads(pifepic_batch* b, int threads) {
-    if (!b || (threads != 256 && threads != 512 && threads != 1024)) return PIFEPIC_EINVAL;
-    if (threads != b->threads) { b->threads = threads; b->dirty = true; }
+pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* b, int cta_nodes) {
+    if (!b || (cta_nodes != 2048 && cta_nodes != 4096 && cta_nodes != 8192)) return PIFEPIC_EINVAL;
+    if (cta_nodes != b->cta_nodes) { b->cta_nodes = cta_nodes; b->dirty = true; }
     return PIFEPIC_OK;
 }
 

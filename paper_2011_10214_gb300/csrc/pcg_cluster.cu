@@ -254,21 +254,24 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
     cl.sync();
 }
 
-// cluster size for an instance of N nodes (H = halo), 0 if it does not fit
-int cluster_size_for(long long N, long long H, bool mixed) {
+// cluster size for an instance of N nodes (H = halo): the smallest C with at
+// most cta_nodes nodes per CTA, else the largest C that fits; 0 if none fits
+// (then the single-instance persistent solver takes the instance)
+int cluster_size_for(long long N, long long H, bool mixed, long long cta_nodes) {
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const long long cap = cl_max_nodes(mixed);
+    int best = 0;
     for (int C = 1; C <= 16; C *= 2) {
         const long long M = (N + C - 1) / C;
-        if (M > cap) continue;
-        if (C > 1 && M < H) return 0;        // the halo would reach past the adjacent CTA
+        if (C > 1 && M < H) break;            // the halo would reach past the adjacent CTA
         const size_t bytes = mixed ? cl_smem_bytes<float>(M, H) : cl_smem_bytes<double>(M, H);
-        if (bytes + sizeof(ClusterShared) + 1024 > (size_t)smem_max) continue;   // a larger cluster, smaller M
-        return C;
+        if (M > cap || bytes + sizeof(ClusterShared) + 1024 > (size_t)smem_max) continue;
+        best = C;
+        if (M <= cta_nodes) break;
     }
-    return 0;
+    return best;
 }
 
 // one launch for `count` instances (items[0..count)) that share cluster size C;

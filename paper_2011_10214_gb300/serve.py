@@ -68,7 +68,7 @@ class Member:
 
 class Server:
     def __init__(self, hbm_budget, precision=capi.MIXED, steps_per_round=10, max_steps=500, window=50,
-                 rel_change=0.01, pcg_tol=1e-6, threads=512, stream=None, keep_phi=False):
+                 rel_change=0.01, pcg_tol=1e-6, cta_nodes=8192, stream=None, keep_phi=False):
         self.budget = int(hbm_budget)
         self.precision = precision
         self.k = int(steps_per_round)
@@ -77,7 +77,7 @@ class Server:
         self.rel = float(rel_change)
         self.pcg_tol = pcg_tol
         self.batch = capi.Batch(stream=stream)
-        self.batch.set_threads(threads)
+        self.batch.set_cta_nodes(cta_nodes)
         self.stream = stream
         self.running = []
         self.used = 0
@@ -160,19 +160,20 @@ class Server:
         self.batch.close()
 
 
-def autotune_batch(batch, trial_steps=2, candidates=(256, 512, 1024)):
-    """Pick the batched-PCG CTA size by timing real steps of the batch (the
-    trial steps advance the members like any other step)."""
+def autotune_batch(batch, trial_steps=2, candidates=(8192, 4096, 2048)):
+    """Pick the clustered solves' nodes per CTA (hence each member's cluster
+    size) by timing real steps of the batch (the trial steps advance the
+    members like any other step)."""
     best, best_t = None, math.inf
-    for th in candidates:
-        batch.set_threads(th)
+    for cn in candidates:
+        batch.set_cta_nodes(cn)
         batch.step(1, stats=False)            # graph rebuild + warm-up
         t0 = time.perf_counter()
         batch.step(trial_steps, stats=False)
         t = time.perf_counter() - t0
         if t < best_t:
-            best, best_t = th, t
-    batch.set_threads(best)
+            best, best_t = cn, t
+    batch.set_cta_nodes(best)
     return best, best_t / trial_steps
 
 
