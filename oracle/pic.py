@@ -10,7 +10,8 @@ One step (reading of the loop's order, also in the design doc):
   1. gather + push every particle with the current node field;
   2. remove particles outside the domain, then collect particles inside the
      object (their charge goes to the surface accumulator of the crossing cell);
-  3. inject new particles at open faces (partial first step; same two tests);
+  3. inject new particles at open faces (partial first step; same two tests),
+     then emit photoelectrons from the sunlit surface (photo.py);
   4. scatter (fixed-point deposit) of all particles;
   5. field solve: right-hand side with the flux jump from the accumulated
      surface charge, Jacobi PCG warm-started from the previous potential;
@@ -22,6 +23,7 @@ import numpy as np
 
 from .field import FieldSystem
 from . import particles as pt
+from .photo import Photoemission
 
 FIELDS = ("x", "y", "z", "vx", "vy", "vz", "id")
 
@@ -31,6 +33,7 @@ class Species:
         self.q, self.m, self.w = float(q), float(m), float(w)
         self.k = (self.q / self.m) * dt      # (q/m) dt
         self.inj = None                      # (face_mask, density, vth, drift, seed)
+        self.photo = None                    # photo.Photoemission of this species
         self.carry = np.zeros(6)
         self.next_id = 0
 
@@ -86,6 +89,11 @@ class Simulation:
     def set_injection(self, s, face_mask, density, vth, drift, seed):
         self.species[s].inj = (int(face_mask), float(density), float(vth),
                                tuple(float(d) for d in drift), int(seed))
+
+    def set_photoemission(self, s, sun_dir, density, vth, seed):
+        """Species s is emitted from the sunlit, unshadowed object surface (Sec. 5.2.2; photo.py)."""
+        sp = self.species[s]
+        sp.photo = Photoemission(self.fs, s, sun_dir, density, vth, sp.w, self.dt, seed)
 
     def injection_rate(self, s, f):
         """Expected macro-particles per step through face f (one-way flux x A dt / w)."""
@@ -184,6 +192,19 @@ class Simulation:
                 sp.next_id += offset
                 for N in new:
                     P = {k: np.concatenate([P[k], N[k]]) for k in FIELDS}
+            if sp.photo is not None:
+                I = sp.photo.emit(self.step_no)
+                inside = self.obj.L(I["x"], I["y"], I["z"]) < 0.0
+                emitted = I["ok"] & ~inside
+                out = pt.outside(m, I["x"], I["y"], I["z"])
+                np.add.at(self.surf[:, s], I["acc"][emitted], -1)
+                keep = emitted & ~out
+                nab += int((emitted & out).sum())
+                nrej += int((~emitted).sum())
+                ninj += int(emitted.sum())
+                I["id"] = sp.next_id + I["index"]
+                sp.next_id += I["count"]
+                P = {k: np.concatenate([P[k], I[k][keep]]) for k in FIELDS}
             self.P[s] = P
             st["absorbed"].append(nab); st["collected"].append(nco)
             st["injected"].append(ninj); st["lost"].append(lost); st["inj_rejected"].append(nrej)
