@@ -165,7 +165,28 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int species, size_t n, c
  * rate = one-way drifting-Maxwellian flux * face area * dt / w. */
 pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int species, int face_mask, double density,
                                      double vth, const double drift[3], uint64_t seed);
+/* The six per-face rates (expected particles per step) of a species' injection. */
 pifepic_status pifepic_get_injection_rate(pifepic_ctx* ctx, int species, double rate[6]);
+
+/* Photoelectron emission (Sec. 5.2.2: photoelectrons are generated at the
+ * sunlit regions by the local sunlight index, the inner product of the sun
+ * vector and the surface normal).  Species s is emitted every step from the
+ * Gamma_h piece of every interface tet T with n_T . s > 0 whose centroid sees
+ * the sun (a ray towards sun_dir, sampled every quarter cell, never enters the
+ * object): rate J S_T A_T dt / w per step with J = density vth / sqrt(2 pi),
+ * held in fixed point (2^-20 particles) with an exact per-tet carry; points
+ * uniform on Gamma_h, flux-weighted half-Maxwellian normal speed, Gaussian
+ * tangential speeds, a partial first step; each emitted particle takes one
+ * count off its cut cell's surface accumulator (the surface charges up).
+ * sun_dir: 3 doubles, host, towards the sun, any length > 0.  Call after
+ * set_object and add_species; again to change it.  Errors: EINVAL (bad species,
+ * density < 0, vth <= 0, zero sun_dir), ESTATE (no object). */
+pifepic_status pifepic_set_photoemission(pifepic_ctx* ctx, int species, const double sun_dir[3], double density,
+                                         double vth, uint64_t seed);
+/* The emission set-up: rate_fixed = sum over emitting tets of the fixed-point
+ * rate (units of 2^-20 particles per step), emitting_tets = their number.
+ * Either pointer may be NULL. */
+pifepic_status pifepic_get_photoemission(pifepic_ctx* ctx, int64_t* rate_fixed, int64_t* emitting_tets);
 
 /* Freeze the node field to the given (nnodes x 3) array: steps then skip the
  * field solve (particle-only parity runs).  E == NULL unfreezes. */

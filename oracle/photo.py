@@ -128,7 +128,7 @@ class Photoemission:
                 g = g + Lv[v] * G[p][t][v]
             n = g / math.sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2])
             S = max(0.0, (n[0] * s[0] + n[1] * s[1]) + n[2] * s[2])
-            if S <= 0.0:
+            if S <= 0.0 or int(fs.it_acc[T]) < 0:
                 continue
             base = np.array([ci, cj, ck], dtype=np.float64)
             tris = [P + base for P in gamma_triangles(Lv, tv)]

@@ -76,6 +76,8 @@ _sigs = {
     "pifepic_load_particles": [_ctx, C.c_int, C.c_size_t] + [_dp] * 7 + [C.c_int],
     "pifepic_set_injection": [_ctx, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double * 3, C.c_uint64],
     "pifepic_get_injection_rate": [_ctx, C.c_int, C.c_double * 6],
+    "pifepic_set_photoemission": [_ctx, C.c_int, C.c_double * 3, C.c_double, C.c_double, C.c_uint64],
+    "pifepic_get_photoemission": [_ctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "pifepic_set_external_E": [_ctx, _dp, C.c_int],
     "pifepic_solve": [_ctx, C.POINTER(Stats)],
     "pifepic_leapfrog_init": [_ctx],
@@ -204,6 +206,18 @@ class Simulation:
     def set_injection(self, s, face_mask, density, vth, drift, seed):
         self._ok(lib.pifepic_set_injection(self._c, s, int(face_mask), float(density), float(vth),
                                            (C.c_double * 3)(*drift), C.c_uint64(int(seed))), "set_injection")
+
+    def set_photoemission(self, s, sun_dir, density, vth, seed):
+        """Species s is emitted from the sunlit, unshadowed object surface (see
+        pifepic_set_photoemission)."""
+        self._ok(lib.pifepic_set_photoemission(self._c, int(s), (C.c_double * 3)(*sun_dir), float(density),
+                                               float(vth), int(seed)), "set_photoemission")
+
+    def photoemission(self):
+        """(sum of the fixed-point rates in 2^-20 particles per step, emitting tets)."""
+        q, n = C.c_int64(), C.c_int64()
+        self._ok(lib.pifepic_get_photoemission(self._c, C.byref(q), C.byref(n)), "get_photoemission")
+        return q.value, n.value
 
     def injection_rate(self, s):
         r = (C.c_double * 6)()

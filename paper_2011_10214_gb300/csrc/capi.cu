@@ -247,7 +247,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
-                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
+                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
     for (auto& s : c.sp) {
@@ -501,6 +501,25 @@ static pifepic_status rebuild(pifepic_ctx* ctx, int s, PArr flat, long long n) {
     return PIFEPIC_OK;
 }
 
+// a species that grows during the run (photoelectrons start empty): when its
+// spill list passes a quarter of the mover capacity, rebuild its bins from the
+// current particles (capacity count * 1.25 + 64 per bin)
+static pifepic_status regrow_if_spilling(pifepic_ctx* ctx, int s) {
+    Ctx& c = ctx->c;
+    Species& q = c.sp[s];
+    unsigned long long w = 0;
+    CUDA_OK(scopy(c.stream, &w, q.mov_n, sizeof(w), cudaMemcpyDeviceToHost));
+    if ((long long)w * 4 <= q.mcap) return PIFEPIC_OK;
+    PArr flat; unsigned long long* nflat = nullptr; long long n0 = 0;
+    pifepic_status st = flatten(ctx, s, 0, &flat, &nflat, &n0);
+    if (st) return st;
+    unsigned long long nt = 0;
+    CUDA_OK(scopy(c.stream, &nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
+    st = rebuild(ctx, s, flat, (long long)nt);
+    free_parr(flat); cudaFree(nflat);
+    return st;
+}
+
 pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double vth, const double drift[3],
                                        uint64_t seed) {
     NEED(ctx); NEED(drift);
@@ -620,6 +639,33 @@ pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, dou
     long long need = std::max<long long>(1 << 16, n / 8 + 4096);
     for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
     return ensure_movers(ctx, s, need);
+}
+
+pifepic_status pifepic_set_photoemission(pifepic_ctx* ctx, int s, const double sun_dir[3], double density,
+                                         double vth, uint64_t seed) {
+    NEED(ctx); NEED(sun_dir);
+    Ctx& c = ctx->c;
+    if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    if (!(density >= 0.0) || !(vth > 0.0)) FAIL(PIFEPIC_EINVAL, "density must be >= 0 and vth > 0");
+    const double sl = (sun_dir[0] * sun_dir[0] + sun_dir[1] * sun_dir[1]) + sun_dir[2] * sun_dir[2];
+    if (!(sl > 0.0)) FAIL(PIFEPIC_EINVAL, "sun direction must be non-zero");
+    c.ph_species = s;
+    c.ph_seed = seed;
+    CUDA_OK(launch_photo_setup(c, sun_dir, density, vth, c.sp[s].w));
+    return ensure_movers(ctx, s, 1 << 16);
+}
+
+pifepic_status pifepic_get_photoemission(pifepic_ctx* ctx, int64_t* rate_fixed, int64_t* emitting_tets) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    std::vector<long long> Q((size_t)c.ph_ne);
+    if (c.ph_ne > 0) CUDA_OK(scopy(c.stream, Q.data(), c.ph_Q, sizeof(long long) * c.ph_ne, cudaMemcpyDeviceToHost));
+    long long sum = 0;
+    for (long long v : Q) sum += v;
+    if (rate_fixed) *rate_fixed = sum;
+    if (emitting_tets) *emitting_tets = c.ph_ne;
+    return PIFEPIC_OK;
 }
 
 pifepic_status pifepic_get_injection_rate(pifepic_ctx* ctx, int s, double rate[6]) {
@@ -796,6 +842,10 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
         CUDA_OK(cudaEventRecord(c.ev[5], c.stream));
         c.step_no += 1;
         CUDA_OK(cudaEventSynchronize(c.ev[5]));
+        if (c.ph_species >= 0) {
+            pifepic_status g = regrow_if_spilling(ctx, c.ph_species);
+            if (g) return g;
+        }
         float t;
         const int map[5] = {0, 1, 2, 3, 5};   // push, movers, inject, rebin, solve(+rhs+E)
         for (int k = 0; k < 5; ++k) {

@@ -50,6 +50,15 @@ struct InjectDev {                  // one (species, face) injection stream
     unsigned long long seed;
 };
 
+// one emitting interface tet of photoelectron emission (Sec. 5.2.2)
+struct PhotoDev {
+    double n[3], t1[3], t2[3];      // surface normal (into the plasma) and tangent basis
+    double P[2][3][3];              // Gamma_h triangles, global cell units
+    double area0, A;                // first triangle's area and the total (cell units)
+    int ntri, acc;                  // triangles; cut-cell accumulator of the tet's cell
+};
+constexpr int PHOTO_RATE_BITS = 20;  // per-tet rates and carries in units of 2^-20 particles
+
 struct Launch {                     // what every particle kernel needs
     Mesh mesh;
     Object obj;
@@ -163,6 +172,18 @@ struct Ctx {
     // graphs
     cudaGraphExec_t pcg_exec = nullptr;
     cudaGraph_t pcg_graph = nullptr;
+    // photoelectron emission: emitting tets in interface-tet order
+    int ph_species = -1;
+    long long ph_ne = 0;
+    PhotoDev* ph_tets = nullptr;
+    long long* ph_Q = nullptr;        // fixed-point rate per step
+    long long* ph_carry = nullptr;
+    int* ph_cnt = nullptr;            // this step's count per tet
+    long long* ph_base = nullptr;     // exclusive scan of ph_cnt
+    long long* ph_tiles = nullptr;    // scan tile sums
+    long long* ph_total = nullptr;    // this step's emissions
+    double ph_vth = 0.0;
+    unsigned long long ph_seed = 0;
     // particles
     std::vector<Species> sp;
     std::vector<InjectDev> inj;
@@ -219,6 +240,9 @@ enum {
 cudaError_t set_tet_tables(const TetTables& t);
 cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
 cudaError_t launch_node_E_tables(Ctx& c);              // field.cu: it_dataf, Lpos
+cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w);  // setup.cu
+cudaError_t launch_photo(Ctx& c);                      // particles.cu: one step of emission (FP64)
+cudaError_t launch_photo_mixed(Ctx& c);                // particles_mixed.cu
 cudaError_t launch_node_E64(Ctx& c);                   // field.cu: FP64 E from phi (E only)
 cudaError_t launch_field_lift(Ctx& c);
 cudaError_t build_pcg_graph(Ctx& c);                   // field.cu

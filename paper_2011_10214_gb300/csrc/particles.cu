@@ -702,18 +702,105 @@ cudaError_t launch_movers(Ctx& c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_inject(Ctx& c) {
-    if (c.inj.empty()) return cudaSuccess;
-    Launch L = make_launch(c);
-    InjArgs a = inj_args(c);
-    k_inject_counts<<<1, 32, 0, c.stream>>>(a);
-    int maxc = 1;
-    for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
-    unsigned gx = (unsigned)((maxc + 255) / 256);
-    if (gx > 1024) gx = 1024;
-    k_inject<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a);
+// ---- photoelectron emission (FP64 state) -------------------------------------
+// scan kernels of setup.cu (graph-safe here: the tile buffer is preallocated)
+__global__ void k_scan_tiles(const int* in, long long n, long long* out, long long* tile_sum);
+__global__ void k_scan_sums(long long* tile_sum, long long ntiles, long long* total);
+__global__ void k_scan_add(long long* out, long long n, const long long* tile_sum);
+
+// this step's count per emitting tet from the fixed-point carry
+__global__ void k_photo_counts(PhotoArgs a) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= a.ne) return;
+    const long long tot = a.carry[e] + a.Q[e];
+    a.cnt[e] = (int)(tot >> PHOTO_RATE_BITS);
+    a.carry[e] = tot & ((1ll << PHOTO_RATE_BITS) - 1);
+}
+
+__global__ void k_photo(Launch L, PhotoArgs a) {
+    __shared__ unsigned long long sctr[NCTR];
+    const SpeciesDev& S = L.sp[a.species];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const long long total = *a.total;
+    const long long idb = a.next_id[a.species];
+    const unsigned long long key1 = stream_key(3, a.species, 0, *a.step);
+    const bool track = L.track;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < total; base += stride) {
+        const long long m = base + threadIdx.x;
+        bool emitted = false, alive = false, out = false;
+        double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+        if (m < total) {
+            const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
+            const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
+            for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
+            emitted = sm.ok && !(level_set(L.obj, p[0], p[1], p[2]) < 0.0);
+            if (emitted) {
+                atomicAdd(&S.surf[d.acc], (unsigned long long)-1ll);   // the electron leaves +e behind
+                out = outside(L.mesh, p[0], p[1], p[2]);
+                alive = !out;
+                if (alive) global_deposit(L, S.W, weights(p[0], p[1], p[2]));
+            }
+        }
+        count_event(&sctr[C_INJECTED], emitted);
+        count_event(&sctr[C_REJECTED], m < total && !emitted);
+        count_event(&sctr[C_ABSORBED], out);
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) put(S.mov_out, slot, p[0], p[1], p[2], v[0], v[1], v[2], idb + m, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+__global__ void k_photo_ids(long long* next_id, const long long* total) { *next_id += *total; }
+
+PhotoArgs photo_args(Ctx& c) {
+    PhotoArgs a;
+    a.tets = c.ph_tets; a.Q = c.ph_Q; a.carry = c.ph_carry; a.cnt = c.ph_cnt; a.base = c.ph_base;
+    a.total = c.ph_total; a.next_id = c.next_id; a.ne = c.ph_ne; a.species = c.ph_species; a.vth = c.ph_vth;
+    a.seed = c.ph_seed; a.step = (const long long*)(c.scal + 42);
+    return a;
+}
+
+// counts and their scan for this step (both precisions)
+cudaError_t launch_photo_counts(Ctx& c) {
+    PhotoArgs a = photo_args(c);
+    const long long ne = c.ph_ne, ntiles = (ne + 2047) / 2048;
+    k_photo_counts<<<nb(ne), 256, 0, c.stream>>>(a);
+    k_scan_tiles<<<(unsigned)ntiles, 256, 0, c.stream>>>(c.ph_cnt, ne, c.ph_base, c.ph_tiles);
+    k_scan_sums<<<1, 32, 0, c.stream>>>(c.ph_tiles, ntiles, c.ph_total);
+    k_scan_add<<<nb(ne), 256, 0, c.stream>>>(c.ph_base, ne, c.ph_tiles);
+    c.launches += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_photo(Ctx& c) {
+    if (c.ph_species < 0 || c.ph_ne <= 0) return cudaSuccess;
+    cudaError_t e = launch_photo_counts(c);
+    if (e != cudaSuccess) return e;
+    k_photo<<<4 * 152, 256, 0, c.stream>>>(make_launch(c), photo_args(c));
+    k_photo_ids<<<1, 1, 0, c.stream>>>(c.next_id + c.ph_species, c.ph_total);
     c.launches += 2;
     return cudaGetLastError();
+}
+
+cudaError_t launch_inject(Ctx& c) {
+    if (!c.inj.empty()) {
+        Launch L = make_launch(c);
+        InjArgs a = inj_args(c);
+        k_inject_counts<<<1, 32, 0, c.stream>>>(a);
+        int maxc = 1;
+        for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
+        unsigned gx = (unsigned)((maxc + 255) / 256);
+        if (gx > 1024) gx = 1024;
+        k_inject<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a);
+        c.launches += 2;
+    }
+    return launch_photo(c);
 }
 
 cudaError_t launch_rebin(Ctx& c) {

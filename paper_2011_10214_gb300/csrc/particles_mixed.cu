@@ -609,16 +609,84 @@ cudaError_t launch_movers_mixed(Ctx& c) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_photo_mixed(Ctx& c);
+
 cudaError_t launch_inject_mixed(Ctx& c) {
-    if (c.inj.empty()) return cudaSuccess;
-    Launch L = make_launch(c);
-    InjArgs a = inj_args_m(c);
-    k_inject_counts<<<1, 32, 0, c.stream>>>(a);
-    int maxc = 1;
-    for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
-    unsigned gx = (unsigned)((maxc + 255) / 256);
-    if (gx > 1024) gx = 1024;
-    k_inject_m<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a, obj_f(c.obj), (float)c.dth);
+    if (!c.inj.empty()) {
+        Launch L = make_launch(c);
+        InjArgs a = inj_args_m(c);
+        k_inject_counts<<<1, 32, 0, c.stream>>>(a);
+        int maxc = 1;
+        for (auto& d : c.inj) maxc = d.maxcnt > maxc ? d.maxcnt : maxc;
+        unsigned gx = (unsigned)((maxc + 255) / 256);
+        if (gx > 1024) gx = 1024;
+        k_inject_m<<<dim3(gx, (unsigned)c.inj.size()), 256, 0, c.stream>>>(L, a, obj_f(c.obj), (float)c.dth);
+        c.launches += 2;
+    }
+    return launch_photo_mixed(c);
+}
+
+// ---- photoelectron emission (MIXED state) ----------------------------------
+// The emitted counts are small, so the sample is taken in FP64 exactly as on the
+// FP64 path and then stored as cell + FP32 offset.
+PhotoArgs photo_args(Ctx& c);                 // particles.cu
+cudaError_t launch_photo_counts(Ctx& c);
+__global__ void k_photo_ids(long long* next_id, const long long* total);
+
+__global__ void k_photo_m(Launch L, PhotoArgs a) {
+    __shared__ unsigned long long sctr[NCTR];
+    const SpeciesDev& S = L.sp[a.species];
+    if (threadIdx.x < NCTR) sctr[threadIdx.x] = 0ull;
+    __syncthreads();
+    const long long total = *a.total;
+    const long long idb = a.next_id[a.species];
+    const unsigned long long key1 = stream_key(3, a.species, 0, *a.step);
+    const bool track = L.track;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x; base < total; base += stride) {
+        const long long m = base + threadIdx.x;
+        bool emitted = false, alive = false, out = false;
+        PF32 p;
+        if (m < total) {
+            const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
+            const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
+            emitted = sm.ok && !(level_set(L.obj, sm.p[0], sm.p[1], sm.p[2]) < 0.0);
+            if (emitted) {
+                atomicAdd(&S.surf[d.acc], (unsigned long long)-1ll);   // the electron leaves +e behind
+                out = (sm.p[0] < 0.0) | (sm.p[0] >= (double)L.mesh.nx) | (sm.p[1] < 0.0) |
+                      (sm.p[1] >= (double)L.mesh.ny) | (sm.p[2] < 0.0) | (sm.p[2] >= (double)L.mesh.nz);
+                alive = !out;
+                if (alive) {
+                    const double fi = floor(sm.p[0]), fj = floor(sm.p[1]), fk = floor(sm.p[2]);
+                    p.i = (int)fi; p.j = (int)fj; p.k = (int)fk;
+                    p.fx = (float)(sm.p[0] - fi); p.fy = (float)(sm.p[1] - fj); p.fz = (float)(sm.p[2] - fk);
+                    if (p.fx >= 1.0f) p.fx = 0.99999994f;
+                    if (p.fy >= 1.0f) p.fy = 0.99999994f;
+                    if (p.fz >= 1.0f) p.fz = 0.99999994f;
+                    p.vx = (float)sm.v[0]; p.vy = (float)sm.v[1]; p.vz = (float)sm.v[2];
+                    global_deposit_f(L, S.W, p);
+                }
+            }
+        }
+        count_event(&sctr[C_INJECTED], emitted);
+        count_event(&sctr[C_REJECTED], m < total && !emitted);
+        count_event(&sctr[C_ABSORBED], out);
+        long long slot = warp_reserve(S.mov_out_n, alive);
+        if (alive) {
+            if (slot < S.mcap) store_p(S.movF_out, slot, p, idb + m, track);
+            else atomicAdd(&S.ctr[C_DROPPED], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
+}
+
+cudaError_t launch_photo_mixed(Ctx& c) {
+    if (c.ph_species < 0 || c.ph_ne <= 0) return cudaSuccess;
+    cudaError_t e = launch_photo_counts(c);
+    if (e != cudaSuccess) return e;
+    k_photo_m<<<4 * 152, 256, 0, c.stream>>>(make_launch(c), photo_args(c));
+    k_photo_ids<<<1, 1, 0, c.stream>>>(c.next_id + c.ph_species, c.ph_total);
     c.launches += 2;
     return cudaGetLastError();
 }

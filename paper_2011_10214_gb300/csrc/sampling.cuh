@@ -75,6 +75,65 @@ PF_D InjSample inject_sample(const InjectDev& d, int mm, long long step, int s, 
     return r;
 }
 
+// ---- photoelectron emission (Sec. 5.2.2) ----------------------------------------
+struct PhotoArgs {
+    const PhotoDev* tets;
+    const long long* Q;
+    long long* carry;
+    int* cnt;
+    const long long* base;
+    const long long* total;
+    long long* next_id;        // per species
+    long long ne;
+    int species;
+    double vth;
+    unsigned long long seed;
+    const long long* step;
+};
+
+struct PhotoSample {
+    double p0[3], p[3], v[3];
+    bool ok;
+};
+
+// particle m of this step's emissions from tet d: point on Gamma_h (triangle by
+// area, then sqrt(r1), r2), flux-weighted normal speed (zero drift), Gaussian
+// tangential speeds, then a fraction U of one step.  Blocks of counter (m, b):
+// 0 -> (triangle, r1, r2, U), 1 -> tangential normals, 2.. -> normal speed.
+PF_D PhotoSample photo_sample(const PhotoDev& d, unsigned long long m, unsigned long long seed,
+                              unsigned long long key1, double vth, double dth) {
+    PhotoSample r;
+    U64x4 b0 = philox4x64(m, 0, 0, 0, seed, key1);
+    U64x4 b1 = philox4x64(m, 1, 0, 0, seed, key1);
+    double vn = 0.0;
+    r.ok = flux_normal(m, seed, key1, 0.0, vn);
+    double g1, g2;
+    box_muller(u01(b1.v[0]), u01(b1.v[1]), g1, g2);
+    const double ut = u01(b0.v[0]), r1 = u01(b0.v[1]), r2 = u01(b0.v[2]), U = u01(b0.v[3]);
+    const int k = (d.ntri > 1 && ut * d.A >= d.area0) ? 1 : 0;
+    const double sq = sqrt(r1);
+    const double a0 = 1.0 - sq, a1 = sq * (1.0 - r2), a2 = sq * r2;
+    const double sl = U * dth;
+    for (int c = 0; c < 3; ++c) {
+        r.p0[c] = (a0 * d.P[k][0][c] + a1 * d.P[k][1][c]) + a2 * d.P[k][2][c];
+        r.v[c] = ((vth * vn) * d.n[c] + (vth * g1) * d.t1[c]) + (vth * g2) * d.t2[c];
+        r.p[c] = r.p0[c] + r.v[c] * sl;
+    }
+    return r;
+}
+
+// emitting tet of emission m: the last tet whose base is <= m (tets with no
+// emission this step share the base of the next one and come before it)
+PF_D long long photo_tet_of(const long long* base, long long ne, long long m) {
+    long long lo = 0, hi = ne;          // first index with base > m
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (base[mid] <= m) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - 1;
+}
+
 // ---- FP32 sampling for the MIXED path -----------------------------------------
 // The same Philox counters and keys as above; uniforms from the top 24 bits,
 // ((x >> 40) + 0.5) 2^-24, strictly inside (0, 1) and exact in FP32, so an

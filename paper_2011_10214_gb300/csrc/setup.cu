@@ -444,6 +444,138 @@ __global__ void k_narrow(const long long* in, long long n, int* out) {
     if (e < n) out[e] = (int)in[e];
 }
 
+// ---------------------------------------------------------------------------
+// photoelectron emission set-up (Sec. 5.2.2: generated at the sunlit surface by
+// the local sunlight index).  Per interface tet: the Gamma_h triangles in cell
+// units, the normal from the P1 gradient of the nodal level set, the sunlight
+// index, a ray-marched shadow test from the Gamma_h centroid, and the
+// fixed-point rate per step.  Operation order follows the definition exactly
+// (this unit is compiled without FMA contraction).
+// ---------------------------------------------------------------------------
+constexpr double PHOTO_RAY_STEP = 0.25;
+
+static __device__ void photo_cut(const double (&V)[4][3], const double (&Lv)[4], int u, int w, double (&out)[3]) {
+    const double t = Lv[u] / (Lv[u] - Lv[w]);
+    for (int d = 0; d < 3; ++d) out[d] = V[u][d] + t * (V[w][d] - V[u][d]);
+}
+
+static __device__ double photo_tri_area(const double (&P)[3][3]) {
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; ++d) { e1[d] = P[1][d] - P[0][d]; e2[d] = P[2][d] - P[0][d]; }
+    const double c0 = e1[1] * e2[2] - e1[2] * e2[1], c1 = e1[2] * e2[0] - e1[0] * e2[2], c2 = e1[0] * e2[1] - e1[1] * e2[0];
+    return 0.5 * sqrt((c0 * c0 + c1 * c1) + c2 * c2);
+}
+
+__global__ void k_photo_setup(Mesh m, Object obj, long long nit, const int* it_cell, const int* it_t,
+                              const double* Lnode, const int* it_acc, double sx, double sy, double sz, double J,
+                              double h2, double dt, double w, PhotoDev* rec, long long* Qall) {
+    const long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (T >= nit) return;
+    Qall[T] = 0;
+    const int c = it_cell[T];
+    const int ci = c % m.nx, cj = (c / m.nx) % m.ny, ck = c / (m.nx * m.ny);
+    const int p = (ci + cj + ck) & 1, t = it_t[T];
+    double V[4][3], Lv[4];
+    for (int v = 0; v < 4; ++v) {
+        const int l = cT.vert[p][t][v];
+        V[v][0] = (double)(l & 1); V[v][1] = (double)((l >> 1) & 1); V[v][2] = (double)((l >> 2) & 1);
+        Lv[v] = Lnode[node_id(m, ci + (l & 1), cj + ((l >> 1) & 1), ck + ((l >> 2) & 1))];
+    }
+    double g[3];
+    for (int d = 0; d < 3; ++d) g[d] = Lv[0] * cT.grad[p][t][0][d];
+    for (int v = 1; v < 4; ++v)
+        for (int d = 0; d < 3; ++d) g[d] = g[d] + Lv[v] * cT.grad[p][t][v][d];
+    const double gn = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+    double n[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+    const double S = fmax(0.0, (n[0] * sx + n[1] * sy) + n[2] * sz);
+    if (!(S > 0.0) || it_acc[T] < 0) return;
+    // Gamma_h triangles (cube-local), same cut and triangulation as the IFE set-up
+    int mi[4], pl[4], nm = 0, np = 0;
+    for (int v = 0; v < 4; ++v) {
+        if (Lv[v] < 0.0) mi[nm++] = v;
+        else pl[np++] = v;
+    }
+    PhotoDev d;
+    double P[2][3][3];
+    int ntri = 1;
+    if (nm == 1) {
+        for (int k = 0; k < 3; ++k) photo_cut(V, Lv, mi[0], pl[k], P[0][k]);
+    } else if (nm == 3) {
+        for (int k = 0; k < 3; ++k) photo_cut(V, Lv, mi[k], pl[0], P[0][k]);
+    } else if (nm == 2) {
+        double pac[3], pad[3], pbc[3], pbd[3];
+        photo_cut(V, Lv, mi[0], pl[0], pac);
+        photo_cut(V, Lv, mi[0], pl[1], pad);
+        photo_cut(V, Lv, mi[1], pl[0], pbc);
+        photo_cut(V, Lv, mi[1], pl[1], pbd);
+        for (int e = 0; e < 3; ++e) {
+            P[0][0][e] = pac[e]; P[0][1][e] = pad[e]; P[0][2][e] = pbd[e];
+            P[1][0][e] = pac[e]; P[1][1][e] = pbd[e]; P[1][2][e] = pbc[e];
+        }
+        ntri = 2;
+    } else {
+        return;
+    }
+    const double base[3] = {(double)ci, (double)cj, (double)ck};
+    for (int q = 0; q < ntri; ++q)
+        for (int k = 0; k < 3; ++k)
+            for (int e = 0; e < 3; ++e) P[q][k][e] = P[q][k][e] + base[e];
+    const double a0 = photo_tri_area(P[0]);
+    const double a1 = ntri > 1 ? photo_tri_area(P[1]) : 0.0;
+    const double A = a0 + a1;
+    if (!(A > 0.0)) return;
+    double cen[3];
+    for (int e = 0; e < 3; ++e) cen[e] = (a0 / 3.0) * ((P[0][0][e] + P[0][1][e]) + P[0][2][e]);
+    if (ntri > 1)
+        for (int e = 0; e < 3; ++e) cen[e] = cen[e] + (a1 / 3.0) * ((P[1][0][e] + P[1][1][e]) + P[1][2][e]);
+    for (int e = 0; e < 3; ++e) cen[e] = cen[e] / A;
+    // shadow: the ray towards the sun, sampled every quarter cell inside the box
+    const long long kmax = 4ll * (m.nx + m.ny + m.nz) + 8;
+    for (long long k = 1; k <= kmax; ++k) {
+        const double tt = PHOTO_RAY_STEP * (double)k;
+        const double qx = cen[0] + tt * sx, qy = cen[1] + tt * sy, qz = cen[2] + tt * sz;
+        if (qx < 0.0 || qx > (double)m.nx || qy < 0.0 || qy > (double)m.ny || qz < 0.0 || qz > (double)m.nz) break;
+        if (level_set(obj, qx, qy, qz) < 0.0) return;
+    }
+    const double R = J * S * (A * h2) * dt / w;
+    const long long Q = (long long)rint(R * (double)(1ll << PHOTO_RATE_BITS));
+    if (Q <= 0) return;
+    // tangent basis: e = the axis least aligned with n (first on ties)
+    const double an[3] = {fabs(n[0]), fabs(n[1]), fabs(n[2])};
+    int ax = 0;
+    if (an[1] < an[ax]) ax = 1;
+    if (an[2] < an[ax]) ax = 2;
+    const double ev[3] = {ax == 0 ? 1.0 : 0.0, ax == 1 ? 1.0 : 0.0, ax == 2 ? 1.0 : 0.0};
+    double cr[3] = {n[1] * ev[2] - n[2] * ev[1], n[2] * ev[0] - n[0] * ev[2], n[0] * ev[1] - n[1] * ev[0]};
+    const double cl = sqrt((cr[0] * cr[0] + cr[1] * cr[1]) + cr[2] * cr[2]);
+    for (int e = 0; e < 3; ++e) { d.n[e] = n[e]; d.t1[e] = cr[e] / cl; }
+    d.t2[0] = n[1] * d.t1[2] - n[2] * d.t1[1];
+    d.t2[1] = n[2] * d.t1[0] - n[0] * d.t1[2];
+    d.t2[2] = n[0] * d.t1[1] - n[1] * d.t1[0];
+    for (int q = 0; q < 2; ++q)
+        for (int k = 0; k < 3; ++k)
+            for (int e = 0; e < 3; ++e) d.P[q][k][e] = q < ntri ? P[q][k][e] : 0.0;
+    d.area0 = a0;
+    d.A = A;
+    d.ntri = ntri;
+    d.acc = it_acc[T];
+    rec[T] = d;
+    Qall[T] = Q;
+}
+
+__global__ void k_photo_flag(long long nit, const long long* Qall, int* flag) {
+    const long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (T < nit) flag[T] = Qall[T] > 0 ? 1 : 0;
+}
+
+__global__ void k_photo_compact(long long nit, const long long* Qall, const PhotoDev* rec, const long long* pos,
+                                PhotoDev* tets, long long* Q) {
+    const long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (T >= nit || Qall[T] <= 0) return;
+    tets[pos[T]] = rec[T];
+    Q[pos[T]] = Qall[T];
+}
+
 #define CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) { err = _e; goto done; } } while (0)
 
 cudaError_t launch_setup(Ctx& c) {
@@ -523,6 +655,61 @@ cudaError_t launch_setup(Ctx& c) {
 done:
     cudaFree(cnt); cudaFree(scan); cudaFree(tot); cudaFree(flag); cudaFree(carea); cudaFree(own);
     cudaFree(bcdir); cudaFree(bcval);
+    return err;
+}
+
+// emission set-up for the context's photo species (all buffers (re)allocated
+// here, outside any captured graph)
+cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w) {
+    void* old[] = {c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total};
+    for (void* p : old) cudaFree(p);
+    c.ph_tets = nullptr; c.ph_Q = c.ph_carry = c.ph_base = c.ph_tiles = c.ph_total = nullptr; c.ph_cnt = nullptr;
+    c.ph_ne = 0;
+    const long long nit = c.nit;
+    const double sl = sqrt((sun[0] * sun[0] + sun[1] * sun[1]) + sun[2] * sun[2]);
+    const double s0 = sun[0] / sl, s1 = sun[1] / sl, s2 = sun[2] / sl;
+    const double J = density * vth / sqrt(2.0 * 3.141592653589793);
+    PhotoDev* rec = nullptr;
+    long long *Qall = nullptr, *pos = nullptr, *tot = nullptr;
+    int* flag = nullptr;
+    cudaError_t err = cudaSuccess;
+    long long ne = 0;
+    const long long n1 = nit > 0 ? nit : 1;
+    CK(cudaMalloc(&rec, sizeof(PhotoDev) * n1));
+    CK(cudaMalloc(&Qall, sizeof(long long) * n1));
+    CK(cudaMalloc(&pos, sizeof(long long) * n1));
+    CK(cudaMalloc(&flag, sizeof(int) * n1));
+    CK(cudaMalloc(&tot, sizeof(long long)));
+    CK(cudaMemsetAsync(Qall, 0, sizeof(long long) * n1, c.stream));
+    CK(cudaMemsetAsync(rec, 0, sizeof(PhotoDev) * n1, c.stream));
+    if (nit > 0) {
+        k_photo_setup<<<nb(nit), 256, 0, c.stream>>>(c.mesh, c.obj, nit, c.it_cell, c.it_t, c.Lnode, c.it_acc, s0, s1,
+                                                     s2, J, c.mesh.h * c.mesh.h, c.dt, w, rec, Qall);
+        k_photo_flag<<<nb(nit), 256, 0, c.stream>>>(nit, Qall, flag);
+        CK(cudaGetLastError());
+        CK(exclusive_scan(flag, nit, pos, tot, c.stream));
+        CK(cudaMemcpyAsync(&ne, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
+    {
+        const long long m1 = ne > 0 ? ne : 1;
+        CK(cudaMalloc(&c.ph_tets, sizeof(PhotoDev) * m1));
+        CK(cudaMalloc(&c.ph_Q, sizeof(long long) * m1));
+        CK(cudaMalloc(&c.ph_carry, sizeof(long long) * m1));
+        CK(cudaMalloc(&c.ph_cnt, sizeof(int) * m1));
+        CK(cudaMalloc(&c.ph_base, sizeof(long long) * m1));
+        CK(cudaMalloc(&c.ph_tiles, sizeof(long long) * (m1 / 2048 + 2)));
+        CK(cudaMalloc(&c.ph_total, sizeof(long long)));
+        CK(cudaMemsetAsync(c.ph_carry, 0, sizeof(long long) * m1, c.stream));
+        CK(cudaMemsetAsync(c.ph_total, 0, sizeof(long long), c.stream));
+        if (ne > 0) k_photo_compact<<<nb(nit), 256, 0, c.stream>>>(nit, Qall, rec, pos, c.ph_tets, c.ph_Q);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c.stream));
+        c.ph_ne = ne;
+        c.ph_vth = vth;
+    }
+done:
+    cudaFree(rec); cudaFree(Qall); cudaFree(pos); cudaFree(flag); cudaFree(tot);
     return err;
 }
 

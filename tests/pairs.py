@@ -16,6 +16,9 @@ CASES = {
                    bc=[("N",)] * 5 + [("D", 0.0)]),
     "plane": dict(n=(12, 12, 12), h=0.5, obj=("plane", (0.3, -0.5, 1.0), 4.37, 10.0, 1.0),
                   bc=[("D", 0.0)] * 6),
+    # off-node ground with a bowl, for photoemission under a low sun (shadows)
+    "crater_sun": dict(n=(24, 24, 12), h=1.0, obj=("cap_crater", 6.3, 12.0, 12.0, 8.0, 3.0, 4.0, 1.0),
+                       bc=[("N",)] * 5 + [("D", 0.0)]),
 }
 
 
