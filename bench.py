@@ -82,15 +82,25 @@ class Clocks:
 def workload(name):
     from paper_2011_10214_gb300 import workloads as wl
     return {"sphere64": wl.SPHERE64, "sphere16": wl.SPHERE16,
-            "sphere32": wl.sphere_config(32, 3.0, 64, 100, seed_offset=6)}[name]
+            "sphere32": wl.sphere_config(32, 3.0, 64, 100, seed_offset=6),
+            "crater160": wl.CRATER160,
+            "crater80": wl.crater_config(80, 80, 40, 10.0, 15.0, 5.0, seed_offset=7)}[name]
 
 
 def cfg_desc(cfg, precision, extra=None):
     n = cfg["n"]
     ppc = cfg["species"][0]["ppc"]
-    d = {"workload": f"sphere charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={cfg['object']['radius']}, "
-                     f"eps_in={cfg['object']['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e=100), "
-                     f"dt={cfg['dt']}, flux injection, phi=0 faces",
+    ob = cfg["object"]
+    if ob["kind"] == "cap_crater":
+        w = (f"crater charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), ground z={ob['z_ground']} eps "
+             f"{ob['eps_in']}, spherical-cap crater rim radius {ob['rim_radius']} depth {ob['depth']}, "
+             f"{ppc} ppc/species solar-wind e-+H+ drifting 8 v_ti at 45 deg, photoelectrons from the sunlit "
+             f"unshadowed surface, dt={cfg['dt']}, phi=0 at Z_max, Neumann elsewhere")
+    else:
+        w = (f"sphere charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={ob['radius']}, "
+             f"eps_in={ob['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e=100), "
+             f"dt={cfg['dt']}, flux injection, phi=0 faces")
+    d = {"workload": w,
          "precision": precision, "pcg_tol": 1e-6, "pcg_max_iter": 150,
          "l2_flush": "inputs larger than L2 (particle state > 1 GB per step)"}
     if extra:
@@ -453,7 +463,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="sphere64", choices=["sphere64", "sphere32", "sphere16"])
+    ap.add_argument("--workload", default="sphere64",
+                    choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")

@@ -352,6 +352,11 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
             sim.load_maxwellian(s, sp["ppc"], sp["vth"], sp["drift"], cfg["seed"])
         if inject:
             sim.set_injection(s, cfg["inject_faces"], sp["density"], sp["vth"], sp["drift"], cfg["seed"])
+    ph = cfg.get("photo")
+    if ph is not None:
+        s = sim.add_species(ph["q"], ph["m"], ph["weight"])
+        if inject:
+            sim.set_photoemission(s, ph["sun"], ph["density"], ph["vth"], cfg["seed"])
     return sim
 
 

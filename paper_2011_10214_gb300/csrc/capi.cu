@@ -247,7 +247,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
-                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
+                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
     for (auto& s : c.sp) {
@@ -494,6 +494,7 @@ static pifepic_status rebuild(pifepic_ctx* ctx, int s, PArr flat, long long n) {
     Ctx& c = ctx->c;
     long long need = std::max<long long>(1 << 16, n / 8 + 4096);
     for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
+    if (s == c.ph_species) need += 4ll * (long long)c.ph_rate + 4096;
     pifepic_status st = ensure_movers(ctx, s, need);
     if (st) return st;
     CUDA_OK(c.precision == PIFEPIC_MIXED ? launch_build_bins_mixed(c, s, flat, n, true)
@@ -638,6 +639,7 @@ pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, dou
     long long n = count_particles(c, s);
     long long need = std::max<long long>(1 << 16, n / 8 + 4096);
     for (auto& d : c.inj) if (d.species == s) need += 4ll * (d.maxcnt + 1);
+    if (s == c.ph_species) need += 4ll * (long long)c.ph_rate + 4096;
     return ensure_movers(ctx, s, need);
 }
 
@@ -653,7 +655,12 @@ pifepic_status pifepic_set_photoemission(pifepic_ctx* ctx, int s, const double s
     c.ph_species = s;
     c.ph_seed = seed;
     CUDA_OK(launch_photo_setup(c, sun_dir, density, vth, c.sp[s].w));
-    return ensure_movers(ctx, s, 1 << 16);
+    int64_t q = 0;
+    pifepic_status st = pifepic_get_photoemission(ctx, &q, nullptr);
+    if (st) return st;
+    c.ph_rate = (double)q / (double)(1ll << PHOTO_RATE_BITS);
+    // the mover list takes each step's emissions before the rebin
+    return ensure_movers(ctx, s, std::max<long long>(1 << 16, 4ll * (long long)c.ph_rate + 4096));
 }
 
 pifepic_status pifepic_get_photoemission(pifepic_ctx* ctx, int64_t* rate_fixed, int64_t* emitting_tets) {

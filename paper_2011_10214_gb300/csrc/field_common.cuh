@@ -149,34 +149,41 @@ static __device__ __forceinline__ unsigned short row_kind(const FieldArgs& f, lo
 }
 
 // A regular row (kind without RK_GENERAL / RK_DIRICHLET) of the operator of
-// apply_row_ld, branch-free: absent neighbours are read from the window (any
-// finite value) and multiplied by zero.  wc points at the node's own entry;
-// NX, NXY are the window strides.  Same closed form as the regular branch of
-// apply_row_ld (summation order differs).
-template <typename T>
-static __device__ __forceinline__ T regular_row_masked(const T* wc, int NX, int NXY, unsigned kd, T h, T eps_plus,
-                                                       T eps_minus) {
+// apply_row_ld, branch-free: absent neighbours are read (any finite value) and
+// multiplied by zero.  ld(o) returns x at offset o from the node; NX, NXY are
+// the strides.  Same closed form as the regular branch of apply_row_ld
+// (summation order differs).
+template <typename T, typename LD>
+static __device__ __forceinline__ T regular_row_masked_ld(LD ld, int NX, int NXY, unsigned kd, T h, T eps_plus,
+                                                          T eps_minus) {
     const T mxm = (kd & RK_XM) ? (T)1 : (T)0, mxp = (kd & RK_XP) ? (T)1 : (T)0;
     const T mym = (kd & RK_YM) ? (T)1 : (T)0, myp = (kd & RK_YP) ? (T)1 : (T)0;
     const T mzm = (kd & RK_ZM) ? (T)1 : (T)0, mzp = (kd & RK_ZP) ? (T)1 : (T)0;
     const bool odd = kd & RK_ODD;
     const T eps = (kd & RK_INNER) ? eps_minus : eps_plus;
     const T cx = mxm + mxp, cy = mym + myp, cz = mzm + mzp;
-    const T ax = mxm * wc[-1] + mxp * wc[1];
-    const T ay = mym * wc[-NX] + myp * wc[NX];
-    const T az = mzm * wc[-NXY] + mzp * wc[NXY];
-    T y = cx * cy * cz * (odd ? (T)0.5 : (T)0.75) * h * wc[0];
+    const T ax = mxm * ld(-1) + mxp * ld(1);
+    const T ay = mym * ld(-NX) + myp * ld(NX);
+    const T az = mzm * ld(-NXY) + mzp * ld(NXY);
+    T y = cx * cy * cz * (odd ? (T)0.5 : (T)0.75) * h * ld(0);
     y -= (h / (T)6) * (cy * cz * ax + cx * cz * ay + cx * cy * az);
     if (!odd) {
-        const T dxy = (mxm * mym) * wc[-1 - NX] + (mxp * mym) * wc[1 - NX] + (mxm * myp) * wc[-1 + NX] +
-                      (mxp * myp) * wc[1 + NX];
-        const T dxz = (mxm * mzm) * wc[-1 - NXY] + (mxp * mzm) * wc[1 - NXY] + (mxm * mzp) * wc[-1 + NXY] +
-                      (mxp * mzp) * wc[1 + NXY];
-        const T dyz = (mym * mzm) * wc[-NX - NXY] + (myp * mzm) * wc[NX - NXY] + (mym * mzp) * wc[-NX + NXY] +
-                      (myp * mzp) * wc[NX + NXY];
+        const T dxy = (mxm * mym) * ld(-1 - NX) + (mxp * mym) * ld(1 - NX) + (mxm * myp) * ld(-1 + NX) +
+                      (mxp * myp) * ld(1 + NX);
+        const T dxz = (mxm * mzm) * ld(-1 - NXY) + (mxp * mzm) * ld(1 - NXY) + (mxm * mzp) * ld(-1 + NXY) +
+                      (mxp * mzp) * ld(1 + NXY);
+        const T dyz = (mym * mzm) * ld(-NX - NXY) + (myp * mzm) * ld(NX - NXY) + (mym * mzp) * ld(-NX + NXY) +
+                      (myp * mzp) * ld(NX + NXY);
         y -= (h / (T)12) * (cz * dxy + cy * dxz + cx * dyz);
     }
     return eps * y;
+}
+
+// the same row over a window in shared memory; wc points at the node's entry
+template <typename T>
+static __device__ __forceinline__ T regular_row_masked(const T* wc, int NX, int NXY, unsigned kd, T h, T eps_plus,
+                                                       T eps_minus) {
+    return regular_row_masked_ld<T>([&](int o) { return wc[o]; }, NX, NXY, kd, h, eps_plus, eps_minus);
 }
 
 // The 19 coefficients of row n of the same operator, in the slot order of

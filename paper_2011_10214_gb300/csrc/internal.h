@@ -165,6 +165,8 @@ struct Ctx {
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;
     bool pcg_rows = false;            // operator rows staged in shared memory
+    unsigned short* rowkind = nullptr;  // global-memory PCG (larger meshes): row kinds, [N]
+    double* pcg_x = nullptr;            // and its FP64 correction vector, [N]
     int pcg_G = 1;
     long long pcg_M = 0;
     size_t pcg_smem = 0;
@@ -183,6 +185,7 @@ struct Ctx {
     long long* ph_tiles = nullptr;    // scan tile sums
     long long* ph_total = nullptr;    // this step's emissions
     double ph_vth = 0.0;
+    double ph_rate = 0.0;             // expected emissions per step (sizes the mover list)
     unsigned long long ph_seed = 0;
     // particles
     std::vector<Species> sp;

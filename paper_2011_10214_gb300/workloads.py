@@ -41,6 +41,43 @@ SPHERE16 = sphere_config(16, 2.0, 16, 100, seed_offset=1)
 SPHERE64 = sphere_config(64, 6.0, 64, 1000, seed_offset=2)
 
 
+def crater_config(nx=160, ny=160, nz=80, z_ground=20.0, rim_radius=30.0, depth=10.0, ppc=125, steps=200,
+                  mass_ratio=100.0, dt=0.05, seed_offset=3):
+    """Crater charging (Sec. 5, scaled to one GPU): cells of one photoelectron
+    Debye length; dielectric ground (eps 4) at z_ground with a spherical-cap
+    crater of the given rim radius and depth centred in x, y; phi = 0 at Z_max,
+    zero Neumann on the other faces; drifting solar-wind electrons and ions
+    (T_e : T_i : T_ph = 6 : 5 : 1, density 8.7/64 of the photoelectron
+    reference, drift 8 ion thermal speeds at 45 degrees towards the ground in
+    the X-Z plane) loaded at ppc per species in the plasma and injected on every
+    face but Z_min; photoelectrons (vth 1, reference density 1) emitted from the
+    sunlit, unshadowed surface, the sun opposite to the flow.  The photoelectron
+    macro-particle carries the solar-wind electrons' charge."""
+    n_sw = 8.7 / 64.0
+    vte, vti = np.sqrt(6.0), np.sqrt(5.0 / mass_ratio)
+    vd = 8.0 * vti
+    c45 = np.sqrt(0.5)
+    drift = (vd * c45, 0.0, -vd * c45)
+    return dict(
+        name=f"crater{nx}",
+        n=(nx, ny, nz), h=1.0, origin=(0.0, 0.0, 0.0), dt=dt, steps=steps,
+        object=dict(kind="cap_crater", z_ground=z_ground, xc=nx / 2, yc=ny / 2, rim_radius=rim_radius,
+                    depth=depth, eps_in=4.0, eps_out=1.0),
+        face_bc=[("N",)] * 5 + [("D", 0.0)],
+        species=[dict(name="sw e-", q=-1.0, m=1.0, vth=vte, ppc=ppc, density=n_sw, drift=drift),
+                 dict(name="sw H+", q=1.0, m=mass_ratio, vth=vti, ppc=ppc, density=n_sw, drift=drift)],
+        photo=dict(name="photo e-", q=-1.0, m=1.0, vth=1.0, density=1.0, weight=n_sw / ppc,
+                   sun=(-c45, 0.0, c45)),
+        inject_faces=0b101111,
+        seed=SEED_BASE + seed_offset,
+    )
+
+
+# 160 x 160 x 80 cells (~10M tets), crater of rim radius 30 and depth 10 in a
+# ground at z = 20, 125 ppc per solar-wind species in the plasma (~384M), 200 steps
+CRATER160 = crater_config()
+
+
 def macro_weight(cfg, sp):
     return sp["density"] * cfg["h"] ** 3 / sp["ppc"]
 

@@ -109,3 +109,29 @@ def test_solve_sizes_of_every_nodes_per_thread_variant(n):
         it2, rr2 = sim.solve_field(F, q)
         assert rr2 <= 1e-12 and it2 <= 2, (precision, it2)
         sim.close()
+
+
+def test_global_memory_solver_on_a_large_crater():
+    """112 x 112 x 56 cells (728k nodes, more than 8 per thread of the
+    register-resident kernel): the global-memory persistent PCG, both
+    precisions, reaches the oracle's FP64 solution at tol 1e-12."""
+    from oracle.field import FieldSystem
+    from oracle.geometry import CapCrater, Mesh
+    from paper_2011_10214_gb300 import capi
+    n = (112, 112, 56)
+    m = Mesh(*n, 1.0)
+    crater = (14.3, 56.0, 56.0, 20.0, 7.0)
+    bc = [("N",)] * 5 + [("D", 0.0)]
+    fs = FieldSystem(m, CapCrater(m, *crater, 4.0, 1.0), bc)
+    g = np.random.default_rng(5)
+    F = g.normal(size=m.nnodes)
+    q = g.normal(size=len(fs.it_cell))
+    phi_o, _, _ = fs.solve(F, q, tol=1e-12, maxit=20000)
+    for precision in (capi.FP64, capi.MIXED):
+        sim = capi.Simulation(n, 1.0, 0.05, precision=precision, pcg_tol=1e-12, pcg_max_iter=20000)
+        sim.set_field_bc(bc)
+        sim.set_object(capi.OBJ_CAP_CRATER, list(crater), 4.0, 1.0)
+        it, rr = sim.solve_field(F, q)
+        assert rr <= 1e-12, (precision, rr)
+        assert _rel(sim.potential(), phi_o) <= TOL_PHI, precision
+        sim.close()
