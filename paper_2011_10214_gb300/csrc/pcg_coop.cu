@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
 // masked stencil selected by a per-node kind word (made once per mesh);
 // interface rows use their patch coefficients.  Each thread takes its nodes
 // four at a time and issues every load of the four before any store, so the
-// L2 round trips of a group overlap.
+// L2 round trips of a group overlap; two 512-thread blocks per SM (64
+// registers, a few spilled) hide more latency than one block without spills.
 
 constexpr int GLOB_THREADS = 512;
 constexpr int GLOB_UNROLL = 4;
@@ -403,7 +404,7 @@ static __device__ __forceinline__ T glob_row(const GlobArgs& a, const T* x, long
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(GLOB_THREADS) k_pcg_glob(GlobArgs a) {
+__global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     __shared__ ExchShared xs;
     const FieldArgs& f = a.f;
@@ -696,7 +697,7 @@ cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_glob<true>, GLOB_THREADS, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_glob<false>, GLOB_THREADS, 0);
     long long G = (long long)nsm * (per > 0 ? per : 1);
-    if (G > 2048) G = 2048;   // partial slots hold 2 x 4 x 2048 values
+    if (G > GLOB_THREADS) G = GLOB_THREADS;   // an exchange reads one block partial per thread
     void* args[] = {&a};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)G);
