@@ -191,7 +191,10 @@ def roofline_solve(precision, st, steps, nnodes):
     alg = nnodes * SOLVE_BYTES_PER_NODE_ITER[precision] * iters
     ach = alg / (solve_ms / 1e3) / 1e9
     peaks, src = _peaks()
-    return {"kernel": "k_pcg_reg (persistent PCG, one launch per solve) in the solve graph", "bound": "hbm",
+    # the register-resident kernel serves meshes of at most 8 nodes per thread of a full grid
+    reg = nnodes <= NSM * 512 * 8
+    kname = "k_pcg_reg (registers)" if reg else "k_pcg_glob (global memory)"
+    return {"kernel": f"{kname}: persistent PCG, one launch per solve, in the solve graph", "bound": "hbm",
             "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
             "alg_bytes_per_launch": alg, "avg_launch_ms": solve_ms, "iters_per_solve": iters,
