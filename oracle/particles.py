@@ -105,6 +105,30 @@ def outside(mesh, x, y, z):
     return (x < 0.0) | (x >= mesh.nx) | (y < 0.0) | (y >= mesh.ny) | (z < 0.0) | (z >= mesh.nz)
 
 
+def reflect(mesh, P, mask):
+    """Reflecting particle faces (bit f of mask for face f = x-, x+, y-, y+, z-,
+    z+; the paper reflects particles at its symmetry plane, Sec. 5.2.2): a
+    particle beyond a reflecting face is mirrored back, xi -> -xi at the minus
+    face and xi -> 2 n - xi at the plus face, and its normal velocity reversed.
+    A mirrored coordinate landing exactly on the plus face (the box is [0, n))
+    takes the largest double below n.  Applied in place after a move and before
+    the boundary and object tests."""
+    if not mask:
+        return
+    n_axes = (mesh.nx, mesh.ny, mesh.nz)
+    for ax, (kx, kv) in enumerate((("x", "vx"), ("y", "vy"), ("z", "vz"))):
+        n = float(n_axes[ax])
+        if (mask >> (2 * ax)) & 1:
+            lo = P[kx] < 0.0
+            P[kx] = np.where(lo, -P[kx], P[kx])
+            P[kv] = np.where(lo, -P[kv], P[kv])
+        if (mask >> (2 * ax + 1)) & 1:
+            hi = P[kx] >= n
+            x2 = np.where(hi, (2.0 * n) - P[kx], P[kx])
+            P[kx] = np.where(hi & (x2 >= n), np.nextafter(n, 0.0), x2)
+            P[kv] = np.where(hi, -P[kv], P[kv])
+
+
 def hit_cells(mesh, obj, xo, yo, zo, xn, yn, zn):
     """Cell index of the crossing point for particles that entered the object."""
     Lo = obj.L(xo, yo, zo)

@@ -8,8 +8,9 @@ potential follows from the non-homogeneous flux jump, Sec. 3.1.2).
 
 One step (reading of the loop's order, also in the design doc):
   1. gather + push every particle with the current node field;
-  2. remove particles outside the domain, then collect particles inside the
-     object (their charge goes to the surface accumulator of the crossing cell);
+  2. mirror particles back at reflecting faces; remove particles outside the
+     domain, then collect particles inside the object (their charge goes to the
+     surface accumulator of the crossing cell);
   3. inject new particles at open faces (partial first step; same two tests),
      then emit photoelectrons from the sunlit surface (photo.py);
   4. scatter (fixed-point deposit) of all particles;
@@ -34,6 +35,7 @@ class Species:
         self.k = (self.q / self.m) * dt      # (q/m) dt
         self.inj = None                      # (face_mask, density, vth, drift, seed)
         self.photo = None                    # photo.Photoemission of this species
+        self.reflect = 0                     # reflecting particle faces (bit f = face f)
         self.carry = np.zeros(6)
         self.next_id = 0
 
@@ -87,8 +89,24 @@ class Simulation:
         self.species[s].next_id = max(self.species[s].next_id, int(np.max(ids)) + 1 if n else 0)
 
     def set_injection(self, s, face_mask, density, vth, drift, seed):
+        if int(face_mask) & self.species[s].reflect:
+            raise ValueError("a reflecting face cannot inject")
         self.species[s].inj = (int(face_mask), float(density), float(vth),
                                tuple(float(d) for d in drift), int(seed))
+
+    def set_particle_bc(self, s, face_kinds):
+        """Per face: "absorb" (default), "inject" (absorbing; injection is set by
+        set_injection) or "reflect" (particles mirrored back, pt.reflect)."""
+        mask = 0
+        for f, kind in enumerate(face_kinds):
+            if kind == "reflect":
+                mask |= 1 << f
+            elif kind not in ("absorb", "inject"):
+                raise ValueError(kind)
+        sp = self.species[s]
+        if sp.inj is not None and (sp.inj[0] & mask):
+            raise ValueError("a reflecting face cannot inject")
+        sp.reflect = mask
 
     def set_photoemission(self, s, sun_dir, density, vth, seed):
         """Species s is emitted from the sunlit, unshadowed object surface (Sec. 5.2.2; photo.py)."""
@@ -167,6 +185,7 @@ class Simulation:
             st["pushed"].append(len(P["x"]))
             xo, yo, zo = P["x"].copy(), P["y"].copy(), P["z"].copy()
             pt.push(m, self.E, P, sp.k, self.dth)
+            pt.reflect(m, P, sp.reflect)
             keep, nab, nco, lost = self._collect(s, np.ones(len(xo), dtype=bool), xo, yo, zo, P)
             P = {k: v[keep] for k, v in P.items()}
             ninj = nrej = 0
@@ -181,6 +200,7 @@ class Simulation:
                     cnt = int(math.floor(sp.carry[f]))
                     sp.carry[f] = sp.carry[f] - cnt
                     I = pt.inject_face(m, self.obj, seed, s, f, self.step_no, cnt, vth, drift, self.dth)
+                    pt.reflect(m, I, sp.reflect)
                     valid = I["accepted"] & (self.obj.L(I["x0"], I["y0"], I["z0"]) >= 0.0)
                     nrej += int((~valid).sum())
                     k2, a2, c2, l2 = self._collect(s, valid, I["x0"], I["y0"], I["z0"], I)
@@ -194,6 +214,7 @@ class Simulation:
                     P = {k: np.concatenate([P[k], N[k]]) for k in FIELDS}
             if sp.photo is not None:
                 I = sp.photo.emit(self.step_no)
+                pt.reflect(m, I, sp.reflect)
                 inside = self.obj.L(I["x"], I["y"], I["z"]) < 0.0
                 emitted = I["ok"] & ~inside
                 out = pt.outside(m, I["x"], I["y"], I["z"])
