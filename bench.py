@@ -84,7 +84,8 @@ def workload(name):
     return {"sphere64": wl.SPHERE64, "sphere16": wl.SPHERE16,
             "sphere32": wl.sphere_config(32, 3.0, 64, 100, seed_offset=6),
             "crater160": wl.CRATER160,
-            "crater80": wl.crater_config(80, 80, 40, 10.0, 15.0, 5.0, seed_offset=7)}[name]
+            "crater80": wl.crater_config(80, 80, 40, 10.0, 15.0, 5.0, seed_offset=7),
+            "oml50": wl.OML50}[name]
 
 
 def cfg_desc(cfg, precision, extra=None):
@@ -96,9 +97,14 @@ def cfg_desc(cfg, precision, extra=None):
              f"{ob['eps_in']}, spherical-cap crater rim radius {ob['rim_radius']} depth {ob['depth']}, "
              f"{ppc} ppc/species solar-wind e-+H+ drifting 8 v_ti at 45 deg, photoelectrons from the sunlit "
              f"unshadowed surface, dt={cfg['dt']}, phi=0 at Z_max, Neumann elsewhere")
+    elif cfg.get("particle_bc"):
+        w = (f"eighth-sphere OML sheath {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={ob['radius']} centred at "
+             f"the origin corner, eps_in={ob['eps_in']}, {ppc} ppc/species e-+H+ "
+             f"(m_i/m_e={cfg['species'][1]['m']:g}), dt={cfg['dt']}, zero-Neumann field and reflecting particle "
+             f"faces at X/Y/Z_min, phi=0 and flux injection at X/Y/Z_max")
     else:
         w = (f"sphere charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={ob['radius']}, "
-             f"eps_in={ob['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e=100), "
+             f"eps_in={ob['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e={cfg['species'][1]['m']:g}), "
              f"dt={cfg['dt']}, flux injection, phi=0 faces")
     d = {"workload": w,
          "precision": precision, "pcg_tol": 1e-6, "pcg_max_iter": 150,
@@ -308,25 +314,37 @@ def oracle_rate(workload_name, sample_frac, steps):
     random 1/sample_frac of the particles.  Particle work scales with the
     particle count, so the rate at full size is extrapolated as
     N / (t_particles * N / n_sample + t_field)."""
-    import numpy as np
-    from oracle.geometry import Mesh, Sphere
+    from oracle.geometry import CapCrater, Mesh, NoObject, Sphere
     from oracle.pic import Simulation
-    from oracle import particles as pt
     from paper_2011_10214_gb300 import workloads as wl
     cfg = workload(workload_name)
     m = Mesh(*cfg["n"], cfg["h"])
     ob = cfg["object"]
-    sim = Simulation(m, Sphere(m, ob["center"], ob["radius"], ob["eps_in"], ob["eps_out"]), cfg["face_bc"],
-                     cfg["dt"])
-    g = np.random.default_rng(0)
+    if ob["kind"] == "sphere":
+        obj = Sphere(m, ob["center"], ob["radius"], ob["eps_in"], ob["eps_out"])
+    elif ob["kind"] == "cap_crater":
+        obj = CapCrater(m, ob["z_ground"], ob["xc"], ob["yc"], ob["rim_radius"], ob["depth"], ob["eps_in"],
+                        ob["eps_out"])
+    else:
+        obj = NoObject()
+    sim = Simulation(m, obj, cfg["face_bc"], cfg["dt"])
     nfull = 0
     for s, sp in enumerate(cfg["species"]):
         sim.add_species(sp["q"], sp["m"], wl.macro_weight(cfg, sp))
+        if cfg.get("particle_bc"):
+            sim.set_particle_bc(s, cfg["particle_bc"])
         sim.load_maxwellian(s, sp["ppc"] // sample_frac if sp["ppc"] >= sample_frac else 1, sp["vth"], sp["drift"],
                             cfg["seed"])
         nfull += sp["ppc"] * m.ncells
         sim.set_injection(s, cfg["inject_faces"], sp["density"], sp["vth"], sp["drift"], cfg["seed"])
         # injection at the sample's weight keeps the density; rates scale with 1/w
+    ph = cfg.get("photo")
+    if ph is not None:
+        s = len(cfg["species"])
+        sim.add_species(ph["q"], ph["m"], ph["weight"])
+        if cfg.get("particle_bc"):
+            sim.set_particle_bc(s, cfg["particle_bc"])
+        sim.set_photoemission(s, ph["sun"], ph["density"], ph["vth"], cfg["seed"])
     sim.solve()
     sim.leapfrog_init()
     tp = tf = 0.0
@@ -467,7 +485,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="sphere64",
-                    choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80"])
+                    choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80", "oml50"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")

@@ -162,9 +162,31 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int species, size_t n, c
 
 /* Injection at open faces every step (Sec. 3.1.3, Sec. 5.2.2): for each face
  * f with bit f of face_mask set, floor(rate + carry) particles per step with
- * rate = one-way drifting-Maxwellian flux * face area * dt / w. */
+ * rate = one-way drifting-Maxwellian flux * face area * dt / w.  Errors:
+ * EINVAL (bad species, vth <= 0, density < 0, mask bits beyond the six faces
+ * or on a face marked REFLECT by set_particle_bc). */
 pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int species, int face_mask, double density,
                                      double vth, const double drift[3], uint64_t seed);
+/* Particle boundary kinds of a face (pifepic_set_particle_bc). */
+enum { PIFEPIC_PBC_ABSORB = 0, PIFEPIC_PBC_INJECT = 1, PIFEPIC_PBC_REFLECT = 2 };
+
+/* Particle boundary of the six faces for one species (Sec. 3.1.3: open faces
+ * absorb the particles that leave and inject new ones; Sec. 5.2.2: particles
+ * are reflected at the symmetry plane of a half-domain run).  face_kind: 6
+ * ints, host, faces x-, x+, y-, y+, z-, z+ (the order of set_field_bc).
+ * ABSORB (the default) and INJECT remove a particle whose new position lies
+ * beyond the face; INJECT marks a face whose injection set_injection turns on.
+ * REFLECT mirrors the position back into the box after every move (pushed,
+ * injected and photoemitted particles alike), xi -> -xi at a minus face and
+ * xi -> 2n - xi at a plus face, before the boundary and object tests, and
+ * reverses the normal velocity; a mirror that lands exactly on the plus face
+ * takes the largest coordinate below n.  The field boundary of the face is
+ * separate (a symmetry plane is normally Neumann, set_field_bc).  Call before
+ * stepping, and before the context joins a batch (a batch's captured step does
+ * not see a later change).  Errors: EINVAL (bad species or kind, a REFLECT face
+ * in the species' injection mask). */
+pifepic_status pifepic_set_particle_bc(pifepic_ctx* ctx, int species, const int face_kind[6]);
+
 /* The six per-face rates (expected particles per step) of a species' injection. */
 pifepic_status pifepic_get_injection_rate(pifepic_ctx* ctx, int species, double rate[6]);
 

@@ -17,6 +17,8 @@ FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 OBJ_NONE, OBJ_SPHERE, OBJ_CAP_CRATER, OBJ_PLANE = 0, 1, 2, 3
 BC_DIRICHLET, BC_NEUMANN = 0, 1
+PBC_ABSORB, PBC_INJECT, PBC_REFLECT = 0, 1, 2
+_PBC_NAMES = {"absorb": PBC_ABSORB, "inject": PBC_INJECT, "reflect": PBC_REFLECT}
 MAX_SPECIES = 8
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESTATE", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOTCONV"}
 
@@ -77,6 +79,7 @@ _sigs = {
     "pifepic_set_injection": [_ctx, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double * 3, C.c_uint64],
     "pifepic_get_injection_rate": [_ctx, C.c_int, C.c_double * 6],
     "pifepic_set_photoemission": [_ctx, C.c_int, C.c_double * 3, C.c_double, C.c_double, C.c_uint64],
+    "pifepic_set_particle_bc": [_ctx, C.c_int, C.c_int * 6],
     "pifepic_get_photoemission": [_ctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "pifepic_set_external_E": [_ctx, _dp, C.c_int],
     "pifepic_solve": [_ctx, C.POINTER(Stats)],
@@ -206,6 +209,14 @@ class Simulation:
     def set_injection(self, s, face_mask, density, vth, drift, seed):
         self._ok(lib.pifepic_set_injection(self._c, s, int(face_mask), float(density), float(vth),
                                            (C.c_double * 3)(*drift), C.c_uint64(int(seed))), "set_injection")
+
+    def set_particle_bc(self, s, face_kinds):
+        """Particle boundary of faces x-, x+, y-, y+, z-, z+ for species s: each
+        "absorb", "inject" or "reflect" (or PBC_* codes); see pifepic_set_particle_bc."""
+        k = [_PBC_NAMES[f] if isinstance(f, str) else int(f) for f in face_kinds]
+        if len(k) != 6:
+            raise ValueError("six face kinds expected")
+        self._ok(lib.pifepic_set_particle_bc(self._c, int(s), (C.c_int * 6)(*k)), "set_particle_bc")
 
     def set_photoemission(self, s, sun_dir, density, vth, seed):
         """Species s is emitted from the sunlit, unshadowed object surface (see
@@ -346,8 +357,11 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
                        ob["eps_in"], ob["eps_out"])
     else:
         sim.set_object(OBJ_NONE, [], 1.0, 1.0)
+    pbc = cfg.get("particle_bc")
     for sp in cfg["species"]:
         s = sim.add_species(sp["q"], sp["m"], sp["density"] * cfg["h"] ** 3 / sp["ppc"])
+        if pbc is not None:
+            sim.set_particle_bc(s, pbc)
         if load:
             sim.load_maxwellian(s, sp["ppc"], sp["vth"], sp["drift"], cfg["seed"])
         if inject:
@@ -355,6 +369,8 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
     ph = cfg.get("photo")
     if ph is not None:
         s = sim.add_species(ph["q"], ph["m"], ph["weight"])
+        if pbc is not None:
+            sim.set_particle_bc(s, pbc)
         if inject:
             sim.set_photoemission(s, ph["sun"], ph["density"], ph["vth"], cfg["seed"])
     return sim

@@ -589,12 +589,31 @@ static double flux_density(double n, double vth, double vdn) {
     return n * vth * (exp(-0.5 * s * s) / sqrt(2.0 * M_PI) + 0.5 * s * (1.0 + erf(s / sqrt(2.0))));
 }
 
+pifepic_status pifepic_set_particle_bc(pifepic_ctx* ctx, int s, const int face_kind[6]) {
+    NEED(ctx); NEED(face_kind);
+    Ctx& c = ctx->c;
+    if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
+    int mask = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int k = face_kind[f];
+        if (k != PIFEPIC_PBC_ABSORB && k != PIFEPIC_PBC_INJECT && k != PIFEPIC_PBC_REFLECT)
+            FAIL(PIFEPIC_EINVAL, "bad particle boundary kind %d on face %d", k, f);
+        if (k == PIFEPIC_PBC_REFLECT) mask |= 1 << f;
+    }
+    if (c.sp[s].inject && (c.sp[s].face_mask & mask))
+        FAIL(PIFEPIC_EINVAL, "species %d injects on a face marked REFLECT", s);
+    c.sp[s].reflect = mask;
+    return PIFEPIC_OK;
+}
+
 pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, double density, double vth,
                                      const double drift[3], uint64_t seed) {
     NEED(ctx); NEED(drift);
     Ctx& c = ctx->c;
     if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
     if (!(vth > 0) || density < 0) FAIL(PIFEPIC_EINVAL, "injection needs vth > 0 and density >= 0");
+    if (face_mask & ~63) FAIL(PIFEPIC_EINVAL, "face_mask 0x%x has bits beyond the six faces", face_mask);
+    if (face_mask & c.sp[s].reflect) FAIL(PIFEPIC_EINVAL, "face_mask 0x%x includes a reflecting face", face_mask);
     Species& q = c.sp[s];
     q.inject = face_mask != 0;
     q.face_mask = face_mask; q.density = density; q.vth = vth;

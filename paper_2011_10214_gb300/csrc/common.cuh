@@ -56,6 +56,28 @@ struct Mesh {
     double h;
 };
 
+// Reflecting particle faces (the symmetry plane of Sec. 5.2.2), bit f of the
+// mask for face f = x-, x+, y-, y+, z-, z+.  A coordinate beyond a reflecting
+// face is mirrored back, xi -> -xi at the minus face and xi -> 2n - xi at the
+// plus face, and the normal velocity reversed; per axis the minus face is
+// tested first.  A mirror landing exactly on n (the box is [0, n)) takes the
+// largest double below n (n >= 1: one less in the bit pattern).
+PF_D void reflect_axis_d(double& x, double& v, int n, int lo, int hi) {
+    const double nd = (double)n;
+    if (lo && x < 0.0) { x = -x; v = -v; }
+    if (hi && x >= nd) {
+        x = (2.0 * nd) - x;
+        if (x >= nd) x = __longlong_as_double(__double_as_longlong(nd) - 1);
+        v = -v;
+    }
+}
+PF_D void reflect_d(const Mesh& m, int mask, double& x, double& y, double& z, double& vx, double& vy,
+                    double& vz) {
+    reflect_axis_d(x, vx, m.nx, mask & 1, mask & 2);
+    reflect_axis_d(y, vy, m.ny, mask & 4, mask & 8);
+    reflect_axis_d(z, vz, m.nz, mask & 16, mask & 32);
+}
+
 struct TetTables {
     int vert[2][5][4];         // [cube parity][tet][k] local vertex
     double grad[2][5][4][3];   // P1 basis gradients for h = 1

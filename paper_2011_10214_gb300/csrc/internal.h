@@ -41,6 +41,7 @@ struct SpeciesDev {
     unsigned long long* W;          // [nnodes] fixed-point charge
     unsigned long long* surf;       // [ncut] collected macro-particles
     unsigned long long* ctr;        // [NCTR] counters
+    int reflect;                    // reflecting particle faces, bit f = face f
 };
 
 struct InjectDev {                  // one (species, face) injection stream
@@ -89,6 +90,7 @@ struct Species {
     int cur = 0;                    // which mover buffer is "in"
     bool inject = false;
     int face_mask = 0;
+    int reflect = 0;                // reflecting particle faces, bit f = face f
     double density = 0, vth = 0, drift[3] = {0, 0, 0};
     unsigned long long seed = 0;
     double rate[6] = {0, 0, 0, 0, 0, 0};

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
             vx = vx + S.k * ex; vy = vy + S.k * ey; vz = vz + S.k * ez;
             const double xo = x, yo = y, zo = z;
             x = x + vx * L.dth; y = y + vy * L.dth; z = z + vz * L.dth;
+            if (S.reflect) reflect_d(L.mesh, S.reflect, x, y, z, vx, vy, vz);
             code = classify(L, xo, yo, zo, x, y, z, acc);
         }
         bool stay = false, mover = false;
@@ -285,6 +286,7 @@ __global__ void k_push_movers(Launch L) {
             vx = vx + S.k * ex; vy = vy + S.k * ey; vz = vz + S.k * ez;
             const double xo = x, yo = y, zo = z;
             x = x + vx * L.dth; y = y + vy * L.dth; z = z + vz * L.dth;
+            if (S.reflect) reflect_d(L.mesh, S.reflect, x, y, z, vx, vy, vz);
             code = classify(L, xo, yo, zo, x, y, z, acc);
             if (code == ALIVE) global_deposit(L, S.W, weights(x, y, z));
             else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
@@ -344,6 +346,7 @@ __global__ void k_inject(Launch L, InjArgs a) {
             double p0[3] = {sm.p0[0], sm.p0[1], sm.p0[2]};
             bool ok = sm.ok;
             for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
+            if (S.reflect) reflect_d(L.mesh, S.reflect, p[0], p[1], p[2], v[0], v[1], v[2]);
             if (!ok || level_set(L.obj, p0[0], p0[1], p0[2]) < 0.0) {
                 rejected = true;
             } else {
@@ -585,6 +588,7 @@ Launch make_launch(Ctx& c) {
         d.mov_in_n = q.mov_n; d.mov_out_n = q.mov_n + 1;
         d.mcap = q.mcap;
         d.W = q.W; d.surf = q.surf; d.ctr = q.ctr;
+        d.reflect = q.reflect;
     }
     return L;
 }
@@ -735,6 +739,7 @@ __global__ void k_photo(Launch L, PhotoArgs a) {
             const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
             const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
             for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
+            if (S.reflect) reflect_d(L.mesh, S.reflect, p[0], p[1], p[2], v[0], v[1], v[2]);
             emitted = sm.ok && !(level_set(L.obj, p[0], p[1], p[2]) < 0.0);
             if (emitted) {
                 atomicAdd(&S.surf[d.acc], (unsigned long long)-1ll);   // the electron leaves +e behind

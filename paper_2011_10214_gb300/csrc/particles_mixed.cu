@@ -113,6 +113,47 @@ PF_D void advance_axis(float& f, int& c) {
     if (f >= 1.0f) { f = 0.0f; c += 1; }   // -tiny - (-1) rounded up to 1
 }
 
+// reflecting faces (bit f = face f, minus face first per axis) on the cell +
+// offset state: the mirror of c + f is -c - f at the minus face and 2n - c - f
+// at the plus face, split again into a cell and an offset in [0, 1); a mirror
+// that rounds onto n takes the last offset below 1 of cell n - 1
+PF_D void reflect_axis_f(int& c, float& f, float& v, int n, int lo, int hi) {
+    if (lo && c < 0) {
+        if (f == 0.0f) {
+            c = -c;
+        } else {
+            c = -c - 1; f = 1.0f - f;
+            if (f >= 1.0f) { f = 0.0f; c += 1; }
+        }
+        v = -v;
+    }
+    if (hi && c >= n) {
+        if (f == 0.0f) {
+            c = 2 * n - c;
+        } else {
+            c = 2 * n - c - 1; f = 1.0f - f;
+            if (f >= 1.0f) { f = 0.0f; c += 1; }
+        }
+        if (c >= n) { c = n - 1; f = 0.99999994f; }
+        v = -v;
+    }
+}
+PF_D void reflect_cell(const Mesh& m, int mask, PF32& p) {
+    reflect_axis_f(p.i, p.fx, p.vx, m.nx, mask & 1, mask & 2);
+    reflect_axis_f(p.j, p.fy, p.vy, m.ny, mask & 4, mask & 8);
+    reflect_axis_f(p.k, p.fz, p.vz, m.nz, mask & 16, mask & 32);
+}
+// the same on a plain FP32 coordinate (injected particles, before the cell split)
+PF_D void reflect_axis_pf(float& x, float& v, int n, int lo, int hi) {
+    const float nf = (float)n;
+    if (lo && x < 0.0f) { x = -x; v = -v; }
+    if (hi && x >= nf) {
+        x = (2.0f * nf) - x;
+        if (x >= nf) x = __int_as_float(__float_as_int(nf) - 1);
+        v = -v;
+    }
+}
+
 PF_D int hit_cell_f(const Launch& L, const ObjF& of, float xo, float yo, float zo, float xn, float yn, float zn) {
     float Lo = level_set_f(of, xo, yo, zo), Ln = level_set_f(of, xn, yn, zn);
     float t = Lo / (Lo - Ln);
@@ -124,7 +165,7 @@ PF_D int hit_cell_f(const Launch& L, const ObjF& of, float xo, float yo, float z
 }
 
 template <class EA>
-PF_D int push_one(const Launch& L, const ObjF& of, float kf, float dthf, PF32& p, const EA& ea, int& acc) {
+PF_D int push_one(const Launch& L, const ObjF& of, float kf, float dthf, int refl, PF32& p, const EA& ea, int& acc) {
     WF w = weights_f(p.fx, p.fy, p.fz);
     float ex, ey, ez;
     gather_f(p.i, p.j, p.k, w, ea, ex, ey, ez);
@@ -132,6 +173,7 @@ PF_D int push_one(const Launch& L, const ObjF& of, float kf, float dthf, PF32& p
     float xo = (float)p.i + p.fx, yo = (float)p.j + p.fy, zo = (float)p.k + p.fz;
     p.fx += p.vx * dthf; p.fy += p.vy * dthf; p.fz += p.vz * dthf;
     advance_axis(p.fx, p.i); advance_axis(p.fy, p.j); advance_axis(p.fz, p.k);
+    if (refl) reflect_cell(L.mesh, refl, p);
     if (p.i < 0 || p.i >= L.mesh.nx || p.j < 0 || p.j >= L.mesh.ny || p.k < 0 || p.k >= L.mesh.nz) return ABSORBED;
     float xn = (float)p.i + p.fx, yn = (float)p.j + p.fy, zn = (float)p.k + p.fz;
     if (level_set_f(of, xn, yn, zn) < 0.0f) {
@@ -234,6 +276,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const long long start = S.bstart[b];
     const bool track = L.track;
     const float kf = (float)S.k;
+    const int refl = S.reflect;
     const int copy = lane & 7;
     int nstay = 0;
     // the next chunk is loaded into registers while this one is processed
@@ -264,6 +307,7 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
             const float xo = (float)p.i + p.fx, yo = (float)p.j + p.fy, zo = (float)p.k + p.fz;
             p.fx += p.vx * dthf; p.fy += p.vy * dthf; p.fz += p.vz * dthf;
             advance_axis(p.fx, p.i); advance_axis(p.fy, p.j); advance_axis(p.fz, p.k);
+            if (refl) reflect_cell(L.mesh, refl, p);
             if (p.i < 0 || p.i >= L.mesh.nx || p.j < 0 || p.j >= L.mesh.ny || p.k < 0 || p.k >= L.mesh.nz) {
                 code = ABSORBED;
             } else {
@@ -353,7 +397,7 @@ __global__ void k_push_movers_m(Launch L, ObjF of, float dthf) {
         if (i < n) {
             load_p(S.movF_in, i, p);
             if (track) id = S.movF_in.id[i];
-            code = push_one(L, of, kf, dthf, p, ea, acc);
+            code = push_one(L, of, kf, dthf, S.reflect, p, ea, acc);
             if (code == ALIVE) global_deposit_f(L, S.W, p);
             else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
@@ -393,7 +437,12 @@ __global__ void k_inject_m(Launch L, InjArgs a, ObjF of, float dthf) {
         PF32 p;
         if (mm < cnt) {
             // FP32 sample (the MIXED state is FP32); tests on the FP32 level set
-            const InjSampleF sm = inject_sample_f(d, mm, *a.step, s, L.mesh, dthf);
+            InjSampleF sm = inject_sample_f(d, mm, *a.step, s, L.mesh, dthf);
+            if (S.reflect) {
+                reflect_axis_pf(sm.p[0], sm.v[0], L.mesh.nx, S.reflect & 1, S.reflect & 2);
+                reflect_axis_pf(sm.p[1], sm.v[1], L.mesh.ny, S.reflect & 4, S.reflect & 8);
+                reflect_axis_pf(sm.p[2], sm.v[2], L.mesh.nz, S.reflect & 16, S.reflect & 32);
+            }
             if (!sm.ok || level_set_f(of, sm.p0[0], sm.p0[1], sm.p0[2]) < 0.0f) {
                 rejected = true;
             } else if (sm.p[0] < 0.0f || sm.p[0] >= nxf || sm.p[1] < 0.0f || sm.p[1] >= nyf || sm.p[2] < 0.0f ||
@@ -649,7 +698,8 @@ __global__ void k_photo_m(Launch L, PhotoArgs a) {
         PF32 p;
         if (m < total) {
             const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
-            const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
+            PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
+            if (S.reflect) reflect_d(L.mesh, S.reflect, sm.p[0], sm.p[1], sm.p[2], sm.v[0], sm.v[1], sm.v[2]);
             emitted = sm.ok && !(level_set(L.obj, sm.p[0], sm.p[1], sm.p[2]) < 0.0);
             if (emitted) {
                 atomicAdd(&S.surf[d.acc], (unsigned long long)-1ll);   // the electron leaves +e behind

@@ -41,6 +41,33 @@ SPHERE16 = sphere_config(16, 2.0, 16, 100, seed_offset=1)
 SPHERE64 = sphere_config(64, 6.0, 64, 1000, seed_offset=2)
 
 
+def oml_eighth_config(n=50, h=0.1, radius=0.401, ppc=125, steps=1000, mass_ratio=1836.0, eps_in=4.0, dt=0.01,
+                      seed_offset=4):
+    """The paper's validation geometry (Sec. 3, the OML sheath of a dielectric
+    sphere): a box of n^3 cells of h Debye lengths with the sphere centred at
+    the origin, so only its positive octant lies in the domain; zero Neumann
+    field faces and reflecting particle faces at X/Y/Z_min (the symmetry
+    planes), phi = 0 and injecting, absorbing faces at X/Y/Z_max; e- and ions of
+    the realistic mass ratio at equal temperature, ppc per species."""
+    vti = 1.0 / np.sqrt(mass_ratio)
+    return dict(
+        name=f"oml{n}",
+        n=(n, n, n), h=h, origin=(0.0, 0.0, 0.0), dt=dt, steps=steps,
+        object=dict(kind="sphere", center=(0.0, 0.0, 0.0), radius=radius, eps_in=eps_in, eps_out=1.0),
+        face_bc=[("N",), ("D", 0.0)] * 3,
+        particle_bc=["reflect", "inject"] * 3,
+        species=[dict(name="e-", q=-1.0, m=1.0, vth=1.0, ppc=ppc, density=1.0, drift=(0.0, 0.0, 0.0)),
+                 dict(name="H+", q=1.0, m=mass_ratio, vth=vti, ppc=ppc, density=1.0, drift=(0.0, 0.0, 0.0))],
+        inject_faces=0b101010,
+        seed=SEED_BASE + seed_offset,
+    )
+
+
+# 50^3 cells of 0.1 Debye length (5 Debye lengths a side), 1/8 of a sphere of
+# radius 0.401, eps 4, m_i/m_e = 1836, dt = 0.01, 125 ppc per species (~31M)
+OML50 = oml_eighth_config()
+
+
 def crater_config(nx=160, ny=160, nz=80, z_ground=20.0, rim_radius=30.0, depth=10.0, ppc=125, steps=200,
                   mass_ratio=100.0, dt=0.05, seed_offset=3):
     """Crater charging (Sec. 5, scaled to one GPU): cells of one photoelectron
