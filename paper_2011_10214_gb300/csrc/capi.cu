@@ -213,7 +213,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.coop_partial, sizeof(double) * 8 * 2048);
     ALLOC(c.scal, sizeof(double) * 64);
     ALLOC(c.red_ticket, sizeof(unsigned) * 4);
-    ALLOC(c.bar64, sizeof(unsigned long long) * 4);
+    ALLOC(c.bar64, sizeof(unsigned long long) * BAR64_WORDS);
     ALLOC(c.err_word, sizeof(int));
     ALLOC(c.next_id, sizeof(long long) * MAX_SPECIES);
     ALLOC(c.inj_count, sizeof(int) * MAX_SPECIES * 6);
@@ -227,7 +227,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     CUDA_OK(szero(c.stream, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR));
     CUDA_OK(szero(c.stream, c.scal, sizeof(double) * 64));
     CUDA_OK(szero(c.stream, c.red_ticket, sizeof(unsigned) * 4));
-    CUDA_OK(szero(c.stream, c.bar64, sizeof(unsigned long long) * 4));
+    CUDA_OK(szero(c.stream, c.bar64, sizeof(unsigned long long) * BAR64_WORDS));
     CUDA_OK(szero(c.stream, c.err_word, sizeof(int)));
     CUDA_OK(szero(c.stream, c.next_id, sizeof(long long) * MAX_SPECIES));
     CUDA_OK(szero(c.stream, c.inj_carry, sizeof(double) * MAX_SPECIES * 6));
@@ -805,7 +805,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
         // the barrier counters are left mid-count: clear them and the flag so
         // that a later solve starts from a clean state
         szero(c.stream, c.red_ticket, sizeof(unsigned) * 4);
-        szero(c.stream, c.bar64, sizeof(unsigned long long) * 4);
+        szero(c.stream, c.bar64, sizeof(unsigned long long) * BAR64_WORDS);
         szero(c.stream, c.err_word, sizeof(int));
         cudaStreamSynchronize(c.stream);
         FAIL(PIFEPIC_ETIMEOUT, "a grid barrier of the PCG solve timed out");

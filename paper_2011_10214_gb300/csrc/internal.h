@@ -59,6 +59,7 @@ struct PhotoDev {
     int ntri, acc;                  // triangles; cut-cell accumulator of the tet's cell
 };
 constexpr int PHOTO_RATE_BITS = 20;  // per-tet rates and carries in units of 2^-20 particles
+constexpr int BAR64_WORDS = 64;      // PCG exchange words per context (Ctx::bar64)
 
 struct Launch {                     // what every particle kernel needs
     Mesh mesh;
@@ -162,7 +163,10 @@ struct Ctx {
     double* coop_partial = nullptr; // [8][2048] block partials of the persistent PCG
     double* scal = nullptr;        // PCG scalars
     unsigned int* red_ticket = nullptr;
-    unsigned long long* bar64 = nullptr;  // arrival counter of the register-resident PCG (multiple of its grid between launches)
+    // PCG exchange words: [0] the arrival counter (a multiple of the grid between
+    // launches); [16], [32], [48] the fixed-point reduction words (one 128-byte
+    // line each)
+    unsigned long long* bar64 = nullptr;
     // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;

@@ -9,9 +9,11 @@
 //              reductions FP32.
 //
 // Reductions are deterministic: each block writes its partial, and after the
-// exchange every block sums all partials in the same order, so all blocks take
-// the same decisions and two runs give identical results.  Exchange waits are
-// bounded (about a second); a timeout raises an error bit and ends the solve.
+// exchange every block sums all partials in the same order (or, in the FP32
+// inner loop of the register-resident kernel, adds them as integers), so all
+// blocks take the same decisions and two runs give identical results.
+// Exchange waits are bounded (about a second); a timeout raises an error bit
+// and ends the solve.
 //
 // Two kernels: k_pcg_reg keeps the vectors in registers (meshes with at most 8
 // nodes per thread of a full grid, e.g. 64^3); k_pcg_glob keeps them in
@@ -45,8 +47,10 @@ constexpr int COOP_MAX_OUTER = 12;
 // outer FP64 residual corrects what FP32 inner products lose).  An exchange
 // is a monotonic arrival counter (below) with the block partials in one of two
 // slots by exchange parity, so a block that races ahead into the next exchange
-// never overwrites partials a slower block is still summing.  MIXED wraps FP32 inner solves in FP64 refinement as the
-// global-memory kernel does.  (The pipelined form of PCG would need one
+// never overwrites partials a slower block is still summing; the FP32 inner
+// loop of MIXED mode uses the fixed-point exchange instead, which needs no
+// second round trip for the partials.  MIXED wraps FP32 inner solves in FP64
+// refinement as the global-memory kernel does.  (The pipelined form of PCG would need one
 // exchange per iteration, but its recurrences stagnated on meshes with mostly
 // Neumann faces, in FP32 and with FP64 recurrences alike, so it is not used.)
 
@@ -63,6 +67,7 @@ struct RegArgs {
     int woff[19];              // staged rows: window offset of each stencil slot
     double* val;               // [2][4][G] block partials
     unsigned long long* arrivals;  // grows by G per exchange
+    unsigned long long* fx;        // fixed-point exchange words: pq at [0], r.r and r.z at [FX_LINE], [2 FX_LINE]
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -115,6 +120,105 @@ static __device__ __forceinline__ bool exchange(const Args& a, int& e, A (&v)[NV
     for (int q = 0; q < NV; ++q) tot[q] = bc[q];
     return true;
 }
+
+// ---- fixed-point exchange (FP32 inner loop of the register-resident kernel) ----
+//
+// The arrival and the partial travel in one fire-and-forget atomic: a block
+// adds to one 64-bit word per value
+//     (rint(v 2^k) << 16) + (fits ? 1 : 257)
+// -- bits 0-7 count arrivals, bits 8-15 blocks whose scaled partial did not
+// fit below 2^39, bits 16-63 the 48-bit two's-complement sum (at most 255
+// blocks, so no field carries into the next).  A block polls the word until
+// its growth since the previous use shows every arrival; the growth then holds
+// the integer total.  The scale 2^k puts the value's previous total near 2^32,
+// so each partial is exact to 2^-32 of it.  Integer sums do not depend on the
+// arrival order: results stay deterministic run to run.  A word is reused only
+// after the other exchange kind (a full barrier) has passed, so its value is
+// stable from the last arrival until every block has read it.  If a partial
+// did not fit, or the total kept fewer than 2^26 units (the value fell far
+// below its previous total), every block sees it and redoes the values with
+// the partial exchange above.
+constexpr int FX_LINE = 16;                  // words per 128-byte line
+constexpr float FX_FIT = 549755813888.0f;    // 2^39
+constexpr long long FX_MIN = 1ll << 26;
+
+// ref: the previous totals (positive, normal); prev: this lane's word value
+// after its last use (lanes 0..NV-1 of warp 0).  Returns 1 with the totals in
+// tot, -1 if the values must be redone, 0 after a timeout.
+template <int NV, typename Args>
+static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long long* words, unsigned long long& prev,
+                                                  const float (&ref)[NV], float (&v)[NV], float (&tot)[NV],
+                                                  ExchShared& xs) {
+    block_sum_t<float, NV>(v, (float*)xs.sh);   // totals in thread 0; ends with __syncthreads
+    float* bc = (float*)xs.bc;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const bool act = lane < NV;
+        float mine = __shfl_sync(0xffffffffu, v[0], 0), rf = ref[0];
+        if (NV > 1) {
+            const float m1 = __shfl_sync(0xffffffffu, v[NV - 1], 0);
+            if (lane == 1) { mine = m1; rf = ref[NV - 1]; }
+        }
+        const int k = 32 - ilogbf(rf);
+        const float sc = ldexpf(mine, k);
+        const bool fits = fabsf(sc) < FX_FIT;
+        const long long fx = fits ? __float2ll_rn(sc) : 0ll;
+        unsigned long long* w = words + lane * FX_LINE;
+        if (act) red_add_release(w, ((unsigned long long)fx << 16) + (fits ? 1ull : 257ull));
+        const unsigned long long G = gridDim.x;
+        unsigned long long d = 0;
+        bool done = !act, timeout = false;
+        const long long c0 = clock64();
+        for (;;) {
+            if (!done) {
+                d = ld_acquire(w) - prev;
+                done = (d & 255ull) == G;
+            }
+            if (__all_sync(0xffffffffu, done)) break;
+            if (__any_sync(0xffffffffu, clock64() - c0 > (1ll << 31))) { timeout = true; break; }
+        }
+        bool good = true;
+        if (act && !timeout) {
+            prev += d;
+            const long long val = (long long)d >> 16;
+            good = ((d >> 8) & 255ull) == 0 && (val >= FX_MIN || val <= -FX_MIN);
+            bc[lane] = ldexpf((float)val, -k);
+        }
+        const bool all_good = __all_sync(0xffffffffu, good);
+        if (lane == 0) {
+            if (timeout) atomicOr(a.err, ERR_BARRIER_TIMEOUT);
+            xs.ok = timeout ? 0 : (all_good ? 1 : 2);
+        }
+    }
+    __syncthreads();
+    // (the next exchange rewrites bc and ok only after its block sum's barrier)
+    const int ok = xs.ok;
+    if (ok == 1) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = bc[q];
+    }
+    return ok == 1 ? 1 : (ok == 2 ? -1 : 0);
+}
+
+// an FP32 exchange: fixed-point when the previous totals give a scale, else
+// (or when the fixed-point totals cannot be trusted) the partial exchange
+template <int NV, typename Args>
+static __device__ __forceinline__ bool exchange_f32(const Args& a, int& e, unsigned long long* words,
+                                                    unsigned long long& prev, const float (&ref)[NV], bool use_fx,
+                                                    float (&v)[NV], float (&tot)[NV], ExchShared& xs) {
+    if (use_fx) {
+        float vc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) vc[q] = v[q];
+        const int rc = exchange_fx<NV>(a, words, prev, ref, vc, tot, xs);
+        if (rc == 1) return true;
+        if (rc == 0) return false;
+    }
+    return exchange<float, NV>(a, e, v, tot, xs);
+}
+
+// a previous total usable as the fixed-point scale
+static __device__ __forceinline__ bool fx_ref_ok(float r) { return r > 1e-30f && r < 1e30f; }
 
 static __device__ __forceinline__ unsigned pack_ijk(int i, int j, int k) {
     return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22);
@@ -213,6 +317,13 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             dv[s] = dinv[n];
         }
     }
+    // this launch's starting values of the fixed-point words (read before the
+    // first exchange, so before any block of this launch adds to them)
+    unsigned long long fxa = 0, fxb = 0;
+    if (MIXED && threadIdx.x < 2) {
+        fxa = ld_relaxed(a.fx);
+        fxb = ld_relaxed(a.fx + (1 + threadIdx.x) * FX_LINE);
+    }
     int it = 0, outer = 0;
     double bb = 0.0, rr = 0.0;
     bool conv = false, alive = true;
@@ -247,6 +358,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         const T rr_stop = (T)(MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
+        float pq_prev = 0.0f;     // no scale for the first p.q of an inner solve
         bool first = true;
         for (;;) {
             // stage the z window (the last exchange ordered every block's z stores
@@ -296,7 +408,14 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             }
             first = false;
             T pq[1];
-            if (!(alive = exchange<T, 1>(a, e, v1, pq, xs))) break;
+            if constexpr (MIXED) {
+                const float rf[1] = {pq_prev};
+                alive = exchange_f32<1>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
+                pq_prev = pq[0];
+            } else {
+                alive = exchange<T, 1>(a, e, v1, pq, xs);
+            }
+            if (!alive) break;
             const T al = rz / pq[0];
             T v2[2] = {(T)0, (T)0};
 #pragma unroll
@@ -312,7 +431,13 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
                 }
             }
             T t2[2];
-            if (!(alive = exchange<T, 2>(a, e, v2, t2, xs))) break;
+            if constexpr (MIXED) {
+                const float rf[2] = {rr_in, rz};
+                alive = exchange_f32<2>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
+            } else {
+                alive = exchange<T, 2>(a, e, v2, t2, xs);
+            }
+            if (!alive) break;
             beta = t2[1] / rz;
             rz = t2[1];
             rr_in = t2[0];
@@ -594,6 +719,7 @@ static void plan_pcg_reg(Ctx& c) {
     long long G = (N + REG_THREADS - 1) / REG_THREADS;
     if (G > nsm) G = nsm;          // one 512-thread block per SM (registers allow no more)
     if (G > REG_THREADS) G = REG_THREADS;   // exchange totals: one partial per thread
+    if (G > 255) G = 255;          // the fixed-point exchange counts arrivals in 8 bits
     if (G < 1) G = 1;
     const long long M = (N + G - 1) / G;
     const long long npt = (M + REG_THREADS - 1) / REG_THREADS;
@@ -655,6 +781,7 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     }
     a.val = c.coop_partial;
     a.arrivals = c.bar64;
+    a.fx = c.bar64 + FX_LINE;
     a.S = (PcgState*)c.scal;
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
