@@ -193,11 +193,23 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.r, sizeof(double) * N);
     ALLOC(c.p, sizeof(double) * N);
     ALLOC(c.q, sizeof(double) * N);
-    // z / zf: the persistent PCG reads them in 16-byte vectors, up to 16 entries past N
-    ALLOC(c.z, sizeof(double) * (N + 16));
-    ALLOC(c.zf, sizeof(float) * (N + 16));
-    CUDA_OK(szero(c.stream, c.z, sizeof(double) * (N + 16)));
-    CUDA_OK(szero(c.stream, c.zf, sizeof(float) * (N + 16)));
+    // z / zf: the persistent PCG reads them in 16-byte vectors, up to 16 entries
+    // past N, and the global-memory PCG's branch-free stencil reads (and
+    // multiplies by zero) the neighbours of a boundary node up to one plane,
+    // one row and one node outside [0, N); both therefore sit inside a zeroed
+    // guard of that reach on each side (16-entry multiples keep the alignment)
+    {
+        c.zguard = ((long long)c.mesh.NX * c.mesh.NY + c.mesh.NX + 1 + 15) / 16 * 16;
+        const long long zlen = N + 2 * c.zguard + 16;
+        double* zb = nullptr;
+        float* zfb = nullptr;
+        ALLOC(zb, sizeof(double) * zlen);
+        c.z = zb + c.zguard;
+        ALLOC(zfb, sizeof(float) * zlen);
+        c.zf = zfb + c.zguard;
+        CUDA_OK(szero(c.stream, zb, sizeof(double) * zlen));
+        CUDA_OK(szero(c.stream, zfb, sizeof(float) * zlen));
+    }
     ALLOC(c.rf, sizeof(float) * N);
     ALLOC(c.pf, sizeof(float) * N);
     ALLOC(c.qf, sizeof(float) * N);
@@ -244,7 +256,8 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (!ctx) return;
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
-    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q, c.z, c.zf,
+    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q,
+                    c.z ? (void*)(c.z - c.zguard) : nullptr, c.zf ? (void*)(c.zf - c.zguard) : nullptr,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,

@@ -124,11 +124,12 @@ struct Ctx {
     double* lift = nullptr;        // (A g) restricted to free nodes
     double* invdiag = nullptr;
     double* phi = nullptr;
-    double* u = nullptr;
-    double* phi_prev = nullptr;    // potential before the last solve (start extrapolation)           // unknown (phi - g)
+    double* u = nullptr;           // unknown (phi - g)
+    double* phi_prev = nullptr;    // potential before the last solve (start extrapolation)
     double* b = nullptr;           // right-hand side
-    double *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
-    float* zf = nullptr;
+    double *r = nullptr, *p = nullptr, *q = nullptr;
+    double* z = nullptr;           // inside a zeroed guard (zguard)
+    float* zf = nullptr;           // inside a zeroed guard (zguard)
     float *rf = nullptr, *pf = nullptr, *qf = nullptr, *uf = nullptr, *invdiagf = nullptr;
     double4* E = nullptr;          // node field (x, y, z, 0)
     float4* Ef = nullptr;          // FP32 copy for the MIXED push
@@ -167,6 +168,7 @@ struct Ctx {
     // launches); [16], [32], [48] the fixed-point reduction words (one 128-byte
     // line each)
     unsigned long long* bar64 = nullptr;
+    long long zguard = 0;           // zeroed entries before z / zf (and after, plus 16)
     // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;

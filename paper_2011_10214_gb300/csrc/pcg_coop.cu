@@ -516,6 +516,9 @@ __global__ void k_row_kind(FieldArgs f, unsigned short* kind) {
     kind[n] = row_kind(f, n, i, j, k);
 }
 
+// x must be readable (and finite) up to NXY + NX + 1 entries outside [0, N):
+// the masked stencil of a boundary node reads its absent neighbours and
+// multiplies them by zero (the context's z / zf carry a zeroed guard)
 template <typename T>
 static __device__ __forceinline__ T glob_row(const GlobArgs& a, const T* x, long long n, unsigned kd, int NX,
                                              int NXY, T h, T ep, T em, const T* coef) {
