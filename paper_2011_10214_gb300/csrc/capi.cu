@@ -814,6 +814,11 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     c.stats = s;
     if (st) *st = s;
     if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
+    if (herr & ERR_CHUNK_TIMEOUT) {
+        szero(c.stream, c.err_word, sizeof(int));
+        cudaStreamSynchronize(c.stream);
+        FAIL(PIFEPIC_ETIMEOUT, "a bin's compaction order wait timed out (its particles were dropped)");
+    }
     if (herr & ERR_BARRIER_TIMEOUT) {
         // the barrier counters are left mid-count: clear them and the flag so
         // that a later solve starts from a clean state

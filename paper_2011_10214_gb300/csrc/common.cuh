@@ -17,7 +17,7 @@ constexpr int TILE_N = TILE * TILE * TILE;
 constexpr int MAX_SPECIES = 8;
 constexpr int NCTR = 8;                   // per-species device counters
 enum { C_PUSHED = 0, C_ABSORBED, C_COLLECTED, C_LOST, C_INJECTED, C_REJECTED, C_SPILLED, C_DROPPED };
-enum { ERR_TMA_TIMEOUT = 1, ERR_CAPACITY = 2, ERR_BARRIER_TIMEOUT = 4 };
+enum { ERR_TMA_TIMEOUT = 1, ERR_CAPACITY = 2, ERR_BARRIER_TIMEOUT = 4, ERR_CHUNK_TIMEOUT = 8 };
 
 // ---------------------------------------------------------------------------
 // Object level sets in cell units (Sec. 2.1 interface Gamma; L >= 0 plasma).

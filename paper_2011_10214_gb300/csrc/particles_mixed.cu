@@ -3,9 +3,10 @@
 // collection) with the state a particle carries cut to 28 bytes: a packed
 // int32 cell (i | j<<11 | k<<22), the FP32 offset inside the cell and the
 // FP32 velocity.  Positions never lose precision far from the origin because
-// the offset is relative to the cell.  Fixed-point deposits stay int64 (exact
-// 2^32 units per particle); the weights are FP32.  Injection samples in FP64
-// (shared sampler) and converts.
+// the offset is relative to the cell.  Node charges stay int64 with exactly
+// 2^32 units per particle; the weights are FP32, rounded to 2^-19 of a particle
+// inside a bin (2^-32 for movers).  Injection samples in FP32 from the same
+// random streams as the FP64 path.
 #include <math.h>
 
 #include "internal.h"
@@ -237,16 +238,27 @@ PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
     return (i - x0) + TILE * ((j - y0) + TILE * (k - z0));
 }
 
-__global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dthf,
+// One CTA per (bin, species); warps take chunks of 32 particles in turn
+// (prefetching their next chunk) and never wait at a block barrier.  Stayers
+// are compacted in place: chunk c writes its stayers right after those of
+// chunks 0..c-1, whose running count it reads from shared memory once the
+// warp of chunk c-1 has published it.  Writes then land only on slots of
+// chunks <= c, all of which were read before their counts were published, so
+// no unread particle is overwritten.
+__global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
-    // fixed-point tile, low 16 bits / high part, with 8 interleaved copies per
-    // node (copy = lane & 7): the lanes of one atomic instruction spread over
-    // the banks instead of colliding on the few nodes of a 4^3-cell bin
-    __shared__ int Wlo[8 * TILE_N];
-    __shared__ int Whi[8 * TILE_N];
+    // deposits of the bin's stayers in units of 2^-19 particle, 8 interleaved
+    // copies per node (copy = lane & 7) so that the lanes of one atomic
+    // instruction spread over the banks.  A particle adds 7 rounded weights and
+    // the remainder 2^19 - sum (at least -4), so a copy, reached by at most
+    // BIN_MAX / 8 + 1 particles, holds a value in [-2^14, 2^31]: exact in 32
+    // bits modulo 2^32.  The flush multiplies by 2^13 (2^32 units per particle).
+    __shared__ unsigned Wt[8 * TILE_N];
+    // stayers of chunks 0..c, plus one, for each chunk c (0: not yet published;
+    // -1: the chain gave up)
+    __shared__ int pre[(BIN_MAX + 31) / 32];
     __shared__ alignas(8) unsigned long long bar;
-    __shared__ int wcnt[2][8];        // stayers per warp, by chunk parity
     __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
     const int s = blockIdx.y;
@@ -257,8 +269,10 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int nch = (n + 31) >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) Wt[t] = 0u;
+    for (int t = tid; t < nch; t += blockDim.x) pre[t] = 0;
     if (tid < NCTR) sctr[tid] = 0u;
     __syncthreads();
     if (tid == 0) {
@@ -278,22 +292,20 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
     const float kf = (float)S.k;
     const int refl = S.reflect;
     const int copy = lane & 7;
-    int nstay = 0;
-    // the next chunk is loaded into registers while this one is processed
-    // (its slots lie beyond every slot this chunk's in-place writes can reach)
+    volatile int* vpre = pre;
+    unsigned c_push = 0, c_abs = 0, c_col = 0, c_lost = 0;
     PF32 pn;
     long long idn = 0;
-    if (tid < n) {
-        load_p(S.binsF, start + tid, pn);
-        if (track) idn = S.binsF.id[start + tid];
+    if (wid * 32 + lane < n) {
+        load_p(S.binsF, start + wid * 32 + lane, pn);
+        if (track) idn = S.binsF.id[start + wid * 32 + lane];
     }
-    int par = 0;
-    for (int base = 0; base < n; base += blockDim.x, par ^= 1) {
-        const int i = base + tid;
+    for (int c = wid; c < nch; c += nw) {
+        const int i = c * 32 + lane;
         int code = NONE, acc = -1;
         PF32 p = pn;
-        long long id = idn;
-        const int inext = i + blockDim.x;
+        const long long id = idn;
+        const int inext = i + nw * 32;
         if (inext < n) {
             load_p(S.binsF, start + inext, pn);
             if (track) idn = S.binsF.id[start + inext];
@@ -324,56 +336,81 @@ __global__ void __launch_bounds__(256) k_push_bins_m(Launch L, ObjF of, float dt
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
             mover = !stay;
-            if (stay) {
+            if (stay) {   // (movers deposit in the rebin, with every mover of the step)
                 const WF w = weights_f(p.fx, p.fy, p.fz);
-                unsigned W[7];
+                const int t0 = 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy;
+                unsigned rest = 1u << 19;
 #pragma unroll
-                for (int l = 0; l < 7; ++l) W[l] = __float2uint_rn(w.w[l] * 4294967296.0f);
-                tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W);
-            } else {
-                global_deposit_f(L, S.W, p);
+                for (int l = 0; l < 7; ++l) {
+                    const unsigned W = __float2uint_rn(w.w[l] * 524288.0f);
+                    rest -= W;
+                    atomicAdd(&Wt[t0 + 8 * tile_corner(l)], W);
+                }
+                atomicAdd(&Wt[t0 + 8 * tile_corner(7)], rest);
             }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
-        count_event32(&sctr[C_PUSHED], code != NONE);
-        count_event32(&sctr[C_ABSORBED], code == ABSORBED);
-        count_event32(&sctr[C_COLLECTED], code == COLLECTED);
-        count_event32(&sctr[C_LOST], code == COLLECTED && acc < 0);
+        c_push += code != NONE;
+        c_abs += code == ABSORBED;
+        c_col += code == COLLECTED;
+        c_lost += code == COLLECTED && acc < 0;
+        // running count of the chunks before this one (bounded wait)
         const unsigned bal = __ballot_sync(0xffffffffu, stay);
-        if (lane == 0) wcnt[par][wid] = __popc(bal);
-        __syncthreads();
-        // this warp's offset among the chunk's stayers: scan of the warp counts
-        const int v = lane < nw ? wcnt[par][lane] : 0;
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+        int before = 0;
+        if (lane == 0 && c > 0) {
+            int v;
+            long long spins = 0;
+            while ((v = vpre[c - 1]) == 0)
+                if (++spins > (1ll << 26)) { v = -1; atomicOr(L.err, ERR_CHUNK_TIMEOUT); break; }
+            before = v;   // count + 1, or -1
+        } else if (lane == 0) {
+            before = 1;
         }
-        const int tot = __shfl_sync(0xffffffffu, incl, nw - 1);
-        const int off = __shfl_sync(0xffffffffu, incl - v, wid);
-        if (stay) store_p(S.binsF, start + nstay + off + __popc(bal & ((1u << lane) - 1)), p, id, track);
+        before = __shfl_sync(0xffffffffu, before, 0);
+        if (before < 0) {   // the chain gave up: pass it on and drop this bin's stayers
+            if (lane == 0) vpre[c] = -1;
+            break;
+        }
+        before -= 1;
+        if (lane == 0) vpre[c] = before + __popc(bal) + 1;
+        if (stay) store_p(S.binsF, start + before + __popc(bal & ((1u << lane) - 1)), p, id, track);
         long long slot = warp_reserve(S.mov_out_n, mover);
         if (mover) {
             if (slot < S.mcap) store_p(S.movF_out, slot, p, id, track);
             else atomicAdd(&S.ctr[C_DROPPED], 1ull);
         }
-        nstay += tot;
-        // one barrier per chunk: wcnt alternates with the chunk parity, and a
-        // warp one chunk ahead writes only slots whose particles every warp
-        // loaded before the barrier it has already passed
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c_push += __shfl_xor_sync(0xffffffffu, c_push, o);
+        c_abs += __shfl_xor_sync(0xffffffffu, c_abs, o);
+        c_col += __shfl_xor_sync(0xffffffffu, c_col, o);
+        c_lost += __shfl_xor_sync(0xffffffffu, c_lost, o);
+    }
+    if (lane == 0) {
+        if (c_push) atomicAdd(&sctr[C_PUSHED], c_push);
+        if (c_abs) atomicAdd(&sctr[C_ABSORBED], c_abs);
+        if (c_col) atomicAdd(&sctr[C_COLLECTED], c_col);
+        if (c_lost) atomicAdd(&sctr[C_LOST], c_lost);
     }
     __syncthreads();
-    if (tid == 0) S.bcount[b] = nstay;
+    if (tid == 0) {
+        const int last = vpre[nch - 1];
+        S.bcount[b] = last > 0 ? last - 1 : 0;
+    }
     for (int t = tid; t < TILE_N; t += blockDim.x) {
         long long v = 0;
-        for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
+        for (int c = 0; c < 8; ++c) {
+            long long u = (long long)Wt[t * 8 + c];
+            if (u >= (3ll << 30)) u -= 1ll << 32;     // a (small) negative copy total
+            v += u;
+        }
         if (!v) continue;
         int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
         if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
-            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
+            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)(v * 8192));
     }
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
@@ -398,8 +435,7 @@ __global__ void k_push_movers_m(Launch L, ObjF of, float dthf) {
             load_p(S.movF_in, i, p);
             if (track) id = S.movF_in.id[i];
             code = push_one(L, of, kf, dthf, S.reflect, p, ea, acc);
-            if (code == ALIVE) global_deposit_f(L, S.W, p);
-            else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
+            if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
         count_event(&sctr[C_PUSHED], code != NONE);
         count_event(&sctr[C_ABSORBED], code == ABSORBED);
@@ -461,8 +497,7 @@ __global__ void k_inject_m(Launch L, InjArgs a, ObjF of, float dthf) {
                     code = COLLECTED;
                     if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
                 } else {
-                    code = ALIVE;
-                    global_deposit_f(L, S.W, p);
+                    code = ALIVE;   // deposits in the rebin
                 }
             }
         }
@@ -482,6 +517,10 @@ __global__ void k_inject_m(Launch L, InjArgs a, ObjF of, float dthf) {
     if (threadIdx.x < NCTR && sctr[threadIdx.x]) atomicAdd(&S.ctr[threadIdx.x], sctr[threadIdx.x]);
 }
 
+// rebin: every particle of this step's mover list (bin leavers of the push,
+// survivors of the spill list, injected and photoemitted particles) deposits
+// its charge here, in one warp-coherent pass, then joins its bin or, if the
+// bin is full, next step's spill list
 __global__ void k_rebin_m(Launch L) {
     const int s = blockIdx.y;
     const SpeciesDev& S = L.sp[s];
@@ -496,6 +535,7 @@ __global__ void k_rebin_m(Launch L) {
         if (i < n) {
             load_p(S.movF_out, i, p);
             if (track) id = S.movF_out.id[i];
+            global_deposit_f(L, S.W, p);
             int b = block_of(L, p.i, p.j, p.k);
             int slot = atomicAdd(&S.bcount[b], 1);
             if (slot < S.bcap[b]) store_p(S.binsF, S.bstart[b] + slot, p, id, track);
@@ -713,8 +753,7 @@ __global__ void k_photo_m(Launch L, PhotoArgs a) {
                     if (p.fx >= 1.0f) p.fx = 0.99999994f;
                     if (p.fy >= 1.0f) p.fy = 0.99999994f;
                     if (p.fz >= 1.0f) p.fz = 0.99999994f;
-                    p.vx = (float)sm.v[0]; p.vy = (float)sm.v[1]; p.vz = (float)sm.v[2];
-                    global_deposit_f(L, S.W, p);
+                    p.vx = (float)sm.v[0]; p.vy = (float)sm.v[1]; p.vz = (float)sm.v[2];   // deposits in the rebin
                 }
             }
         }
