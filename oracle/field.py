@@ -23,6 +23,13 @@ Readings where the paper is silent (also in the design doc):
   * node field: E_i = -(sum |P| grad phi_h|_P) / (sum |P|) over the element
     pieces P around node i that lie in Omega^+ if their volume is positive,
     otherwise over all pieces;
+  * layered object (geometry.set_bedrock): regular tets take the permittivity
+    of their region (plasma, regolith, bedrock); a tet inside the object cut by
+    the bedrock plane is an interface tet of that plane (bedrock on its minus
+    side, homogeneous flux jump, no surface charge, no Gamma_h area for the
+    surface bookkeeping); a tet cut by the object's surface stays an interface
+    tet of the surface alone even if the bedrock plane also crosses it (its
+    object side takes the regolith's permittivity);
   * Dirichlet value of a node on several Dirichlet faces: the first such face
     in the order x-, x+, y-, y+, z-, z+.
 """
@@ -52,6 +59,18 @@ class FieldSystem:
         ni, nj, nk = mesh.node_ijk()
         self.Lnode = obj.L(ni.astype(np.float64), nj.astype(np.float64), nk.astype(np.float64))
         self.minus = self.Lnode < 0
+        # layered object: bedrock (L_b = z - z_b < 0, inside the object) under the regolith
+        bed = getattr(obj, "bed", None)
+        if bed is not None:
+            zb, eb = bed
+            self.Lbed = nk.astype(np.float64) - zb
+            self.bmask = self.Lbed < 0
+            if np.any(self.bmask & ~self.minus):
+                raise ValueError("the bedrock must lie inside the object")
+        else:
+            eb = None
+            self.Lbed = None
+            self.bmask = np.zeros(mesh.nnodes, dtype=bool)
         cv = mesh.cube_vertex_nodes()
         par = mesh.cell_parity()
         G, V = regular_grad_table(h)
@@ -59,14 +78,17 @@ class FieldSystem:
         rows, cols, vals = [], [], []
         # per-tet piece data for the node field: regular tets by shape
         self.reg = []          # list of (cells, tet nodes (m,4), grads (4,3), vol, region_plus (m,))
-        it_cell, it_t, it_nodes, it_data = [], [], [], []
+        it_cell, it_t, it_nodes, it_data, it_kind = [], [], [], [], []
         for p in range(2):
             cells_p = np.nonzero(par == p)[0]
             for t, tv in enumerate(TETS[p]):
                 nodes = cv[cells_p][:, list(tv)]
                 nm = self.minus[nodes].sum(axis=1)
-                for region, mask in (("+", nm == 0), ("-", nm == 4)):
-                    eps = ep if region == "+" else em
+                nb = self.bmask[nodes].sum(axis=1)
+                regions = [("+", ep, nm == 0), ("-", em, (nm == 4) & (nb == 0))]
+                if bed is not None:
+                    regions.append(("b", eb, nb == 4))
+                for region, eps, mask in regions:
                     sel = nodes[mask]
                     Kt = eps * V[t] * (G[p][t] @ G[p][t].T)
                     for a in range(4):
@@ -74,23 +96,35 @@ class FieldSystem:
                             rows.append(sel[:, a]); cols.append(sel[:, b])
                             vals.append(np.full(len(sel), Kt[a, b]))
                     self.reg.append((sel, G[p][t], V[t], region == "+"))
-                icells = cells_p[(nm > 0) & (nm < 4)]
-                for c in icells:
-                    nd = cv[c][list(tv)]
-                    verts = VERT_OFF[list(tv)].astype(np.float64) * h
-                    d = ife_local(verts, self.Lnode[nd], em, ep)
-                    it_cell.append(c); it_t.append(t); it_nodes.append(nd); it_data.append(d)
+                # interface tets: cut by the object's surface (kind 0; also when the
+                # bedrock plane crosses the same tet: that tet keeps the surface
+                # only, its object side with the regolith's permittivity), or lying
+                # inside the object and cut by the bedrock plane only (kind 1:
+                # homogeneous flux jump, no surface charge)
+                for kind, icells in ((0, cells_p[(nm > 0) & (nm < 4)]),
+                                     (1, cells_p[(nm == 4) & (nb > 0) & (nb < 4)])):
+                    for c in icells:
+                        nd = cv[c][list(tv)]
+                        verts = VERT_OFF[list(tv)].astype(np.float64) * h
+                        if kind == 0:
+                            d = ife_local(verts, self.Lnode[nd], em, ep)
+                        else:
+                            d = ife_local(verts, self.Lbed[nd], eb, em)
+                        it_cell.append(c); it_t.append(t); it_nodes.append(nd); it_data.append(d)
+                        it_kind.append(kind)
         order = np.lexsort((np.array(it_t, dtype=np.int64), np.array(it_cell, dtype=np.int64))) \
             if it_cell else np.zeros(0, dtype=np.int64)
         self.it_cell = np.array(it_cell, dtype=np.int64)[order]
         self.it_t = np.array(it_t, dtype=np.int64)[order]
         self.it_nodes = np.array(it_nodes, dtype=np.int64).reshape(-1, 4)[order]
+        self.it_kind = np.array(it_kind, dtype=np.int64)[order]
         data = [it_data[i] for i in order]
         self.it = data
         nit = len(data)
         self.it_K = np.array([d["K"] for d in data]).reshape(nit, 4, 4)
         self.it_c = np.array([d["c"] for d in data]).reshape(nit, 4)
-        self.it_area = np.array([d["area"] for d in data])
+        # Gamma_h area of the charged surface only (bedrock-plane tets carry none)
+        self.it_area = np.array([d["area"] if k == 0 else 0.0 for d, k in zip(data, self.it_kind)])
         self.it_volp = np.array([d["vol_plus"] for d in data])
         self.it_volm = np.array([d["vol_minus"] for d in data])
         self.it_gp = np.array([d["gp"] for d in data]).reshape(nit, 5, 3)
@@ -125,8 +159,10 @@ class FieldSystem:
             fill = (target < 0) & (cand >= 0)
             target[fill] = cand[fill]
         self.cell_to_acc = target
-        # cut-cell index of each interface tet (-1 if its cell has no Gamma_h area)
-        self.it_acc = acc[self.it_cell] if len(self.it_cell) else np.zeros(0, dtype=np.int64)
+        # cut-cell index of each interface tet (-1 if its cell has no Gamma_h area,
+        # and for the bedrock-plane tets)
+        self.it_acc = np.where(self.it_kind == 0, acc[self.it_cell], -1) if len(self.it_cell) \
+            else np.zeros(0, dtype=np.int64)
 
     def _setup_dirichlet(self, face_bc):
         m = self.mesh
@@ -226,7 +262,8 @@ class FieldSystem:
             gpl = np.einsum("ta,tak->tk", ph, self.it_gp[:, :4]) + qT[:, None] * self.it_gp[:, 4]
             gmi = np.einsum("ta,tak->tk", ph, self.it_gm[:, :4]) + qT[:, None] * self.it_gm[:, 4]
             nit = len(self.it_cell)
-            scatter(self.it_nodes, gpl, self.it_volp, np.ones(nit, dtype=bool))
+            # the + piece is plasma only on the object's surface, not on the bedrock plane
+            scatter(self.it_nodes, gpl, self.it_volp, self.it_kind == 0)
             scatter(self.it_nodes, gmi, self.it_volm, np.zeros(nit, dtype=bool))
         use_pl = vol_pl > 0
         E = np.empty((N, 3))
@@ -240,6 +277,8 @@ class FieldSystem:
             return 0.0
         tot = 0.0
         for n, d in enumerate(self.it):
+            if self.it_kind[n] != 0:
+                continue
             coef = d["coef"]
             for tri in d["tris"]:
                 cen = tri.mean(axis=0)

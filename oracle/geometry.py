@@ -16,6 +16,8 @@ Readings where the paper is silent (also listed in the design doc):
     neighbours.  Face diagonals then match between neighbouring cubes.
   * The object is given by an analytic level set L, L >= 0 in the plasma
     (Omega^+), L < 0 in the object (Omega^-).  A node with L == 0 is in Omega^+.
+  * A layered object (set_bedrock) has a second, planar level set L_b = z - z_b
+    inside it: bedrock where L_b < 0.
   * Gamma_h on a tet is the zero set of the linear interpolant of the nodal L
     values (a plane piece: a triangle for a 1-3 sign split, a planar quad for a
     2-2 split).
@@ -148,6 +150,72 @@ class CapCrater:
         inside = r2 < self.a2
         zs = np.where(inside, self.zc - np.sqrt(np.where(inside, self.Rs2 - r2, 0.0)), self.zg)
         return z - zs
+
+
+class RimCrater:
+    """Planar ground at height z_g with a raised-rim crater centred at (xc, yc).
+
+    Sec. 5.2.1 describes the lunar crater by an algebraic surface z = z(x, y)
+    set by its inner-rim, top-rim and outer-rim radii and its top height; the
+    profile between them is not printed.  This reading: a flat floor at depth D
+    below the ground inside the inner-rim radius Ri; an inner wall rising from
+    the floor to the rim top, H above the ground, at the top-rim radius Rt; an
+    outer flank falling back to the ground at the outer-rim radius Ro.  Both
+    ramps are the cubic smoothstep s(t) = t^2 (3 - 2t) of the radial
+    coordinate, so the surface is continuous with a continuous slope.  All
+    arguments physical; L = z - z_s(x, y) in cell units.
+    """
+
+    kind = "rim_crater"
+
+    def __init__(self, mesh, z_ground, xc, yc, r_inner, r_top, r_outer, height, depth, eps_in, eps_out):
+        h = mesh.h
+        self.zg = (float(z_ground) - mesh.origin[2]) / h
+        self.xc = (float(xc) - mesh.origin[0]) / h
+        self.yc = (float(yc) - mesh.origin[1]) / h
+        self.ri = float(r_inner) / h
+        self.rt = float(r_top) / h
+        self.ro = float(r_outer) / h
+        H = float(height) / h
+        D = float(depth) / h
+        if not (0.0 <= self.ri < self.rt < self.ro) or H < 0.0 or D < 0.0:
+            raise ValueError("rim crater needs 0 <= r_inner < r_top < r_outer, height >= 0, depth >= 0")
+        self.H = H
+        self.zfloor = self.zg - D
+        self.ztop = self.zg + H
+        self.rise = D + H
+        self.w_in = self.rt - self.ri
+        self.w_out = self.ro - self.rt
+        self.eps_minus = float(eps_in)
+        self.eps_plus = float(eps_out)
+
+    def surface(self, x, y):
+        dx = x - self.xc
+        dy = y - self.yc
+        r = np.sqrt(dx * dx + dy * dy)
+        t1 = (r - self.ri) / self.w_in
+        s1 = (t1 * t1) * (3.0 - 2.0 * t1)
+        t2 = (r - self.rt) / self.w_out
+        s2 = (t2 * t2) * (3.0 - 2.0 * t2)
+        z_in = self.zfloor + self.rise * s1
+        z_out = self.ztop - self.H * s2
+        return np.where(r <= self.ri, self.zfloor,
+                        np.where(r <= self.rt, z_in, np.where(r < self.ro, z_out, self.zg)))
+
+    def L(self, x, y, z):
+        return z - self.surface(x, y)
+
+
+def set_bedrock(obj, mesh, z_bed, eps_bed):
+    """A second dielectric layer of the object (Sec. 5.2.1: lunar regolith over
+    bedrock).  Below the plane z = z_bed (physical) the object has permittivity
+    eps_bed; its level set is L_b = z - z_bed in cell units, L_b < 0 in the
+    bedrock, which must lie inside the object (checked by the field set-up).
+    Returns obj with the attribute bed = (z_bed in cell units, eps_bed)."""
+    if not (float(eps_bed) > 0.0):
+        raise ValueError("eps_bed must be positive")
+    obj.bed = ((float(z_bed) - mesh.origin[2]) / mesh.h, float(eps_bed))
+    return obj
 
 
 class Plane:

@@ -117,6 +117,8 @@ class Photoemission:
         self.dth = dt / mesh.h
         rows = []
         for T in range(len(fs.it_cell)):
+            if int(fs.it_kind[T]) != 0:
+                continue                      # bedrock plane: not a surface
             c = int(fs.it_cell[T])
             ci, cj, ck = c % mesh.nx, (c // mesh.nx) % mesh.ny, c // (mesh.nx * mesh.ny)
             p = (ci + cj + ck) & 1
