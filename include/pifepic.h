@@ -82,8 +82,23 @@ typedef struct {
  *   CAP_CRATER: params = {z_ground, xc, yc, rim_radius, depth}; planar ground
  *               with a spherical-cap crater             (reading of Sec. 5.2.1)
  *   PLANE:      params = {n_x, n_y, n_z, d0} in cell units: L = n.xi - d0
+ *   RIM_CRATER: params = {z_ground, xc, yc, r_inner, r_top, r_outer, height,
+ *               depth}: planar ground with a raised-rim crater (Sec. 5.2.1
+ *               names the crater by its inner-rim, top-rim and outer-rim radii
+ *               and its top height; the profile is this library's reading): a
+ *               flat floor at depth below the ground inside r_inner, an inner
+ *               wall rising to the rim top (height above the ground) at r_top
+ *               and an outer flank falling to the ground at r_outer, both
+ *               ramps the cubic smoothstep t^2 (3 - 2t) of the radius.  EINVAL
+ *               unless 0 <= r_inner < r_top < r_outer, height, depth >= 0.
  *   NONE:       no object. */
-enum { PIFEPIC_OBJ_NONE = 0, PIFEPIC_OBJ_SPHERE = 1, PIFEPIC_OBJ_CAP_CRATER = 2, PIFEPIC_OBJ_PLANE = 3 };
+enum {
+    PIFEPIC_OBJ_NONE = 0,
+    PIFEPIC_OBJ_SPHERE = 1,
+    PIFEPIC_OBJ_CAP_CRATER = 2,
+    PIFEPIC_OBJ_PLANE = 3,
+    PIFEPIC_OBJ_RIM_CRATER = 4
+};
 typedef struct {
     int kind;
     double params[8];
@@ -138,6 +153,17 @@ const char* pifepic_last_error(const pifepic_ctx* ctx);
  * FP64 solve each), stiffness patch rows, cut cells.  Must precede particle
  * calls.  set_field_bc may be called before or after set_object. */
 pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* obj);
+
+/* A second dielectric layer of the object (Sec. 5.2.1: the lunar regolith lies
+ * on bedrock of higher permittivity): below the plane z = z_bed (physical
+ * height) the object has permittivity eps_bed.  Tets inside the object that
+ * the plane cuts become interface tets of the plane (homogeneous flux jump, no
+ * surface charge, no photoemission); a tet cut by the object's surface keeps
+ * the surface alone even where the plane also crosses it.  The bedrock must
+ * lie inside the object: set_object fails with EINVAL if a mesh node below
+ * z_bed is outside it.  Call before pifepic_set_object.  Errors: EINVAL
+ * (eps_bed <= 0, z_bed not finite), ESTATE (after set_object). */
+pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_bed);
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
 
 /* Species with charge q, mass m (q/m sets the push) and macro-particle

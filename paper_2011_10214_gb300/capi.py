@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpifepic.so")
 
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
-OBJ_NONE, OBJ_SPHERE, OBJ_CAP_CRATER, OBJ_PLANE = 0, 1, 2, 3
+OBJ_NONE, OBJ_SPHERE, OBJ_CAP_CRATER, OBJ_PLANE, OBJ_RIM_CRATER = 0, 1, 2, 3, 4
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PBC_ABSORB, PBC_INJECT, PBC_REFLECT = 0, 1, 2
 _PBC_NAMES = {"absorb": PBC_ABSORB, "inject": PBC_INJECT, "reflect": PBC_REFLECT}
@@ -80,6 +80,7 @@ _sigs = {
     "pifepic_get_injection_rate": [_ctx, C.c_int, C.c_double * 6],
     "pifepic_set_photoemission": [_ctx, C.c_int, C.c_double * 3, C.c_double, C.c_double, C.c_uint64],
     "pifepic_set_particle_bc": [_ctx, C.c_int, C.c_int * 6],
+    "pifepic_set_bedrock": [_ctx, C.c_double, C.c_double],
     "pifepic_get_photoemission": [_ctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "pifepic_set_external_E": [_ctx, _dp, C.c_int],
     "pifepic_solve": [_ctx, C.POINTER(Stats)],
@@ -177,6 +178,11 @@ class Simulation:
         p = list(params) + [0.0] * (8 - len(params))
         od = ObjectDesc(int(kind), (C.c_double * 8)(*p), float(eps_in), float(eps_out))
         self._ok(lib.pifepic_set_object(self._c, C.byref(od)), "set_object")
+
+    def set_bedrock(self, z_bed, eps_bed):
+        """Bedrock of permittivity eps_bed below the plane z = z_bed inside the
+        object (see pifepic_set_bedrock); call before set_object."""
+        self._ok(lib.pifepic_set_bedrock(self._c, float(z_bed), float(eps_bed)), "set_bedrock")
 
     def set_field_bc(self, faces):
         arr = (FaceBC * 6)()
@@ -350,11 +356,16 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
                      pcg_max_iter, track_ids, stream)
     sim.set_field_bc(cfg["face_bc"])
     ob = cfg["object"]
+    if ob.get("bedrock") is not None:
+        sim.set_bedrock(*ob["bedrock"])
     if ob["kind"] == "sphere":
         sim.set_object(OBJ_SPHERE, list(ob["center"]) + [ob["radius"]], ob["eps_in"], ob["eps_out"])
     elif ob["kind"] == "cap_crater":
         sim.set_object(OBJ_CAP_CRATER, [ob["z_ground"], ob["xc"], ob["yc"], ob["rim_radius"], ob["depth"]],
                        ob["eps_in"], ob["eps_out"])
+    elif ob["kind"] == "rim_crater":
+        sim.set_object(OBJ_RIM_CRATER, [ob["z_ground"], ob["xc"], ob["yc"], ob["r_inner"], ob["r_top"],
+                                        ob["r_outer"], ob["height"], ob["depth"]], ob["eps_in"], ob["eps_out"])
     else:
         sim.set_object(OBJ_NONE, [], 1.0, 1.0)
     pbc = cfg.get("particle_bc")

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <new>
 
+#include <cmath>
+
 #include "internal.h"
 
 namespace pf {
@@ -317,7 +319,9 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     c.it_cell = c.it_t = c.it_acc = c.cut_cell = nullptr;
     c.it_data = c.qT = c.cut_area = c.qcut = c.patch_coef = nullptr;
     c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr; c.it_dataf = nullptr;
-    CUDA_OK(launch_setup(c));
+    cudaError_t se = launch_setup(c);
+    if (c.bed_outside) FAIL(PIFEPIC_EINVAL, "the bedrock must lie inside the object (a bedrock node has L >= 0)");
+    CUDA_OK(se);
     ALLOC(c.it_dataf, sizeof(float) * 32 * (c.nit > 0 ? c.nit : 1));
     CUDA_OK(launch_node_E_tables(c));
     ALLOC(c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1));
@@ -364,10 +368,36 @@ pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* o
     case PIFEPIC_OBJ_PLANE:
         ob.kind = 3; ob.a0 = q[0]; ob.a1 = q[1]; ob.a2 = q[2]; ob.a3 = q[3];
         break;
+    case PIFEPIC_OBJ_RIM_CRATER: {
+        double zg = (q[0] - c.origin[2]) / h, xc = (q[1] - c.origin[0]) / h, yc = (q[2] - c.origin[1]) / h;
+        double ri = q[3] / h, rt = q[4] / h, ro = q[5] / h, H = q[6] / h, D = q[7] / h;
+        if (!(ri >= 0.0 && ri < rt && rt < ro) || !(H >= 0.0) || !(D >= 0.0))
+            FAIL(PIFEPIC_EINVAL, "rim crater needs 0 <= r_inner < r_top < r_outer, height >= 0, depth >= 0");
+        ob.kind = 4;
+        ob.a0 = xc; ob.a1 = yc; ob.a2 = ri; ob.a3 = rt; ob.a4 = ro;
+        ob.a5 = zg - D; ob.a6 = zg + H; ob.a7 = D + H; ob.a8 = H; ob.a9 = rt - ri; ob.a10 = ro - rt; ob.a11 = zg;
+        break;
+    }
     default: FAIL(PIFEPIC_EINVAL, "unknown object kind %d", o->kind);
+    }
+    if (c.bed_on && ob.kind != 0) {
+        ob.bed = 1;
+        ob.zb = (c.bed_z - c.origin[2]) / h;
+        ob.eps_bed = c.bed_eps;
     }
     c.obj = ob;
     return do_setup(ctx);
+}
+
+pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_bed) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (c.have_object) FAIL(PIFEPIC_ESTATE, "set_bedrock must precede set_object");
+    if (!(eps_bed > 0.0) || !std::isfinite(z_bed)) FAIL(PIFEPIC_EINVAL, "eps_bed must be positive and z_bed finite");
+    c.bed_on = true;
+    c.bed_z = z_bed;
+    c.bed_eps = eps_bed;
+    return PIFEPIC_OK;
 }
 
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]) {

@@ -25,9 +25,13 @@ enum { ERR_TMA_TIMEOUT = 1, ERR_CAPACITY = 2, ERR_BARRIER_TIMEOUT = 4, ERR_CHUNK
 // is compiled without FMA contraction) so hit decisions are reproducible.
 // ---------------------------------------------------------------------------
 struct Object {
-    int kind;          // 0 none, 1 sphere, 2 cap crater, 3 plane
-    double a0, a1, a2, a3, a4, a5;
+    int kind;          // 0 none, 1 sphere, 2 cap crater, 3 plane, 4 rim crater
+    double a0, a1, a2, a3, a4, a5, a6, a7, a8, a9, a10, a11;
     double eps_minus, eps_plus;
+    // layered object: bedrock (permittivity eps_bed) below the plane z = zb
+    // (cell units) inside the object; L_b = z - zb < 0 there
+    int bed;
+    double zb, eps_bed;
 };
 
 PF_HD double level_set(const Object& o, double x, double y, double z) {
@@ -41,9 +45,30 @@ PF_HD double level_set(const Object& o, double x, double y, double z) {
         return z - zs;
     } else if (o.kind == 3) {                // plane: n.xi - d0
         return ((o.a0 * x + o.a1 * y) + o.a2 * z) - o.a3;
+    } else if (o.kind == 4) {                // rim crater (see pifepic_set_object)
+        // a0, a1 centre; a2, a3, a4 inner-rim, top-rim, outer-rim radii;
+        // a5 floor, a6 rim top, a11 ground heights; a7 = depth + height;
+        // a8 height; a9, a10 widths of the inner wall and the outer flank
+        double dx = x - o.a0, dy = y - o.a1;
+        double r = sqrt(dx * dx + dy * dy);
+        double zs;
+        if (r <= o.a2) {
+            zs = o.a5;
+        } else if (r <= o.a3) {
+            double t = (r - o.a2) / o.a9;
+            zs = o.a5 + o.a7 * ((t * t) * (3.0 - 2.0 * t));
+        } else if (r < o.a4) {
+            double t = (r - o.a3) / o.a10;
+            zs = o.a6 - o.a8 * ((t * t) * (3.0 - 2.0 * t));
+        } else {
+            zs = o.a11;
+        }
+        return z - zs;
     }
     return 1.0;
 }
+// bedrock level set of a layered object at a node of height k (cell units)
+PF_HD double bed_level(const Object& o, int k) { return (double)k - o.zb; }
 
 // ---------------------------------------------------------------------------
 // Mesh and 5-tet split (reading of Sec. 3.1.1): tet 0 = the 4 vertices of the

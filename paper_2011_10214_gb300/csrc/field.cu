@@ -163,7 +163,8 @@ __global__ void k_node_E(FieldArgs f, const double* L, const unsigned char* imas
                                 ph[3] * rec[IT_GM + 9 + d] + qt * rec[IT_GM + 12 + d];
                     }
                     double vp = rec[IT_VOLP], vm = rec[IT_VOLM];
-                    if (vp > 0.0) {
+                    // the + piece is plasma on the object's surface only (not on the bedrock plane)
+                    if (vp > 0.0 && rec[IT_KIND] == 0.0) {
                         for (int d = 0; d < 3; ++d) apl[d] += vp * gp[d];
                         vpl += vp;
                     }
@@ -203,7 +204,9 @@ __global__ void k_node_E_tables(long long nit, const double* it_data, float* itf
         float* o = itf + t * 32;
         for (int q = 0; q < 15; ++q) o[q] = (float)rec[IT_GP + q];
         for (int q = 0; q < 15; ++q) o[15 + q] = (float)rec[IT_GM + q];
-        o[30] = (float)rec[IT_VOLP];
+        // |o[30]| = the + piece's volume; negative on the bedrock plane, whose
+        // + piece is not plasma
+        o[30] = rec[IT_KIND] == 0.0 ? (float)rec[IT_VOLP] : -(float)rec[IT_VOLP];
         o[31] = (float)rec[IT_VOLM];
     }
     if (t < N) Lpos[t] = L[t] >= 0.0 ? 1 : 0;
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, cons
                         gm[d] = pv[0] * rec[15 + d] + pv[1] * rec[18 + d] + pv[2] * rec[21 + d] +
                                 pv[3] * rec[24 + d] + qt * rec[27 + d];
                     }
-                    const float vp = rec[30], vm = rec[31];
-                    if (vp > 0.f) {
+                    const float vp = fabsf(rec[30]), vm = rec[31];
+                    if (rec[30] > 0.f) {
                         for (int d = 0; d < 3; ++d) apl[d] += vp * gp[d];
                         vpl += vp;
                     }

@@ -169,6 +169,10 @@ struct Ctx {
     // line each)
     unsigned long long* bar64 = nullptr;
     long long zguard = 0;           // zeroed entries before z / zf (and after, plus 16)
+    // layered object (pifepic_set_bedrock), copied into obj by set_object
+    bool bed_on = false;
+    double bed_z = 0.0, bed_eps = 1.0;
+    bool bed_outside = false;       // set-up found a bedrock node outside the object
     // register-resident PCG launch plan (pcg_coop.cu): nodes per thread (0: the
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;
@@ -244,7 +248,8 @@ enum {
     IT_GM = 38,          // 15
     IT_S = 53,           // 4  int_Gamma psi_i
     IT_SJ = 57,          // 1  int_Gamma phi_J (unit q)
-    IT_STRIDE = 58
+    IT_KIND = 58,        // 1  0: the object's surface; 1: the bedrock plane (no charge, no area)
+    IT_STRIDE = 59
 };
 
 // ---- launchers ---------------------------------------------------------------

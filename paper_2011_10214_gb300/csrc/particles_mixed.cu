@@ -23,7 +23,7 @@ __global__ void k_clamp_counts(Launch L);
 
 struct ObjF {
     int kind;
-    float a0, a1, a2, a3, a4, a5;
+    float a0, a1, a2, a3, a4, a5, a6, a7, a8, a9, a10, a11;
 };
 
 static ObjF obj_f(const Object& o) {
@@ -31,6 +31,8 @@ static ObjF obj_f(const Object& o) {
     f.kind = o.kind;
     f.a0 = (float)o.a0; f.a1 = (float)o.a1; f.a2 = (float)o.a2;
     f.a3 = (float)o.a3; f.a4 = (float)o.a4; f.a5 = (float)o.a5;
+    f.a6 = (float)o.a6; f.a7 = (float)o.a7; f.a8 = (float)o.a8;
+    f.a9 = (float)o.a9; f.a10 = (float)o.a10; f.a11 = (float)o.a11;
     return f;
 }
 
@@ -45,6 +47,22 @@ PF_D float level_set_f(const ObjF& o, float x, float y, float z) {
         return z - zs;
     } else if (o.kind == 3) {
         return o.a0 * x + o.a1 * y + o.a2 * z - o.a3;
+    } else if (o.kind == 4) {   // rim crater, parameters as in level_set
+        const float dx = x - o.a0, dy = y - o.a1;
+        const float r = sqrtf(dx * dx + dy * dy);
+        float zs;
+        if (r <= o.a2) {
+            zs = o.a5;
+        } else if (r <= o.a3) {
+            const float t = (r - o.a2) / o.a9;
+            zs = o.a5 + o.a7 * ((t * t) * (3.0f - 2.0f * t));
+        } else if (r < o.a4) {
+            const float t = (r - o.a3) / o.a10;
+            zs = o.a6 - o.a8 * ((t * t) * (3.0f - 2.0f * t));
+        } else {
+            zs = o.a11;
+        }
+        return z - zs;
     }
     return 1.0f;
 }

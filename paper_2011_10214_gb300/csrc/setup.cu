@@ -34,22 +34,28 @@ __global__ void k_levelset(Mesh m, Object o, double* L) {
     L[n] = level_set(o, (double)i, (double)j, (double)k);
 }
 
-__global__ void k_classify(Mesh m, const double* L, unsigned char* mask, int* cnt) {
+// interface tets: cut by the object's surface (also when the bedrock plane
+// crosses the same tet: the surface alone then defines it), or inside the
+// object and cut by the bedrock plane only; bad counts bedrock nodes outside
+// the object
+__global__ void k_classify(Mesh m, Object o, const double* L, unsigned char* mask, int* cnt, int* bad) {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= m.ncells) return;
     int i = (int)(c % m.nx), j = (int)((c / m.nx) % m.ny), k = (int)(c / ((long long)m.nx * m.ny));
     int p = (i + j + k) & 1;
-    bool neg[8];
+    bool neg[8], bneg[8];
     for (int l = 0; l < 8; ++l) {
         int a, b, cc; loff(l, a, b, cc);
         neg[l] = L[node_id(m, i + a, j + b, k + cc)] < 0.0;
+        bneg[l] = o.bed && bed_level(o, k + cc) < 0.0;
+        if (bneg[l] && !neg[l]) atomicAdd(bad, 1);
     }
     unsigned char mk = 0;
     int n = 0;
     for (int t = 0; t < 5; ++t) {
-        int nm = 0;
-        for (int v = 0; v < 4; ++v) nm += neg[cT.vert[p][t][v]];
-        if (nm > 0 && nm < 4) { mk |= (unsigned char)(1u << t); ++n; }
+        int nm = 0, nbd = 0;
+        for (int v = 0; v < 4; ++v) { nm += neg[cT.vert[p][t][v]]; nbd += bneg[cT.vert[p][t][v]]; }
+        if ((nm > 0 && nm < 4) || (nm == 4 && nbd > 0 && nbd < 4)) { mk |= (unsigned char)(1u << t); ++n; }
     }
     mask[c] = mk;
     cnt[c] = n;
@@ -211,15 +217,26 @@ __global__ void k_interface(Mesh m, Object o, const double* L, const unsigned ch
     int T = ibase[c];
     for (int t = 0; t < 5; ++t) {
         if (!((mk >> t) & 1)) continue;
-        double vx[4][3], Lv[4];
+        double vx[4][3], Lv[4], Lb[4];
+        int nm = 0;
         for (int v = 0; v < 4; ++v) {
             int l = cT.vert[p][t][v];
             int a, b, cc; loff(l, a, b, cc);
             vx[v][0] = a * m.h; vx[v][1] = b * m.h; vx[v][2] = cc * m.h;
             Lv[v] = L[node_id(m, i + a, j + b, k + cc)];
+            Lb[v] = o.bed ? bed_level(o, k + cc) : 0.0;
+            nm += Lv[v] < 0.0;
         }
         double V = cT.vol[t] * m.h * m.h * m.h;
-        ife_tet(vx, Lv, o.eps_minus, o.eps_plus, V, it_data + (long long)T * IT_STRIDE);
+        double* rec = it_data + (long long)T * IT_STRIDE;
+        if (nm > 0 && nm < 4) {      // the object's surface
+            ife_tet(vx, Lv, o.eps_minus, o.eps_plus, V, rec);
+            rec[IT_KIND] = 0.0;
+        } else {                     // the bedrock plane: bedrock on the minus side
+            ife_tet(vx, Lb, o.eps_bed, o.eps_minus, V, rec);
+            rec[IT_AREA] = 0.0;
+            rec[IT_KIND] = 1.0;
+        }
         it_cell[T] = (int)c;
         it_t[T] = t;
         ++T;
@@ -274,15 +291,16 @@ __global__ void k_cell_acc(Mesh m, const int* own, int* acc) {
     acc[c] = v;
 }
 
-__global__ void k_it_acc(long long nit, const int* it_cell, const int* own, int* it_acc) {
+// cut-cell accumulator of each interface tet (-1 on the bedrock plane)
+__global__ void k_it_acc(long long nit, const int* it_cell, const double* it_data, const int* own, int* it_acc) {
     long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (T >= nit) return;
-    it_acc[T] = own[it_cell[T]];
+    it_acc[T] = it_data[T * IT_STRIDE + IT_KIND] != 0.0 ? -1 : own[it_cell[T]];
 }
 
-// node kinds: Dirichlet (-3), touching an interface tet (patch, flag 1),
-// regular plus (-1) or minus (-2)
-__global__ void k_node_kind(Mesh m, const double* L, const unsigned char* mask, const int* bcdir,
+// node kinds: Dirichlet (-3), touching an interface tet or in the bedrock
+// (patch, flag 1), regular plus (-1) or minus (-2)
+__global__ void k_node_kind(Mesh m, Object o, const double* L, const unsigned char* mask, const int* bcdir,
                             const double* bcval, int* ntype, int* patchflag, double* gdir) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= m.nnodes) return;
@@ -294,7 +312,7 @@ __global__ void k_node_kind(Mesh m, const double* L, const unsigned char* mask, 
     patchflag[n] = 0;
     if (dface >= 0) { ntype[n] = -3; gdir[n] = bcval[dface]; return; }
     gdir[n] = 0.0;
-    bool touch = false;
+    bool touch = o.bed && bed_level(o, k) < 0.0;
     for (int c8 = 0; c8 < 8 && !touch; ++c8) {
         int a, b, cc; loff(c8, a, b, cc);
         int ci = i - a, cj = j - b, ck = k - cc;
@@ -342,9 +360,12 @@ __global__ void k_patch_rows(Mesh m, Object o, const double* L, const unsigned c
                     const double* rec = it_data + (long long)T * IT_STRIDE;
                     for (int v = 0; v < 4; ++v) e[v] = rec[IT_K + 4 * kk + v];
                 } else {
+                    // a regular tet: the region of its first vertex
                     int l0 = cT.vert[p][t][0];
                     int a0, b0, c0; loff(l0, a0, b0, c0);
-                    double eps = L[node_id(m, ci + a0, cj + b0, ck + c0)] < 0.0 ? o.eps_minus : o.eps_plus;
+                    double eps = L[node_id(m, ci + a0, cj + b0, ck + c0)] < 0.0
+                                     ? ((o.bed && bed_level(o, ck + c0) < 0.0) ? o.eps_bed : o.eps_minus)
+                                     : o.eps_plus;
                     double s = eps * m.h * cT.vol[t];
                     for (int v = 0; v < 4; ++v)
                         e[v] = s * (cT.grad[p][t][kk][0] * cT.grad[p][t][v][0] +
@@ -585,6 +606,7 @@ cudaError_t launch_setup(Ctx& c) {
     int* cnt = nullptr; long long* scan = nullptr; long long* tot = nullptr;
     int* flag = nullptr; double* carea = nullptr; int* own = nullptr;
     int* bcdir = nullptr; double* bcval = nullptr;
+    int* bad = nullptr;
     long long hv = 0;
     long long nit_alloc = 1;
     long long nmax = m.nnodes > m.ncells ? m.nnodes : m.ncells;
@@ -597,10 +619,18 @@ cudaError_t launch_setup(Ctx& c) {
     CK(cudaMalloc(&own, sizeof(int) * m.ncells));
     CK(cudaMalloc(&bcdir, sizeof(int) * 6));
     CK(cudaMalloc(&bcval, sizeof(double) * 6));
+    CK(cudaMalloc(&bad, sizeof(int)));
 
+    c.bed_outside = false;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
     k_levelset<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode);
-    k_classify<<<nb(m.ncells), 256, 0, st>>>(m, c.Lnode, c.imask, cnt);
+    k_classify<<<nb(m.ncells), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, cnt, bad);
     CK(cudaGetLastError());
+    {
+        int hbad = 0;
+        CK(scopy(st, &hbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+        if (hbad) { c.bed_outside = true; err = cudaErrorInvalidValue; goto done; }
+    }
     // interface-tet offsets per cell
     CK(exclusive_scan(cnt, m.ncells, scan, tot, st));
     CK(scopy(st, &hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
@@ -629,13 +659,13 @@ cudaError_t launch_setup(Ctx& c) {
     }
     k_cut_list<<<nb(m.ncells), 256, 0, st>>>(m, flag, scan, carea, c.cut_cell, c.cut_area, own);
     k_cell_acc<<<nb(m.ncells), 256, 0, st>>>(m, own, c.cell_acc);
-    if (c.nit > 0) k_it_acc<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_cell, own, c.it_acc);
+    if (c.nit > 0) k_it_acc<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_cell, c.it_data, own, c.it_acc);
     CK(cudaGetLastError());
     // nodes
     for (int f = 0; f < 6; ++f) { hdir[f] = c.bc[f].kind == PIFEPIC_BC_DIRICHLET; hval[f] = c.bc[f].value; }
     CK(scopy(st, bcdir, hdir, sizeof(hdir), cudaMemcpyHostToDevice));
     CK(scopy(st, bcval, hval, sizeof(hval), cudaMemcpyHostToDevice));
-    k_node_kind<<<nb(m.nnodes), 256, 0, st>>>(m, c.Lnode, c.imask, bcdir, bcval, c.ntype, cnt, c.gdir);
+    k_node_kind<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, bcdir, bcval, c.ntype, cnt, c.gdir);
     CK(cudaGetLastError());
     CK(exclusive_scan(cnt, m.nnodes, scan, tot, st));
     CK(scopy(st, &hv, tot, sizeof(long long), cudaMemcpyDeviceToHost));
@@ -654,7 +684,7 @@ cudaError_t launch_setup(Ctx& c) {
     CK(cudaStreamSynchronize(st));
 done:
     cudaFree(cnt); cudaFree(scan); cudaFree(tot); cudaFree(flag); cudaFree(carea); cudaFree(own);
-    cudaFree(bcdir); cudaFree(bcval);
+    cudaFree(bcdir); cudaFree(bcval); cudaFree(bad);
     return err;
 }
 

@@ -1,7 +1,7 @@
 """Paired CUDA-library / oracle instances on identical seeded inputs (test helper)."""
 import numpy as np
 
-from oracle.geometry import CapCrater, Mesh, NoObject, Plane, Sphere
+from oracle.geometry import CapCrater, Mesh, NoObject, Plane, RimCrater, Sphere, set_bedrock
 from oracle.field import FieldSystem
 from oracle.pic import Simulation as OracleSim
 from paper_2011_10214_gb300 import workloads as wl
@@ -19,25 +19,44 @@ CASES = {
     # off-node ground with a bowl, for photoemission under a low sun (shadows)
     "crater_sun": dict(n=(24, 24, 12), h=1.0, obj=("cap_crater", 6.3, 12.0, 12.0, 8.0, 3.0, 4.0, 1.0),
                        bc=[("N",)] * 5 + [("D", 0.0)]),
+    # layered lunar ground: raised-rim crater in regolith (eps 4) over bedrock
+    # (eps 10) below z = 2.45, the crater centred on the y = 0 face (a half crater)
+    "lunar": dict(n=(30, 16, 16), h=1.0,
+                  obj=("rim_crater", 7.37, 15.0, 0.0, 4.1, 7.9, 11.6, 2.6, 2.2, 4.0, 1.0),
+                  bed=(2.45, 10.0), bc=[("N",)] * 5 + [("D", 0.0)]),
+    # the same with a floor below the top of the bedrock's cells: tets cut twice
+    "lunar_deep": dict(n=(30, 16, 16), h=1.0,
+                       obj=("rim_crater", 7.37, 15.0, 0.0, 4.1, 7.9, 11.6, 2.6, 4.6, 4.0, 1.0),
+                       bed=(2.45, 10.0), bc=[("N",)] * 5 + [("D", 0.0)]),
 }
 
 
-def oracle_object(m, o):
+def oracle_object(m, o, bed=None):
     if o[0] == "sphere":
-        return Sphere(m, o[1], o[2], o[3], o[4])
-    if o[0] == "cap_crater":
-        return CapCrater(m, *o[1:])
-    if o[0] == "plane":
-        return Plane(o[1], o[2], o[3], o[4])
-    return NoObject()
+        obj = Sphere(m, o[1], o[2], o[3], o[4])
+    elif o[0] == "cap_crater":
+        obj = CapCrater(m, *o[1:])
+    elif o[0] == "rim_crater":
+        obj = RimCrater(m, *o[1:])
+    elif o[0] == "plane":
+        obj = Plane(o[1], o[2], o[3], o[4])
+    else:
+        obj = NoObject()
+    if bed is not None:
+        set_bedrock(obj, m, *bed)
+    return obj
 
 
-def gpu_object(sim, o):
+def gpu_object(sim, o, bed=None):
     from paper_2011_10214_gb300 import capi
+    if bed is not None:
+        sim.set_bedrock(*bed)
     if o[0] == "sphere":
         sim.set_object(capi.OBJ_SPHERE, list(o[1]) + [o[2]], o[3], o[4])
     elif o[0] == "cap_crater":
         sim.set_object(capi.OBJ_CAP_CRATER, list(o[1:6]), o[6], o[7])
+    elif o[0] == "rim_crater":
+        sim.set_object(capi.OBJ_RIM_CRATER, list(o[1:9]), o[9], o[10])
     elif o[0] == "plane":
         sim.set_object(capi.OBJ_PLANE, list(o[1]) + [o[2]], o[3], o[4])
 
@@ -46,12 +65,12 @@ def make_pair(case, dt=0.05, tol=1e-12, maxit=2000, track=True, precision=0):
     from paper_2011_10214_gb300 import capi
     c = CASES[case]
     m = Mesh(*c["n"], c["h"])
-    obj = oracle_object(m, c["obj"])
+    obj = oracle_object(m, c["obj"], c.get("bed"))
     orc = OracleSim(m, obj, c["bc"], dt, tol=tol, maxit=maxit)
     gpu = capi.Simulation(c["n"], c["h"], dt, precision=precision, pcg_tol=tol, pcg_max_iter=maxit,
                           track_ids=track)
     gpu.set_field_bc(c["bc"])
-    gpu_object(gpu, c["obj"])
+    gpu_object(gpu, c["obj"], c.get("bed"))
     return gpu, orc
 
 
