@@ -85,14 +85,23 @@ def workload(name):
             "sphere32": wl.sphere_config(32, 3.0, 64, 100, seed_offset=6),
             "crater160": wl.CRATER160,
             "crater80": wl.crater_config(80, 80, 40, 10.0, 15.0, 5.0, seed_offset=7),
-            "oml50": wl.OML50}[name]
+            "oml50": wl.OML50,
+            "lunar200": wl.LUNAR200,
+            "lunar100": wl.lunar_config(100, 50, 50, 4.75, 2.25, 5.25, 10.1, 15.45, 1.35, 2.0, seed_offset=9)}[name]
 
 
 def cfg_desc(cfg, precision, extra=None):
     n = cfg["n"]
     ppc = cfg["species"][0]["ppc"]
     ob = cfg["object"]
-    if ob["kind"] == "cap_crater":
+    if ob["kind"] == "rim_crater":
+        w = (f"lunar crater charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), half raised-rim crater (radii "
+             f"{ob['r_inner']}/{ob['r_top']}/{ob['r_outer']}, rim {ob['height']} above and floor {ob['depth']} below "
+             f"the ground) in regolith eps {ob['eps_in']} at z={ob['z_ground']} over bedrock eps "
+             f"{ob['bedrock'][1]} below z={ob['bedrock'][0]}, {ppc} ppc/species solar-wind e-+H+ drifting 8 v_ti "
+             f"at 10 deg, photoelectrons (sun 10 deg above the ground), reflecting Y_min, injection at X_min/X_max/"
+             f"Y_max/Z_max, dt={cfg['dt']}, phi=0 at Z_max, Neumann elsewhere")
+    elif ob["kind"] == "cap_crater":
         w = (f"crater charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), ground z={ob['z_ground']} eps "
              f"{ob['eps_in']}, spherical-cap crater rim radius {ob['rim_radius']} depth {ob['depth']}, "
              f"{ppc} ppc/species solar-wind e-+H+ drifting 8 v_ti at 45 deg, photoelectrons from the sunlit "
@@ -314,7 +323,7 @@ def oracle_rate(workload_name, sample_frac, steps):
     random 1/sample_frac of the particles.  Particle work scales with the
     particle count, so the rate at full size is extrapolated as
     N / (t_particles * N / n_sample + t_field)."""
-    from oracle.geometry import CapCrater, Mesh, NoObject, Sphere
+    from oracle.geometry import CapCrater, Mesh, NoObject, RimCrater, Sphere, set_bedrock
     from oracle.pic import Simulation
     from paper_2011_10214_gb300 import workloads as wl
     cfg = workload(workload_name)
@@ -325,8 +334,13 @@ def oracle_rate(workload_name, sample_frac, steps):
     elif ob["kind"] == "cap_crater":
         obj = CapCrater(m, ob["z_ground"], ob["xc"], ob["yc"], ob["rim_radius"], ob["depth"], ob["eps_in"],
                         ob["eps_out"])
+    elif ob["kind"] == "rim_crater":
+        obj = RimCrater(m, ob["z_ground"], ob["xc"], ob["yc"], ob["r_inner"], ob["r_top"], ob["r_outer"],
+                        ob["height"], ob["depth"], ob["eps_in"], ob["eps_out"])
     else:
         obj = NoObject()
+    if ob.get("bedrock") is not None:
+        set_bedrock(obj, m, *ob["bedrock"])
     sim = Simulation(m, obj, cfg["face_bc"], cfg["dt"])
     nfull = 0
     for s, sp in enumerate(cfg["species"]):
@@ -485,7 +499,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="sphere64",
-                    choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80", "oml50"])
+                    choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80", "oml50", "lunar200",
+                             "lunar100"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")

@@ -105,6 +105,47 @@ def crater_config(nx=160, ny=160, nz=80, z_ground=20.0, rim_radius=30.0, depth=1
 CRATER160 = crater_config()
 
 
+def lunar_config(nx=200, ny=100, nz=100, z_ground=9.5, z_bed=4.5, r_inner=10.5, r_top=20.2, r_outer=30.9,
+                 height=2.7, depth=4.0, ppc=125, steps=200, mass_ratio=100.0, dt=0.05, angle_deg=10.0,
+                 seed_offset=8):
+    """The lunar crater charging run of Sec. 5.2 on one GPU: cells of one
+    photoelectron Debye length; a half crater (centred on the Y_min face, the
+    symmetry plane, which reflects particles) with inner-rim, top-rim and
+    outer-rim radii 10.5, 20.2, 30.9 cells in a regolith ground (eps 4) at
+    z = 9.5 over bedrock (eps 10) below z = 4.5; the rim profile's height and
+    depth (2.7 + 4.0 = the quoted 6.7 cells of relief) are this reading's;
+    phi = 0 at Z_max, zero Neumann elsewhere; solar-wind e- and ions
+    (T_e : T_i : T_ph = 6 : 5 : 1, density 8.7/64 of the photoelectron
+    reference, drift 8 ion thermal speeds at 10 degrees towards the ground in
+    the X-Z plane) loaded at ppc per species and injected at X_min, X_max,
+    Y_max and Z_max; photoelectrons from the sunlit, unshadowed surface, the
+    sun 10 degrees above the ground opposite to the flow."""
+    n_sw = 8.7 / 64.0
+    vte, vti = np.sqrt(6.0), np.sqrt(5.0 / mass_ratio)
+    vd = 8.0 * vti
+    a = np.radians(angle_deg)
+    drift = (vd * np.cos(a), 0.0, -vd * np.sin(a))
+    return dict(
+        name=f"lunar{nx}",
+        n=(nx, ny, nz), h=1.0, origin=(0.0, 0.0, 0.0), dt=dt, steps=steps,
+        object=dict(kind="rim_crater", z_ground=z_ground, xc=nx / 2, yc=0.0, r_inner=r_inner, r_top=r_top,
+                    r_outer=r_outer, height=height, depth=depth, eps_in=4.0, eps_out=1.0,
+                    bedrock=(z_bed, 10.0)),
+        face_bc=[("N",)] * 5 + [("D", 0.0)],
+        particle_bc=["inject", "inject", "reflect", "inject", "absorb", "inject"],
+        species=[dict(name="sw e-", q=-1.0, m=1.0, vth=vte, ppc=ppc, density=n_sw, drift=drift),
+                 dict(name="sw H+", q=1.0, m=mass_ratio, vth=vti, ppc=ppc, density=n_sw, drift=drift)],
+        photo=dict(name="photo e-", q=-1.0, m=1.0, vth=1.0, density=1.0, weight=n_sw / ppc,
+                   sun=(-np.cos(a), 0.0, np.sin(a))),
+        inject_faces=0b101011,
+        seed=SEED_BASE + seed_offset,
+    )
+
+
+# 200 x 100 x 100 cells (10M tets) as in Sec. 5.2, 125 ppc per solar-wind species
+LUNAR200 = lunar_config()
+
+
 def macro_weight(cfg, sp):
     return sp["density"] * cfg["h"] ** 3 / sp["ppc"]
 
