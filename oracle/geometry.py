@@ -206,6 +206,28 @@ class RimCrater:
         return z - self.surface(x, y)
 
 
+class Refined:
+    """An object seen from a mesh r times finer than the one it was built on
+    (the IFE mesh of a hybrid grid, Sec. 2.2: the PIC and IFE meshes may have
+    different resolutions): L_fine(xi) = L(xi / r) in the fine mesh's cell
+    units.  r is a power of two, so xi / r is exact and the fine level set is
+    the coarse one scaled by an exact power of two: same signs, same
+    interpolation ratios.  A bedrock plane moves to fine units (z_b r)."""
+
+    def __init__(self, obj, r):
+        self.obj = obj
+        self.r = float(r)
+        self.kind = obj.kind
+        self.eps_minus = obj.eps_minus
+        self.eps_plus = obj.eps_plus
+        bed = getattr(obj, "bed", None)
+        if bed is not None:
+            self.bed = (bed[0] * self.r, bed[1])
+
+    def L(self, x, y, z):
+        return self.obj.L(x / self.r, y / self.r, z / self.r)
+
+
 def set_bedrock(obj, mesh, z_bed, eps_bed):
     """A second dielectric layer of the object (Sec. 5.2.1: lunar regolith over
     bedrock).  Below the plane z = z_bed (physical) the object has permittivity

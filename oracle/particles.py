@@ -129,17 +129,21 @@ def reflect(mesh, P, mask):
             P[kv] = np.where(hi, -P[kv], P[kv])
 
 
-def hit_cells(mesh, obj, xo, yo, zo, xn, yn, zn):
-    """Cell index of the crossing point for particles that entered the object."""
+def hit_cells(mesh, obj, xo, yo, zo, xn, yn, zn, r=1):
+    """Cell index of the crossing point for particles that entered the object.
+
+    Positions are in the particle mesh's cell units; mesh is the field (IFE)
+    mesh, r times finer (r a power of two, 1 when the meshes coincide): the
+    crossing point's IFE cell is floor(r xi_c)."""
     Lo = obj.L(xo, yo, zo)
     Ln = obj.L(xn, yn, zn)
     t = Lo / (Lo - Ln)
     xc = xo + t * (xn - xo)
     yc = yo + t * (yn - yo)
     zc = zo + t * (zn - zo)
-    i = np.clip(np.floor(xc), 0, mesh.nx - 1).astype(np.int64)
-    j = np.clip(np.floor(yc), 0, mesh.ny - 1).astype(np.int64)
-    kk = np.clip(np.floor(zc), 0, mesh.nz - 1).astype(np.int64)
+    i = np.clip(np.floor(r * xc), 0, mesh.nx - 1).astype(np.int64)
+    j = np.clip(np.floor(r * yc), 0, mesh.ny - 1).astype(np.int64)
+    kk = np.clip(np.floor(r * zc), 0, mesh.nz - 1).astype(np.int64)
     return mesh.cell(i, j, kk)
 
 

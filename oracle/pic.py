@@ -23,6 +23,7 @@ import math
 import numpy as np
 
 from .field import FieldSystem
+from .geometry import Mesh, Refined
 from . import particles as pt
 from .photo import Photoemission
 
@@ -47,20 +48,35 @@ def _empty():
 class Simulation:
     """Plain FP64 IFE-PIC (Sec. 2.1, Fig. 1).
 
-    mesh: geometry.Mesh; obj: a level-set object; face_bc: 6 field BCs;
-    dt: time step (1/omega_pe units); absorbing particle faces on all six sides.
+    mesh: geometry.Mesh (the PIC mesh); obj: a level-set object built on it;
+    face_bc: 6 field BCs; dt: time step (1/omega_pe units); absorbing particle
+    faces on all six sides.  refine: the IFE mesh is the PIC mesh with each
+    cell split r x r x r (Sec. 2.2: PIC and IFE meshes may differ in
+    resolution; r a power of two, 1 = the same mesh).  Particles move, gather
+    and are binned on the PIC mesh; they deposit their charge on the IFE mesh
+    (trilinear weights of the IFE cell); the node field is solved on the IFE
+    mesh and read at the PIC nodes, which are IFE nodes.
     """
 
-    def __init__(self, mesh, obj, face_bc, dt, tol=1e-6, maxit=150):
+    def __init__(self, mesh, obj, face_bc, dt, tol=1e-6, maxit=150, refine=1):
         self.mesh, self.obj, self.dt = mesh, obj, float(dt)
         self.dth = self.dt / mesh.h
-        self.fs = FieldSystem(mesh, obj, face_bc)
+        self.r = int(refine)
+        if self.r < 1 or (self.r & (self.r - 1)):
+            raise ValueError("refine must be a power of two")
+        if self.r == 1:
+            self.fmesh, fobj = mesh, obj
+        else:
+            r = self.r
+            self.fmesh = Mesh(r * mesh.nx, r * mesh.ny, r * mesh.nz, mesh.h / r, mesh.origin)
+            fobj = Refined(obj, r)
+        self.fs = FieldSystem(self.fmesh, fobj, face_bc)
         self.tol, self.maxit = tol, maxit
         self.species = []
         self.P = []
         self.surf = np.zeros((len(self.fs.cut_cells), 0), dtype=np.int64)
         self.phi = self.fs.g.copy()
-        self.E = np.zeros((mesh.nnodes, 3))
+        self.E = np.zeros((self.fmesh.nnodes, 3))
         self.W = None
         self.qT = np.zeros(len(self.fs.it_cell))
         self.external_E = False
@@ -73,6 +89,16 @@ class Simulation:
         self.P.append(_empty())
         self.surf = np.zeros((len(self.fs.cut_cells), len(self.species)), dtype=np.int64)
         return len(self.species) - 1
+
+    def pic_nodes(self):
+        """IFE node index of every PIC node (they coincide on a hybrid grid)."""
+        m, r = self.mesh, self.r
+        i, j, k = m.node_ijk()
+        return self.fmesh.node(r * i, r * j, r * k)
+
+    def E_pic(self):
+        """The node field at the PIC nodes (what the gather reads)."""
+        return self.E if self.r == 1 else self.E[self.pic_nodes()]
 
     def load_maxwellian(self, s, ppc, vth, drift, seed):
         P = pt.load_maxwellian(self.mesh, self.obj, seed, s, ppc, vth, drift)
@@ -125,17 +151,21 @@ class Simulation:
         return pt.flux_density(dens, vth, vdn) * area * self.dt / self.species[s].w
 
     def set_external_E(self, E):
+        """Freeze the node field (given at the IFE nodes)."""
         self.E = np.array(E, dtype=np.float64).reshape(-1, 3)
         self.external_E = True
 
     # -- scatter / field-solve ---------------------------------------------------
     def deposit_all(self):
-        self.W = np.stack([pt.deposit(self.mesh, P["x"], P["y"], P["z"]) for P in self.P]) \
-            if self.P else np.zeros((0, self.mesh.nnodes), dtype=np.int64)
+        """Fixed-point charge of every particle on the IFE nodes (positions
+        scaled to IFE cell units: exact, r a power of two)."""
+        r = float(self.r)
+        self.W = np.stack([pt.deposit(self.fmesh, r * P["x"], r * P["y"], r * P["z"]) for P in self.P]) \
+            if self.P else np.zeros((0, self.fmesh.nnodes), dtype=np.int64)
         return self.W
 
     def node_load(self):
-        F = np.zeros(self.mesh.nnodes)
+        F = np.zeros(self.fmesh.nnodes)
         for s, sp in enumerate(self.species):
             F = F + ((sp.q * sp.w) / 4294967296.0) * self.W[s].astype(np.float64)
         return F
@@ -158,8 +188,9 @@ class Simulation:
         self.last.update(pcg_iters=it, pcg_relres=rr)
 
     def leapfrog_init(self):
+        E = self.E_pic()
         for s, sp in enumerate(self.species):
-            pt.half_kick_back(self.mesh, self.E, self.P[s], sp.k)
+            pt.half_kick_back(self.mesh, E, self.P[s], sp.k)
 
     # -- one PIC step --------------------------------------------------------------
     def _collect(self, s, keep_mask, xo, yo, zo, P):
@@ -170,7 +201,8 @@ class Simulation:
         hit = keep_mask & ~out & (Ln < 0.0)
         lost = 0
         if hit.any():
-            cells = pt.hit_cells(m, obj, xo[hit], yo[hit], zo[hit], P["x"][hit], P["y"][hit], P["z"][hit])
+            cells = pt.hit_cells(self.fmesh, obj, xo[hit], yo[hit], zo[hit], P["x"][hit], P["y"][hit],
+                                 P["z"][hit], self.r)
             acc = self.fs.cell_to_acc[cells]
             np.add.at(self.surf[:, s], acc[acc >= 0], 1)
             lost = int((acc < 0).sum())
@@ -180,11 +212,12 @@ class Simulation:
     def step(self):
         st = dict(pushed=[], absorbed=[], collected=[], injected=[], lost=[], inj_rejected=[])
         m = self.mesh
+        E = self.E_pic()
         for s, sp in enumerate(self.species):
             P = self.P[s]
             st["pushed"].append(len(P["x"]))
             xo, yo, zo = P["x"].copy(), P["y"].copy(), P["z"].copy()
-            pt.push(m, self.E, P, sp.k, self.dth)
+            pt.push(m, E, P, sp.k, self.dth)
             pt.reflect(m, P, sp.reflect)
             keep, nab, nco, lost = self._collect(s, np.ones(len(xo), dtype=bool), xo, yo, zo, P)
             P = {k: v[keep] for k, v in P.items()}
@@ -214,6 +247,10 @@ class Simulation:
                     P = {k: np.concatenate([P[k], N[k]]) for k in FIELDS}
             if sp.photo is not None:
                 I = sp.photo.emit(self.step_no)
+                if self.r > 1:   # emitted in IFE cell units: to PIC units (exact)
+                    for k in ("x", "y", "z"):
+                        I[k] = I[k] / float(self.r)
+                    I["p0"] = I["p0"] / float(self.r)
                 pt.reflect(m, I, sp.reflect)
                 inside = self.obj.L(I["x"], I["y"], I["z"]) < 0.0
                 emitted = I["ok"] & ~inside
