@@ -60,6 +60,15 @@ typedef struct {
     int nx, ny, nz;
     double h;
     double origin[3];
+    /* Hybrid grid (Sec. 2.2: PIC and IFE meshes may differ in resolution):
+     * the IFE mesh is this PIC mesh with every cell split r x r x r, r = 1
+     * (0 reads as 1), 2, 4 or 8.  Particles move, gather and are binned on the
+     * PIC mesh; they deposit on the IFE mesh (trilinear weights of the IFE
+     * cell), the field is solved there, and the PIC nodes (IFE nodes) read the
+     * node field.  Node and cell arrays of the API (potential, node field,
+     * charges, cut cells, external field) are on the IFE mesh; particle
+     * positions and the PLANE object's parameters are in PIC cell units. */
+    int ife_refine;
 } pifepic_mesh_desc;
 
 /* Time step and field-solver controls.  pcg_tol is the relative-residual

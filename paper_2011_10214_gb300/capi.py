@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESTATE", 4: "ECUDA", 5: "ETIMEO
 
 
 class MeshDesc(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("origin", C.c_double * 3)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("origin", C.c_double * 3),
+                ("ife_refine", C.c_int)]
 
 
 class SolverDesc(C.Structure):
@@ -143,11 +144,14 @@ class Simulation:
     """One IFE-PIC instance (one context) on the current CUDA device."""
 
     def __init__(self, n, h, dt, origin=(0.0, 0.0, 0.0), precision=FP64, pcg_tol=1e-6, pcg_max_iter=150,
-                 track_ids=False, stream=None):
-        md = MeshDesc(int(n[0]), int(n[1]), int(n[2]), float(h), (C.c_double * 3)(*origin))
+                 track_ids=False, stream=None, ife_refine=1):
+        """n, h: the PIC mesh; ife_refine: the IFE mesh splits each PIC cell
+        ife_refine^3 times (1, 2, 4 or 8; see pifepic_mesh_desc)."""
+        md = MeshDesc(int(n[0]), int(n[1]), int(n[2]), float(h), (C.c_double * 3)(*origin), int(ife_refine))
         sd = SolverDesc(float(dt), int(precision), float(pcg_tol), int(pcg_max_iter), int(bool(track_ids)))
         self._c = _ctx()
         self.n = tuple(int(v) for v in n)
+        self.refine = int(ife_refine)
         self.nspecies = 0
         self.track_ids = bool(track_ids)
         st = lib.pifepic_create(C.byref(md), C.byref(sd), C.c_void_p(stream or 0), C.byref(self._c))
@@ -353,7 +357,7 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
                 stream=None):
     """Build a Simulation for a workload dict of paper_2011_10214_gb300.workloads."""
     sim = Simulation(cfg["n"], cfg["h"], cfg["dt"], cfg.get("origin", (0.0, 0.0, 0.0)), precision, pcg_tol,
-                     pcg_max_iter, track_ids, stream)
+                     pcg_max_iter, track_ids, stream, cfg.get("ife_refine", 1))
     sim.set_field_bc(cfg["face_bc"])
     ob = cfg["object"]
     if ob.get("bedrock") is not None:

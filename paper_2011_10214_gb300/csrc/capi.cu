@@ -155,7 +155,10 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     *out = nullptr;
     if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->h > 0.0) || !(solver->dt > 0.0))
         return PIFEPIC_EINVAL;
-    if (mesh->nx > 2047 || mesh->ny > 2047 || mesh->nz > 1023) return PIFEPIC_EINVAL;
+    const int rf = mesh->ife_refine > 1 ? mesh->ife_refine : 1;
+    if (rf != 1 && rf != 2 && rf != 4 && rf != 8) return PIFEPIC_EINVAL;
+    if ((long long)mesh->nx * rf > 2047 || (long long)mesh->ny * rf > 2047 || (long long)mesh->nz * rf > 1023)
+        return PIFEPIC_EINVAL;
     if (solver->precision != PIFEPIC_FP64 && solver->precision != PIFEPIC_MIXED) return PIFEPIC_EINVAL;
     pifepic_ctx* ctx = new (std::nothrow) pifepic_ctx();
     if (!ctx) return PIFEPIC_ENOMEM;
@@ -163,12 +166,20 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     Ctx& c = ctx->c;
     c.stream = (cudaStream_t)stream;
     CUDA_OK(cudaGetDevice(&c.device));
+    // the PIC mesh, and the IFE mesh: the PIC mesh with each cell split rf^3 times
+    auto make_mesh = [](int nx, int ny, int nz, double h) {
+        Mesh q{};
+        q.nx = nx; q.ny = ny; q.nz = nz;
+        q.NX = nx + 1; q.NY = ny + 1; q.NZ = nz + 1;
+        q.nnodes = (long long)q.NX * q.NY * q.NZ;
+        q.ncells = (long long)nx * ny * nz;
+        q.h = h;
+        return q;
+    };
+    c.refine = rf;
+    c.pmesh = make_mesh(mesh->nx, mesh->ny, mesh->nz, mesh->h);
+    c.mesh = make_mesh(mesh->nx * rf, mesh->ny * rf, mesh->nz * rf, mesh->h / rf);
     Mesh& m = c.mesh;
-    m.nx = mesh->nx; m.ny = mesh->ny; m.nz = mesh->nz;
-    m.NX = m.nx + 1; m.NY = m.ny + 1; m.NZ = m.nz + 1;
-    m.nnodes = (long long)m.NX * m.NY * m.NZ;
-    m.ncells = (long long)m.nx * m.ny * m.nz;
-    m.h = mesh->h;
     for (int d = 0; d < 3; ++d) c.origin[d] = mesh->origin[d];
     c.dt = solver->dt;
     c.dth = solver->dt / mesh->h;
@@ -176,7 +187,8 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     c.tol = solver->pcg_tol > 0 ? solver->pcg_tol : 1e-6;
     c.maxit = solver->pcg_max_iter > 0 ? solver->pcg_max_iter : 150;
     c.track = solver->track_ids ? 1 : 0;
-    c.nbx = (m.nx + BLK - 1) / BLK; c.nby = (m.ny + BLK - 1) / BLK; c.nbz = (m.nz + BLK - 1) / BLK;
+    const Mesh& pm = c.pmesh;
+    c.nbx = (pm.nx + BLK - 1) / BLK; c.nby = (pm.ny + BLK - 1) / BLK; c.nbz = (pm.nz + BLK - 1) / BLK;
     c.nblocks = c.nbx * c.nby * c.nbz;
     for (int f = 0; f < 6; ++f) { c.bc[f].kind = PIFEPIC_BC_DIRICHLET; c.bc[f].value = 0.0; }
     long long N = m.nnodes, C = m.ncells;
@@ -218,6 +230,15 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.uf, sizeof(float) * N);
     ALLOC(c.E, sizeof(double4) * N);
     ALLOC(c.Ef, sizeof(float4) * N);
+    if (rf > 1) {
+        ALLOC(c.Ep, sizeof(double4) * c.pmesh.nnodes);
+        ALLOC(c.Efp, sizeof(float4) * c.pmesh.nnodes);
+        CUDA_OK(szero(c.stream, c.Ep, sizeof(double4) * c.pmesh.nnodes));
+        CUDA_OK(szero(c.stream, c.Efp, sizeof(float4) * c.pmesh.nnodes));
+    } else {
+        c.Ep = c.E;
+        c.Efp = c.Ef;
+    }
     ALLOC(c.Wall, sizeof(unsigned long long) * MAX_SPECIES * N);
     ALLOC(c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR);
     ALLOC(c.imask, C);
@@ -265,6 +286,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
+    if (c.refine > 1) { cudaFree(c.Ep); cudaFree(c.Efp); }
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
         cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.mov_n);
@@ -293,17 +315,17 @@ static pifepic_status encode_tmaps(pifepic_ctx* ctx) {
     CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
     if (!fn || q != cudaDriverEntryPointSuccess) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled not available");
     EncodeFn enc = (EncodeFn)fn;
-    const Mesh& m = c.mesh;
+    const Mesh& m = c.pmesh;   // the push reads the node field at the PIC nodes
     cuuint64_t dims[4] = {4, (cuuint64_t)m.NX, (cuuint64_t)m.NY, (cuuint64_t)m.NZ};
     cuuint32_t box[4] = {4, TILE, TILE, TILE};
     cuuint32_t es[4] = {1, 1, 1, 1};
     cuuint64_t sd[3] = {32, (cuuint64_t)m.NX * 32, (cuuint64_t)m.NX * m.NY * 32};
-    CUresult r = enc(&c.tmapE, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c.E, dims, sd, box, es,
+    CUresult r = enc(&c.tmapE, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c.Ep, dims, sd, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled(E) failed: %d", (int)r);
     cuuint64_t sf[3] = {16, (cuuint64_t)m.NX * 16, (cuuint64_t)m.NX * m.NY * 16};
-    r = enc(&c.tmapEf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c.Ef, dims, sf, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    r = enc(&c.tmapEf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c.Efp, dims, sf, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) FAIL(PIFEPIC_ECUDA, "cuTensorMapEncodeTiled(Ef) failed: %d", (int)r);
     c.tmap_ok = true;
@@ -344,7 +366,7 @@ pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* o
     Object ob{};
     ob.eps_minus = o->eps_in;
     ob.eps_plus = o->eps_out;
-    double h = c.mesh.h;
+    double h = c.pmesh.h;   // the object lives in PIC cell units (the set-up scales IFE nodes by 1/refine)
     const double* q = o->params;
     switch (o->kind) {
     case PIFEPIC_OBJ_NONE: ob.kind = 0; ob.eps_minus = ob.eps_plus = o->eps_out; break;
@@ -382,7 +404,7 @@ pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* o
     }
     if (c.bed_on && ob.kind != 0) {
         ob.bed = 1;
-        ob.zb = (c.bed_z - c.origin[2]) / h;
+        ob.zb = (c.bed_z - c.origin[2]) / c.mesh.h;   // the set-up's IFE cell units
         ob.eps_bed = c.bed_eps;
     }
     c.obj = ob;
@@ -571,7 +593,7 @@ pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double 
     if (s < 0 || s >= (int)c.sp.size()) FAIL(PIFEPIC_EINVAL, "bad species %d", s);
     if (ppc < 0 || !(vth >= 0)) FAIL(PIFEPIC_EINVAL, "ppc and vth must be non-negative");
     PArr flat; unsigned long long* nflat = nullptr; long long n0 = 0;
-    long long add = c.mesh.ncells * (long long)ppc;
+    long long add = c.pmesh.ncells * (long long)ppc;
     pifepic_status st = flatten(ctx, s, add, &flat, &nflat, &n0);
     if (st) return st;
     CUDA_OK(launch_load_maxwellian(c, s, ppc, vth, drift, seed, flat, nflat, n0 + add));
@@ -581,7 +603,7 @@ pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double 
     free_parr(flat); cudaFree(nflat);
     if (st) return st;
     Species& q = c.sp[s];
-    q.next_id = std::max<long long>(q.next_id, c.mesh.ncells * (long long)ppc);
+    q.next_id = std::max<long long>(q.next_id, c.pmesh.ncells * (long long)ppc);
     CUDA_OK(scopy(c.stream, c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
     return PIFEPIC_OK;
 }
@@ -662,7 +684,7 @@ pifepic_status pifepic_set_injection(pifepic_ctx* ctx, int s, int face_mask, dou
     q.face_mask = face_mask; q.density = density; q.vth = vth;
     for (int d = 0; d < 3; ++d) q.drift[d] = drift[d];
     q.seed = seed;
-    const Mesh& m = c.mesh;
+    const Mesh& m = c.pmesh;
     double nax[3] = {(double)m.nx, (double)m.ny, (double)m.nz};
     for (int f = 0; f < 6; ++f) {
         int ax = f >> 1;
@@ -756,6 +778,7 @@ pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem
                        mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     k_pack_E<<<nb256(N), 256, 0, c.stream>>>(N, tmp, c.E, c.Ef);
     CUDA_OK(cudaGetLastError());
+    CUDA_OK(launch_E_to_pic(c, c.stream, true));
     CUDA_OK(cudaStreamSynchronize(c.stream));
     cudaFree(tmp);
     c.external_E = true;

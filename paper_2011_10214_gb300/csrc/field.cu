@@ -378,6 +378,24 @@ cudaError_t launch_field_lift(Ctx& c) {
 cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st);   // pcg_coop.cu
 
 // q_T, RHS, warm start, then the persistent PCG and the node field
+// hybrid grid: the PIC nodes are the IFE nodes (r i, r j, r k); the push reads
+// the node field there
+__global__ void k_E_to_pic(Mesh pm, Mesh fm, int r, const double4* E, const float4* Ef, double4* Ep, float4* Efp,
+                           int both) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= pm.nnodes) return;
+    int i = (int)(n % pm.NX), j = (int)((n / pm.NX) % pm.NY), k = (int)(n / ((long long)pm.NX * pm.NY));
+    long long f = node_id(fm, r * i, r * j, r * k);
+    Efp[n] = Ef[f];
+    if (both) Ep[n] = E[f];
+}
+
+cudaError_t launch_E_to_pic(const Ctx& c, cudaStream_t st, bool both) {
+    if (c.refine == 1) return cudaSuccess;
+    k_E_to_pic<<<nb(c.pmesh.nnodes), 256, 0, st>>>(c.pmesh, c.mesh, c.refine, c.E, c.Ef, c.Ep, c.Efp, both ? 1 : 0);
+    return cudaGetLastError();
+}
+
 static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
     FieldArgs f = fargs(c);
     RhsArgs a = rargs(c);
@@ -394,7 +412,9 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
     if (e != cudaSuccess) return e;
     if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
     else k_node_E<<<nb(N), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_E_to_pic(c, st, c.precision != PIFEPIC_MIXED);
 }
 
 // the solve's pieces around the PCG, for the batched step (batch.cu)
@@ -412,11 +432,13 @@ cudaError_t launch_solve_suffix(Ctx& c, cudaStream_t st) {
     FieldArgs f = fargs(c);
     if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
     else k_node_E<<<nb(c.mesh.nnodes), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_E_to_pic(c, st, c.precision != PIFEPIC_MIXED);
 }
 
 // kernels launched per solve
-int solve_graph_fixed_kernels(const Ctx& c) { return (c.ncut > 0) + (c.nit > 0) + 4; }
+int solve_graph_fixed_kernels(const Ctx& c) { return (c.ncut > 0) + (c.nit > 0) + 4 + (c.refine > 1); }
 
 // The solve as one CUDA graph (both precisions): q_T -> RHS -> warm start ->
 // persistent PCG -> node field

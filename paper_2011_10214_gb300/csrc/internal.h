@@ -72,6 +72,9 @@ struct Launch {                     // what every particle kernel needs
     const double4* E;               // node field
     const float4* Ef;               // node field, FP32 copy
     int* err;                       // device error word
+    Mesh fmesh;                     // field (IFE) mesh: mesh refined refine times
+    int refine;                     // 1: the meshes coincide
+    double rf;                      // refine as a double (a power of two: exact scaling)
     SpeciesDev sp[MAX_SPECIES];
 };
 
@@ -103,7 +106,9 @@ struct Ctx {
     std::string err;
     cudaStream_t stream = nullptr;
     int device = 0;
-    Mesh mesh{};
+    Mesh mesh{};                    // the field (IFE) mesh
+    Mesh pmesh{};                   // the particle (PIC) mesh; mesh is it refined refine times
+    int refine = 1;
     double origin[3] = {0, 0, 0};
     double dt = 0, dth = 0;
     int precision = PIFEPIC_FP64;
@@ -133,6 +138,8 @@ struct Ctx {
     float *rf = nullptr, *pf = nullptr, *qf = nullptr, *uf = nullptr, *invdiagf = nullptr;
     double4* E = nullptr;          // node field (x, y, z, 0)
     float4* Ef = nullptr;          // FP32 copy for the MIXED push
+    double4* Ep = nullptr;         // node field at the PIC nodes (E itself when refine == 1)
+    float4* Efp = nullptr;         // its FP32 copy (Ef itself when refine == 1)
     unsigned long long* Wall = nullptr;     // [MAX_SPECIES][nnodes] fixed-point charge
     unsigned long long* surfall = nullptr;  // [MAX_SPECIES][ncut] collected particles
     unsigned long long* ctrall = nullptr;   // [MAX_SPECIES][NCTR]
@@ -260,6 +267,9 @@ cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double
 cudaError_t launch_photo(Ctx& c);                      // particles.cu: one step of emission (FP64)
 cudaError_t launch_photo_mixed(Ctx& c);                // particles_mixed.cu
 cudaError_t launch_node_E64(Ctx& c);                   // field.cu: FP64 E from phi (E only)
+// field.cu: the node field at the PIC nodes from the IFE nodes (refine > 1;
+// both: the FP64 field too, else the FP32 copy only)
+cudaError_t launch_E_to_pic(const Ctx& c, cudaStream_t st, bool both);
 cudaError_t launch_field_lift(Ctx& c);
 cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
 void plan_pcg(Ctx& c);                                 // pcg_coop.cu

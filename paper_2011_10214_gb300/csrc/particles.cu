@@ -93,11 +93,13 @@ PF_D int hit_target(const Launch& L, double xo, double yo, double zo, double xn,
     double Ln = level_set(L.obj, xn, yn, zn);
     double t = Lo / (Lo - Ln);
     double xc = xo + t * (xn - xo), yc = yo + t * (yn - yo), zc = zo + t * (zn - zo);
-    double fi = floor(xc), fj = floor(yc), fk = floor(zc);
-    fi = fi < 0.0 ? 0.0 : (fi > (double)(L.mesh.nx - 1) ? (double)(L.mesh.nx - 1) : fi);
-    fj = fj < 0.0 ? 0.0 : (fj > (double)(L.mesh.ny - 1) ? (double)(L.mesh.ny - 1) : fj);
-    fk = fk < 0.0 ? 0.0 : (fk > (double)(L.mesh.nz - 1) ? (double)(L.mesh.nz - 1) : fk);
-    return L.cell_acc[cell_id(L.mesh, (int)fi, (int)fj, (int)fk)];
+    // the crossing point's cell on the IFE mesh (refine times finer; exact scaling)
+    const Mesh& f = L.fmesh;
+    double fi = floor(L.rf * xc), fj = floor(L.rf * yc), fk = floor(L.rf * zc);
+    fi = fi < 0.0 ? 0.0 : (fi > (double)(f.nx - 1) ? (double)(f.nx - 1) : fi);
+    fj = fj < 0.0 ? 0.0 : (fj > (double)(f.ny - 1) ? (double)(f.ny - 1) : fj);
+    fk = fk < 0.0 ? 0.0 : (fk > (double)(f.nz - 1) ? (double)(f.nz - 1) : fk);
+    return L.cell_acc[cell_id(f, (int)fi, (int)fj, (int)fk)];
 }
 
 enum { ALIVE = 0, ABSORBED = 1, COLLECTED = 2, NONE = 3 };
@@ -123,13 +125,19 @@ PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
     return (ci / BLK) + L.nbx * ((cj / BLK) + L.nby * (ck / BLK));
 }
 
+// deposit with weights w of a cell of the IFE mesh (the PIC mesh when refine == 1)
 PF_D void global_deposit(const Launch& L, unsigned long long* W, const Wts& w) {
     long long Wf[8];
     fixed_weights(w, Wf);
 #pragma unroll
     for (int l = 0; l < 8; ++l)
-        atomicAdd(&W[node_id(L.mesh, w.ci + (l & 1), w.cj + ((l >> 1) & 1), w.ck + ((l >> 2) & 1))],
+        atomicAdd(&W[node_id(L.fmesh, w.ci + (l & 1), w.cj + ((l >> 1) & 1), w.ck + ((l >> 2) & 1))],
                   (unsigned long long)Wf[l]);
+}
+// deposit of a particle at (x, y, z) (PIC cell units) on the IFE mesh
+PF_D void deposit_at(const Launch& L, unsigned long long* W, double x, double y, double z) {
+    if (L.refine == 1) global_deposit(L, W, weights(x, y, z));
+    else global_deposit(L, W, weights(L.rf * x, L.rf * y, L.rf * z));
 }
 
 PF_D void put(const PArr& a, long long i, double x, double y, double z, double vx, double vy, double vz,
@@ -211,7 +219,9 @@ __global__ void __launch_bounds__(256) k_push_bins(Launch L, const __grid_consta
             stay = (w.ci >= x0) & (w.ci < x0 + BLK) & (w.cj >= y0) & (w.cj < y0 + BLK) & (w.ck >= z0) &
                    (w.ck < z0 + BLK);
             mover = !stay;
-            if (stay) {
+            if (L.refine != 1) {
+                deposit_at(L, S.W, x, y, z);      // hybrid grid: straight onto the IFE nodes
+            } else if (stay) {
                 long long Wf[8];
                 fixed_weights(w, Wf);
                 const long long W7[7] = {Wf[0], Wf[1], Wf[2], Wf[3], Wf[4], Wf[5], Wf[6]};
@@ -288,7 +298,7 @@ __global__ void k_push_movers(Launch L) {
             x = x + vx * L.dth; y = y + vy * L.dth; z = z + vz * L.dth;
             if (S.reflect) reflect_d(L.mesh, S.reflect, x, y, z, vx, vy, vz);
             code = classify(L, xo, yo, zo, x, y, z, acc);
-            if (code == ALIVE) global_deposit(L, S.W, weights(x, y, z));
+            if (code == ALIVE) deposit_at(L, S.W, x, y, z);
             else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
         }
         count_event(&sctr[C_PUSHED], code != NONE);
@@ -351,7 +361,7 @@ __global__ void k_inject(Launch L, InjArgs a) {
                 rejected = true;
             } else {
                 code = classify(L, p0[0], p0[1], p0[2], p[0], p[1], p[2], acc);
-                if (code == ALIVE) global_deposit(L, S.W, weights(p[0], p[1], p[2]));
+                if (code == ALIVE) deposit_at(L, S.W, p[0], p[1], p[2]);
                 else if (code == COLLECTED && acc >= 0) atomicAdd(&S.surf[acc], 1ull);
             }
         }
@@ -520,7 +530,7 @@ __global__ void k_deposit_bins(Launch L) {
     long long st = S.bstart[b];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         long long g = st + i;
-        global_deposit(L, S.W, weights(S.bins.x[g], S.bins.y[g], S.bins.z[g]));
+        deposit_at(L, S.W, S.bins.x[g], S.bins.y[g], S.bins.z[g]);
     }
 }
 __global__ void k_deposit_list(Launch L) {
@@ -528,7 +538,7 @@ __global__ void k_deposit_list(Launch L) {
     const SpeciesDev& S = L.sp[s];
     long long n = list_len(S.mov_in_n, S.mcap);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        global_deposit(L, S.W, weights(S.mov_in.x[i], S.mov_in.y[i], S.mov_in.z[i]));
+        deposit_at(L, S.W, S.mov_in.x[i], S.mov_in.y[i], S.mov_in.z[i]);
 }
 
 // v <- v - (k/2) E(x)
@@ -570,12 +580,13 @@ static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
 Launch make_launch(Ctx& c) {
     Launch L;
     memset(&L, 0, sizeof(L));
-    L.mesh = c.mesh; L.obj = c.obj; L.dth = c.dth;
+    L.mesh = c.pmesh; L.obj = c.obj; L.dth = c.dth;
+    L.fmesh = c.mesh; L.refine = c.refine; L.rf = (double)c.refine;
     L.nbx = c.nbx; L.nby = c.nby; L.nbz = c.nbz; L.nblocks = c.nblocks;
     L.nspecies = (int)c.sp.size();
     L.track = c.track;
     L.cell_acc = c.cell_acc;
-    L.E = c.E; L.Ef = c.Ef;
+    L.E = c.Ep; L.Ef = c.Efp;   // the node field at the PIC nodes
     L.err = c.err_word;
     for (int s = 0; s < L.nspecies; ++s) {
         Species& q = c.sp[s];
@@ -604,7 +615,7 @@ static InjArgs inj_args(Ctx& c) {
 cudaError_t launch_load_maxwellian(Ctx& c, int s, int ppc, double vth, const double drift[3],
                                    unsigned long long seed, PArr flat, unsigned long long* nflat, long long cap) {
     Launch L = make_launch(c);
-    long long n = c.mesh.ncells * (long long)ppc;
+    long long n = c.pmesh.ncells * (long long)ppc;
     k_load<<<nb(n), 256, 0, c.stream>>>(L, s, ppc, vth, drift[0], drift[1], drift[2], seed, flat, nflat, cap);
     return cudaGetLastError();
 }
@@ -737,15 +748,15 @@ __global__ void k_photo(Launch L, PhotoArgs a) {
         double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
         if (m < total) {
             const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
-            const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
-            for (int c = 0; c < 3; ++c) { p[c] = sm.p[c]; v[c] = sm.v[c]; }
+            const PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, a.dth);
+            for (int c = 0; c < 3; ++c) { p[c] = sm.p[c] * a.inv_r; v[c] = sm.v[c]; }   // to PIC units
             if (S.reflect) reflect_d(L.mesh, S.reflect, p[0], p[1], p[2], v[0], v[1], v[2]);
             emitted = sm.ok && !(level_set(L.obj, p[0], p[1], p[2]) < 0.0);
             if (emitted) {
                 atomicAdd(&S.surf[d.acc], (unsigned long long)-1ll);   // the electron leaves +e behind
                 out = outside(L.mesh, p[0], p[1], p[2]);
                 alive = !out;
-                if (alive) global_deposit(L, S.W, weights(p[0], p[1], p[2]));
+                if (alive) deposit_at(L, S.W, p[0], p[1], p[2]);
             }
         }
         count_event(&sctr[C_INJECTED], emitted);
@@ -768,6 +779,8 @@ PhotoArgs photo_args(Ctx& c) {
     a.tets = c.ph_tets; a.Q = c.ph_Q; a.carry = c.ph_carry; a.cnt = c.ph_cnt; a.base = c.ph_base;
     a.total = c.ph_total; a.next_id = c.next_id; a.ne = c.ph_ne; a.species = c.ph_species; a.vth = c.ph_vth;
     a.seed = c.ph_seed; a.step = (const long long*)(c.scal + 42);
+    a.dth = c.dt / c.mesh.h;
+    a.inv_r = 1.0 / (double)c.refine;
     return a;
 }
 

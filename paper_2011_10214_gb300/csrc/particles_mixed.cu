@@ -177,10 +177,12 @@ PF_D int hit_cell_f(const Launch& L, const ObjF& of, float xo, float yo, float z
     float Lo = level_set_f(of, xo, yo, zo), Ln = level_set_f(of, xn, yn, zn);
     float t = Lo / (Lo - Ln);
     float xc = xo + t * (xn - xo), yc = yo + t * (yn - yo), zc = zo + t * (zn - zo);
-    int ci = min(max((int)floorf(xc), 0), L.mesh.nx - 1);
-    int cj = min(max((int)floorf(yc), 0), L.mesh.ny - 1);
-    int ck = min(max((int)floorf(zc), 0), L.mesh.nz - 1);
-    return L.cell_acc[cell_id(L.mesh, ci, cj, ck)];
+    // the crossing point's cell on the IFE mesh (refine times finer; exact scaling)
+    const float r = (float)L.refine;
+    int ci = min(max((int)floorf(r * xc), 0), L.fmesh.nx - 1);
+    int cj = min(max((int)floorf(r * yc), 0), L.fmesh.ny - 1);
+    int ck = min(max((int)floorf(r * zc), 0), L.fmesh.nz - 1);
+    return L.cell_acc[cell_id(L.fmesh, ci, cj, ck)];
 }
 
 template <class EA>
@@ -202,12 +204,22 @@ PF_D int push_one(const Launch& L, const ObjF& of, float kf, float dthf, int ref
     return ALIVE;
 }
 
+// deposit on the IFE mesh: with refine r the IFE cell of (i + f) is r i +
+// floor(r f) and its offset frac(r f) (exact in FP32: r is a power of two)
 PF_D void global_deposit_f(const Launch& L, unsigned long long* W, const PF32& p) {
     long long Wf[8];
-    fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+    int i = p.i, j = p.j, k = p.k;
+    float fx = p.fx, fy = p.fy, fz = p.fz;
+    if (L.refine != 1) {
+        const float r = (float)L.refine;
+        const float sx = floorf(r * fx), sy = floorf(r * fy), sz = floorf(r * fz);
+        i = L.refine * i + (int)sx; j = L.refine * j + (int)sy; k = L.refine * k + (int)sz;
+        fx = r * fx - sx; fy = r * fy - sy; fz = r * fz - sz;
+    }
+    fixed_weights_f(weights_f(fx, fy, fz), Wf);
 #pragma unroll
     for (int l = 0; l < 8; ++l)
-        atomicAdd(&W[node_id(L.mesh, p.i + (l & 1), p.j + ((l >> 1) & 1), p.k + ((l >> 2) & 1))],
+        atomicAdd(&W[node_id(L.fmesh, i + (l & 1), j + ((l >> 1) & 1), k + ((l >> 2) & 1))],
                   (unsigned long long)Wf[l]);
 }
 
@@ -354,7 +366,9 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
             mover = !stay;
-            if (stay) {   // (movers deposit in the rebin, with every mover of the step)
+            if (stay && L.refine != 1) {
+                global_deposit_f(L, S.W, p);   // hybrid grid: straight onto the IFE nodes
+            } else if (stay) {   // (movers deposit in the rebin, with every mover of the step)
                 const WF w = weights_f(p.fx, p.fy, p.fz);
                 const int t0 = 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy;
                 unsigned rest = 1u << 19;
@@ -756,7 +770,8 @@ __global__ void k_photo_m(Launch L, PhotoArgs a) {
         PF32 p;
         if (m < total) {
             const PhotoDev& d = a.tets[photo_tet_of(a.base, a.ne, m)];
-            PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, L.dth);
+            PhotoSample sm = photo_sample(d, (unsigned long long)m, a.seed, key1, a.vth, a.dth);
+            for (int c = 0; c < 3; ++c) sm.p[c] *= a.inv_r;   // IFE to PIC cell units (exact)
             if (S.reflect) reflect_d(L.mesh, S.reflect, sm.p[0], sm.p[1], sm.p[2], sm.v[0], sm.v[1], sm.v[2]);
             emitted = sm.ok && !(level_set(L.obj, sm.p[0], sm.p[1], sm.p[2]) < 0.0);
             if (emitted) {

@@ -89,6 +89,8 @@ struct PhotoArgs {
     double vth;
     unsigned long long seed;
     const long long* step;
+    double dth;                // dt / h of the IFE mesh: emission works in IFE cell units
+    double inv_r;              // 1 / refine (a power of two): IFE to PIC cell units, exact
 };
 
 struct PhotoSample {

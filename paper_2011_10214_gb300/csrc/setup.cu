@@ -27,11 +27,13 @@ static __device__ __forceinline__ void loff(int l, int& a, int& b, int& c) {
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_levelset(Mesh m, Object o, double* L) {
+// node level set on the IFE mesh; the object lives in PIC cell units, so node
+// (i, j, k) sits at (i, j, k) / refine (inv_r = 1 / refine, a power of two: exact)
+__global__ void k_levelset(Mesh m, Object o, double inv_r, double* L) {
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= m.nnodes) return;
     int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
-    L[n] = level_set(o, (double)i, (double)j, (double)k);
+    L[n] = level_set(o, (double)i * inv_r, (double)j * inv_r, (double)k * inv_r);
 }
 
 // interface tets: cut by the object's surface (also when the bedrock plane
@@ -487,7 +489,7 @@ static __device__ double photo_tri_area(const double (&P)[3][3]) {
     return 0.5 * sqrt((c0 * c0 + c1 * c1) + c2 * c2);
 }
 
-__global__ void k_photo_setup(Mesh m, Object obj, long long nit, const int* it_cell, const int* it_t,
+__global__ void k_photo_setup(Mesh m, Object obj, double inv_r, long long nit, const int* it_cell, const int* it_t,
                               const double* Lnode, const int* it_acc, double sx, double sy, double sz, double J,
                               double h2, double dt, double w, PhotoDev* rec, long long* Qall) {
     const long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -556,7 +558,7 @@ __global__ void k_photo_setup(Mesh m, Object obj, long long nit, const int* it_c
         const double tt = PHOTO_RAY_STEP * (double)k;
         const double qx = cen[0] + tt * sx, qy = cen[1] + tt * sy, qz = cen[2] + tt * sz;
         if (qx < 0.0 || qx > (double)m.nx || qy < 0.0 || qy > (double)m.ny || qz < 0.0 || qz > (double)m.nz) break;
-        if (level_set(obj, qx, qy, qz) < 0.0) return;
+        if (level_set(obj, qx * inv_r, qy * inv_r, qz * inv_r) < 0.0) return;   // the object in PIC units
     }
     const double R = J * S * (A * h2) * dt / w;
     const long long Q = (long long)rint(R * (double)(1ll << PHOTO_RATE_BITS));
@@ -623,7 +625,7 @@ cudaError_t launch_setup(Ctx& c) {
 
     c.bed_outside = false;
     CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    k_levelset<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode);
+    k_levelset<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, 1.0 / (double)c.refine, c.Lnode);
     k_classify<<<nb(m.ncells), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, cnt, bad);
     CK(cudaGetLastError());
     {
@@ -713,7 +715,8 @@ cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double
     CK(cudaMemsetAsync(Qall, 0, sizeof(long long) * n1, c.stream));
     CK(cudaMemsetAsync(rec, 0, sizeof(PhotoDev) * n1, c.stream));
     if (nit > 0) {
-        k_photo_setup<<<nb(nit), 256, 0, c.stream>>>(c.mesh, c.obj, nit, c.it_cell, c.it_t, c.Lnode, c.it_acc, s0, s1,
+        k_photo_setup<<<nb(nit), 256, 0, c.stream>>>(c.mesh, c.obj, 1.0 / (double)c.refine, nit, c.it_cell, c.it_t,
+                                                     c.Lnode, c.it_acc, s0, s1,
                                                      s2, J, c.mesh.h * c.mesh.h, c.dt, w, rec, Qall);
         k_photo_flag<<<nb(nit), 256, 0, c.stream>>>(nit, Qall, flag);
         CK(cudaGetLastError());

@@ -24,6 +24,11 @@ CASES = {
     "lunar": dict(n=(30, 16, 16), h=1.0,
                   obj=("rim_crater", 7.37, 15.0, 0.0, 4.1, 7.9, 11.6, 2.6, 2.2, 4.0, 1.0),
                   bed=(2.45, 10.0), bc=[("N",)] * 5 + [("D", 0.0)]),
+    # hybrid grids: the IFE mesh twice (four times) as fine as the PIC mesh
+    "sphere_h2": dict(n=(12, 10, 9), h=0.5, obj=("sphere", (2.71, 2.43, 2.12), 1.13, 6.0, 1.0),
+                      bc=[("D", 0.0), ("D", 0.25), ("N",), ("D", -0.1), ("N",), ("N",)], refine=2),
+    "crater_h4": dict(n=(8, 8, 6), h=1.0, obj=("cap_crater", 3.3, 4.0, 4.0, 3.0, 1.5, 4.0, 1.0),
+                      bed=(1.3, 10.0), bc=[("N",)] * 5 + [("D", 0.0)], refine=4),
     # the same with a floor below the top of the bedrock's cells: tets cut twice
     "lunar_deep": dict(n=(30, 16, 16), h=1.0,
                        obj=("rim_crater", 7.37, 15.0, 0.0, 4.1, 7.9, 11.6, 2.6, 4.6, 4.0, 1.0),
@@ -61,14 +66,15 @@ def gpu_object(sim, o, bed=None):
         sim.set_object(capi.OBJ_PLANE, list(o[1]) + [o[2]], o[3], o[4])
 
 
-def make_pair(case, dt=0.05, tol=1e-12, maxit=2000, track=True, precision=0):
+def make_pair(case, dt=0.05, tol=1e-12, maxit=2000, track=True, precision=0, refine=None):
     from paper_2011_10214_gb300 import capi
     c = CASES[case]
+    r = c.get("refine", 1) if refine is None else refine
     m = Mesh(*c["n"], c["h"])
     obj = oracle_object(m, c["obj"], c.get("bed"))
-    orc = OracleSim(m, obj, c["bc"], dt, tol=tol, maxit=maxit)
+    orc = OracleSim(m, obj, c["bc"], dt, tol=tol, maxit=maxit, refine=r)
     gpu = capi.Simulation(c["n"], c["h"], dt, precision=precision, pcg_tol=tol, pcg_max_iter=maxit,
-                          track_ids=track)
+                          track_ids=track, ife_refine=r)
     gpu.set_field_bc(c["bc"])
     gpu_object(gpu, c["obj"], c.get("bed"))
     return gpu, orc

@@ -22,7 +22,7 @@ def test_solve_field_matches_oracle(case):
     gpu, orc = make_pair(case)
     fs = orc.fs
     g = np.random.default_rng(11)
-    F = g.normal(size=orc.mesh.nnodes) * orc.mesh.h ** 3
+    F = g.normal(size=fs.mesh.nnodes) * fs.mesh.h ** 3
     q = g.normal(size=len(fs.it_cell))
     phi_o, it_o, rr_o = fs.solve(F, q, tol=1e-12, maxit=5000)
     it, rr = gpu.solve_field(F, q)

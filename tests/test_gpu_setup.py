@@ -15,7 +15,7 @@ def test_interface_tets_match_oracle(case):
     g = gpu.interface()
     # bit-exact: which tets are interface tets, in (cell, local tet) order
     assert np.array_equal(g["cell"], fs.it_cell) and np.array_equal(g["tet"], fs.it_t)
-    h = orc.mesh.h
+    h = fs.mesh.h
     V = h ** 3
     assert np.allclose(g["vol_plus"], fs.it_volp, rtol=0, atol=1e-13 * V)
     assert np.allclose(g["vol_minus"], fs.it_volm, rtol=0, atol=1e-13 * V)
