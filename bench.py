@@ -86,6 +86,7 @@ def workload(name):
             "crater160": wl.CRATER160,
             "crater80": wl.crater_config(80, 80, 40, 10.0, 15.0, 5.0, seed_offset=7),
             "oml50": wl.OML50,
+            "sphere64h2": dict(wl.SPHERE64, name="sphere64h2", ife_refine=2),
             "lunar200": wl.LUNAR200,
             "lunar100": wl.lunar_config(100, 50, 50, 4.75, 2.25, 5.25, 10.1, 15.45, 1.35, 2.0, seed_offset=9)}[name]
 
@@ -115,6 +116,10 @@ def cfg_desc(cfg, precision, extra=None):
         w = (f"sphere charging {n[0]}x{n[1]}x{n[2]} cells (h={cfg['h']}), R={ob['radius']}, "
              f"eps_in={ob['eps_in']}, {ppc} ppc/species e-+H+ (m_i/m_e={cfg['species'][1]['m']:g}), "
              f"dt={cfg['dt']}, flux injection, phi=0 faces")
+    if cfg.get("ife_refine", 1) > 1:
+        r = cfg["ife_refine"]
+        w += (f"; hybrid grid: IFE mesh {r * n[0]}x{r * n[1]}x{r * n[2]} cells (h={cfg['h'] / r}), the PIC "
+              f"mesh refined {r}x per axis")
     d = {"workload": w,
          "precision": precision, "pcg_tol": 1e-6, "pcg_max_iter": 150,
          "l2_flush": "inputs larger than L2 (particle state > 1 GB per step)"}
@@ -341,7 +346,7 @@ def oracle_rate(workload_name, sample_frac, steps):
         obj = NoObject()
     if ob.get("bedrock") is not None:
         set_bedrock(obj, m, *ob["bedrock"])
-    sim = Simulation(m, obj, cfg["face_bc"], cfg["dt"])
+    sim = Simulation(m, obj, cfg["face_bc"], cfg["dt"], refine=cfg.get("ife_refine", 1))
     nfull = 0
     for s, sp in enumerate(cfg["species"]):
         sim.add_species(sp["q"], sp["m"], wl.macro_weight(cfg, sp))
@@ -500,7 +505,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="sphere64",
                     choices=["sphere64", "sphere32", "sphere16", "crater160", "crater80", "oml50", "lunar200",
-                             "lunar100"])
+                             "lunar100", "sphere64h2"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision's measurement")
