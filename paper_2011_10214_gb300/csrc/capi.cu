@@ -174,6 +174,8 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
         q.nnodes = (long long)q.NX * q.NY * q.NZ;
         q.ncells = (long long)nx * ny * nz;
         q.h = h;
+        q.h6 = h / 6.0; q.h12 = h / 12.0;
+        q.h6f = (float)h / 6.0f; q.h12f = (float)h / 12.0f;
         return q;
     };
     c.refine = rf;

@@ -79,6 +79,10 @@ struct Mesh {
     int nx, ny, nz, NX, NY, NZ;
     long long nnodes, ncells;
     double h;
+    // the regular stencil's h/6 and h/12, once per mesh instead of once per
+    // row (the same IEEE quotients, in FP64 and from the FP32 h in FP32)
+    double h6, h12;
+    float h6f, h12f;
 };
 
 // Reflecting particle faces (the symmetry plane of Sec. 5.2.2), bit f of the

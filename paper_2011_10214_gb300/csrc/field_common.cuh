@@ -15,6 +15,12 @@ struct PcgState {
     int inner_it, outer_it, inner_max, done_in;
 };
 
+// h/6 and h/12 of the regular stencil in the working precision
+template <typename T>
+static __device__ __forceinline__ T h_over6(const Mesh& m) { return sizeof(T) == 8 ? (T)m.h6 : (T)m.h6f; }
+template <typename T>
+static __device__ __forceinline__ T h_over12(const Mesh& m) { return sizeof(T) == 8 ? (T)m.h12 : (T)m.h12f; }
+
 struct FieldArgs {
     Mesh m;
     Object o;
@@ -101,7 +107,7 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
     if (yp) ay += ld(n + sy);
     if (zm) az += ld(n - sz);
     if (zp) az += ld(n + sz);
-    T h6 = h / (T)6;
+    const T h6 = h_over6<T>(m);
     y -= h6 * ((T)(cy * cz) * ax + (T)(cx * cz) * ay + (T)(cx * cy) * az);
     if (!odd) {
         T dxy = (T)0, dxz = (T)0, dyz = (T)0;
@@ -117,7 +123,7 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
         if (yp && zm) dyz += ld(n + sy - sz);
         if (ym && zp) dyz += ld(n - sy + sz);
         if (yp && zp) dyz += ld(n + sy + sz);
-        T h12 = h / (T)12;
+        const T h12 = h_over12<T>(m);
         y -= h12 * ((T)cz * dxy + (T)cy * dxz + (T)cx * dyz);
     }
     return eps * y;
@@ -154,8 +160,8 @@ static __device__ __forceinline__ unsigned short row_kind(const FieldArgs& f, lo
 // the strides.  Same closed form as the regular branch of apply_row_ld
 // (summation order differs).
 template <typename T, typename LD>
-static __device__ __forceinline__ T regular_row_masked_ld(LD ld, int NX, int NXY, unsigned kd, T h, T eps_plus,
-                                                          T eps_minus) {
+static __device__ __forceinline__ T regular_row_masked_ld(LD ld, int NX, int NXY, unsigned kd, T h, T h6, T h12,
+                                                          T eps_plus, T eps_minus) {
     const T mxm = (kd & RK_XM) ? (T)1 : (T)0, mxp = (kd & RK_XP) ? (T)1 : (T)0;
     const T mym = (kd & RK_YM) ? (T)1 : (T)0, myp = (kd & RK_YP) ? (T)1 : (T)0;
     const T mzm = (kd & RK_ZM) ? (T)1 : (T)0, mzp = (kd & RK_ZP) ? (T)1 : (T)0;
@@ -166,7 +172,7 @@ static __device__ __forceinline__ T regular_row_masked_ld(LD ld, int NX, int NXY
     const T ay = mym * ld(-NX) + myp * ld(NX);
     const T az = mzm * ld(-NXY) + mzp * ld(NXY);
     T y = cx * cy * cz * (odd ? (T)0.5 : (T)0.75) * h * ld(0);
-    y -= (h / (T)6) * (cy * cz * ax + cx * cz * ay + cx * cy * az);
+    y -= h6 * (cy * cz * ax + cx * cz * ay + cx * cy * az);
     if (!odd) {
         const T dxy = (mxm * mym) * ld(-1 - NX) + (mxp * mym) * ld(1 - NX) + (mxm * myp) * ld(-1 + NX) +
                       (mxp * myp) * ld(1 + NX);
@@ -174,16 +180,16 @@ static __device__ __forceinline__ T regular_row_masked_ld(LD ld, int NX, int NXY
                       (mxp * mzp) * ld(1 + NXY);
         const T dyz = (mym * mzm) * ld(-NX - NXY) + (myp * mzm) * ld(NX - NXY) + (mym * mzp) * ld(-NX + NXY) +
                       (myp * mzp) * ld(NX + NXY);
-        y -= (h / (T)12) * (cz * dxy + cy * dxz + cx * dyz);
+        y -= h12 * (cz * dxy + cy * dxz + cx * dyz);
     }
     return eps * y;
 }
 
 // the same row over a window in shared memory; wc points at the node's entry
 template <typename T>
-static __device__ __forceinline__ T regular_row_masked(const T* wc, int NX, int NXY, unsigned kd, T h, T eps_plus,
-                                                       T eps_minus) {
-    return regular_row_masked_ld<T>([&](int o) { return wc[o]; }, NX, NXY, kd, h, eps_plus, eps_minus);
+static __device__ __forceinline__ T regular_row_masked(const T* wc, int NX, int NXY, unsigned kd, T h, T h6, T h12,
+                                                       T eps_plus, T eps_minus) {
+    return regular_row_masked_ld<T>([&](int o) { return wc[o]; }, NX, NXY, kd, h, h6, h12, eps_plus, eps_minus);
 }
 
 // The 19 coefficients of row n of the same operator, in the slot order of
@@ -214,13 +220,13 @@ static __device__ __forceinline__ void row_coeffs(const FieldArgs& f, long long 
     const T h = (T)m.h;
     const int cx = (int)xm + (int)xp, cy = (int)ym + (int)yp, cz = (int)zm + (int)zp;
     c[0] = eps * ((T)(cx * cy * cz) * (odd ? (T)0.5 : (T)0.75) * h);
-    const T a6 = eps * (h / (T)6);
+    const T a6 = eps * h_over6<T>(m);
     const T ax = -a6 * (T)(cy * cz), ay = -a6 * (T)(cx * cz), az = -a6 * (T)(cx * cy);
     const T axis[6] = {ax, ax, ay, ay, az, az};
 #pragma unroll
     for (int q = 1; q < 7; ++q) c[q] = has[q] ? axis[q - 1] : (T)0;
     if (odd) return;
-    const T a12 = eps * (h / (T)12);
+    const T a12 = eps * h_over12<T>(m);
     const T dxy = -a12 * (T)cz, dxz = -a12 * (T)cy, dyz = -a12 * (T)cx;
 #pragma unroll
     for (int q = 7; q < 19; ++q) c[q] = has[q] ? (q < 11 ? dxy : q < 15 ? dxz : dyz) : (T)0;

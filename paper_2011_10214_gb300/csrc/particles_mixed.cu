@@ -275,6 +275,9 @@ PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
 // warp of chunk c-1 has published it.  Writes then land only on slots of
 // chunks <= c, all of which were read before their counts were published, so
 // no unread particle is overwritten.
+// HYBRID: the IFE mesh is finer than the PIC mesh, stayers deposit straight
+// onto its nodes (a separate instantiation keeps the common path's registers)
+template <bool HYBRID>
 __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
     __shared__ alignas(128) float4 Et[TILE_N];
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
             mover = !stay;
-            if (stay && L.refine != 1) {
+            if (HYBRID && stay) {
                 global_deposit_f(L, S.W, p);   // hybrid grid: straight onto the IFE nodes
             } else if (stay) {   // (movers deposit in the rebin, with every mover of the step)
                 const WF w = weights_f(p.fx, p.fy, p.fz);
@@ -717,7 +720,10 @@ cudaError_t launch_push_mixed(Ctx& c) {
     int ns = (int)c.sp.size();
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
-    k_push_bins_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
+    if (c.refine == 1)
+        k_push_bins_m<false><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
+    else
+        k_push_bins_m<true><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
     c.launches += 1;
     return cudaGetLastError();
 }

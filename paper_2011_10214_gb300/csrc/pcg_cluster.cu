@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
                 T az;
                 if (kd & RK_DIRICHLET) az = (T)0;
                 else if (kd & RK_GENERAL) az = row(li, ldw, coef);
-                else az = regular_row_masked<T>(wc, NXw, NXYw, kd, hT, epsP, epsM);
+                else az = regular_row_masked<T>(wc, NXw, NXYw, kd, hT, h_over6<T>(m), h_over12<T>(m), epsP, epsM);
                 const T zl = wc[0];
                 T pl, ql;
                 if (first) {

@@ -528,7 +528,8 @@ static __device__ __forceinline__ T glob_row(const GlobArgs& a, const T* x, long
         node_ijk(a.f.m, n, i, j, k);
         return apply_row<T, true>(a.f, n, i, j, k, x, coef);
     }
-    return regular_row_masked_ld<T>([&](int o) { return __ldcg(x + n + o); }, NX, NXY, kd, h, ep, em);
+    return regular_row_masked_ld<T>([&](int o) { return __ldcg(x + n + o); }, NX, NXY, kd, h, h_over6<T>(a.f.m),
+                                    h_over12<T>(a.f.m), ep, em);
 }
 
 template <bool MIXED>
