@@ -306,6 +306,7 @@ def run_gpu(args):
         "roofline": roof, "roofline_other": roof_other, "clocks": ck, "e2e": e2e,
         "gpu_launches": int(st["kernel_launches"]),
         "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
+        "pcg_refinements_per_step": st["pcg_outer_total"] / args.steps,
         "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st["phase_ms"]) if v},
         "compare": alt,
     }

@@ -145,6 +145,9 @@ typedef struct {
     double phase_ms[8];                        /* GPU time per phase, this call:
                                                   push, movers, inject, rebin,
                                                   rhs, pcg, node_E, other        */
+    int64_t pcg_outer_total;                   /* MIXED refinement steps in this
+                                                  call (FP64 residuals - 1 per
+                                                  solve)                         */
 } pifepic_stats;
 
 typedef struct pifepic_ctx pifepic_ctx;
@@ -173,6 +176,17 @@ pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* o
  * z_bed is outside it.  Call before pifepic_set_object.  Errors: EINVAL
  * (eps_bed <= 0, z_bed not finite), ESTATE (after set_object). */
 pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_bed);
+
+/* MIXED-mode refinement controls (FP64 iterative refinement around FP32
+ * inner PCG solves; a reading of the PCG of Sec. 2.5 for FP32 arithmetic).
+ * Each inner solve stops once its FP32 residual norm is at most
+ * max(margin * pcg_tol * ||b||, reduction * ||r0||), r0 the FP64 residual it
+ * started from; the refinement ends when the FP64 residual meets pcg_tol.
+ * Defaults reduction = 1e-4, margin = 0.5.  Takes effect at the next solve;
+ * call before the context joins a batch (a batch's captured step does not see
+ * a later change).  No effect in FP64 mode.  Errors: EINVAL unless
+ * 0 < reduction < 1 and 0 < margin <= 1. */
+pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double margin);
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
 
 /* Species with charge q, mass m (q/m sets the push) and macro-particle

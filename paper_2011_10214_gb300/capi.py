@@ -50,7 +50,7 @@ class Stats(C.Structure):
                 ("spilled", _I64S), ("dropped", _I64S), ("pcg_iters_total", C.c_int64),
                 ("kernel_launches", C.c_int64), ("pcg_iters", C.c_int), ("pcg_converged", C.c_int),
                 ("pcg_relres", C.c_double), ("surface_charge", C.c_double), ("surface_potential", C.c_double),
-                ("phase_ms", C.c_double * 8)]
+                ("phase_ms", C.c_double * 8), ("pcg_outer_total", C.c_int64)]
 
     def as_dict(self, nspecies):
         d = {}
@@ -82,6 +82,7 @@ _sigs = {
     "pifepic_set_photoemission": [_ctx, C.c_int, C.c_double * 3, C.c_double, C.c_double, C.c_uint64],
     "pifepic_set_particle_bc": [_ctx, C.c_int, C.c_int * 6],
     "pifepic_set_bedrock": [_ctx, C.c_double, C.c_double],
+    "pifepic_set_refinement": [_ctx, C.c_double, C.c_double],
     "pifepic_get_photoemission": [_ctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "pifepic_set_external_E": [_ctx, _dp, C.c_int],
     "pifepic_solve": [_ctx, C.POINTER(Stats)],
@@ -187,6 +188,11 @@ class Simulation:
         """Bedrock of permittivity eps_bed below the plane z = z_bed inside the
         object (see pifepic_set_bedrock); call before set_object."""
         self._ok(lib.pifepic_set_bedrock(self._c, float(z_bed), float(eps_bed)), "set_bedrock")
+
+    def set_refinement(self, reduction=1e-4, margin=0.5):
+        """MIXED refinement controls (see pifepic_set_refinement): an FP32 inner
+        solve stops at max(margin tol |b|, reduction |r0|)."""
+        self._ok(lib.pifepic_set_refinement(self._c, float(reduction), float(margin)), "set_refinement")
 
     def set_field_bc(self, faces):
         arr = (FaceBC * 6)()

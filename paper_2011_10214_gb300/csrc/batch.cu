@@ -50,6 +50,8 @@ static BatchItem make_item(Ctx& c) {
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
     a.tol2 = c.tol * c.tol;
+    a.inner_red2 = c.inner_red * c.inner_red;
+    a.margin2 = c.inner_margin * c.inner_margin;
     a.maxit = c.maxit;
     return a;
 }

@@ -216,15 +216,18 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     // guard of that reach on each side (16-entry multiples keep the alignment)
     {
         c.zguard = ((long long)c.mesh.NX * c.mesh.NY + c.mesh.NX + 1 + 15) / 16 * 16;
-        const long long zlen = N + 2 * c.zguard + 16;
+        const long long zlen = (N + 2 * c.zguard + 16 + 15) / 16 * 16;   // one guarded copy
         double* zb = nullptr;
         float* zfb = nullptr;
-        ALLOC(zb, sizeof(double) * zlen);
+        // two copies each (the PCG alternates them by iteration parity)
+        ALLOC(zb, sizeof(double) * 2 * zlen);
         c.z = zb + c.zguard;
-        ALLOC(zfb, sizeof(float) * zlen);
+        c.z2 = c.z + zlen;
+        ALLOC(zfb, sizeof(float) * 2 * zlen);
         c.zf = zfb + c.zguard;
-        CUDA_OK(szero(c.stream, zb, sizeof(double) * zlen));
-        CUDA_OK(szero(c.stream, zfb, sizeof(float) * zlen));
+        c.zf2 = c.zf + zlen;
+        CUDA_OK(szero(c.stream, zb, sizeof(double) * 2 * zlen));
+        CUDA_OK(szero(c.stream, zfb, sizeof(float) * 2 * zlen));
     }
     ALLOC(c.rf, sizeof(float) * N);
     ALLOC(c.pf, sizeof(float) * N);
@@ -421,6 +424,16 @@ pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_be
     c.bed_on = true;
     c.bed_z = z_bed;
     c.bed_eps = eps_bed;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double margin) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (!(reduction > 0.0 && reduction < 1.0) || !(margin > 0.0 && margin <= 1.0))
+        FAIL(PIFEPIC_EINVAL, "refinement needs 0 < reduction < 1 and 0 < margin <= 1");
+    c.inner_red = reduction;
+    c.inner_margin = margin;
     return PIFEPIC_OK;
 }
 
@@ -852,7 +865,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     s.pcg_iters_total = iters_total(c) - it0;
     // host-launched kernels + the solve graph's kernels (the PCG is one persistent launch)
     s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c);
-    (void)ot0;
+    s.pcg_outer_total = outer_total(c) - ot0;
     s.pcg_iters = c.last_iters;
     s.pcg_relres = c.last_relres;
     s.pcg_converged = c.last_conv;

@@ -467,6 +467,8 @@ static cudaError_t set_pcg_state(Ctx& c) {
     PcgState h = {};
     h.tol2 = c.tol * c.tol;
     h.maxit = c.maxit;
+    h.inner_red2 = c.inner_red * c.inner_red;
+    h.margin2 = c.inner_margin * c.inner_margin;
     return cudaMemcpyAsync(c.scal, &h, sizeof(PcgState), cudaMemcpyHostToDevice, c.stream);
 }
 

@@ -10,10 +10,13 @@ namespace pf {
 struct PcgState {
     double bb, rz, rr, pq, alpha, beta, tol2, relres;
     int it, maxit, done, converged;
-    // mixed mode: FP32 inner PCG inside FP64 refinement
-    double rr64, inner_tol2, inner_bb;
-    int inner_it, outer_it, inner_max, done_in;
+    // mixed mode (FP32 inner PCG inside FP64 refinement): refinement steps of
+    // the last solve; an inner solve stops at max(margin2 tol2 bb, inner_red2 rr0)
+    int outer_it;
+    double inner_red2, margin2;
 };
+// the state shares the context's scalar block with other slots from double 16 on
+static_assert(sizeof(PcgState) <= 16 * sizeof(double), "PcgState overlaps the scalar slots");
 
 // h/6 and h/12 of the regular stencil in the working precision
 template <typename T>
@@ -44,6 +47,7 @@ struct BatchItem {
     long long* it_total;
     long long* outer_total;
     double tol2;
+    double inner_red2, margin2;   // MIXED inner stop (as in PcgState)
     int maxit;
 };
 
@@ -304,6 +308,9 @@ static __device__ __forceinline__ unsigned long long atom_add_release(unsigned l
 }
 static __device__ __forceinline__ void red_add_release(unsigned long long* p, unsigned long long v) {
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void red_add_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 static __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
     unsigned long long v;

@@ -114,6 +114,8 @@ struct Ctx {
     int precision = PIFEPIC_FP64;
     double tol = 1e-6;
     int maxit = 150;
+    double inner_red = 1e-4;      // MIXED: inner solves stop at max(margin tol |b|, red |r0|)
+    double inner_margin = 0.5;
     int track = 0;
     int nbx = 0, nby = 0, nbz = 0, nblocks = 0;
 
@@ -135,6 +137,8 @@ struct Ctx {
     double *r = nullptr, *p = nullptr, *q = nullptr;
     double* z = nullptr;           // inside a zeroed guard (zguard)
     float* zf = nullptr;           // inside a zeroed guard (zguard)
+    double* z2 = nullptr;          // second guarded copies in the same allocations
+    float* zf2 = nullptr;
     float *rf = nullptr, *pf = nullptr, *qf = nullptr, *uf = nullptr, *invdiagf = nullptr;
     double4* E = nullptr;          // node field (x, y, z, 0)
     float4* Ef = nullptr;          // FP32 copy for the MIXED push

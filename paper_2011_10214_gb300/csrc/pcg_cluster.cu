@@ -35,8 +35,7 @@ namespace cg = cooperative_groups;
 namespace pf {
 
 constexpr int CL_THREADS = 1024;
-constexpr double CL_INNER_TOL = 1e-4;   // MIXED: least relative reduction per refinement step
-constexpr int CL_MAX_OUTER = 12;
+constexpr int CL_MAX_OUTER = 12;   // MIXED: refinement steps at most
 
 // nodes per CTA at most: the working set of one CTA must fit in shared memory
 constexpr int cl_max_nodes(bool mixed) { return mixed ? 8192 : 4096; }
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* 
         T rz = (T)t3[2];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= CL_MAX_OUTER)) break;
-        const T rr_stop = (T)(MIXED ? fmax(0.25 * tol2 * bb, CL_INNER_TOL * CL_INNER_TOL * rr) : tol2 * bb);
+        const T rr_stop = (T)(MIXED ? fmax(a.margin2 * tol2 * bb, a.inner_red2 * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
         bool first = true;

@@ -27,8 +27,7 @@
 
 namespace pf {
 
-constexpr double COOP_INNER_TOL = 1e-4;   // MIXED: least relative reduction per refinement step
-constexpr int COOP_MAX_OUTER = 12;
+constexpr int COOP_MAX_OUTER = 12;   // MIXED: refinement steps at most
 
 // ---- register-resident PCG --------------------------------------------------
 //
@@ -49,8 +48,13 @@ constexpr int COOP_MAX_OUTER = 12;
 // slots by exchange parity, so a block that races ahead into the next exchange
 // never overwrites partials a slower block is still summing; the FP32 inner
 // loop of MIXED mode uses the fixed-point exchange instead, which needs no
-// second round trip for the partials.  MIXED wraps FP32 inner solves in FP64
-// refinement as the global-memory kernel does.  (The pipelined form of PCG would need one
+// second round trip for the partials.  z alternates between two copies by
+// iteration parity: the update writes the copy that the previous iteration's
+// staging read, whose readers the previous r.z exchange (release/acquire)
+// already ordered before the writer.  So the p.q exchange orders no global
+// data (the products write none) and its fixed-point atomic is relaxed: the
+// release fence is about a third of an exchange's latency.  MIXED wraps FP32
+// inner solves in FP64 refinement as the global-memory kernel does.  (The pipelined form of PCG would need one
 // exchange per iteration, but its recurrences stagnated on meshes with mostly
 // Neumann faces, in FP32 and with FP64 recurrences alike, so it is not used.)
 
@@ -62,7 +66,7 @@ struct RegArgs {
     double* u;                 // FP64 unknown (warm start in, solution out)
     const double* g;           // Dirichlet values
     double* phi;
-    void* zg;                  // exchanged vector z (T), padded by 16 entries
+    void* zg[2];               // exchanged vector z (T), two guarded copies
     long long M;               // nodes per block
     int woff[19];              // staged rows: window offset of each stencil slot
     double* val;               // [2][4][G] block partials
@@ -145,7 +149,7 @@ constexpr long long FX_MIN = 1ll << 26;
 // ref: the previous totals (positive, normal); prev: this lane's word value
 // after its last use (lanes 0..NV-1 of warp 0).  Returns 1 with the totals in
 // tot, -1 if the values must be redone, 0 after a timeout.
-template <int NV, typename Args>
+template <int NV, bool REL, typename Args>
 static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long long* words, unsigned long long& prev,
                                                   const float (&ref)[NV], float (&v)[NV], float (&tot)[NV],
                                                   ExchShared& xs) {
@@ -164,7 +168,11 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
         const bool fits = fabsf(sc) < FX_FIT;
         const long long fx = fits ? __float2ll_rn(sc) : 0ll;
         unsigned long long* w = words + lane * FX_LINE;
-        if (act) red_add_release(w, ((unsigned long long)fx << 16) + (fits ? 1ull : 257ull));
+        if (act) {
+            const unsigned long long add = ((unsigned long long)fx << 16) + (fits ? 1ull : 257ull);
+            if (REL) red_add_release(w, add);
+            else red_add_relaxed(w, add);
+        }
         const unsigned long long G = gridDim.x;
         unsigned long long d = 0;
         bool done = !act, timeout = false;
@@ -202,7 +210,7 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
 
 // an FP32 exchange: fixed-point when the previous totals give a scale, else
 // (or when the fixed-point totals cannot be trusted) the partial exchange
-template <int NV, typename Args>
+template <int NV, bool REL, typename Args>
 static __device__ __forceinline__ bool exchange_f32(const Args& a, int& e, unsigned long long* words,
                                                     unsigned long long& prev, const float (&ref)[NV], bool use_fx,
                                                     float (&v)[NV], float (&tot)[NV], ExchShared& xs) {
@@ -210,7 +218,7 @@ static __device__ __forceinline__ bool exchange_f32(const Args& a, int& e, unsig
         float vc[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) vc[q] = v[q];
-        const int rc = exchange_fx<NV>(a, words, prev, ref, vc, tot, xs);
+        const int rc = exchange_fx<NV, REL>(a, words, prev, ref, vc, tot, xs);
         if (rc == 1) return true;
         if (rc == 0) return false;
     }
@@ -283,10 +291,11 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
     else z_window<T>(N, f.m.NX, NXY, b0, b1, ws, we);
     const int nvec = (int)((we - ws) / VEC);
     const long long nvec_in = (N + VEC - 1) / VEC;   // vectors of z inside the padded allocation
-    T* zg = (T*)a.zg;
+    T* const zbuf[2] = {(T*)a.zg[0], (T*)a.zg[1]};
+    int zc = 0;   // the copy the next staging reads
     const T* coef = MIXED ? (const T*)f.coeff : (const T*)f.coef;
     const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
-    const double tol2 = a.S->tol2;
+    const double tol2 = a.S->tol2, inner_red2 = a.S->inner_red2, margin2 = a.S->margin2;
     const int maxit = a.S->maxit;
     auto ldw = [&](long long m) { return win[m - ws]; };
     auto ldu = [&](long long m) { return __ldcg(a.u + m); };
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
                 r[s] = (T)rn;
                 z[s] = dv[s] * r[s];
                 p[s] = z[s];
-                zg[n] = z[s];
+                zbuf[zc][n] = z[s];
                 v3[0] += bn * bn;
                 v3[1] += rn * rn;
                 v3[2] += (double)r[s] * (double)z[s];
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
         // inner target: the final tolerance, or (MIXED) a 1e-4 reduction of this residual
-        const T rr_stop = (T)(MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb);
+        const T rr_stop = (T)(MIXED ? fmax(margin2 * tol2 * bb, inner_red2 * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
         float pq_prev = 0.0f;     // no scale for the first p.q of an inner solve
@@ -364,6 +373,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             // stage the z window (the last exchange ordered every block's z stores
             // and every read of the previous window)
             {
+                const T* zg = zbuf[zc];
                 V* dst = (V*)win;
                 if (ROWS) {
                     const long long v0 = ws / VEC;   // exact: ws is a multiple of VEC
@@ -410,7 +420,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             T pq[1];
             if constexpr (MIXED) {
                 const float rf[1] = {pq_prev};
-                alive = exchange_f32<1>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
+                alive = exchange_f32<1, false>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
                 pq_prev = pq[0];
             } else {
                 alive = exchange<T, 1>(a, e, v1, pq, xs);
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
                     x[s] = x[s] + al * p[s];
                     r[s] = r[s] - al * q[s];
                     z[s] = dv[s] * r[s];
-                    zg[n] = z[s];
+                    zbuf[zc ^ 1][n] = z[s];
                     v2[0] += r[s] * r[s];
                     v2[1] += r[s] * z[s];
                 }
@@ -433,11 +443,12 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             T t2[2];
             if constexpr (MIXED) {
                 const float rf[2] = {rr_in, rz};
-                alive = exchange_f32<2>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
+                alive = exchange_f32<2, true>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
             } else {
                 alive = exchange<T, 2>(a, e, v2, t2, xs);
             }
             if (!alive) break;
+            zc ^= 1;
             beta = t2[1] / rz;
             rz = t2[1];
             rr_in = t2[0];
@@ -549,7 +560,7 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
     const T* dinv = MIXED ? (const T*)f.invdiagf : (const T*)f.invdiag;
     const int NX = f.m.NX, NXY = f.m.NX * f.m.NY;
     const T hT = (T)f.m.h, ep = (T)f.o.eps_plus, em = (T)f.o.eps_minus;
-    const double tol2 = a.S->tol2;
+    const double tol2 = a.S->tol2, inner_red2 = a.S->inner_red2, margin2 = a.S->margin2;
     const int maxit = a.S->maxit;
     int e = 0, it = 0, outer = 0;
     double bb = 0.0, rr = 0.0;
@@ -575,7 +586,7 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
         T rz = (T)t3[2];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
-        const T rr_stop = (T)(MIXED ? fmax(0.25 * tol2 * bb, COOP_INNER_TOL * COOP_INNER_TOL * rr) : tol2 * bb);
+        const T rr_stop = (T)(MIXED ? fmax(margin2 * tol2 * bb, inner_red2 * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
         bool first = true;
@@ -774,7 +785,8 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     a.f.m = c.mesh; a.f.o = c.obj; a.f.ntype = c.ntype; a.f.coef = c.patch_coef; a.f.coeff = c.patch_coeff;
     a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;
     a.b = c.b; a.u = c.u; a.g = c.gdir; a.phi = c.phi;
-    a.zg = mixed ? (void*)c.zf : (void*)c.z;
+    a.zg[0] = mixed ? (void*)c.zf : (void*)c.z;
+    a.zg[1] = mixed ? (void*)c.zf2 : (void*)c.z2;
     a.M = c.pcg_M;
     {
         const int NX = c.mesh.NX, NXY = c.mesh.NX * c.mesh.NY;

@@ -127,11 +127,42 @@ def test_global_memory_solver_on_a_large_crater():
     F = g.normal(size=m.nnodes)
     q = g.normal(size=len(fs.it_cell))
     phi_o, _, _ = fs.solve(F, q, tol=1e-12, maxit=20000)
-    for precision in (capi.FP64, capi.MIXED):
+    for precision, refinement in ((capi.FP64, None), (capi.MIXED, None), (capi.MIXED, (1e-3, 0.2))):
         sim = capi.Simulation(n, 1.0, 0.05, precision=precision, pcg_tol=1e-12, pcg_max_iter=20000)
         sim.set_field_bc(bc)
         sim.set_object(capi.OBJ_CAP_CRATER, list(crater), 4.0, 1.0)
+        if refinement:
+            sim.set_refinement(*refinement)
         it, rr = sim.solve_field(F, q)
         assert rr <= 1e-12, (precision, rr)
         assert _rel(sim.potential(), phi_o) <= TOL_PHI, precision
         sim.close()
+
+
+def test_refinement_controls():
+    """MIXED refinement with other inner stops (pifepic_set_refinement) still
+    reaches the oracle's FP64 solution; bad controls are refused."""
+    from oracle.field import FieldSystem
+    from oracle.geometry import Mesh, Sphere
+    from paper_2011_10214_gb300 import capi
+    n = 64
+    m = Mesh(n, n, n, 0.5)
+    fs = FieldSystem(m, Sphere(m, (16.0, 16.0, 16.0), 6.0, 4.0, 1.0), [("D", 0.0)] * 6)
+    g = np.random.default_rng(8)
+    F = g.normal(size=m.nnodes) * m.h ** 3
+    q = g.normal(size=len(fs.it_cell))
+    phi_o, _, _ = fs.solve(F, q, tol=1e-12, maxit=5000)
+    for red, margin in ((1e-3, 0.1), (1e-5, 1.0), (1e-2, 0.5)):
+        sim = capi.Simulation((n, n, n), 0.5, 0.05, precision=capi.MIXED, pcg_tol=1e-12, pcg_max_iter=5000)
+        sim.set_field_bc([("D", 0.0)] * 6)
+        sim.set_object(capi.OBJ_SPHERE, [16.0, 16.0, 16.0, 6.0], 4.0, 1.0)
+        sim.set_refinement(red, margin)
+        it, rr = sim.solve_field(F, q)
+        assert rr <= 1e-12, (red, margin, rr)
+        assert _rel(sim.potential(), phi_o) <= TOL_PHI, (red, margin)
+        sim.close()
+    sim = capi.Simulation((8, 8, 8), 0.5, 0.05, precision=capi.MIXED)
+    for red, margin in ((0.0, 0.5), (1.0, 0.5), (1e-4, 0.0), (1e-4, 1.5), (float("nan"), 0.5)):
+        with pytest.raises(RuntimeError):
+            sim.set_refinement(red, margin)
+    sim.close()
