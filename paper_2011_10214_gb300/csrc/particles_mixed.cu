@@ -269,12 +269,14 @@ PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
 }
 
 // One CTA per (bin, species); warps take chunks of 32 particles in turn
-// (prefetching their next chunk) and never wait at a block barrier.  Stayers
-// are compacted in place: chunk c writes its stayers right after those of
-// chunks 0..c-1, whose running count it reads from shared memory once the
-// warp of chunk c-1 has published it.  Writes then land only on slots of
-// chunks <= c, all of which were read before their counts were published, so
-// no unread particle is overwritten.
+// (chunk c to warp c mod 8, prefetching the next) and never wait at a block
+// barrier.  Stayers are compacted in place: chunk c writes its stayers right
+// after those of chunks 0..c-1.  Each chunk publishes its own stayer count in
+// shared memory as soon as it has it; the warp of chunk c adds the counts of
+// chunks c-7..c-1 (one per lane: the other warps' latest chunks) to its own
+// running total up to chunk c-8, so no warp waits on a chain of publications.
+// Writes land only on slots of chunks <= c, all of which were read before
+// their counts were published, so no unread particle is overwritten.
 // HYBRID: the IFE mesh is finer than the PIC mesh, stayers deposit straight
 // onto its nodes (a separate instantiation keeps the common path's registers)
 template <bool HYBRID>
@@ -288,9 +290,9 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     // BIN_MAX / 8 + 1 particles, holds a value in [-2^14, 2^31]: exact in 32
     // bits modulo 2^32.  The flush multiplies by 2^13 (2^32 units per particle).
     __shared__ unsigned Wt[8 * TILE_N];
-    // stayers of chunks 0..c, plus one, for each chunk c (0: not yet published;
-    // -1: the chain gave up)
-    __shared__ int pre[(BIN_MAX + 31) / 32];
+    // stayers of chunk c plus one, for each chunk c (0: not yet published)
+    __shared__ int agg[(BIN_MAX + 31) / 32];
+    __shared__ int s_total, s_fail;   // stayers of the bin plus one; a wait gave up
     __shared__ alignas(8) unsigned long long bar;
     __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
@@ -305,8 +307,9 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     const int nch = (n + 31) >> 5;
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
     for (int t = tid; t < 8 * TILE_N; t += blockDim.x) Wt[t] = 0u;
-    for (int t = tid; t < nch; t += blockDim.x) pre[t] = 0;
+    for (int t = tid; t < nch; t += blockDim.x) agg[t] = 0;
     if (tid < NCTR) sctr[tid] = 0u;
+    if (tid == 0) { s_total = 0; s_fail = 0; }
     __syncthreads();
     if (tid == 0) {
         mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(float4));
@@ -325,7 +328,9 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     const float kf = (float)S.k;
     const int refl = S.reflect;
     const int copy = lane & 7;
-    volatile int* vpre = pre;
+    volatile int* vagg = agg;
+    volatile int* vfail = &s_fail;
+    int run = 0;   // stayers of chunks 0..c-nw (this warp's previous chunk included)
     unsigned c_push = 0, c_abs = 0, c_col = 0, c_lost = 0;
     PF32 pn;
     long long idn = 0;
@@ -390,25 +395,25 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         c_abs += code == ABSORBED;
         c_col += code == COLLECTED;
         c_lost += code == COLLECTED && acc < 0;
-        // running count of the chunks before this one (bounded wait)
+        // publish this chunk's count, then add those of chunks c-7..c-1 (bounded waits)
         const unsigned bal = __ballot_sync(0xffffffffu, stay);
-        int before = 0;
-        if (lane == 0 && c > 0) {
+        if (lane == 0) vagg[c] = __popc(bal) + 1;
+        unsigned got = 0;
+        bool ok = true;
+        if (lane >= 1 && lane < nw && c - lane >= 0) {
             int v;
             long long spins = 0;
-            while ((v = vpre[c - 1]) == 0)
-                if (++spins > (1ll << 26)) { v = -1; atomicOr(L.err, ERR_CHUNK_TIMEOUT); break; }
-            before = v;   // count + 1, or -1
-        } else if (lane == 0) {
-            before = 1;
+            while ((v = vagg[c - lane]) == 0)
+                if (++spins > (1ll << 26) || *vfail) { ok = false; break; }
+            got = ok ? (unsigned)(v - 1) : 0u;
         }
-        before = __shfl_sync(0xffffffffu, before, 0);
-        if (before < 0) {   // the chain gave up: pass it on and drop this bin's stayers
-            if (lane == 0) vpre[c] = -1;
+        if (!__all_sync(0xffffffffu, ok)) {   // give up: this bin's stayers are dropped
+            if (lane == 0) { *vfail = 1; atomicOr(L.err, ERR_CHUNK_TIMEOUT); }
             break;
         }
-        before -= 1;
-        if (lane == 0) vpre[c] = before + __popc(bal) + 1;
+        const int before = run + (int)__reduce_add_sync(0xffffffffu, got);
+        run = before + __popc(bal);
+        if (lane == 0 && c == nch - 1) s_total = run + 1;
         if (stay) store_p(S.binsF, start + before + __popc(bal & ((1u << lane) - 1)), p, id, track);
         long long slot = warp_reserve(S.mov_out_n, mover);
         if (mover) {
@@ -430,10 +435,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         if (c_lost) atomicAdd(&sctr[C_LOST], c_lost);
     }
     __syncthreads();
-    if (tid == 0) {
-        const int last = vpre[nch - 1];
-        S.bcount[b] = last > 0 ? last - 1 : 0;
-    }
+    if (tid == 0) S.bcount[b] = (s_fail || s_total == 0) ? 0 : s_total - 1;
     for (int t = tid; t < TILE_N; t += blockDim.x) {
         long long v = 0;
         for (int c = 0; c < 8; ++c) {
