@@ -223,6 +223,16 @@ PF_D void global_deposit_f(const Launch& L, unsigned long long* W, const PF32& p
                   (unsigned long long)Wf[l]);
 }
 
+// asynchronous 4-byte global -> shared copies (cp.async), committed in groups
+PF_D void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+PF_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+PF_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+PF_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 PF_D void load_p(const PArrF& a, long long g, PF32& p) {
     unpack_cell(a.cell[g], p.i, p.j, p.k);
     p.fx = a.fx[g]; p.fy = a.fy[g]; p.fz = a.fz[g];
@@ -277,8 +287,15 @@ PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
 // running total up to chunk c-8, so no warp waits on a chain of publications.
 // Writes land only on slots of chunks <= c, all of which were read before
 // their counts were published, so no unread particle is overwritten.
+// A warp's next PUSH_DEPTH chunks are in flight at any time: each lane copies
+// its particle's seven words into the warp's stage in shared memory with
+// cp.async (no registers held while the loads travel) and reads them back
+// when the chunk comes up.
 // HYBRID: the IFE mesh is finer than the PIC mesh, stayers deposit straight
 // onto its nodes (a separate instantiation keeps the common path's registers)
+constexpr int PUSH_WARPS = 8;   // 256 threads
+constexpr int PUSH_DEPTH = 3;   // chunks in flight per warp
+
 template <bool HYBRID>
 __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
@@ -293,6 +310,8 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     // stayers of chunk c plus one, for each chunk c (0: not yet published)
     __shared__ int agg[(BIN_MAX + 31) / 32];
     __shared__ int s_total, s_fail;   // stayers of the bin plus one; a wait gave up
+    // per warp and stage: cell, fx, fy, fz, vx, vy, vz of 32 particles
+    __shared__ unsigned stg[PUSH_WARPS][PUSH_DEPTH][7][32];
     __shared__ alignas(8) unsigned long long bar;
     __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
@@ -305,6 +324,25 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int nch = (n + 31) >> 5;
+    const long long start = S.bstart[b];
+    // copies of chunk cc (this warp's) into stage slot sl; one group per call
+    auto stage = [&](int cc, int sl) {
+        const int ii = cc * 32 + lane;
+        if (cc < nch && ii < n) {
+            const long long g = start + ii;
+            unsigned(&d)[7][32] = stg[wid][sl];
+            cp_async4(&d[0][lane], S.binsF.cell + g);
+            cp_async4(&d[1][lane], S.binsF.fx + g);
+            cp_async4(&d[2][lane], S.binsF.fy + g);
+            cp_async4(&d[3][lane], S.binsF.fz + g);
+            cp_async4(&d[4][lane], S.binsF.vx + g);
+            cp_async4(&d[5][lane], S.binsF.vy + g);
+            cp_async4(&d[6][lane], S.binsF.vz + g);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < PUSH_DEPTH; ++d) stage(wid + d * nw, d);
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
     for (int t = tid; t < 8 * TILE_N; t += blockDim.x) Wt[t] = 0u;
     for (int t = tid; t < nch; t += blockDim.x) agg[t] = 0;
@@ -322,8 +360,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) return;
-    const long long start = S.bstart[b];
+    if (!s_ok) { cp_async_wait_all(); return; }
     const bool track = L.track;
     const float kf = (float)S.k;
     const int refl = S.reflect;
@@ -332,22 +369,21 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     volatile int* vfail = &s_fail;
     int run = 0;   // stayers of chunks 0..c-nw (this warp's previous chunk included)
     unsigned c_push = 0, c_abs = 0, c_col = 0, c_lost = 0;
-    PF32 pn;
-    long long idn = 0;
-    if (wid * 32 + lane < n) {
-        load_p(S.binsF, start + wid * 32 + lane, pn);
-        if (track) idn = S.binsF.id[start + wid * 32 + lane];
-    }
+    int sl = 0;   // stage slot of the current chunk
     for (int c = wid; c < nch; c += nw) {
         const int i = c * 32 + lane;
         int code = NONE, acc = -1;
-        PF32 p = pn;
-        const long long id = idn;
-        const int inext = i + nw * 32;
-        if (inext < n) {
-            load_p(S.binsF, start + inext, pn);
-            if (track) idn = S.binsF.id[start + inext];
+        PF32 p;
+        long long id = 0;
+        cp_async_wait<PUSH_DEPTH - 1>();   // this chunk's group (each lane reads only its own copies)
+        {
+            const unsigned(&d)[7][32] = stg[wid][sl];
+            unpack_cell((int)d[0][lane], p.i, p.j, p.k);
+            p.fx = __uint_as_float(d[1][lane]); p.fy = __uint_as_float(d[2][lane]);
+            p.fz = __uint_as_float(d[3][lane]); p.vx = __uint_as_float(d[4][lane]);
+            p.vy = __uint_as_float(d[5][lane]); p.vz = __uint_as_float(d[6][lane]);
         }
+        if (track && i < n) id = S.binsF.id[start + i];
         if (i < n) {
             // kick with the field gathered at the old position, then drift
             const WF w = weights_f(p.fx, p.fy, p.fz);
@@ -370,6 +406,9 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
                 }
             }
         }
+        // refill the slot (its values have been used, so its reads are done)
+        stage(c + PUSH_DEPTH * nw, sl);
+        sl = sl + 1 == PUSH_DEPTH ? 0 : sl + 1;
         bool stay = false, mover = false;
         if (code == ALIVE) {
             stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
@@ -421,6 +460,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
             else atomicAdd(&S.ctr[C_DROPPED], 1ull);
         }
     }
+    cp_async_wait_all();   // (a warp that gave up may still have copies in flight)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         c_push += __shfl_xor_sync(0xffffffffu, c_push, o);
