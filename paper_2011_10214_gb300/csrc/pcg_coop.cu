@@ -129,27 +129,36 @@ static __device__ __forceinline__ bool exchange(const Args& a, int& e, A (&v)[NV
 //
 // The arrival and the partial travel in one fire-and-forget atomic: a block
 // adds to one 64-bit word per value
-//     (rint(v 2^k) << 16) + (fits ? 1 : 257)
-// -- bits 0-7 count arrivals, bits 8-15 blocks whose scaled partial did not
-// fit below 2^39, bits 16-63 the 48-bit two's-complement sum (at most 255
-// blocks, so no field carries into the next).  A block polls the word until
-// its growth since the previous use shows every arrival; the growth then holds
-// the integer total.  The scale 2^k puts the value's previous total near 2^32,
-// so each partial is exact to 2^-32 of it.  Integer sums do not depend on the
+//     (rint(v 2^k) << 2W) + (fits ? 1 : 1 + 2^W)
+// -- bits 0..W-1 count arrivals, bits W..2W-1 blocks whose scaled partial did
+// not fit, bits 2W..63 the two's-complement sum.  W = 8 (at most 255 blocks):
+// partials below 2^39, a 48-bit sum, the scale 2^k puts the value's previous
+// total near 2^32; W = 9 (at most 511 blocks): partials below 2^36, a 46-bit
+// sum, previous total near 2^29.  No field carries into the next within one
+// exchange.  A block polls the word until its growth since the previous use
+// shows every arrival; the growth then holds the integer total, each partial
+// exact to 2^-32 (2^-29) of the previous total.  Integer sums do not depend on the
 // arrival order: results stay deterministic run to run.  A word is reused only
 // after the other exchange kind (a full barrier) has passed, so its value is
 // stable from the last arrival until every block has read it.  If a partial
-// did not fit, or the total kept fewer than 2^26 units (the value fell far
-// below its previous total), every block sees it and redoes the values with
-// the partial exchange above.
+// did not fit, or the total kept fewer than 2^26 (2^23) units (the value fell
+// far below its previous total), every block sees it and redoes the values
+// with the partial exchange above.
 constexpr int FX_LINE = 16;                  // words per 128-byte line
-constexpr float FX_FIT = 549755813888.0f;    // 2^39
-constexpr long long FX_MIN = 1ll << 26;
+template <int W>
+struct FxLayout {
+    static_assert(W == 8 || W == 9, "layouts for up to 255 or 511 blocks");
+    static constexpr int SUM = 2 * W;                                        // sum field shift
+    static constexpr unsigned long long MASK = (1ull << W) - 1;
+    static constexpr float FIT = W == 8 ? 549755813888.0f : 68719476736.0f;   // 2^39, 2^36
+    static constexpr int SCALE = W == 8 ? 32 : 29;
+    static constexpr long long MIN = W == 8 ? (1ll << 26) : (1ll << 23);
+};
 
 // ref: the previous totals (positive, normal); prev: this lane's word value
 // after its last use (lanes 0..NV-1 of warp 0).  Returns 1 with the totals in
 // tot, -1 if the values must be redone, 0 after a timeout.
-template <int NV, bool REL, typename Args>
+template <int NV, bool REL, int W, typename Args>
 static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long long* words, unsigned long long& prev,
                                                   const float (&ref)[NV], float (&v)[NV], float (&tot)[NV],
                                                   ExchShared& xs) {
@@ -163,13 +172,14 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
             const float m1 = __shfl_sync(0xffffffffu, v[NV - 1], 0);
             if (lane == 1) { mine = m1; rf = ref[NV - 1]; }
         }
-        const int k = 32 - ilogbf(rf);
+        using FL = FxLayout<W>;
+        const int k = FL::SCALE - ilogbf(rf);
         const float sc = ldexpf(mine, k);
-        const bool fits = fabsf(sc) < FX_FIT;
+        const bool fits = fabsf(sc) < FL::FIT;
         const long long fx = fits ? __float2ll_rn(sc) : 0ll;
         unsigned long long* w = words + lane * FX_LINE;
         if (act) {
-            const unsigned long long add = ((unsigned long long)fx << 16) + (fits ? 1ull : 257ull);
+            const unsigned long long add = ((unsigned long long)fx << FL::SUM) + (fits ? 1ull : 1ull + (1ull << W));
             if (REL) red_add_release(w, add);
             else red_add_relaxed(w, add);
         }
@@ -180,7 +190,7 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
         for (;;) {
             if (!done) {
                 d = ld_acquire(w) - prev;
-                done = (d & 255ull) == G;
+                done = (d & FL::MASK) == G;
             }
             if (__all_sync(0xffffffffu, done)) break;
             if (__any_sync(0xffffffffu, clock64() - c0 > (1ll << 31))) { timeout = true; break; }
@@ -188,8 +198,8 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
         bool good = true;
         if (act && !timeout) {
             prev += d;
-            const long long val = (long long)d >> 16;
-            good = ((d >> 8) & 255ull) == 0 && (val >= FX_MIN || val <= -FX_MIN);
+            const long long val = (long long)d >> FL::SUM;
+            good = ((d >> W) & FL::MASK) == 0 && (val >= FL::MIN || val <= -FL::MIN);
             bc[lane] = ldexpf((float)val, -k);
         }
         const bool all_good = __all_sync(0xffffffffu, good);
@@ -210,7 +220,7 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
 
 // an FP32 exchange: fixed-point when the previous totals give a scale, else
 // (or when the fixed-point totals cannot be trusted) the partial exchange
-template <int NV, bool REL, typename Args>
+template <int NV, bool REL, int W, typename Args>
 static __device__ __forceinline__ bool exchange_f32(const Args& a, int& e, unsigned long long* words,
                                                     unsigned long long& prev, const float (&ref)[NV], bool use_fx,
                                                     float (&v)[NV], float (&tot)[NV], ExchShared& xs) {
@@ -218,7 +228,7 @@ static __device__ __forceinline__ bool exchange_f32(const Args& a, int& e, unsig
         float vc[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) vc[q] = v[q];
-        const int rc = exchange_fx<NV, REL>(a, words, prev, ref, vc, tot, xs);
+        const int rc = exchange_fx<NV, REL, W>(a, words, prev, ref, vc, tot, xs);
         if (rc == 1) return true;
         if (rc == 0) return false;
     }
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             T pq[1];
             if constexpr (MIXED) {
                 const float rf[1] = {pq_prev};
-                alive = exchange_f32<1, false>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
+                alive = exchange_f32<1, false, 8>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
                 pq_prev = pq[0];
             } else {
                 alive = exchange<T, 1>(a, e, v1, pq, xs);
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             T t2[2];
             if constexpr (MIXED) {
                 const float rf[2] = {rr_in, rz};
-                alive = exchange_f32<2, true>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
+                alive = exchange_f32<2, true, 8>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
             } else {
                 alive = exchange<T, 2>(a, e, v2, t2, xs);
             }
@@ -492,8 +502,10 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
 //
 // Vectors in global memory (a 2M-node mesh keeps them in L2), otherwise the
 // same iteration as k_pcg_reg: Jacobi PCG with the q recurrence, two
-// exchanges per iteration on the arrival counter, FP32 inner arithmetic in
-// MIXED mode, FP64 refinement residual.  Regular rows are the branch-free
+// exchanges per iteration (MIXED: the fixed-point exchange for up to 511
+// blocks, the p.q one relaxed, z in two copies by iteration parity; FP64: the
+// partial exchange), FP32 inner arithmetic in MIXED mode, FP64 refinement
+// residual.  Regular rows are the branch-free
 // masked stencil selected by a per-node kind word (made once per mesh);
 // interface rows use their patch coefficients.  Each thread takes its nodes
 // four at a time and issues every load of the four before any store, so the
@@ -510,9 +522,10 @@ struct GlobArgs {
     double* u;
     const double* g;
     double* phi;
-    void *r, *z, *p, *q, *x;      // working-precision vectors
+    void *r, *z, *z2, *p, *q, *x;   // working-precision vectors (z in two guarded copies)
     double* val;
     unsigned long long* arrivals;
+    unsigned long long* fx;         // fixed-point exchange words (as RegArgs::fx)
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -552,7 +565,8 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
     const long long TT = (long long)gridDim.x * blockDim.x;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     T* r = (T*)a.r;
-    T* z = (T*)a.z;
+    T* const zb[2] = {(T*)a.z, (T*)a.z2};
+    int zc = 0;   // the copy the next products read
     T* p = (T*)a.p;
     T* q = (T*)a.q;
     T* x = (T*)a.x;
@@ -565,6 +579,12 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
     int e = 0, it = 0, outer = 0;
     double bb = 0.0, rr = 0.0;
     bool conv = false, alive = true;
+    // this launch's starting values of the fixed-point words (before any block adds)
+    unsigned long long fxa = 0, fxb = 0;
+    if (MIXED && threadIdx.x < 2) {
+        fxa = ld_relaxed(a.fx);
+        fxb = ld_relaxed(a.fx + (1 + threadIdx.x) * FX_LINE);
+    }
     for (;;) {
         // true residual of u in FP64; z = D^-1 r, p = z, x = 0
         double v3[3] = {0.0, 0.0, 0.0};
@@ -574,7 +594,7 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
             const double bn = a.b[n];
             const double rn = (f.ntype[n] == -3) ? 0.0 : bn - apply_row<double, true>(f, n, i, j, k, a.u, f.coef);
             const T rt = (T)rn, zt = dinv[n] * rt;
-            r[n] = rt; z[n] = zt; p[n] = zt; x[n] = (T)0;
+            r[n] = rt; zb[zc][n] = zt; p[n] = zt; x[n] = (T)0;
             v3[0] += bn * bn;
             v3[1] += rn * rn;
             v3[2] += (double)rt * (double)zt;
@@ -589,9 +609,11 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
         const T rr_stop = (T)(MIXED ? fmax(margin2 * tol2 * bb, inner_red2 * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
+        float pq_prev = 0.0f;     // no scale for the first p.q of an inner solve
         bool first = true;
         for (;;) {
             // p = z + beta p, q = A z + beta q (first pass: p = z, q = A z)
+            const T* z = zb[zc];
             T v1[1] = {(T)0};
             for (long long n0 = t0; n0 < N; n0 += GLOB_UNROLL * TT) {
                 T az[GLOB_UNROLL], zl[GLOB_UNROLL], pl[GLOB_UNROLL], ql[GLOB_UNROLL];
@@ -618,8 +640,16 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
             }
             first = false;
             T pq[1];
-            if (!(alive = exchange<T, 1>(a, e, v1, pq, xs))) break;
+            if constexpr (MIXED) {
+                const float rf[1] = {pq_prev};
+                alive = exchange_f32<1, false, 9>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
+                pq_prev = pq[0];
+            } else {
+                alive = exchange<T, 1>(a, e, v1, pq, xs);
+            }
+            if (!alive) break;
             const T al = rz / pq[0];
+            T* zn_out = zb[zc ^ 1];
             T v2[2] = {(T)0, (T)0};
             for (long long n0 = t0; n0 < N; n0 += GLOB_UNROLL * TT) {
                 T xl[GLOB_UNROLL], rl[GLOB_UNROLL], pl[GLOB_UNROLL], ql[GLOB_UNROLL], dl[GLOB_UNROLL];
@@ -640,14 +670,22 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
                         const T zn = dl[u] * rn;
                         x[n] = xl[u] + al * pl[u];
                         r[n] = rn;
-                        z[n] = zn;
+                        zn_out[n] = zn;
                         v2[0] += rn * rn;
                         v2[1] += rn * zn;
                     }
                 }
             }
             T t2[2];
-            if (!(alive = exchange<T, 2>(a, e, v2, t2, xs))) break;
+            if constexpr (MIXED) {
+                const float rf[2] = {rr_in, rz};
+                alive = exchange_f32<2, true, 9>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2,
+                                                 t2, xs);
+            } else {
+                alive = exchange<T, 2>(a, e, v2, t2, xs);
+            }
+            if (!alive) break;
+            zc ^= 1;
             beta = t2[1] / rz;
             rz = t2[1];
             rr_in = t2[0];
@@ -827,8 +865,9 @@ cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;
     a.kind = c.rowkind;
     a.b = c.b; a.u = c.u; a.g = c.gdir; a.phi = c.phi;
-    if (mixed) { a.r = c.rf; a.z = c.zf; a.p = c.pf; a.q = c.qf; a.x = c.uf; }
-    else { a.r = c.r; a.z = c.z; a.p = c.p; a.q = c.q; a.x = c.pcg_x; }
+    if (mixed) { a.r = c.rf; a.z = c.zf; a.z2 = c.zf2; a.p = c.pf; a.q = c.qf; a.x = c.uf; }
+    else { a.r = c.r; a.z = c.z; a.z2 = c.z2; a.p = c.p; a.q = c.q; a.x = c.pcg_x; }
+    a.fx = c.bar64 + FX_LINE;
     a.val = c.coop_partial;
     a.arrivals = c.bar64;
     a.S = (PcgState*)c.scal;
@@ -841,6 +880,7 @@ cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_glob<false>, GLOB_THREADS, 0);
     long long G = (long long)nsm * (per > 0 ? per : 1);
     if (G > GLOB_THREADS) G = GLOB_THREADS;   // an exchange reads one block partial per thread
+    if (G > 511) G = 511;                     // the fixed-point exchange counts arrivals in 9 bits
     void* args[] = {&a};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)G);
