@@ -18,7 +18,6 @@ cudaError_t set_field_tables(const TetTables& t);
 cudaError_t set_particle_tables(const TetTables& t);
 cudaError_t set_mixed_tables(const TetTables& t);
 cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double* relres);
-cudaError_t read_pcg_state(Ctx& c);
 int solve_graph_fixed_kernels(const Ctx& c);
 cudaError_t launch_pcg_mixed(Ctx& c);
 cudaError_t alloc_parrf(PArrF& a, long long n, bool id);
@@ -255,6 +254,12 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     ALLOC(c.red_ticket, sizeof(unsigned) * 4);
     ALLOC(c.bar64, sizeof(unsigned long long) * BAR64_WORDS);
     ALLOC(c.err_word, sizeof(int));
+    ALLOC(c.stat_dev, sizeof(StatPack));
+    if (cudaMallocHost(&c.stat_host, sizeof(StatPack)) != cudaSuccess) {
+        cudaGetLastError();
+        c.stat_host = nullptr;
+        FAIL(PIFEPIC_ENOMEM, "pinned statistics buffer");
+    }
     ALLOC(c.next_id, sizeof(long long) * MAX_SPECIES);
     ALLOC(c.inj_count, sizeof(int) * MAX_SPECIES * 6);
     ALLOC(c.inj_base, sizeof(long long) * MAX_SPECIES * 6);
@@ -288,9 +293,10 @@ void pifepic_destroy(pifepic_ctx* ctx) {
                     c.z ? (void*)(c.z - c.zguard) : nullptr, c.zf ? (void*)(c.zf - c.zguard) : nullptr,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
-                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.inj_dev, c.inj_count,
+                    c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.stat_dev, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
     for (void* p : ptrs) cudaFree(p);
+    if (c.stat_host) cudaFreeHost(c.stat_host);
     if (c.refine > 1) { cudaFree(c.Ep); cudaFree(c.Efp); }
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
@@ -800,21 +806,6 @@ pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem
     return PIFEPIC_OK;
 }
 
-static void read_counters(Ctx& c, unsigned long long* out) {
-    scopy(c.stream, out, c.ctrall, sizeof(unsigned long long) * MAX_SPECIES * NCTR, cudaMemcpyDeviceToHost);
-}
-
-static long long iters_total(Ctx& c) {
-    long long v = 0;
-    scopy(c.stream, &v, (long long*)(c.scal + 40), sizeof(v), cudaMemcpyDeviceToHost);
-    return v;
-}
-static long long outer_total(Ctx& c) {
-    long long v = 0;
-    scopy(c.stream, &v, (long long*)(c.scal + 41), sizeof(v), cudaMemcpyDeviceToHost);
-    return v;
-}
-
 static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* before, pifepic_stats* st,
                                  const float* phase_ms, long long it0, long long l0, long long nsolves,
                                  long long ot0);
@@ -824,9 +815,11 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
 namespace pf {
 // counters before a batched call, and the statistics after it (batch.cu)
 void snapshot_counters(pifepic_ctx* ctx, unsigned long long* before, long long* it0, long long* ot0, long long* l0) {
-    read_counters(ctx->c, before);
-    *it0 = iters_total(ctx->c);
-    *ot0 = outer_total(ctx->c);
+    StatPack pk;
+    if (gather_stats(ctx->c, &pk, false) != cudaSuccess) memset(&pk, 0, sizeof(pk));
+    memcpy(before, pk.ctr, sizeof(pk.ctr));
+    *it0 = pk.it_total;
+    *ot0 = pk.outer_total;
     *l0 = ctx->c.launches;
 }
 pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, long long it0, long long ot0,
@@ -842,8 +835,10 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
                                  const float* phase_ms, long long it0, long long l0, long long nsolves,
                                  long long ot0) {
     Ctx& c = ctx->c;
-    unsigned long long now[MAX_SPECIES * NCTR];
-    read_counters(c, now);
+    StatPack pk;
+    cudaError_t e = gather_stats(c, &pk, c.have_object);
+    if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "statistics: %s", cudaGetErrorString(e));
+    const unsigned long long* now = pk.ctr;
     pifepic_stats s;
     memset(&s, 0, sizeof(s));
     s.steps = c.step_no;
@@ -858,27 +853,19 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
         s.inj_rejected[q] = (int64_t)(a[C_REJECTED] - b[C_REJECTED]);
         s.spilled[q] = (int64_t)a[C_SPILLED];
         s.dropped[q] = (int64_t)(a[C_DROPPED] - b[C_DROPPED]);
-        s.count[q] = count_particles(c, (int)q);
+        s.count[q] = pk.count[q];
     }
-    cudaError_t e = read_pcg_state(c);
-    if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "pcg state: %s", cudaGetErrorString(e));
-    s.pcg_iters_total = iters_total(c) - it0;
+    s.pcg_iters_total = pk.it_total - it0;
     // host-launched kernels + the solve graph's kernels (the PCG is one persistent launch)
     s.kernel_launches = (c.launches - l0) + nsolves * solve_graph_fixed_kernels(c);
-    s.pcg_outer_total = outer_total(c) - ot0;
+    s.pcg_outer_total = pk.outer_total - ot0;
     s.pcg_iters = c.last_iters;
     s.pcg_relres = c.last_relres;
     s.pcg_converged = c.last_conv;
-    double d2[2] = {0, 0};
-    if (c.have_object) {
-        e = launch_surface_diag(c, d2);
-        if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "surface diagnostics: %s", cudaGetErrorString(e));
-    }
-    s.surface_charge = d2[0];
-    s.surface_potential = d2[1];
+    s.surface_charge = pk.surface_charge;
+    s.surface_potential = pk.surface_potential;
     if (phase_ms) for (int k = 0; k < 8; ++k) s.phase_ms[k] = phase_ms[k];
-    int herr = 0;
-    scopy(c.stream, &herr, c.err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    const int herr = pk.err;
     c.stats = s;
     if (st) *st = s;
     if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
@@ -912,8 +899,8 @@ pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
     Ctx& c = ctx->c;
     if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
     unsigned long long before[MAX_SPECIES * NCTR];
-    read_counters(c, before);
-    long long it0 = iters_total(c), l0 = c.launches, ot0 = outer_total(c);
+    long long it0, l0, ot0;
+    snapshot_counters(ctx, before, &it0, &ot0, &l0);
     if (c.precision == PIFEPIC_MIXED) CUDA_OK(launch_deposit_all_mixed(c));
     else CUDA_OK(launch_deposit_all(c));
     if (!c.external_E) CUDA_OK(run_solve(c));
@@ -936,8 +923,8 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
     if (!c.have_object) FAIL(PIFEPIC_ESTATE, "set_object first");
     if (nsteps < 0) FAIL(PIFEPIC_EINVAL, "nsteps < 0");
     unsigned long long before[MAX_SPECIES * NCTR];
-    read_counters(c, before);
-    long long it0 = iters_total(c), l0 = c.launches, ot0 = outer_total(c);
+    long long it0, l0, ot0;
+    snapshot_counters(ctx, before, &it0, &ot0, &l0);
     float ph[8] = {0};
     bool mixed = c.precision == PIFEPIC_MIXED;
     for (int it = 0; it < nsteps; ++it) {

@@ -179,6 +179,31 @@ PF_D long long warp_reserve(unsigned long long* counter, bool want) {
     return (long long)(base + __popc(mask & ((1u << lane) - 1)));
 }
 
+// atomicAdd(p, 1) with one atomic per group of active lanes that share the
+// address (match_any): each lane gets a distinct value, as if the lanes had
+// added one by one in lane order.  Lanes hitting one counter (particles of one
+// bin in a warp) no longer serialise on it.
+PF_D int warp_inc(int* p) {
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, (unsigned long long)p);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(p, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1));
+}
+// the same for one counter shared by all active lanes
+PF_D unsigned long long warp_inc64(unsigned long long* p) {
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(p, (unsigned long long)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    return base + __popc(act & ((1u << lane) - 1));
+}
+
 constexpr int BIN_MAX = 32767;
 // corner offsets in a (BLK+1)^3 tile, node order 000,100,010,110,001,101,011,111
 PF_HD constexpr int tile_corner(int l) {

@@ -521,6 +521,89 @@ cudaError_t launch_surface_diag(Ctx& c, double* out2) {
     return cudaStreamSynchronize(c.stream);
 }
 
+struct StatArgs {
+    const unsigned long long* ctrall;
+    const int* bcount[MAX_SPECIES];
+    const unsigned long long* mov_n[MAX_SPECIES];
+    int nspecies, nblocks;
+    const double* scal;
+    const double* diag;   // surface charge, potential; null: not gathered
+    const int* err;
+    StatPack* out;
+};
+
+// one block of 256 threads
+__global__ void k_stat_pack(StatArgs a) {
+    __shared__ long long part[8];
+    const int t = threadIdx.x;
+    for (int i = t; i < MAX_SPECIES * NCTR; i += blockDim.x) a.out->ctr[i] = a.ctrall[i];
+    for (int s = 0; s < MAX_SPECIES; ++s) {
+        long long v = 0;
+        if (s < a.nspecies && a.bcount[s])
+            for (int b = t; b < a.nblocks; b += blockDim.x) v += a.bcount[s][b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) part[t >> 5] = v;
+        __syncthreads();
+        if (t == 0) {
+            long long tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+            if (s < a.nspecies && a.mov_n[s]) tot += (long long)a.mov_n[s][0];
+            a.out->count[s] = s < a.nspecies ? tot : 0;
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const PcgState* S = (const PcgState*)a.scal;
+        a.out->it = S->it;
+        a.out->converged = S->converged;
+        a.out->relres = S->relres;
+        a.out->it_total = ((const long long*)a.scal)[40];
+        a.out->outer_total = ((const long long*)a.scal)[41];
+        a.out->surface_charge = a.diag ? a.diag[0] : 0.0;
+        a.out->surface_potential = a.diag ? a.diag[1] : 0.0;
+        a.out->err = *a.err;
+    }
+}
+
+cudaError_t gather_stats(Ctx& c, StatPack* out, bool diag) {
+    double* d = diag_dev(c);
+    if (diag) {
+        RhsArgs ra = rargs(c);
+        if (c.nit > 0)
+            k_surface_diag<<<nb(c.nit), 256, 0, c.stream>>>(c.mesh, c.nit, c.it_cell, c.it_t, c.it_data, c.qT, c.phi,
+                                                            c.red, c.red_ticket, d + 1);
+        else
+            cudaMemsetAsync(d + 1, 0, sizeof(double), c.stream);
+        if (c.ncut > 0)
+            k_surface_charge<<<nb(c.ncut), 256, 0, c.stream>>>(ra, c.red, c.red_ticket, d);
+        else
+            cudaMemsetAsync(d, 0, sizeof(double), c.stream);
+    }
+    StatArgs a = {};
+    a.ctrall = c.ctrall;
+    a.nspecies = (int)c.sp.size();
+    for (int s = 0; s < a.nspecies && s < MAX_SPECIES; ++s) {
+        a.bcount[s] = c.sp[s].bcount;
+        a.mov_n[s] = c.sp[s].mov_n;
+    }
+    a.nblocks = c.nblocks;
+    a.scal = c.scal;
+    a.diag = diag ? d : nullptr;
+    a.err = c.err_word;
+    a.out = c.stat_dev;
+    k_stat_pack<<<1, 256, 0, c.stream>>>(a);
+    cudaError_t e = cudaMemcpyAsync(c.stat_host, c.stat_dev, sizeof(StatPack), cudaMemcpyDeviceToHost, c.stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return e;
+    *out = *c.stat_host;
+    c.last_iters = out->it;
+    c.last_relres = out->relres;
+    c.last_conv = out->converged;
+    return cudaSuccess;
+}
+
 cudaError_t launch_node_E_tables(Ctx& c) {
     long long n = c.nit > c.mesh.nnodes ? c.nit : c.mesh.nnodes;
     k_node_E_tables<<<nb(n), 256, 0, c.stream>>>(c.nit, c.it_data, c.it_dataf, c.mesh.nnodes, c.Lnode, c.Lpos);

@@ -102,6 +102,16 @@ struct Species {
     long long next_id = 0;
 };
 
+// the values a call's statistics need, gathered on the device into one block
+// (one copy and one synchronisation per read)
+struct StatPack {
+    unsigned long long ctr[MAX_SPECIES * NCTR];   // the species' event counters
+    long long count[MAX_SPECIES];                 // particles in bins + waiting list
+    long long it_total, outer_total;              // PCG iteration counters
+    double relres, surface_charge, surface_potential;
+    int it, converged, err, pad;
+};
+
 struct Ctx {
     std::string err;
     cudaStream_t stream = nullptr;
@@ -194,6 +204,8 @@ struct Ctx {
     long long pcg_M = 0;
     size_t pcg_smem = 0;
     int* err_word = nullptr;
+    StatPack* stat_dev = nullptr;   // gather_stats: device block and its pinned host copy
+    StatPack* stat_host = nullptr;
     // graphs
     cudaGraphExec_t pcg_exec = nullptr;
     cudaGraph_t pcg_graph = nullptr;
@@ -280,6 +292,8 @@ void plan_pcg(Ctx& c);                                 // pcg_coop.cu
 cudaError_t launch_rhs(Ctx& c);
 cudaError_t launch_pcg(Ctx& c);
 cudaError_t launch_surface_diag(Ctx& c, double* out2);   // [charge, potential]
+// diag: also the surface charge and mean surface potential (a few kernels)
+cudaError_t gather_stats(Ctx& c, StatPack* out, bool diag);
 cudaError_t launch_qtets(Ctx& c);
 
 Launch make_launch(Ctx& c);

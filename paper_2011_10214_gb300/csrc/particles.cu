@@ -400,7 +400,7 @@ __global__ void k_rebin(Launch L) {
             vx = S.mov_out.vx[i]; vy = S.mov_out.vy[i]; vz = S.mov_out.vz[i];
             if (track) id = S.mov_out.id[i];
             int b = block_of(L, (int)floor(x), (int)floor(y), (int)floor(z));
-            int slot = atomicAdd(&S.bcount[b], 1);
+            int slot = warp_inc(&S.bcount[b]);
             if (slot < S.bcap[b]) put(S.bins, S.bstart[b] + slot, x, y, z, vx, vy, vz, id, track);
             else spill = true;
         }
@@ -447,7 +447,7 @@ __global__ void k_load(Launch L, int s, int ppc, double vth, double dx, double d
     double g0, g1, g2, g3;
     box_muller(u01(b1.v[0]), u01(b1.v[1]), g0, g1);
     box_muller(u01(b1.v[2]), u01(b1.v[3]), g2, g3);
-    unsigned long long slot = atomicAdd(nout, 1ull);
+    unsigned long long slot = warp_inc64(nout);
     if ((long long)slot >= cap) return;
     put(out, (long long)slot, x, y, z, dx + vth * g0, dy + vth * g1, dz + vth * g2, c * ppc + pc, true);
 }
@@ -456,7 +456,7 @@ __global__ void k_bin_count(Launch L, PArr a, long long n, int* cnt) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int b = block_of(L, (int)floor(a.x[i]), (int)floor(a.y[i]), (int)floor(a.z[i]));
-    atomicAdd(&cnt[b], 1);
+    warp_inc(&cnt[b]);
 }
 
 // capacity per bin: count + 25% + 64 slack, multiple of 32
@@ -482,7 +482,7 @@ __global__ void k_bin_scatter(Launch L, int s, PArr a, long long n, bool track) 
     if (i >= n) return;
     const SpeciesDev& S = L.sp[s];
     int b = block_of(L, (int)floor(a.x[i]), (int)floor(a.y[i]), (int)floor(a.z[i]));
-    int slot = atomicAdd(&S.bcount[b], 1);
+    int slot = warp_inc(&S.bcount[b]);
     long long id = track ? a.id[i] : 0;
     if (slot < S.bcap[b]) {
         put(S.bins, S.bstart[b] + slot, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], id, track);

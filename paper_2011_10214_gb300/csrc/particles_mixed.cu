@@ -278,6 +278,36 @@ PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
     return (i - x0) + TILE * ((j - y0) + TILE * (k - z0));
 }
 
+// a bin's deposit tile: 8 interleaved 32-bit copies per node (copy = lane & 7),
+// units of 2^-19 particle (see k_push_bins_m).  One particle: 7 rounded
+// weights and the remainder, so it adds exactly 2^19.
+PF_D void tile_deposit19(unsigned* Wt, int t0, const WF& w) {
+    unsigned rest = 1u << 19;
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        const unsigned W = __float2uint_rn(w.w[l] * 524288.0f);
+        rest -= W;
+        atomicAdd(&Wt[t0 + 8 * tile_corner(l)], W);
+    }
+    atomicAdd(&Wt[t0 + 8 * tile_corner(7)], rest);
+}
+// add the tile to the node charges (2^32 units per particle), all threads of the block
+PF_D void tile_flush19(const Launch& L, unsigned long long* W, const unsigned* Wt, int x0, int y0, int z0) {
+    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+        long long v = 0;
+        for (int c = 0; c < 8; ++c) {
+            long long u = (long long)Wt[t * 8 + c];
+            if (u >= (3ll << 30)) u -= 1ll << 32;     // a (small) negative copy total
+            v += u;
+        }
+        if (!v) continue;
+        int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
+            atomicAdd(&W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)(v * 8192));
+    }
+}
+
 // One CTA per (bin, species); warps take chunks of 32 particles in turn
 // (chunk c to warp c mod 8, prefetching the next) and never wait at a block
 // barrier.  Stayers are compacted in place: chunk c writes its stayers right
@@ -416,16 +446,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
             if (HYBRID && stay) {
                 global_deposit_f(L, S.W, p);   // hybrid grid: straight onto the IFE nodes
             } else if (stay) {   // (movers deposit in the rebin, with every mover of the step)
-                const WF w = weights_f(p.fx, p.fy, p.fz);
-                const int t0 = 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy;
-                unsigned rest = 1u << 19;
-#pragma unroll
-                for (int l = 0; l < 7; ++l) {
-                    const unsigned W = __float2uint_rn(w.w[l] * 524288.0f);
-                    rest -= W;
-                    atomicAdd(&Wt[t0 + 8 * tile_corner(l)], W);
-                }
-                atomicAdd(&Wt[t0 + 8 * tile_corner(7)], rest);
+                tile_deposit19(Wt, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, weights_f(p.fx, p.fy, p.fz));
             }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
@@ -476,19 +497,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     }
     __syncthreads();
     if (tid == 0) S.bcount[b] = (s_fail || s_total == 0) ? 0 : s_total - 1;
-    for (int t = tid; t < TILE_N; t += blockDim.x) {
-        long long v = 0;
-        for (int c = 0; c < 8; ++c) {
-            long long u = (long long)Wt[t * 8 + c];
-            if (u >= (3ll << 30)) u -= 1ll << 32;     // a (small) negative copy total
-            v += u;
-        }
-        if (!v) continue;
-        int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
-        int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
-        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
-            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)(v * 8192));
-    }
+    tile_flush19(L, S.W, Wt, x0, y0, z0);
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
 
@@ -614,7 +623,7 @@ __global__ void k_rebin_m(Launch L) {
             if (track) id = S.movF_out.id[i];
             global_deposit_f(L, S.W, p);
             int b = block_of(L, p.i, p.j, p.k);
-            int slot = atomicAdd(&S.bcount[b], 1);
+            int slot = warp_inc(&S.bcount[b]);
             if (slot < S.bcap[b]) store_p(S.binsF, S.bstart[b] + slot, p, id, track);
             else spill = true;
         }
@@ -640,7 +649,7 @@ __global__ void k_bin_scatter_m(Launch L, int s, PArr a, long long n, bool track
     if (p.fz >= 1.0f) p.fz = 0.99999994f;
     p.vx = (float)a.vx[i]; p.vy = (float)a.vy[i]; p.vz = (float)a.vz[i];
     int b = block_of(L, p.i, p.j, p.k);
-    int slot = atomicAdd(&S.bcount[b], 1);
+    int slot = warp_inc(&S.bcount[b]);
     long long id = track ? a.id[i] : 0;
     if (slot < S.bcap[b]) {
         store_p(S.binsF, S.bstart[b] + slot, p, id, track);
@@ -685,15 +694,52 @@ __global__ void k_flatten_list_m(Launch L, int s, PArr out, unsigned long long* 
     }
 }
 
+// every binned particle's deposit (a full recount of the node charges) with
+// the 2^-32 weights of global_deposit_f: on the PIC mesh through a shared tile
+// of split 32-bit counters (tile_deposit; integer sums, so the node charges
+// equal those of one global atomic per weight), on a finer IFE mesh straight
+// to its nodes
+template <bool HYBRID>
 __global__ void k_deposit_bins_m(Launch L) {
+    __shared__ int Wlo[8 * TILE_N];
+    __shared__ int Whi[8 * TILE_N];
     const SpeciesDev& S = L.sp[blockIdx.y];
-    int b = blockIdx.x;
-    int n = S.bcount[b];
-    long long st = S.bstart[b];
+    const int b = blockIdx.x;
+    const int n = S.bcount[b];
+    if (n == 0) return;
+    const long long st = S.bstart[b];
+    if (HYBRID) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            PF32 p;
+            load_p(S.binsF, st + i, p);
+            global_deposit_f(L, S.W, p);
+        }
+        return;
+    }
+    const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
+    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
+    for (int t = threadIdx.x; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    __syncthreads();
+    const int copy = threadIdx.x & 7;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         PF32 p;
         load_p(S.binsF, st + i, p);
-        global_deposit_f(L, S.W, p);
+        long long Wf[8];
+        fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+        unsigned W7[7];
+#pragma unroll
+        for (int l = 0; l < 7; ++l) W7[l] = (unsigned)Wf[l];
+        tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+        long long v = 0;
+        for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
+        if (!v) continue;
+        const int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        const int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
+            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
     }
 }
 __global__ void k_deposit_list_m(Launch L) {
@@ -877,7 +923,8 @@ cudaError_t launch_deposit_all_mixed(Ctx& c) {
     int ns = (int)c.sp.size();
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * c.mesh.nnodes, c.stream);
     if (ns == 0) return cudaGetLastError();
-    k_deposit_bins_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    if (c.refine > 1) k_deposit_bins_m<true><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    else k_deposit_bins_m<false><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
     k_deposit_list_m<<<dim3(64, ns), 256, 0, c.stream>>>(L);
     c.launches += 2;
     return cudaGetLastError();
