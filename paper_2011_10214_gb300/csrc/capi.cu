@@ -127,22 +127,26 @@ using namespace pf;
 
 static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
+// the six FP64 arrays (and ids) in one allocation: one cudaMalloc and one
+// cudaFree per buffer instead of seven (both cost a fraction of a millisecond)
 static PArr alloc_parr_raw(long long n, bool id, cudaError_t* err) {
     PArr a{};
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    char* b = nullptr;
+    *err = cudaMalloc(&b, sizeof(double) * m * (id ? 7 : 6));
+    if (*err != cudaSuccess) return a;
+    a.base = b;
     double** arr[6] = {&a.x, &a.y, &a.z, &a.vx, &a.vy, &a.vz};
-    *err = cudaSuccess;
-    for (auto p : arr) {
-        cudaError_t e = cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1));
-        if (e != cudaSuccess) *err = e;
-    }
-    if (id) {
-        cudaError_t e = cudaMalloc(&a.id, sizeof(long long) * (n > 0 ? n : 1));
-        if (e != cudaSuccess) *err = e;
-    }
+    for (int d = 0; d < 6; ++d) *arr[d] = (double*)(b + sizeof(double) * m * d);
+    if (id) a.id = (long long*)(b + sizeof(double) * m * 6);
     return a;
 }
 static void free_parr(PArr& a) {
-    cudaFree(a.x); cudaFree(a.y); cudaFree(a.z); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz); cudaFree(a.id);
+    if (a.base) {
+        cudaFree(a.base);
+    } else {
+        cudaFree(a.x); cudaFree(a.y); cudaFree(a.z); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz); cudaFree(a.id);
+    }
     a = PArr{};
 }
 
@@ -301,12 +305,8 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
         cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.mov_n);
-        cudaFree(s.binsF.cell); cudaFree(s.binsF.fx); cudaFree(s.binsF.fy); cudaFree(s.binsF.fz);
-        cudaFree(s.binsF.vx); cudaFree(s.binsF.vy); cudaFree(s.binsF.vz); cudaFree(s.binsF.id);
-        for (int q = 0; q < 2; ++q) {
-            cudaFree(s.movF[q].cell); cudaFree(s.movF[q].fx); cudaFree(s.movF[q].fy); cudaFree(s.movF[q].fz);
-            cudaFree(s.movF[q].vx); cudaFree(s.movF[q].vy); cudaFree(s.movF[q].vz); cudaFree(s.movF[q].id);
-        }
+        free_parrf(s.binsF);
+        for (int q = 0; q < 2; ++q) free_parrf(s.movF[q]);
     }
     if (c.pcg_exec) cudaGraphExecDestroy(c.pcg_exec);
     if (c.pcg_graph) cudaGraphDestroy(c.pcg_graph);

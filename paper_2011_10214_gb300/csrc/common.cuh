@@ -205,6 +205,7 @@ PF_D unsigned long long warp_inc64(unsigned long long* p) {
 }
 
 constexpr int BIN_MAX = 32767;
+constexpr int BIN_SCAN_THREADS = 1024;   // k_bin_scan's block
 // corner offsets in a (BLK+1)^3 tile, node order 000,100,010,110,001,101,011,111
 PF_HD constexpr int tile_corner(int l) {
     return (l & 1) + TILE * ((l >> 1) & 1) + TILE * TILE * ((l >> 2) & 1);

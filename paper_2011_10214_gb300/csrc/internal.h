@@ -17,11 +17,13 @@ namespace pf {
 struct PArr {            // FP64 mode: xi in cell units, physical velocity
     double *x, *y, *z, *vx, *vy, *vz;
     long long* id;
+    void* base;          // the one allocation holding all arrays (null: allocated one by one)
 };
 struct PArrF {           // MIXED mode: packed cell (i | j<<11 | k<<22), FP32 offset and velocity
     int* cell;
     float *fx, *fy, *fz, *vx, *vy, *vz;
     long long* id;
+    void* base;          // as PArr::base
 };
 
 // per-species parameters and pointers handed to kernels by value

@@ -469,11 +469,37 @@ __global__ void k_bin_caps(int nb, const int* cnt, int* cap, int* cnt_copy) {
     cnt_copy[b] = 0;
 }
 
+// exclusive scan of the bin capacities, one block of BIN_SCAN_THREADS: each
+// thread sums a contiguous run of bins, the runs' totals are scanned across
+// the block, then each thread writes its run's starts
 __global__ void k_bin_scan(int nb, const int* cap, long long* start, long long* total) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    long long run = 0;
-    for (int b = 0; b < nb; ++b) { start[b] = run; run += cap[b]; }
-    *total = run;
+    __shared__ long long wsum[BIN_SCAN_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (nb + BIN_SCAN_THREADS - 1) / BIN_SCAN_THREADS;
+    const int b0 = t * per, b1 = min(b0 + per, nb);
+    long long mine = 0;
+    for (int b = b0; b < b1; ++b) mine += cap[b];
+    long long inc = mine;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long v = lane < BIN_SCAN_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < BIN_SCAN_THREADS / 32) wsum[lane] = v;   // inclusive over warps
+    }
+    __syncthreads();
+    long long run = inc - mine + (w > 0 ? wsum[w - 1] : 0);
+    for (int b = b0; b < b1; ++b) { start[b] = run; run += cap[b]; }
+    if (t == BIN_SCAN_THREADS - 1) *total = wsum[BIN_SCAN_THREADS / 32 - 1];
 }
 
 // a bin already at capacity sends the particle to the waiting (mover) list
@@ -647,7 +673,7 @@ cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool) {
         cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
     }
     k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
-    k_bin_scan<<<1, 32, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
+    k_bin_scan<<<1, BIN_SCAN_THREADS, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
     e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }

@@ -948,20 +948,30 @@ cudaError_t launch_flatten_mixed_to_f64(Ctx& c, int s, PArr flat, unsigned long 
 }
 
 void free_parrf(PArrF& a) {
-    cudaFree(a.cell); cudaFree(a.fx); cudaFree(a.fy); cudaFree(a.fz); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz);
-    cudaFree(a.id);
+    if (a.base) {
+        cudaFree(a.base);
+    } else {
+        cudaFree(a.cell); cudaFree(a.fx); cudaFree(a.fy); cudaFree(a.fz); cudaFree(a.vx); cudaFree(a.vy);
+        cudaFree(a.vz); cudaFree(a.id);
+    }
     a = PArrF{};
 }
 
+// the seven 4-byte arrays (and 8-byte ids first, for their alignment) in one allocation
 cudaError_t alloc_parrf(PArrF& a, long long n, bool id) {
     free_parrf(a);
-    long long m = n > 0 ? n : 1;
-    cudaError_t e = cudaMalloc(&a.cell, sizeof(int) * m);
-    float** f[6] = {&a.fx, &a.fy, &a.fz, &a.vx, &a.vy, &a.vz};
-    for (auto p : f)
-        if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * m);
-    if (e == cudaSuccess && id) e = cudaMalloc(&a.id, sizeof(long long) * m);
-    return e;
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    const size_t mid = id ? sizeof(long long) * m : 0;
+    char* b = nullptr;
+    cudaError_t e = cudaMalloc(&b, mid + 7 * sizeof(float) * m);
+    if (e != cudaSuccess) return e;
+    a.base = b;
+    if (id) a.id = (long long*)b;
+    char* f = b + mid;
+    a.cell = (int*)f;
+    float** arr[6] = {&a.fx, &a.fy, &a.fz, &a.vx, &a.vy, &a.vz};
+    for (int d = 0; d < 6; ++d) *arr[d] = (float*)(f + sizeof(float) * m * (d + 1));
+    return cudaSuccess;
 }
 
 // (re)build MIXED bins of species s from a flat FP64 list of n particles
@@ -984,7 +994,7 @@ cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool)
         cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
     }
     k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
-    k_bin_scan<<<1, 32, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
+    k_bin_scan<<<1, BIN_SCAN_THREADS, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
     e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
