@@ -39,9 +39,55 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region: NVML
+    through ctypes every 2 ms (the driver's library; reads only), else
+    nvidia-smi every 200 ms."""
+
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, index=0):
+        self.p = None
+        self.nvml = None
+        self.sm, self.mx, self.reasons = [], [], set()
+        try:
+            self._start_nvml(index)
+        except Exception:
+            self.nvml = None
+            self._start_smi(index)
+
+    def _start_nvml(self, index):
+        import ctypes
+        import threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        dev = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(dev)) != 0:
+            raise RuntimeError("nvml handle")
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+            self.mx.append(float(mx.value))
+        self.nvml = lib
+        self.stop_flag = False
+
+        def run():
+            clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop_flag:
+                if lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0:
+                    self.sm.append(float(clk.value))
+                if get_reasons(dev, ctypes.byref(rs)) == 0:
+                    for bit, nm in self.REASONS.items():
+                        if rs.value & bit:
+                            self.reasons.add(nm)
+                time.sleep(0.002)
+
+        self.th = threading.Thread(target=run, daemon=True)
+        self.th.start()
+
+    def _start_smi(self, index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -53,6 +99,16 @@ class Clocks:
             self.p = None
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_flag = True
+            self.th.join(timeout=5)
+            try:
+                self.nvml.nvmlShutdown()
+            except Exception:
+                pass
+            sm = self.sm
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(self.mx) if self.mx else None,
+                    "reasons": sorted(self.reasons), "samples": len(sm), "sampler": "nvml 2 ms"}
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -76,7 +132,7 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "sampler": "nvidia-smi 200 ms"}
 
 
 def workload(name):
