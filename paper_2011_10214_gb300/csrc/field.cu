@@ -25,6 +25,13 @@ namespace pf {
 __constant__ TetTables cTf;
 __constant__ float cGradF[2][5][4][3];   // cTf.grad in FP32
 __constant__ float cVolF[5];
+// A node's share of one cube, summed over the cube's tets that contain it: the
+// node is local corner c8 of a cube of parity p; G[p][c8][corner][d] = sum over
+// those tets t and their vertices v at that corner of vol_t grad_t,v[d] (h = 1)
+// and V[p][c8] = sum of their vol_t.  Away from interface tets the node field
+// is -(sum over present cubes of G phi) / (h sum of V).
+__constant__ float cNodeG[2][8][8][3];
+__constant__ float cNodeV[2][8];
 
 // ---- right-hand side ----------------------------------------------------------
 struct RhsArgs {
@@ -224,26 +231,79 @@ __global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, cons
                                                                     const float* itf, const double* qT,
                                                                     const double* phi, float4* Ef) {
     __shared__ float ph[NE_TX * NE_TY * NE_TZ];
+    // the interface-tet masks of the cubes around the brick's nodes
+    constexpr int CX = NE_BX + 1, CY = NE_BY + 1, CZ = NE_BZ + 1;
+    __shared__ unsigned char smk[CX * CY * CZ];
+    __shared__ int sib[CX * CY * CZ];                      // and their first interface record
+    __shared__ unsigned char sLp[NE_TX * NE_TY * NE_TZ];   // Lpos of the staged nodes
+    // the per-cube tables (neighbouring nodes differ in parity, so a warp's
+    // table reads diverge; constant memory would serialise them)
+    __shared__ float sG[2][8][8][3];
+    __shared__ float sV[2][8];
     const int i0 = blockIdx.x * NE_BX, j0 = blockIdx.y * NE_BY, k0 = blockIdx.z * NE_BZ;
     const int tid = threadIdx.x + NE_BX * (threadIdx.y + NE_BY * threadIdx.z);
+    for (int q = tid; q < 2 * 8 * 8 * 3; q += NE_BX * NE_BY * NE_BZ) (&sG[0][0][0][0])[q] = (&cNodeG[0][0][0][0])[q];
+    if (tid < 16) (&sV[0][0])[tid] = (&cNodeV[0][0])[tid];
     for (int q = tid; q < NE_TX * NE_TY * NE_TZ; q += NE_BX * NE_BY * NE_BZ) {
         const int gi = i0 - 1 + q % NE_TX, gj = j0 - 1 + (q / NE_TX) % NE_TY, gk = k0 - 1 + q / (NE_TX * NE_TY);
         const bool in = gi >= 0 && gj >= 0 && gk >= 0 && gi < m.NX && gj < m.NY && gk < m.NZ;
-        ph[q] = in ? (float)phi[node_id(m, gi, gj, gk)] : 0.0f;
+        const long long nid = in ? node_id(m, gi, gj, gk) : 0;
+        ph[q] = in ? (float)phi[nid] : 0.0f;
+        sLp[q] = in ? Lpos[nid] : (unsigned char)0;
+    }
+    for (int q = tid; q < CX * CY * CZ; q += NE_BX * NE_BY * NE_BZ) {
+        const int ci = i0 - 1 + q % CX, cj = j0 - 1 + (q / CX) % CY, ck = k0 - 1 + q / (CX * CY);
+        const bool in = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
+        const long long cell = in ? cell_id(m, ci, cj, ck) : 0;
+        smk[q] = in ? imask[cell] : (unsigned char)0;
+        sib[q] = in ? ibase[cell] : 0;
     }
     __syncthreads();
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y, k = k0 + threadIdx.z;
     if (i >= m.NX || j >= m.NY || k >= m.NZ) return;
-    float apl[3] = {0.f, 0.f, 0.f}, vpl = 0.f, aal[3] = {0.f, 0.f, 0.f}, val = 0.f;
     const float ih = 1.0f / (float)m.h, V3 = (float)m.h * (float)m.h * (float)m.h;
+    // a node whose cubes hold no interface tet: every tet around it lies on one
+    // side, so the plasma-side preference changes nothing; the closed form
+    bool regular = true;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) {
+        const int ci = i - (c8 & 1), cj = j - ((c8 >> 1) & 1), ck = k - ((c8 >> 2) & 1);
+        const bool present = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
+        if (present && smk[(ci - i0 + 1) + CX * ((cj - j0 + 1) + CY * (ck - k0 + 1))]) regular = false;
+    }
+    if (regular) {
+        float e[3] = {0.f, 0.f, 0.f}, vol = 0.f;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            const int a = c8 & 1, b = (c8 >> 1) & 1, c = (c8 >> 2) & 1;
+            const int ci = i - a, cj = j - b, ck = k - c;
+            const bool present = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
+            const int p = (ci + cj + ck) & 1;
+            const float w = present ? 1.0f : 0.0f;
+            // the cube's corner (ci, cj, ck) in the staged brick (halo entries are zero)
+            const int tb = (ci - i0 + 1) + NE_TX * ((cj - j0 + 1) + NE_TY * (ck - k0 + 1));
+#pragma unroll
+            for (int cn = 0; cn < 8; ++cn) {
+                const float f = w * ph[tb + (cn & 1) + NE_TX * (((cn >> 1) & 1) + NE_TY * ((cn >> 2) & 1))];
+                e[0] += sG[p][c8][cn][0] * f;
+                e[1] += sG[p][c8][cn][1] * f;
+                e[2] += sG[p][c8][cn][2] * f;
+            }
+            vol += w * sV[p][c8];
+        }
+        const float s = -ih / vol;
+        Ef[node_id(m, i, j, k)] = make_float4(s * e[0], s * e[1], s * e[2], 0.f);
+        return;
+    }
+    float apl[3] = {0.f, 0.f, 0.f}, vpl = 0.f, aal[3] = {0.f, 0.f, 0.f}, val = 0.f;
     for (int c8 = 0; c8 < 8; ++c8) {
         const int a = c8 & 1, b = (c8 >> 1) & 1, c = (c8 >> 2) & 1;
         const int ci = i - a, cj = j - b, ck = k - c;
         if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
-        const long long cell = cell_id(m, ci, cj, ck);
-        const unsigned mk = imask[cell];
+        const int cq = (ci - i0 + 1) + CX * ((cj - j0 + 1) + CY * (ck - k0 + 1));
+        const unsigned mk = smk[cq];
         const int p = (ci + cj + ck) & 1;
-        int T = ibase[cell];
+        int T = sib[cq];
         // the cube's corner (ci, cj, ck) in the staged brick
         const int tb = (ci - i0 + 1) + NE_TX * ((cj - j0 + 1) + NE_TY * (ck - k0 + 1));
         for (int t = 0; t < 5; ++t) {
@@ -282,7 +342,7 @@ __global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, cons
                                 pv[2] * cGradF[p][t][2][d] + pv[3] * cGradF[p][t][3][d]) * ih;
                     const float V = cVolF[t] * V3;
                     const int a0 = lv0 & 1, b0 = (lv0 >> 1) & 1, c0 = (lv0 >> 2) & 1;
-                    if (Lpos[node_id(m, ci + a0, cj + b0, ck + c0)]) {
+                    if (sLp[tb + a0 + NE_TX * (b0 + NE_TY * c0)]) {
                         for (int d = 0; d < 3; ++d) apl[d] += V * g[d];
                         vpl += V;
                     }
@@ -626,9 +686,28 @@ cudaError_t set_field_tables(const TetTables& t) {
             for (int a = 0; a < 4; ++a)
                 for (int d = 0; d < 3; ++d) g[p][q][a][d] = (float)t.grad[p][q][a][d];
     for (int q = 0; q < 5; ++q) v[q] = (float)t.vol[q];
+    // per-cube node tables (see cNodeG), summed in FP64
+    double G[2][8][8][3] = {}, V[2][8] = {};
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 5; ++q)
+            for (int a = 0; a < 4; ++a) {
+                const int c8 = t.vert[p][q][a];   // the tet contains local corner c8
+                V[p][c8] += t.vol[q];
+                for (int b = 0; b < 4; ++b)
+                    for (int d = 0; d < 3; ++d) G[p][c8][t.vert[p][q][b]][d] += t.vol[q] * t.grad[p][q][b][d];
+            }
+    float Gf[2][8][8][3], Vf[2][8];
+    for (int p = 0; p < 2; ++p)
+        for (int c8 = 0; c8 < 8; ++c8) {
+            Vf[p][c8] = (float)V[p][c8];
+            for (int cn = 0; cn < 8; ++cn)
+                for (int d = 0; d < 3; ++d) Gf[p][c8][cn][d] = (float)G[p][c8][cn][d];
+        }
     cudaError_t e = cudaMemcpyToSymbol(cTf, &t, sizeof(TetTables));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGradF, g, sizeof(g));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cVolF, v, sizeof(v));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cNodeG, Gf, sizeof(Gf));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cNodeV, Vf, sizeof(Vf));
     return e;
 }
 
