@@ -311,6 +311,8 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (c.pcg_exec) cudaGraphExecDestroy(c.pcg_exec);
     if (c.pcg_graph) cudaGraphDestroy(c.pcg_graph);
     if (c.ev_ok) for (int e = 0; e < 16; ++e) cudaEventDestroy(c.ev[e]);
+    for (cudaEvent_t e : c.step_ev) cudaEventDestroy(e);
+    if (c.spill_host) cudaFreeHost(c.spill_host);
     delete ctx;
 }
 
@@ -927,30 +929,80 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
     snapshot_counters(ctx, before, &it0, &ot0, &l0);
     float ph[8] = {0};
     bool mixed = c.precision == PIFEPIC_MIXED;
-    for (int it = 0; it < nsteps; ++it) {
-        CUDA_OK(cudaEventRecord(c.ev[0], c.stream));
-        CUDA_OK(mixed ? launch_push_mixed(c) : launch_push(c));
-        CUDA_OK(cudaEventRecord(c.ev[1], c.stream));
-        CUDA_OK(mixed ? launch_movers_mixed(c) : launch_movers(c));
-        CUDA_OK(cudaEventRecord(c.ev[2], c.stream));
-        CUDA_OK(mixed ? launch_inject_mixed(c) : launch_inject(c));
-        CUDA_OK(cudaEventRecord(c.ev[3], c.stream));
-        CUDA_OK(mixed ? launch_rebin_mixed(c) : launch_rebin(c));
-        CUDA_OK(cudaEventRecord(c.ev[4], c.stream));
-        if (!c.external_E) CUDA_OK(run_solve(c));
-        CUDA_OK(cudaEventRecord(c.ev[5], c.stream));
-        c.step_no += 1;
-        CUDA_OK(cudaEventSynchronize(c.ev[5]));
-        if (c.ph_species >= 0) {
-            pifepic_status g = regrow_if_spilling(ctx, c.ph_species);
-            if (g) return g;
-        }
-        float t;
+    // The host does not wait for each step: every step records its six phase
+    // events into one of STEP_RING sets, and a set is read (after its last
+    // event) only when it is reused and at the end, so the host keeps the
+    // stream fed.  A photoemitting species' waiting list is watched with a
+    // lag of one step: each step copies its length to pinned memory before
+    // its last event, and the host reads step it-1's copy while step it is
+    // queued; only a list past a quarter of its capacity stops the stream for
+    // a rebuild (the lists are sized for more than one step of growth).
+    constexpr int STEP_RING = 64;
+    if (c.step_ev.empty()) {
+        c.step_ev.resize(6 * STEP_RING);
+        for (auto& e : c.step_ev) CUDA_OK(cudaEventCreate(&e));
+    }
+    if (!c.spill_host && cudaMallocHost(&c.spill_host, sizeof(unsigned long long) * STEP_RING) != cudaSuccess) {
+        cudaGetLastError();
+        c.spill_host = nullptr;
+        FAIL(PIFEPIC_ENOMEM, "pinned step buffer");
+    }
+    const bool each = c.ph_species >= 0;
+    auto check_spill = [&](int slot) -> pifepic_status {
+        const Species& q = c.sp[c.ph_species];
+        if ((long long)c.spill_host[slot] * 4 <= q.mcap) return PIFEPIC_OK;
+        CUDA_OK(cudaStreamSynchronize(c.stream));
+        return regrow_if_spilling(ctx, c.ph_species);
+    };
+    std::vector<char> unread(STEP_RING, 0);
+    auto read_set = [&](int slot) -> cudaError_t {
+        cudaEvent_t* ev = &c.step_ev[6 * slot];
+        cudaError_t e = cudaEventSynchronize(ev[5]);
+        if (e != cudaSuccess) return e;
         const int map[5] = {0, 1, 2, 3, 5};   // push, movers, inject, rebin, solve(+rhs+E)
         for (int k = 0; k < 5; ++k) {
-            CUDA_OK(cudaEventElapsedTime(&t, c.ev[k], c.ev[k + 1]));
+            float t;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            if (e != cudaSuccess) return e;
             ph[map[k]] += t;
         }
+        unread[slot] = 0;
+        return cudaSuccess;
+    };
+    for (int it = 0; it < nsteps; ++it) {
+        const int slot = it % STEP_RING;
+        if (unread[slot]) CUDA_OK(read_set(slot));
+        cudaEvent_t* ev = &c.step_ev[6 * slot];
+        CUDA_OK(cudaEventRecord(ev[0], c.stream));
+        CUDA_OK(mixed ? launch_push_mixed(c) : launch_push(c));
+        CUDA_OK(cudaEventRecord(ev[1], c.stream));
+        CUDA_OK(mixed ? launch_movers_mixed(c) : launch_movers(c));
+        CUDA_OK(cudaEventRecord(ev[2], c.stream));
+        CUDA_OK(mixed ? launch_inject_mixed(c) : launch_inject(c));
+        CUDA_OK(cudaEventRecord(ev[3], c.stream));
+        CUDA_OK(mixed ? launch_rebin_mixed(c) : launch_rebin(c));
+        CUDA_OK(cudaEventRecord(ev[4], c.stream));
+        if (!c.external_E) CUDA_OK(run_solve(c));
+        if (each)
+            CUDA_OK(cudaMemcpyAsync(c.spill_host + slot, c.sp[c.ph_species].mov_n, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, c.stream));
+        CUDA_OK(cudaEventRecord(ev[5], c.stream));
+        c.step_no += 1;
+        unread[slot] = 1;
+        if (each && it > 0) {   // the previous step, while this one runs
+            const int prev = (it - 1) % STEP_RING;
+            if (unread[prev]) CUDA_OK(read_set(prev));
+            pifepic_status g = check_spill(prev);
+            if (g) return g;
+        }
+    }
+    for (int k = 0; k < STEP_RING; ++k) {   // the sets not read yet, oldest first
+        const int slot = (nsteps + k) % STEP_RING;
+        if (unread[slot]) CUDA_OK(read_set(slot));
+    }
+    if (each && nsteps > 0) {
+        pifepic_status g = check_spill((nsteps - 1) % STEP_RING);
+        if (g) return g;
     }
     return fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps, ot0);
 }

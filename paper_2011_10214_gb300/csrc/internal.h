@@ -240,6 +240,8 @@ struct Ctx {
     bool tmap_ok = false;
     // timers
     cudaEvent_t ev[16];
+    std::vector<cudaEvent_t> step_ev;   // phase events of up to STEP_RING steps in flight (created on first step)
+    unsigned long long* spill_host = nullptr;   // pinned: a photoemitting species' waiting-list length per step
     bool ev_ok = false;
     pifepic_stats stats{};
     int last_iters = 0;
