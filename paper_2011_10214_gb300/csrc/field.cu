@@ -597,9 +597,10 @@ __global__ void k_stat_pack(StatArgs a) {
     __shared__ long long part[8];
     const int t = threadIdx.x;
     for (int i = t; i < MAX_SPECIES * NCTR; i += blockDim.x) a.out->ctr[i] = a.ctrall[i];
-    for (int s = 0; s < MAX_SPECIES; ++s) {
+    if (t < MAX_SPECIES) a.out->count[t] = 0;
+    for (int s = 0; s < a.nspecies && s < MAX_SPECIES; ++s) {   // (a.nspecies is the same in every thread)
         long long v = 0;
-        if (s < a.nspecies && a.bcount[s])
+        if (a.bcount[s])
             for (int b = t; b < a.nblocks; b += blockDim.x) v += a.bcount[s][b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -608,8 +609,8 @@ __global__ void k_stat_pack(StatArgs a) {
         if (t == 0) {
             long long tot = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
-            if (s < a.nspecies && a.mov_n[s]) tot += (long long)a.mov_n[s][0];
-            a.out->count[s] = s < a.nspecies ? tot : 0;
+            if (a.mov_n[s]) tot += (long long)a.mov_n[s][0];
+            a.out->count[s] = tot;
         }
         __syncthreads();
     }
