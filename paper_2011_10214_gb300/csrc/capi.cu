@@ -304,7 +304,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (c.refine > 1) { cudaFree(c.Ep); cudaFree(c.Efp); }
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
-        cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.mov_n);
+        cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.bstay); cudaFree(s.mov_n);
         free_parrf(s.binsF);
         for (int q = 0; q < 2; ++q) free_parrf(s.movF[q]);
     }

@@ -35,6 +35,7 @@ struct SpeciesDev {
     const long long* bstart;        // [nblocks] first slot of each bin
     const int* bcap;                // [nblocks] capacity
     int* bcount;                    // [nblocks] live particles
+    int* bstay;                     // [nblocks] MIXED: the bin's stayers after the push (its arrivals follow)
     PArr mov_in, mov_out;           // mover lists (previous-step spill, this step)
     PArrF movF_in, movF_out;
     unsigned long long* mov_in_n;   // counters (device)
@@ -89,6 +90,7 @@ struct Species {
     long long* bstart = nullptr;
     int* bcap = nullptr;
     int* bcount = nullptr;
+    int* bstay = nullptr;
     unsigned long long* mov_n = nullptr;   // [2]
     unsigned long long* W = nullptr;
     unsigned long long* surf = nullptr;

@@ -619,7 +619,7 @@ Launch make_launch(Ctx& c) {
         SpeciesDev& d = L.sp[s];
         d.k = q.k; d.khalf = 0.5 * q.k;
         d.bins = q.bins; d.binsF = q.binsF;
-        d.bstart = q.bstart; d.bcap = q.bcap; d.bcount = q.bcount;
+        d.bstart = q.bstart; d.bcap = q.bcap; d.bcount = q.bcount; d.bstay = q.bstay;
         d.mov_in = q.mov[0]; d.mov_out = q.mov[1];
         d.movF_in = q.movF[0]; d.movF_out = q.movF[1];
         d.mov_in_n = q.mov_n; d.mov_out_n = q.mov_n + 1;

@@ -349,7 +349,10 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
     const int b = blockIdx.x;
     const SpeciesDev& S = L.sp[s];
     const int n = S.bcount[b];
-    if (n == 0) return;
+    if (n == 0) {
+        if (threadIdx.x == 0) S.bstay[b] = 0;
+        return;
+    }
     const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
     const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -390,7 +393,11 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) { cp_async_wait_all(); return; }
+    if (!s_ok) {   // (the bin is left as it was; the error flag reports it)
+        cp_async_wait_all();
+        if (tid == 0) S.bstay[b] = n;
+        return;
+    }
     const bool track = L.track;
     const float kf = (float)S.k;
     const int refl = S.reflect;
@@ -496,7 +503,10 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         if (c_lost) atomicAdd(&sctr[C_LOST], c_lost);
     }
     __syncthreads();
-    if (tid == 0) S.bcount[b] = (s_fail || s_total == 0) ? 0 : s_total - 1;
+    if (tid == 0) {
+        S.bcount[b] = (s_fail || s_total == 0) ? 0 : s_total - 1;
+        S.bstay[b] = S.bcount[b];
+    }
     tile_flush19(L, S.W, Wt, x0, y0, z0);
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
@@ -607,6 +617,9 @@ __global__ void k_inject_m(Launch L, InjArgs a, ObjF of, float dthf) {
 // survivors of the spill list, injected and photoemitted particles) deposits
 // its charge here, in one warp-coherent pass, then joins its bin or, if the
 // bin is full, next step's spill list
+// DEFER: a mover stored into a bin deposits later with the bin's other arrivals
+// (k_deposit_arrivals_m); one that waits in the list deposits here
+template <bool DEFER>
 __global__ void k_rebin_m(Launch L) {
     const int s = blockIdx.y;
     const SpeciesDev& S = L.sp[s];
@@ -621,11 +634,11 @@ __global__ void k_rebin_m(Launch L) {
         if (i < n) {
             load_p(S.movF_out, i, p);
             if (track) id = S.movF_out.id[i];
-            global_deposit_f(L, S.W, p);
             int b = block_of(L, p.i, p.j, p.k);
             int slot = warp_inc(&S.bcount[b]);
             if (slot < S.bcap[b]) store_p(S.binsF, S.bstart[b] + slot, p, id, track);
             else spill = true;
+            if (!DEFER || spill) global_deposit_f(L, S.W, p);
         }
         long long slot = warp_reserve(S.mov_in_n, spill);
         if (spill) {
@@ -907,14 +920,56 @@ cudaError_t launch_photo_mixed(Ctx& c) {
     return cudaGetLastError();
 }
 
+// the bin's arrivals of this step, slots [bstay, bcount), deposit through a
+// shared tile of split 32-bit counters with the 2^-32 weights of
+// global_deposit_f (integer sums: the node charges equal those of one global
+// atomic per weight, with an eighth of the global atomics or fewer)
+__global__ void k_deposit_arrivals_m(Launch L) {
+    __shared__ int Wlo[8 * TILE_N];
+    __shared__ int Whi[8 * TILE_N];
+    const SpeciesDev& S = L.sp[blockIdx.y];
+    const int b = blockIdx.x;
+    const int n0 = S.bstay[b], n1 = S.bcount[b];   // (bcount clamped to the capacity)
+    if (n1 <= n0) return;
+    const long long st = S.bstart[b];
+    const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
+    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
+    for (int t = threadIdx.x; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    __syncthreads();
+    const int copy = threadIdx.x & 7;
+    for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
+        PF32 p;
+        load_p(S.binsF, st + i, p);
+        long long Wf[8];
+        fixed_weights_f(weights_f(p.fx, p.fy, p.fz), Wf);
+        unsigned W7[7];
+#pragma unroll
+        for (int l = 0; l < 7; ++l) W7[l] = (unsigned)Wf[l];
+        tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+        long long v = 0;
+        for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
+        if (!v) continue;
+        const int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        const int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
+        if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
+            atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
+    }
+}
+
 cudaError_t launch_rebin_mixed(Ctx& c) {
     Launch L = make_launch(c);
     int ns = (int)c.sp.size();
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n, 0, sizeof(unsigned long long), c.stream);
-    k_rebin_m<<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
+    const bool defer = c.refine == 1;   // (a finer IFE mesh takes the deposits node by node)
+    if (defer) k_rebin_m<true><<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
+    else k_rebin_m<false><<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
     k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
+    if (defer) k_deposit_arrivals_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
     k_step_advance<<<1, 1, 0, c.stream>>>((long long*)(c.scal + 42));
-    c.launches += 3;
+    c.launches += defer ? 4 : 3;
     return cudaGetLastError();
 }
 
@@ -992,7 +1047,9 @@ cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool)
         cudaMalloc(&q.bcap, sizeof(int) * c.nblocks);
         cudaMalloc(&q.bcount, sizeof(int) * c.nblocks);
         cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
+        cudaMalloc(&q.bstay, sizeof(int) * c.nblocks);
     }
+    cudaMemsetAsync(q.bstay, 0, sizeof(int) * c.nblocks, c.stream);
     k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
     k_bin_scan<<<1, BIN_SCAN_THREADS, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
     e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
