@@ -133,6 +133,35 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
     return eps * y;
 }
 
+// (A x)_n in FP64 for the refinement residual: a regular row with all six
+// neighbours present (no interface tet, not Dirichlet) takes the interior
+// closed form of apply_row_ld's regular branch -- eps [(4 or 6) h x_n - 4 h/6
+// (six face neighbours) - (even nodes) 2 h/12 (twelve edge neighbours)], the
+// same sums in the same order, without the per-node integer weights and their
+// conversions (FP64 issues slowly on this part); any other row goes through
+// apply_row_ld
+template <typename LD>
+static __device__ __forceinline__ double apply_row64(const FieldArgs& f, long long n, int i, int j, int k, LD ld,
+                                                     const double* coef) {
+    const Mesh& m = f.m;
+    const int ty = f.ntype[n];
+    if (ty >= 0 || ty == -3 || i == 0 || j == 0 || k == 0 || i == m.nx || j == m.ny || k == m.nz)
+        return apply_row_ld<double>(f, n, i, j, k, ld, coef);
+    const long long sx = 1, sy = m.NX, sz = (long long)m.NX * m.NY;
+    const double eps = ty == -2 ? f.o.eps_minus : f.o.eps_plus;
+    const bool odd = (i + j + k) & 1;
+    double y = (odd ? 4.0 : 6.0) * m.h * ld(n);
+    const double ax = ld(n - sx) + ld(n + sx), ay = ld(n - sy) + ld(n + sy), az = ld(n - sz) + ld(n + sz);
+    y -= (4.0 * m.h6) * ((ax + ay) + az);
+    if (!odd) {
+        const double dxy = ((ld(n - sx - sy) + ld(n + sx - sy)) + ld(n - sx + sy)) + ld(n + sx + sy);
+        const double dxz = ((ld(n - sx - sz) + ld(n + sx - sz)) + ld(n - sx + sz)) + ld(n + sx + sz);
+        const double dyz = ((ld(n - sy - sz) + ld(n + sy - sz)) + ld(n - sy + sz)) + ld(n + sy + sz);
+        y -= (2.0 * m.h12) * ((dxy + dxz) + dyz);
+    }
+    return eps * y;
+}
+
 // Row kinds for the masked regular stencil: the six neighbour-presence flags,
 // the node parity, the region, and whether the row is general (an interface
 // patch row) or Dirichlet (zero).

@@ -356,7 +356,10 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
             x[s] = r[s] = z[s] = p[s] = q[s] = (T)0;
             if (n < b1) {
                 const double bn = a.b[n];
-                const double rn = (f.ntype[n] == -3) ? 0.0 : bn - row_at<double>(f, n, pk[s], ldu, f.coef);
+                const double rn = (f.ntype[n] == -3) ? 0.0
+                                                     : bn - apply_row64(f, n, (int)(pk[s] & 2047u),
+                                                                        (int)((pk[s] >> 11) & 2047u), (int)(pk[s] >> 22),
+                                                                        ldu, f.coef);
                 r[s] = (T)rn;
                 z[s] = dv[s] * r[s];
                 p[s] = z[s];
@@ -592,7 +595,9 @@ __global__ void __launch_bounds__(GLOB_THREADS, 2) k_pcg_glob(GlobArgs a) {
             int i, j, k;
             node_ijk(f.m, n, i, j, k);
             const double bn = a.b[n];
-            const double rn = (f.ntype[n] == -3) ? 0.0 : bn - apply_row<double, true>(f, n, i, j, k, a.u, f.coef);
+            const double rn =
+                (f.ntype[n] == -3) ? 0.0
+                                   : bn - apply_row64(f, n, i, j, k, [&](long long m) { return __ldcg(a.u + m); }, f.coef);
             const T rt = (T)rn, zt = dinv[n] * rt;
             r[n] = rt; zb[zc][n] = zt; p[n] = zt; x[n] = (T)0;
             v3[0] += bn * bn;
