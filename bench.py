@@ -193,7 +193,7 @@ SOLVE_BYTES_PER_NODE_ITER = {"mixed": 7 * 4, "fp64": 7 * 8}
 # DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 32^3 sphere
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch's particles); None when not measured
 # for the current kernel
-PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (115829248 + 58601472) / 4074575, "fp64": None}
+PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (115822080 + 58377216) / 4074575, "fp64": None}
 NSM, DFMA_PER_CLK_SM = 152, 2          # GB300: 2 FP64 FMA per SM per clock
 
 
