@@ -79,20 +79,29 @@ __global__ void k_rhs(FieldArgs f, RhsArgs a, const unsigned char* imask, const 
     if (ty >= 0) {   // touches interface tets: flux-jump load
         int i, j, k;
         node_ijk(m, n, i, j, k);
+        // the cubes' masks and first records first (independent loads), then
+        // each interface tet's record index from the mask (no load chain)
+        unsigned mk[8];
+        int T0[8];
+#pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) {
             int aa, bb, cc; loff(c8, aa, bb, cc);
-            int ci = i - aa, cj = j - bb, ck = k - cc;
-            if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
-            long long cell = cell_id(m, ci, cj, ck);
-            unsigned mk = imask[cell];
-            if (!mk) continue;
-            int p = (ci + cj + ck) & 1;
-            int T = ibase[cell];
+            const int ci = i - aa, cj = j - bb, ck = k - cc;
+            const bool in = !(ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz);
+            const long long cell = in ? cell_id(m, ci, cj, ck) : 0;
+            mk[c8] = in ? imask[cell] : 0u;
+            T0[c8] = in ? ibase[cell] : 0;
+        }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            if (!mk[c8]) continue;
+            int aa, bb, cc; loff(c8, aa, bb, cc);
+            const int p = (i - aa + j - bb + k - cc) & 1;
             for (int t = 0; t < 5; ++t) {
-                if (!((mk >> t) & 1)) continue;
+                if (!((mk[c8] >> t) & 1)) continue;
+                const int T = T0[c8] + __popc(mk[c8] & ((1u << t) - 1u));
                 for (int v = 0; v < 4; ++v)
                     if (cTf.vert[p][t][v] == c8) F += qT[T] * it_data[(long long)T * IT_STRIDE + IT_C + v];
-                ++T;
             }
         }
     }
