@@ -564,32 +564,6 @@ cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double
     return e;
 }
 
-cudaError_t read_pcg_state(Ctx& c) {
-    PcgState hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, c.scal, sizeof(PcgState), cudaMemcpyDeviceToHost, c.stream);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(c.stream);
-    c.last_iters = hs.it; c.last_relres = hs.relres; c.last_conv = hs.converged;
-    return e;
-}
-
-cudaError_t launch_surface_diag(Ctx& c, double* out2) {
-    double* d = diag_dev(c);
-    RhsArgs a = rargs(c);
-    if (c.nit > 0)
-        k_surface_diag<<<nb(c.nit), 256, 0, c.stream>>>(c.mesh, c.nit, c.it_cell, c.it_t, c.it_data, c.qT, c.phi,
-                                                        c.red, c.red_ticket, d + 1);
-    else
-        cudaMemsetAsync(d + 1, 0, sizeof(double), c.stream);
-    if (c.ncut > 0)
-        k_surface_charge<<<nb(c.ncut), 256, 0, c.stream>>>(a, c.red, c.red_ticket, d);
-    else
-        cudaMemsetAsync(d, 0, sizeof(double), c.stream);
-    cudaError_t e = cudaMemcpyAsync(out2, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(c.stream);
-}
-
 struct StatArgs {
     const unsigned long long* ctrall;
     const int* bcount[MAX_SPECIES];

@@ -297,7 +297,6 @@ cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
 void plan_pcg(Ctx& c);                                 // pcg_coop.cu
 cudaError_t launch_rhs(Ctx& c);
 cudaError_t launch_pcg(Ctx& c);
-cudaError_t launch_surface_diag(Ctx& c, double* out2);   // [charge, potential]
 // diag: also the surface charge and mean surface potential (a few kernels)
 cudaError_t gather_stats(Ctx& c, StatPack* out, bool diag);
 cudaError_t launch_qtets(Ctx& c);
