@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         T rz = (T)t3[2];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
-        // inner target: the final tolerance, or (MIXED) a 1e-4 reduction of this residual
+        // inner target: the final tolerance, or (MIXED) max(margin tol |b|, reduction |r0|) (set_refinement)
         const T rr_stop = (T)(MIXED ? fmax(margin2 * tol2 * bb, inner_red2 * rr) : tol2 * bb);
         ++outer;
         T beta = (T)0, rr_in = (T)rr;
