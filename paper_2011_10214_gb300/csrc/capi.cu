@@ -19,7 +19,6 @@ cudaError_t set_particle_tables(const TetTables& t);
 cudaError_t set_mixed_tables(const TetTables& t);
 cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double* relres);
 int solve_graph_fixed_kernels(const Ctx& c);
-cudaError_t launch_pcg_mixed(Ctx& c);
 cudaError_t alloc_parrf(PArrF& a, long long n, bool id);
 void free_parrf(PArrF& a);
 pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
@@ -892,8 +891,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
 }
 
 static cudaError_t run_solve(Ctx& c) {
-    if (c.precision == PIFEPIC_MIXED) return launch_pcg_mixed(c);
-    return launch_pcg(c);
+    return launch_pcg(c);   // (the solve graph holds the precision's kernels)
 }
 
 pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {

@@ -546,9 +546,7 @@ cudaError_t launch_pcg(Ctx& c) {
     if (e != cudaSuccess) return e;
     return cudaGraphLaunch(c.pcg_exec, c.stream);
 }
-cudaError_t launch_pcg_mixed(Ctx& c) { return launch_pcg(c); }
 
-cudaError_t launch_rhs(Ctx& c) { return cudaSuccess; }
 
 // standalone solve with an external node load (solver parity)
 cudaError_t launch_solve_external(Ctx& c, const double* Fdev, int* iters, double* relres) {

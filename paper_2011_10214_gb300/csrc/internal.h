@@ -295,7 +295,6 @@ cudaError_t launch_E_to_pic(const Ctx& c, cudaStream_t st, bool both);
 cudaError_t launch_field_lift(Ctx& c);
 cudaError_t build_pcg_graph(Ctx& c);                   // field.cu
 void plan_pcg(Ctx& c);                                 // pcg_coop.cu
-cudaError_t launch_rhs(Ctx& c);
 cudaError_t launch_pcg(Ctx& c);
 // diag: also the surface charge and mean surface potential (a few kernels)
 cudaError_t gather_stats(Ctx& c, StatPack* out, bool diag);
