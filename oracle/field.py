@@ -11,7 +11,7 @@ non-homogeneous IFE solution is phi_h = u_h + phi_J with phi_J the element-wise
 jump function (zero at every node, flux jump q on interface tets) and u_h in
 the IFE space solving a_h(u_h, psi_i) = F_i - int_Gamma q psi_i - a_h(phi_J, psi_i).
 
-Readings where the paper is silent (also in the design doc):
+Readings where the paper is silent:
   * load vector F_i = sum_p q_p S_i(x_p), S_i the trilinear (Q1) weight of the
     PIC cell -- the scatter result itself, which conserves charge exactly;
   * surface charge: each cut PIC cell c collects the charge Q_c of the

@@ -10,7 +10,7 @@ Follows arXiv:2011.10214:
     on interface elements to satisfy the interface conditions, with the same
     degrees of freedom (nodal values) as the standard linear FE space.
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   * 5-tet split: one central tet on the cube's four globally even vertices
     ((i+j+k) even), four corner tets, each an odd vertex with its three axis
     neighbours.  Face diagonals then match between neighbouring cubes.

@@ -9,7 +9,7 @@ Oracle; test infrastructure only.  Follows arXiv:2011.10214:
   * Sec. 5.2.2: particles injected at an angle (drifting plasma); particles
     hitting the object surface are collected and their charge accumulated.
 
-Readings where the paper is silent (also in the design doc):
+Readings where the paper is silent:
   * positions in cell units xi = (x - origin)/h; velocities physical;
   * gather: trilinear weights of the PIC cell, node order 000,100,...,111,
     w = (wx*wy)*wz, E_p accumulated left to right; leapfrog

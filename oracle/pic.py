@@ -6,7 +6,7 @@ injection at open faces each step, absorption at open faces) and Sec. 5.2.2
 (collection at the object surface with accumulated charge; the floating
 potential follows from the non-homogeneous flux jump, Sec. 3.1.2).
 
-One step (reading of the loop's order, also in the design doc):
+One step (a reading of the loop's order):
   1. gather + push every particle with the current node field;
   2. mirror particles back at reflecting faces; remove particles outside the
      domain, then collect particles inside the object (their charge goes to the

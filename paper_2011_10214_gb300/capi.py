@@ -361,7 +361,9 @@ class Simulation:
 
 def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter=150, load=True, inject=True,
                 stream=None):
-    """Build a Simulation for a workload dict of paper_2011_10214_gb300.workloads."""
+    """Build a Simulation for a workload dict of paper_2011_10214_gb300.workloads
+    (the macro-particle weights are the workload's own, workloads.macro_weight)."""
+    from .workloads import macro_weight
     sim = Simulation(cfg["n"], cfg["h"], cfg["dt"], cfg.get("origin", (0.0, 0.0, 0.0)), precision, pcg_tol,
                      pcg_max_iter, track_ids, stream, cfg.get("ife_refine", 1))
     sim.set_field_bc(cfg["face_bc"])
@@ -380,7 +382,7 @@ def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter
         sim.set_object(OBJ_NONE, [], 1.0, 1.0)
     pbc = cfg.get("particle_bc")
     for sp in cfg["species"]:
-        s = sim.add_species(sp["q"], sp["m"], sp["density"] * cfg["h"] ** 3 / sp["ppc"])
+        s = sim.add_species(sp["q"], sp["m"], macro_weight(cfg, sp))
         if pbc is not None:
             sim.set_particle_bc(s, pbc)
         if load:
