@@ -280,6 +280,13 @@ pifepic_status pifepic_get_sizes(pifepic_ctx* ctx, int64_t* nnodes, int64_t* nce
                                  int64_t* n_interface_tets, int64_t* n_cut_cells);
 pifepic_status pifepic_get_potential(pifepic_ctx* ctx, double* phi, int mem_kind);        /* nnodes   */
 pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind);             /* nnodes*3 */
+/* The FP32 node field the MIXED push gathers from (nnodes x 3 floats,
+ * interleaved xyz, IFE-mesh nodes): in MIXED mode the field the last solve's
+ * FP32 node-field kernel wrote (the node field of Sec. 2.1's gather, evaluated
+ * in FP32 from the FP64 potential), in FP64 mode the FP32 rounding of the FP64
+ * field.  pifepic_get_node_E returns the FP64 field instead, which MIXED mode
+ * computes from phi on demand. */
+pifepic_status pifepic_get_node_E_f32(pifepic_ctx* ctx, float* E, int mem_kind);          /* nnodes*3 */
 pifepic_status pifepic_get_node_charge(pifepic_ctx* ctx, int species, int64_t* W, int mem_kind); /* nnodes, 2^32 per particle */
 pifepic_status pifepic_get_surface_charge(pifepic_ctx* ctx, int species, int64_t* counts,
                                           int mem_kind);                                   /* n_cut_cells */
@@ -333,25 +340,31 @@ void pifepic_batch_destroy(pifepic_batch* batch);
 
 /* Field solve that allocates nothing.  (The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory once they are
- * running -- a serving loop whose memory comes from a pool it does not own,
- * code that issues work while a stream is being captured into a CUDA graph,
- * or a host application that forbids allocation after start-up.
+ * running -- a serving loop whose device memory comes from a pool it does not
+ * own, where a cudaMalloc can fail or stall every stream of the process, or a
+ * host application that forbids allocation after start-up.
  * pifepic_solve_field allocates a staging buffer and builds a CUDA graph on
  * every call; this variant does neither.)
  *
  * Same system and stopping rule as pifepic_solve_field, on the context's
  * operator, tolerance and iteration cap; the context's own potential, node
- * field and solver state are left untouched.  F (nnodes), q
- * (n_interface_tets, may be NULL for no flux jump) and phi (nnodes, output)
- * are caller-owned DEVICE arrays.  The PCG work vectors live in one fixed
+ * field and solver state are left untouched.  It always runs the plain FP64
+ * Jacobi PCG, whatever the context's precision (a MIXED context's refined
+ * solve reaches the same solution at the same tolerance).  F (nnodes), q
+ * (n_interface_tets; NULL means no flux jump) and phi (nnodes, output) are
+ * caller-owned DEVICE arrays of the context's GPU, which must be the current
+ * device (EINVAL otherwise).  The PCG work vectors live in one fixed
  * __device__ array of the library, 5.3 MB, which every GPU that loads the
  * library holds until the process exits; meshes with more than
  * PIFEPIC_NOALLOC_MAX_NODES nodes are rejected with EINVAL.  The first call
  * on a device looks up that array's address (cudaGetSymbolAddress), so make
  * it before any stream capture.  Every call shares the array and it keeps the
- * previous call's contents: calls that overlap on the GPU (other streams,
- * other contexts on the same device) race.  Synchronises the context's stream
- * to return iters and relres. */
+ * previous call's contents (each call sets what it reads before reading it):
+ * calls that overlap on the GPU (other streams, other contexts on the same
+ * device) race.  Each call queues 3 * pcg_max_iter + 5 kernel launches on the
+ * context's stream (those after convergence return at once; on small meshes
+ * the launches, not the arithmetic, set the call's time) and synchronises that
+ * stream to return iters and relres. */
 #define PIFEPIC_NOALLOC_MAX_NODES 131072
 pifepic_status pifepic_solve_field_noalloc(pifepic_ctx* ctx, const double* F, const double* q, double* phi,
                                            int* iters, double* relres);

@@ -91,6 +91,7 @@ _sigs = {
     "pifepic_get_sizes": [_ctx] + [C.POINTER(C.c_int64)] * 4,
     "pifepic_get_potential": [_ctx, _dp, C.c_int],
     "pifepic_get_node_E": [_ctx, _dp, C.c_int],
+    "pifepic_get_node_E_f32": [_ctx, _dp, C.c_int],
     "pifepic_get_node_charge": [_ctx, C.c_int, _dp, C.c_int],
     "pifepic_get_surface_charge": [_ctx, C.c_int, _dp, C.c_int],
     "pifepic_get_cut_cells": [_ctx, _dp, _dp],
@@ -308,6 +309,12 @@ class Simulation:
     def node_E(self):
         out = np.empty((self.sizes()["nnodes"], 3))
         self._ok(lib.pifepic_get_node_E(self._c, _addr(out), HOST), "get_node_E")
+        return out
+
+    def node_E_f32(self):
+        """The FP32 node field the MIXED push gathers from (pifepic_get_node_E_f32)."""
+        out = np.empty((self.sizes()["nnodes"], 3), dtype=np.float32)
+        self._ok(lib.pifepic_get_node_E_f32(self._c, _addr(out), HOST), "get_node_E_f32")
         return out
 
     def node_charge(self, s):

@@ -90,6 +90,12 @@ __global__ void k_unpack_E(long long n, const double4* E, double* E3) {
     double4 e = E[i];
     E3[3 * i] = e.x; E3[3 * i + 1] = e.y; E3[3 * i + 2] = e.z;
 }
+__global__ void k_unpack_Ef(long long n, const float4* E, float* E3) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 e = E[i];
+    E3[3 * i] = e.x; E3[3 * i + 1] = e.y; E3[3 * i + 2] = e.z;
+}
 __global__ void k_max_id(long long n, const long long* id, unsigned long long* out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) atomicMax(out, (unsigned long long)id[i]);
@@ -1038,6 +1044,19 @@ pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind) {
     k_unpack_E<<<nb256(N), 256, 0, c.stream>>>(N, c.E, tmp);
     CUDA_OK(cudaStreamSynchronize(c.stream));
     CUDA_OK(scopy(c.stream, E, tmp, sizeof(double) * 3 * N, out_kind(mem_kind)));
+    cudaFree(tmp);
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_node_E_f32(pifepic_ctx* ctx, float* E, int mem_kind) {
+    NEED(ctx); NEED(E);
+    Ctx& c = ctx->c;
+    long long N = c.mesh.nnodes;
+    float* tmp = nullptr;
+    ALLOC(tmp, sizeof(float) * 3 * N);
+    k_unpack_Ef<<<nb256(N), 256, 0, c.stream>>>(N, c.Ef, tmp);
+    CUDA_OK(cudaStreamSynchronize(c.stream));
+    CUDA_OK(scopy(c.stream, E, tmp, sizeof(float) * 3 * N, out_kind(mem_kind)));
     cudaFree(tmp);
     return PIFEPIC_OK;
 }

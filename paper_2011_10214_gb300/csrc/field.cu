@@ -16,6 +16,7 @@
 // partials, summed in a fixed order by the last block to finish.
 #include <math.h>
 #include <stdio.h>
+#include <atomic>
 
 #include "internal.h"
 #include "field_common.cuh"
@@ -76,7 +77,7 @@ __global__ void k_rhs(FieldArgs f, RhsArgs a, const unsigned char* imask, const 
         for (int s = 0; s < ns; ++s)
             F = F + (a.coefs[s] * 2.3283064365386963e-10) * (double)(long long)a.W[(long long)s * m.nnodes + n];
     }
-    if (ty >= 0) {   // touches interface tets: flux-jump load
+    if (ty >= 0 && qT) {   // touches interface tets: flux-jump load (none when qT is NULL)
         int i, j, k;
         node_ijk(m, n, i, j, k);
         // the cubes' masks and first records first (independent loads), then
@@ -382,7 +383,8 @@ __global__ void k_surface_diag(Mesh m, long long nit, const int* it_cell, const 
                                double* out) {
     long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[2] = {0, 0};
-    if (T < nit) {
+    // the object's surface only: a bedrock-plane tet lies inside the object
+    if (T < nit && it_data[T * IT_STRIDE + IT_KIND] == 0.0) {
         const double* rec = it_data + T * IT_STRIDE;
         int c = it_cell[T], t = it_t[T];
         int i = c % m.nx, j = (c / m.nx) % m.ny, k = c / (m.nx * m.ny);
@@ -704,14 +706,16 @@ cudaError_t launch_qtets(Ctx& c) {
 // Field solve that allocates nothing (pifepic_solve_field_noalloc).
 //
 // Some callers cannot call cudaMalloc once their run is under way: a serving
-// loop whose device memory is handed out by a pool it does not own, code that
-// runs while a stream is being captured into a CUDA graph, or an embedding
-// that forbids allocation after start-up.  pifepic_solve_field allocates a
-// staging buffer and builds a CUDA graph on every call, so those callers need
-// this variant.  It reuses the context's operator (read only), takes the load
-// F, the flux jumps q and the output phi as caller-owned device arrays, and
-// keeps every work vector of the PCG in one file-scope device array of fixed
-// size, found once per device with cudaGetSymbolAddress.
+// loop whose device memory is handed out by a pool it does not own (a
+// cudaMalloc there can fail or stall the whole process on a device
+// synchronisation), or an embedding that forbids allocation after start-up.
+// pifepic_solve_field allocates a staging buffer and builds a CUDA graph on
+// every call, so those callers need this variant.  It reuses the context's
+// operator (read only), takes the load F, the flux jumps q (NULL: none) and
+// the output phi as caller-owned device arrays, and keeps every work vector of
+// the PCG in one file-scope device array of fixed size, found once per device
+// with cudaGetSymbolAddress.  It always runs the FP64 PCG, whatever the
+// context's precision.
 // ======================================================================================
 constexpr long long NOALLOC_MAX_NODES = 131072;                  // 2^17 mesh nodes
 constexpr long long NOALLOC_PARTIALS = 4 * (NOALLOC_MAX_NODES / 256 + 1);
@@ -803,9 +807,9 @@ __global__ void k_na_state(PcgState* S, unsigned* ticket, double tol2, int maxit
 // set-up once per device (with that device current): in host code the name of
 // a __device__ array is a host-side stand-in, not a device address, so the
 // address is looked up with cudaGetSymbolAddress and cached per device.  Two
-// threads doing the first call on one device at once both store the same value.
-static void* g_noalloc_dev[64];
-static int g_noalloc_ready[64];
+// threads doing the first call on one device at once both look it up and
+// store the same value (an atomic store, so neither sees a torn pointer).
+static std::atomic<void*> g_noalloc_dev[64];
 
 pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
                                    double* relres) {
@@ -817,19 +821,27 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
         c.err = b;
         return PIFEPIC_EINVAL;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { c.err = "solve_field_noalloc: no device"; return PIFEPIC_ECUDA; }
-    if (!g_noalloc_ready[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
+    // the scratch address is per device and the kernels run on the context's
+    // stream, so the context's device must be the current one
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { c.err = "solve_field_noalloc: no current device"; return PIFEPIC_ECUDA; }
+    if (dev != c.device || dev < 0 || dev >= 64) {
+        char b[160];
+        snprintf(b, sizeof(b), "solve_field_noalloc: current device %d is not the context's device %d", dev,
+                 c.device);
+        c.err = b;
+        return PIFEPIC_EINVAL;
+    }
+    void* base_ptr = g_noalloc_dev[dev].load(std::memory_order_acquire);
+    if (!base_ptr) {
+        cudaError_t e = cudaGetSymbolAddress(&base_ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !base_ptr) {
             c.err = std::string("solve_field_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
             return PIFEPIC_ECUDA;
         }
-        g_noalloc_dev[dev] = ptr;
-        g_noalloc_ready[dev] = 1;
+        g_noalloc_dev[dev].store(base_ptr, std::memory_order_release);
     }
-    double* base = (double*)g_noalloc_dev[dev];
+    double* base = (double*)base_ptr;
     double* u = base;
     double* bvec = base + NOALLOC_MAX_NODES;
     double* r = base + 2 * NOALLOC_MAX_NODES;

@@ -87,3 +87,30 @@ def test_mixed_pic_steps_track_oracle():
         rel = np.abs(gpu.potential() - orc.phi).max() / np.abs(orc.phi).max()
         assert rel <= TOL32, rel
     gpu.close()
+
+
+@pytest.mark.parametrize("case", ["sphere16", "crater", "lunar"])
+def test_mixed_node_field_the_push_reads(case):
+    """The FP32 node field that MIXED steps build for the push
+    (pifepic_get_node_E_f32), element by element against the oracle's node
+    field of the same potential and flux jumps: interior nodes take the
+    closed-form path, nodes near the interface the FP32 piece average with the
+    plasma side preferred and the q_T jump-gradient term."""
+    gpu, orc = make_pair(case, precision=MIXED)
+    fs = orc.fs
+    g = np.random.default_rng(17)
+    F = g.normal(size=orc.mesh.nnodes) * orc.mesh.h ** 3
+    q = np.where(fs.it_kind == 0, g.normal(size=len(fs.it_cell)), 0.0)   # bedrock planes carry no jump
+    gpu.solve_field(F, q)
+    phi = gpu.potential()
+    Ef = gpu.node_E_f32().astype(np.float64)
+    Eo = fs.node_E(phi, q)
+    scale = np.abs(Eo).max()
+    err = np.abs(Ef - Eo).max() / scale
+    assert err <= 2e-6, err
+    # the interface nodes (the general path) are covered and agree as well
+    near = np.zeros(orc.mesh.nnodes, dtype=bool)
+    near[fs.it_nodes.ravel()] = True
+    assert near.sum() > 50
+    assert np.abs(Ef[near] - Eo[near]).max() / scale <= 2e-6
+    gpu.close()
