@@ -274,7 +274,9 @@ def roofline_solve(precision, st, steps, nnodes):
             "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
             "alg_bytes_per_launch": alg, "avg_launch_ms": solve_ms, "iters_per_solve": iters,
-            "note": "latency-bound: two grid exchanges per iteration, vectors in registers and L2"}
+            "note": ("latency-bound: one grid exchange per inner iteration (pipelined PCG), vectors in registers "
+                     "and L2" if precision == "mixed" else
+                     "latency-bound: two grid exchanges per iteration, vectors in registers and L2")}
 
 
 def run_gpu(args):

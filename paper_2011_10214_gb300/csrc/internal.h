@@ -62,7 +62,7 @@ struct PhotoDev {
     int ntri, acc;                  // triangles; cut-cell accumulator of the tet's cell
 };
 constexpr int PHOTO_RATE_BITS = 20;  // per-tet rates and carries in units of 2^-20 particles
-constexpr int BAR64_WORDS = 64;      // PCG exchange words per context (Ctx::bar64)
+constexpr int BAR64_WORDS = 160;     // PCG exchange words per context (Ctx::bar64): 10 lines of 16
 
 struct Launch {                     // what every particle kernel needs
     Mesh mesh;

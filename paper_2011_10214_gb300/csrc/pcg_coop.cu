@@ -28,6 +28,11 @@
 namespace pf {
 
 constexpr int COOP_MAX_OUTER = 12;   // MIXED: refinement steps at most
+// MIXED, pipelined inner loop: an inner solve whose FP64 residual ends more
+// than 30x (in norm) above its recurrence residual switches the context to the
+// classic loop (the sphere meshes measure about 8x, mostly-Neumann craters 80x)
+constexpr double PIPE_GAP2 = 900.0;
+constexpr int PIPE_STALL = 40;
 
 // ---- register-resident PCG --------------------------------------------------
 //
@@ -71,7 +76,9 @@ struct RegArgs {
     int woff[19];              // staged rows: window offset of each stencil slot
     double* val;               // [2][4][G] block partials
     unsigned long long* arrivals;  // grows by G per exchange
-    unsigned long long* fx;        // fixed-point exchange words: pq at [0], r.r and r.z at [FX_LINE], [2 FX_LINE]
+    unsigned long long* fx;        // fixed-point exchange words: pq at [0], r.r and r.z at [FX_LINE], [2 FX_LINE];
+                                   // pipelined loop: two sets of three at [(3 + 3 set + q) FX_LINE]
+    int* classic;                  // MIXED: 1 once a solve found the pipelined recurrences too inexact
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -167,10 +174,11 @@ static __device__ __forceinline__ int exchange_fx(const Args& a, unsigned long l
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const bool act = lane < NV;
-        float mine = __shfl_sync(0xffffffffu, v[0], 0), rf = ref[0];
-        if (NV > 1) {
-            const float m1 = __shfl_sync(0xffffffffu, v[NV - 1], 0);
-            if (lane == 1) { mine = m1; rf = ref[NV - 1]; }
+        float mine = 0.0f, rf = ref[0];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {      // lane q takes value q (the block total sits in thread 0)
+            const float t = __shfl_sync(0xffffffffu, v[q], 0);
+            if (lane == q) { mine = t; rf = ref[q]; }
         }
         using FL = FxLayout<W>;
         const int k = FL::SCALE - ilogbf(rf);
@@ -343,8 +351,54 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         fxa = ld_relaxed(a.fx);
         fxb = ld_relaxed(a.fx + (1 + threadIdx.x) * FX_LINE);
     }
+    // pipelined loop: two word sets used in turn (a set is reused only after an
+    // exchange on the other one, so every block has read its last total);
+    // fxp0 belongs to the set of the next exchange, fxp1 to the other one
+    unsigned long long fxp0 = 0, fxp1 = 0;
+    int pset = 0;
+    if (MIXED && threadIdx.x < 3) {
+        fxp0 = ld_relaxed(a.fx + (3 + threadIdx.x) * FX_LINE);
+        fxp1 = ld_relaxed(a.fx + (6 + threadIdx.x) * FX_LINE);
+    }
+    // MIXED inner loop: pipelined unless an earlier solve of this context found
+    // its recurrences too far from the true residual (then the classic loop)
+    bool pipe = MIXED && *a.classic == 0;
+    bool switched = false;
+    // copy the window of zg that this block's rows read into shared memory (the
+    // last exchange ordered every block's stores to zg and every read of the
+    // previous window)
+    auto stage = [&](const T* zg) {
+        V* dst = (V*)win;
+        if (ROWS) {
+            const long long v0 = ws / VEC;   // exact: ws is a multiple of VEC
+            for (int c = threadIdx.x; c < nvec; c += REG_THREADS) {
+                const long long gv = v0 + c;
+                V val = {};
+                if (gv >= 0 && gv < nvec_in) val = __ldcg((const V*)zg + gv);
+                dst[c] = val;
+            }
+        } else {
+            const V* src = (const V*)(zg + ws);
+            for (int c = threadIdx.x; c < nvec; c += REG_THREADS) dst[c] = __ldcg(src + c);
+        }
+        __syncthreads();
+    };
+    // row n (slot s of this thread) of the operator times the staged window
+    auto apply = [&](int s, long long n) -> T {
+        if (ROWS) {
+            const int li = threadIdx.x + s * REG_THREADS;
+            const T* rw = rows + li * 19;
+            const T* wc = win + (n - ws);
+            T az = rw[0] * wc[0];
+#pragma unroll
+            for (int q = 1; q < 19; ++q) az += rw[q] * wc[a.woff[q]];
+            return az;
+        }
+        return row_at<T>(f, n, pk[s], ldw, coef);
+    };
     int it = 0, outer = 0;
     double bb = 0.0, rr = 0.0;
+    T rr_exit = (T)0;     // recurrence residual at the end of the last inner solve
     bool conv = false, alive = true;
     for (;;) {
         // true residual of u in FP64 (neighbours of u through L2); z = D^-1 r, p = z
@@ -375,100 +429,179 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         rr = t3[1];
         T rz = (T)t3[2];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
+        // the pipelined recurrences drift from the true residual by the rounding
+        // they amplify; if the last inner solve ended far above what it claimed,
+        // finish with the classic loop (and keep it for this context's next solves)
+        if (MIXED && pipe && outer > 0 && !conv && rr > PIPE_GAP2 * (double)rr_exit) {
+            pipe = false;
+            switched = true;
+        }
         if (conv || it >= maxit || (MIXED && outer >= COOP_MAX_OUTER)) break;
         // inner target: the final tolerance, or (MIXED) max(margin tol |b|, reduction |r0|) (set_refinement)
         const T rr_stop = (T)(MIXED ? fmax(margin2 * tol2 * bb, inner_red2 * rr) : tol2 * bb);
         ++outer;
-        T beta = (T)0, rr_in = (T)rr;
-        float pq_prev = 0.0f;     // no scale for the first p.q of an inner solve
-        bool first = true;
-        for (;;) {
-            // stage the z window (the last exchange ordered every block's z stores
-            // and every read of the previous window)
-            {
-                const T* zg = zbuf[zc];
-                V* dst = (V*)win;
-                if (ROWS) {
-                    const long long v0 = ws / VEC;   // exact: ws is a multiple of VEC
-                    for (int c = threadIdx.x; c < nvec; c += REG_THREADS) {
-                        const long long gv = v0 + c;
-                        V val = {};
-                        if (gv >= 0 && gv < nvec_in) val = __ldcg((const V*)zg + gv);
-                        dst[c] = val;
+        T rr_in = (T)rr;
+        if (MIXED && pipe) {
+          if constexpr (MIXED) {
+            // Pipelined Jacobi PCG (Ghysels and Vanroose): the recurrences for
+            // u = D^-1 r, w = A u, m = D^-1 w, and A p, D^-1 A p, A D^-1 A p
+            // move the matrix product behind the iteration's one exchange, which
+            // carries r.u, w.u and r.r and also publishes m for the product.
+            // u starts as z (written above, ordered by the residual exchange).
+            T w[NPT], sv[NPT], nz[NPT];
+            stage(zbuf[zc]);
+#pragma unroll
+            for (int s = 0; s < NPT; ++s) {
+                const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                w[s] = sv[s] = nz[s] = (T)0;
+                if (n < b1) w[s] = apply(s, n);
+            }
+            float ref[3] = {0.0f, 0.0f, 0.0f};
+            bool have_ref = false;
+            T gam_old = (T)1, al_old = (T)1;
+            bool first = true;
+            // progress: the recurrence residual must halve within PIPE_STALL
+            // iterations, else (FP32 pipelined recurrences can stall and drift
+            // on hard meshes) the inner solve ends and the classic loop takes over
+            T rr_mark = rr_in;
+            int it_mark = it;
+            for (;;) {
+                T v[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+                for (int s = 0; s < NPT; ++s) {
+                    const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                    if (n < b1) {
+                        zbuf[zc ^ 1][n] = dv[s] * w[s];
+                        v[0] += r[s] * z[s];
+                        v[1] += w[s] * z[s];
+                        v[2] += r[s] * r[s];
                     }
+                }
+                T t[3];
+                alive = exchange_f32<3, true, 8>(a, e, a.fx + (3 + 3 * pset) * FX_LINE, fxp0, ref, have_ref, v, t,
+                                                 xs);
+                if (!alive) break;
+                {
+                    const unsigned long long tmp = fxp0;
+                    fxp0 = fxp1;
+                    fxp1 = tmp;
+                    pset ^= 1;
+                }
+                zc ^= 1;
+                rr_in = t[2];
+                if (rr_in <= rr_stop || it >= maxit) break;
+                if (rr_in <= (T)0.25 * rr_mark) {
+                    rr_mark = rr_in;
+                    it_mark = it;
+                } else if (it - it_mark > PIPE_STALL) {
+                    pipe = false;
+                    switched = true;
+                    break;
+                }
+                const T gam = t[0], dl = t[1];
+                T be, al;
+                if (first) {
+                    be = (T)0;
+                    al = gam / dl;
                 } else {
-                    const V* src = (const V*)(zg + ws);
-                    for (int c = threadIdx.x; c < nvec; c += REG_THREADS) dst[c] = __ldcg(src + c);
+                    be = gam / gam_old;
+                    al = gam / (dl - be * gam / al_old);
                 }
-            }
-            __syncthreads();
-            // p = z + beta p, q = A z + beta q (= A p); first pass: q = A z
-            T v1[1] = {(T)0};
-            const T bt = beta;
+                stage(zbuf[zc]);
 #pragma unroll
-            for (int s = 0; s < NPT; ++s) {
-                const long long n = b0 + threadIdx.x + s * REG_THREADS;
-                if (n < b1) {
-                    T az;
-                    if (ROWS) {
-                        const int li = threadIdx.x + s * REG_THREADS;
-                        const T* rw = rows + li * 19;
-                        const T* wc = win + (n - ws);
-                        az = rw[0] * wc[0];
-#pragma unroll
-                        for (int q = 1; q < 19; ++q) az += rw[q] * wc[a.woff[q]];
-                    } else {
-                        az = row_at<T>(f, n, pk[s], ldw, coef);
+                for (int s = 0; s < NPT; ++s) {
+                    const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                    if (n < b1) {
+                        const T nn = apply(s, n);
+                        const T m = dv[s] * w[s];
+                        if (first) {
+                            nz[s] = nn; q[s] = m; sv[s] = w[s]; p[s] = z[s];
+                        } else {
+                            nz[s] = nn + be * nz[s];
+                            q[s] = m + be * q[s];
+                            sv[s] = w[s] + be * sv[s];
+                            p[s] = z[s] + be * p[s];
+                        }
+                        x[s] = x[s] + al * p[s];
+                        r[s] = r[s] - al * sv[s];
+                        z[s] = z[s] - al * q[s];
+                        w[s] = w[s] - al * nz[s];
                     }
-                    if (first) {
-                        q[s] = az;
-                    } else {
-                        p[s] = z[s] + bt * p[s];
-                        q[s] = az + bt * q[s];
-                    }
-                    v1[0] += p[s] * q[s];
                 }
+                first = false;
+                gam_old = gam;
+                al_old = al;
+                ref[0] = t[0]; ref[1] = t[1]; ref[2] = t[2];
+                have_ref = fx_ref_ok(t[0]) && fx_ref_ok(t[1]) && fx_ref_ok(t[2]);
+                ++it;
             }
-            first = false;
-            T pq[1];
-            if constexpr (MIXED) {
-                const float rf[1] = {pq_prev};
-                alive = exchange_f32<1, false, 8>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
-                pq_prev = pq[0];
-            } else {
-                alive = exchange<T, 1>(a, e, v1, pq, xs);
-            }
-            if (!alive) break;
-            const T al = rz / pq[0];
-            T v2[2] = {(T)0, (T)0};
+          }
+        } else {
+            T beta = (T)0;
+            float pq_prev = 0.0f;     // no scale for the first p.q of an inner solve
+            bool first = true;
+            for (;;) {
+                stage(zbuf[zc]);
+                // p = z + beta p, q = A z + beta q (= A p); first pass: q = A z
+                T v1[1] = {(T)0};
+                const T bt = beta;
 #pragma unroll
-            for (int s = 0; s < NPT; ++s) {
-                const long long n = b0 + threadIdx.x + s * REG_THREADS;
-                if (n < b1) {
-                    x[s] = x[s] + al * p[s];
-                    r[s] = r[s] - al * q[s];
-                    z[s] = dv[s] * r[s];
-                    zbuf[zc ^ 1][n] = z[s];
-                    v2[0] += r[s] * r[s];
-                    v2[1] += r[s] * z[s];
+                for (int s = 0; s < NPT; ++s) {
+                    const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                    if (n < b1) {
+                        const T az = apply(s, n);
+                        if (first) {
+                            q[s] = az;
+                        } else {
+                            p[s] = z[s] + bt * p[s];
+                            q[s] = az + bt * q[s];
+                        }
+                        v1[0] += p[s] * q[s];
+                    }
                 }
+                first = false;
+                T pq[1];
+                if constexpr (MIXED) {
+                    const float rf[1] = {pq_prev};
+                    alive = exchange_f32<1, false, 8>(a, e, a.fx, fxa, rf, fx_ref_ok(pq_prev), v1, pq, xs);
+                    pq_prev = pq[0];
+                } else {
+                    alive = exchange<T, 1>(a, e, v1, pq, xs);
+                }
+                if (!alive) break;
+                const T al = rz / pq[0];
+                T v2[2] = {(T)0, (T)0};
+#pragma unroll
+                for (int s = 0; s < NPT; ++s) {
+                    const long long n = b0 + threadIdx.x + s * REG_THREADS;
+                    if (n < b1) {
+                        x[s] = x[s] + al * p[s];
+                        r[s] = r[s] - al * q[s];
+                        z[s] = dv[s] * r[s];
+                        zbuf[zc ^ 1][n] = z[s];
+                        v2[0] += r[s] * r[s];
+                        v2[1] += r[s] * z[s];
+                    }
+                }
+                T t2[2];
+                if constexpr (MIXED) {
+                    const float rf[2] = {rr_in, rz};
+                    alive = exchange_f32<2, true, 8>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz),
+                                                     v2, t2, xs);
+                } else {
+                    alive = exchange<T, 2>(a, e, v2, t2, xs);
+                }
+                if (!alive) break;
+                zc ^= 1;
+                beta = t2[1] / rz;
+                rz = t2[1];
+                rr_in = t2[0];
+                ++it;
+                if (rr_in <= rr_stop || it >= maxit) break;
             }
-            T t2[2];
-            if constexpr (MIXED) {
-                const float rf[2] = {rr_in, rz};
-                alive = exchange_f32<2, true, 8>(a, e, a.fx + FX_LINE, fxb, rf, fx_ref_ok(rr_in) && fx_ref_ok(rz), v2, t2, xs);
-            } else {
-                alive = exchange<T, 2>(a, e, v2, t2, xs);
-            }
-            if (!alive) break;
-            zc ^= 1;
-            beta = t2[1] / rz;
-            rz = t2[1];
-            rr_in = t2[0];
-            ++it;
-            if (rr_in <= rr_stop || it >= maxit) break;
         }
         if (!alive) break;
+        rr_exit = rr_in;
         // u += x; MIXED: an exchange so that the next residual sees the new u
 #pragma unroll
         for (int s = 0; s < NPT; ++s) {
@@ -498,6 +631,7 @@ __global__ void __launch_bounds__(REG_THREADS, 1) k_pcg_reg(RegArgs a) {
         S->relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
         *a.it_total += it;
         *a.outer_total += MIXED ? outer : 0;
+        if (MIXED && switched) *a.classic = 1;
     }
 }
 
@@ -841,6 +975,7 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     a.val = c.coop_partial;
     a.arrivals = c.bar64;
     a.fx = c.bar64 + FX_LINE;
+    a.classic = (int*)(c.scal + 44);
     a.S = (PcgState*)c.scal;
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
