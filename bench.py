@@ -190,10 +190,10 @@ def cfg_desc(cfg, precision, extra=None):
 FP64_FLOPS_PER_PARTICLE_STEP = 80     # trilinear weights 19, gather 45, kick and drift 12, cell test 4
 # PCG: 7 node-vector passes per iteration (p, x, r, z updates, the operator's read of p and write of q)
 SOLVE_BYTES_PER_NODE_ITER = {"mixed": 7 * 4, "fp64": 7 * 8}
-# DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 32^3 sphere
-# (dram__bytes_read.sum + dram__bytes_write.sum over the launch's particles); None when not measured
-# for the current kernel
-PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (115822080 + 58377216) / 4074575, "fp64": None}
+# DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 64^3 sphere
+# bench workload (dram__bytes_read.sum + dram__bytes_write.sum over the launch's particles); None when
+# not measured for the current kernel
+PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (930549248 + 860526336) / 32619866, "fp64": None}
 NSM, DFMA_PER_CLK_SM = 152, 2          # GB300: 2 FP64 FMA per SM per clock
 
 
@@ -245,7 +245,8 @@ def roofline(precision, st, steps, ck):
                 "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / peaks["hbm_gbs"], 4),
                 "traffic": None if tpp is None else round(tpp * per_launch),
-                "traffic_note": "ncu DRAM bytes per particle of a 32^3 launch, scaled to this launch's particles",
+                "traffic_note": "ncu DRAM bytes per particle of a 64^3 sphere launch (54.9 B, 0.98 of the "
+                                "algorithmic 56 B), scaled to this launch's particles",
                 "peak_source": src, "alg_bytes_per_launch": alg, "avg_launch_ms": push_ms}
     flops = per_launch * FP64_FLOPS_PER_PARTICLE_STEP
     ach = flops / (push_ms / 1e3) / 1e9

@@ -201,9 +201,10 @@ pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int species, int ppc, d
                                        const double drift[3], uint64_t seed);
 
 /* Append n explicit particles: positions in cell units xi = (x-origin)/h,
- * physical velocities, optional int64 ids (NULL: consecutive ids).  All must
- * lie inside the box; EINVAL otherwise is not checked on the device, so the
- * caller guarantees it. */
+ * physical velocities, optional int64 ids (NULL: consecutive ids).  Every
+ * position must lie inside the box [0, n) per axis and every value be finite
+ * (checked on the device after the copy): otherwise EINVAL and nothing is
+ * appended. */
 pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int species, size_t n, const double* x,
                                       const double* y, const double* z, const double* vx,
                                       const double* vy, const double* vz, const int64_t* ids,
@@ -260,7 +261,8 @@ pifepic_status pifepic_set_photoemission(pifepic_ctx* ctx, int species, const do
 pifepic_status pifepic_get_photoemission(pifepic_ctx* ctx, int64_t* rate_fixed, int64_t* emitting_tets);
 
 /* Freeze the node field to the given (nnodes x 3) array: steps then skip the
- * field solve (particle-only parity runs).  E == NULL unfreezes. */
+ * field solve (particle-only parity runs).  E == NULL unfreezes.  EINVAL if a
+ * value is not finite (the field is then left as it was). */
 pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem_kind);
 
 /* Scatter all particles, solve the IFE system, compute the node field (the
@@ -308,7 +310,8 @@ pifepic_status pifepic_get_stats(pifepic_ctx* ctx, pifepic_stats* stats);
 /* Field solve on its own (Sec. 2.1 Eqs. 2.1-2.5, PCG level of Sec. 2.5): node
  * load F (nnodes, FP64) and flux jump q per interface tet (n_interface_tets,
  * in pifepic_get_interface order) -> phi and the node field.  Used by the
- * solver parity tests; F and q may be host or device arrays. */
+ * solver parity tests; F and q may be host or device arrays.  EINVAL if a
+ * value of F or q is not finite. */
 pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const double* q, int mem_kind,
                                    int* iters, double* relres);
 
@@ -337,6 +340,27 @@ pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* batch, int cta_nodes);
 pifepic_status pifepic_batch_step(pifepic_batch* batch, int nsteps, pifepic_stats* stats);
 const char* pifepic_batch_last_error(const pifepic_batch* batch);
 void pifepic_batch_destroy(pifepic_batch* batch);
+
+/* Device memory of the library, process-wide (every context and batch in the
+ * process): *bytes receives the bytes it holds now.  pifepic_set_memory_limit
+ * caps that total (0 = no cap, the default): an allocation that would pass
+ * the cap fails as if the device were out of memory, and the call that needed
+ * it returns ENOMEM (a context whose creation fails this way is freed by
+ * pifepic_destroy as usual).  A serving loop can hold the library to an HBM
+ * budget with it, and tests reach the out-of-memory paths without exhausting
+ * the GPU.  Errors: EINVAL (bytes NULL). */
+pifepic_status pifepic_get_memory_use(size_t* bytes);
+pifepic_status pifepic_set_memory_limit(size_t bytes);
+
+/* Test hook for the bounded waits of the persistent PCG (the solve of a single
+ * context, not of a batch): the first grid exchange of the context's next
+ * solve waits for `extra` arrivals beyond its grid, which never come, so its
+ * bounded wait (about a second) gives up.  That solve's call returns ETIMEOUT;
+ * the library then clears the exchange counters, the error word and the hook,
+ * and the context stays usable.  extra = 0 turns the hook off.  Nothing
+ * faults: every wait of the solve is bounded.  Errors: EINVAL unless
+ * 0 <= extra <= 1. */
+pifepic_status pifepic_test_hold_exchange(pifepic_ctx* ctx, int extra);
 
 /* Field solve that allocates nothing.  (The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory once they are

@@ -102,6 +102,9 @@ _sigs = {
     "pifepic_get_stats": [_ctx, C.POINTER(Stats)],
     "pifepic_solve_field": [_ctx, _dp, _dp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "pifepic_solve_field_noalloc": [_ctx, _dp, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "pifepic_get_memory_use": [C.POINTER(C.c_size_t)],
+    "pifepic_set_memory_limit": [C.c_size_t],
+    "pifepic_test_hold_exchange": [_ctx, C.c_int],
     "pifepic_batch_create": [C.POINTER(_ctx), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)],
     "pifepic_batch_add": [C.c_void_p, _ctx],
     "pifepic_batch_remove": [C.c_void_p, _ctx],
@@ -127,6 +130,22 @@ EXPORTED = sorted(list(_sigs) + ["pifepic_destroy", "pifepic_last_error", "pifep
 
 class PifepicError(RuntimeError):
     pass
+
+
+def memory_use():
+    """Bytes of device memory the library holds, process-wide (pifepic_get_memory_use)."""
+    v = C.c_size_t()
+    st = lib.pifepic_get_memory_use(C.byref(v))
+    if st != 0:
+        raise PifepicError(f"get_memory_use: {STATUS.get(st, st)}")
+    return int(v.value)
+
+
+def set_memory_limit(nbytes):
+    """Cap the library's device memory, process-wide (0 = no cap; pifepic_set_memory_limit)."""
+    st = lib.pifepic_set_memory_limit(C.c_size_t(int(nbytes)))
+    if st != 0:
+        raise PifepicError(f"set_memory_limit: {STATUS.get(st, st)}")
 
 
 def _addr(a):
@@ -285,6 +304,10 @@ class Simulation:
         self._ok(lib.pifepic_solve_field(self._c, _addr(F), _addr(q), DEVICE if dev else HOST, C.byref(it),
                                          C.byref(rr)), "solve_field")
         return it.value, rr.value
+
+    def test_hold_exchange(self, extra=1):
+        """Make the next solve's first grid exchange wait in vain (pifepic_test_hold_exchange)."""
+        self._ok(lib.pifepic_test_hold_exchange(self._c, int(extra)), "test_hold_exchange")
 
     def solve_field_noalloc(self, F, q, phi):
         """Field solve into phi without any device allocation; F, q, phi are

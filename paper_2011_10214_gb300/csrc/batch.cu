@@ -106,8 +106,8 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     if (n == 0) { b->dirty = false; return cudaSuccess; }
     bool mixed = b->ctx[0]->c.precision == PIFEPIC_MIXED;
     if (n > b->items_cap) {
-        cudaFree(b->items);
-        cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * n);
+        lib_free(b->items);
+        cudaError_t e = lib_malloc(&b->items, sizeof(BatchItem) * n);
         if (e != cudaSuccess) return e;
         b->items_cap = n;
     }
@@ -290,7 +290,7 @@ void pifepic_batch_destroy(pifepic_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    cudaFree(b->items);
+    lib_free(b->items);
     delete b;
 }
 

@@ -6,14 +6,56 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include <cmath>
 
 #include "internal.h"
 
 namespace pf {
+
+// ---- the library's device memory: a process-wide count and an optional cap ----
+static std::mutex g_mem_mu;
+static std::unordered_map<void*, size_t> g_mem_blocks;
+static size_t g_mem_used = 0;
+static size_t g_mem_limit = 0;   // 0: no cap
+
+cudaError_t lib_malloc_bytes(void** p, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        if (g_mem_limit && g_mem_used + bytes > g_mem_limit) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_blocks[*p] = bytes;
+    g_mem_used += bytes;
+    return cudaSuccess;
+}
+
+cudaError_t lib_free(void* p) {
+    if (!p) return cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        auto it = g_mem_blocks.find(p);
+        if (it != g_mem_blocks.end()) {
+            g_mem_used -= it->second;
+            g_mem_blocks.erase(it);
+        }
+    }
+    return cudaFree(p);
+}
+
+// the tet tables are the same for every context: uploaded once per device
+static std::atomic<int> g_tables_ready[64];
+
 cudaError_t set_field_tables(const TetTables& t);
 cudaError_t set_particle_tables(const TetTables& t);
 cudaError_t set_mixed_tables(const TetTables& t);
@@ -96,6 +138,27 @@ __global__ void k_unpack_Ef(long long n, const float4* E, float* E3) {
     float4 e = E[i];
     E3[3 * i] = e.x; E3[3 * i + 1] = e.y; E3[3 * i + 2] = e.z;
 }
+// entries that are not finite
+__global__ void k_count_nonfinite(long long n, const double* a, unsigned long long* bad) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool b = i < n && !isfinite(a[i]);
+    const unsigned m = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(bad, (unsigned long long)__popc(m));
+}
+// particles outside the box [0, n) in cell units, or with a velocity that is not finite
+__global__ void k_count_bad_particles(long long n, const double* x, const double* y, const double* z,
+                                      const double* vx, const double* vy, const double* vz, double nx, double ny,
+                                      double nz, unsigned long long* bad) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool b = false;
+    if (i < n) {
+        const double px = x[i], py = y[i], pz = z[i];
+        const bool in = px >= 0.0 && px < nx && py >= 0.0 && py < ny && pz >= 0.0 && pz < nz;
+        b = !in || !isfinite(vx[i]) || !isfinite(vy[i]) || !isfinite(vz[i]);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(bad, (unsigned long long)__popc(m));
+}
 __global__ void k_max_id(long long n, const long long* id, unsigned long long* out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) atomicMax(out, (unsigned long long)id[i]);
@@ -124,13 +187,26 @@ using namespace pf;
     } while (0)
 #define ALLOC(ptr, bytes)                                                                        \
     do {                                                                                         \
-        cudaError_t _e = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (size_t)(bytes) : (size_t)16); \
-        if (_e != cudaSuccess) FAIL(PIFEPIC_ENOMEM, "cudaMalloc(%lld bytes) failed: %s",         \
+        cudaError_t _e = lib_malloc((void**)&(ptr), (bytes) > 0 ? (size_t)(bytes) : (size_t)16); \
+        if (_e != cudaSuccess) FAIL(PIFEPIC_ENOMEM, "lib_malloc(%lld bytes) failed: %s",         \
                                     (long long)(bytes), cudaGetErrorString(_e));                 \
     } while (0)
 #define NEED(ptr) do { if (!(ptr)) return PIFEPIC_EINVAL; } while (0)
 
 static unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+
+// input checks on the device (counter in a scalar slot of the context, read back)
+static unsigned long long* bad_counter(Ctx& c) { return (unsigned long long*)(c.scal + 46); }
+static cudaError_t count_nonfinite(Ctx& c, long long n, const double* a, unsigned long long* bad) {
+    *bad = 0;
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bad_counter(c), 0, sizeof(unsigned long long), c.stream);
+    if (e != cudaSuccess) return e;
+    k_count_nonfinite<<<nb256(n), 256, 0, c.stream>>>(n, a, bad_counter(c));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return scopy(c.stream, bad, bad_counter(c), sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+}
 
 // the six FP64 arrays (and ids) in one allocation: one cudaMalloc and one
 // cudaFree per buffer instead of seven (both cost a fraction of a millisecond)
@@ -138,7 +214,7 @@ static PArr alloc_parr_raw(long long n, bool id, cudaError_t* err) {
     PArr a{};
     const size_t m = (size_t)(n > 0 ? n : 1);
     char* b = nullptr;
-    *err = cudaMalloc(&b, sizeof(double) * m * (id ? 7 : 6));
+    *err = lib_malloc(&b, sizeof(double) * m * (id ? 7 : 6));
     if (*err != cudaSuccess) return a;
     a.base = b;
     double** arr[6] = {&a.x, &a.y, &a.z, &a.vx, &a.vy, &a.vz};
@@ -148,9 +224,9 @@ static PArr alloc_parr_raw(long long n, bool id, cudaError_t* err) {
 }
 static void free_parr(PArr& a) {
     if (a.base) {
-        cudaFree(a.base);
+        lib_free(a.base);
     } else {
-        cudaFree(a.x); cudaFree(a.y); cudaFree(a.z); cudaFree(a.vx); cudaFree(a.vy); cudaFree(a.vz); cudaFree(a.id);
+        lib_free(a.x); lib_free(a.y); lib_free(a.z); lib_free(a.vx); lib_free(a.vy); lib_free(a.vz); lib_free(a.id);
     }
     a = PArr{};
 }
@@ -285,10 +361,15 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     CUDA_OK(szero(c.stream, c.err_word, sizeof(int)));
     CUDA_OK(szero(c.stream, c.next_id, sizeof(long long) * MAX_SPECIES));
     CUDA_OK(szero(c.stream, c.inj_carry, sizeof(double) * MAX_SPECIES * 6));
-    TetTables t = make_tables();
-    CUDA_OK(set_tet_tables(t));
-    CUDA_OK(set_field_tables(t));
-    CUDA_OK(set_particle_tables(t));
+    // constant tables (unit-cube tets, independent of the mesh): once per device,
+    // so that a context created while others run does not rewrite them
+    if (c.device < 0 || c.device >= 64 || !g_tables_ready[c.device].load(std::memory_order_acquire)) {
+        TetTables t = make_tables();
+        CUDA_OK(set_tet_tables(t));
+        CUDA_OK(set_field_tables(t));
+        CUDA_OK(set_particle_tables(t));
+        if (c.device >= 0 && c.device < 64) g_tables_ready[c.device].store(1, std::memory_order_release);
+    }
     for (int e = 0; e < 16; ++e) CUDA_OK(cudaEventCreate(&c.ev[e]));
     c.ev_ok = true;
     return PIFEPIC_OK;
@@ -304,12 +385,12 @@ void pifepic_destroy(pifepic_ctx* ctx) {
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
                     c.patch_coef, c.patch_coeff, c.red, c.coop_partial, c.rowkind, c.pcg_x, c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total, c.scal, c.red_ticket, c.bar64, c.err_word, c.stat_dev, c.inj_dev, c.inj_count,
                     c.inj_base, c.inj_carry, c.next_id};
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) lib_free(p);
     if (c.stat_host) cudaFreeHost(c.stat_host);
-    if (c.refine > 1) { cudaFree(c.Ep); cudaFree(c.Efp); }
+    if (c.refine > 1) { lib_free(c.Ep); lib_free(c.Efp); }
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
-        cudaFree(s.bstart); cudaFree(s.bcap); cudaFree(s.bcount); cudaFree(s.bstay); cudaFree(s.mov_n);
+        lib_free(s.bstart); lib_free(s.bcap); lib_free(s.bcount); lib_free(s.bstay); lib_free(s.mov_n);
         free_parrf(s.binsF);
         for (int q = 0; q < 2; ++q) free_parrf(s.movF[q]);
     }
@@ -355,7 +436,7 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     // free a previous interface set-up
     void* old[] = {c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut,
                    c.patch_node, c.patch_coef, c.patch_coeff, c.surfall, c.it_dataf};
-    for (void* p : old) cudaFree(p);
+    for (void* p : old) lib_free(p);
     c.it_cell = c.it_t = c.it_acc = c.cut_cell = nullptr;
     c.it_data = c.qT = c.cut_area = c.qcut = c.patch_coef = nullptr;
     c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr; c.it_dataf = nullptr;
@@ -561,7 +642,10 @@ static pifepic_status flatten(pifepic_ctx* ctx, int s, long long extra, PArr* fl
     cudaError_t e;
     *flat = alloc_parr_raw(n0 + extra, true, &e);
     if (e != cudaSuccess) { free_parr(*flat); FAIL(PIFEPIC_ENOMEM, "flat particle buffer allocation failed"); }
-    ALLOC(*nflat, sizeof(unsigned long long));
+    if (lib_malloc(nflat, sizeof(unsigned long long)) != cudaSuccess) {
+        free_parr(*flat);
+        FAIL(PIFEPIC_ENOMEM, "flat particle counter allocation failed");
+    }
     CUDA_OK(szero(c.stream, *nflat, sizeof(unsigned long long)));
     if (!c.track) {   // without ids the flat copy still carries an id array: fill it later
     }
@@ -610,7 +694,7 @@ static pifepic_status regrow_if_spilling(pifepic_ctx* ctx, int s) {
     unsigned long long nt = 0;
     CUDA_OK(scopy(c.stream, &nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
     st = rebuild(ctx, s, flat, (long long)nt);
-    free_parr(flat); cudaFree(nflat);
+    free_parr(flat); lib_free(nflat);
     return st;
 }
 
@@ -628,7 +712,7 @@ pifepic_status pifepic_load_maxwellian(pifepic_ctx* ctx, int s, int ppc, double 
     unsigned long long nt = 0;
     CUDA_OK(scopy(c.stream, &nt, nflat, sizeof(nt), cudaMemcpyDeviceToHost));
     st = rebuild(ctx, s, flat, (long long)nt);
-    free_parr(flat); cudaFree(nflat);
+    free_parr(flat); lib_free(nflat);
     if (st) return st;
     Species& q = c.sp[s];
     q.next_id = std::max<long long>(q.next_id, c.pmesh.ncells * (long long)ppc);
@@ -654,6 +738,21 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int s, size_t n, const d
     Species& q = c.sp[s];
     if (n > 0) {
         for (int d = 0; d < 6; ++d) CUDA_OK(scopy(c.stream, dst[d] + cur, src[d], sizeof(double) * n, k));
+        // every new particle must lie inside the box with finite state; otherwise
+        // nothing is appended
+        CUDA_OK(cudaMemsetAsync(bad_counter(c), 0, sizeof(unsigned long long), c.stream));
+        k_count_bad_particles<<<nb256((long long)n), 256, 0, c.stream>>>(
+            (long long)n, flat.x + cur, flat.y + cur, flat.z + cur, flat.vx + cur, flat.vy + cur, flat.vz + cur,
+            (double)c.pmesh.nx, (double)c.pmesh.ny, (double)c.pmesh.nz, bad_counter(c));
+        CUDA_OK(cudaGetLastError());
+        unsigned long long bad = 0;
+        CUDA_OK(scopy(c.stream, &bad, bad_counter(c), sizeof(bad), cudaMemcpyDeviceToHost));
+        if (bad) {
+            st = rebuild(ctx, s, flat, (long long)cur);
+            free_parr(flat); lib_free(nflat);
+            if (st) return st;
+            FAIL(PIFEPIC_EINVAL, "load_particles: %llu of %zu particles outside the box or not finite", bad, n);
+        }
         long long newmax = q.next_id + (long long)n - 1;
         if (ids) {
             CUDA_OK(scopy(c.stream, flat.id + cur, ids, sizeof(long long) * n, k));
@@ -663,7 +762,7 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int s, size_t n, const d
             k_max_id<<<nb256((long long)n), 256, 0, c.stream>>>((long long)n, (const long long*)flat.id + cur, mx);
             unsigned long long hm = 0;
             CUDA_OK(scopy(c.stream, &hm, mx, sizeof(hm), cudaMemcpyDeviceToHost));
-            cudaFree(mx);
+            lib_free(mx);
             newmax = (long long)hm;
         } else {
             k_seq_id<<<nb256((long long)n), 256, 0, c.stream>>>((long long)n, q.next_id, flat.id + cur);
@@ -673,7 +772,7 @@ pifepic_status pifepic_load_particles(pifepic_ctx* ctx, int s, size_t n, const d
         CUDA_OK(scopy(c.stream, c.next_id + s, &q.next_id, sizeof(long long), cudaMemcpyHostToDevice));
     }
     st = rebuild(ctx, s, flat, (long long)cur + (long long)n);
-    free_parr(flat); cudaFree(nflat);
+    free_parr(flat); lib_free(nflat);
     return st;
 }
 
@@ -804,11 +903,17 @@ pifepic_status pifepic_set_external_E(pifepic_ctx* ctx, const double* E, int mem
     ALLOC(tmp, sizeof(double) * 3 * N);
     CUDA_OK(scopy(c.stream, tmp, E, sizeof(double) * 3 * N,
                        mem_kind == PIFEPIC_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    unsigned long long bad = 0;
+    CUDA_OK(count_nonfinite(c, 3 * N, tmp, &bad));
+    if (bad) {
+        lib_free(tmp);
+        FAIL(PIFEPIC_EINVAL, "set_external_E: %llu field values not finite", bad);
+    }
     k_pack_E<<<nb256(N), 256, 0, c.stream>>>(N, tmp, c.E, c.Ef);
     CUDA_OK(cudaGetLastError());
     CUDA_OK(launch_E_to_pic(c, c.stream, true));
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    cudaFree(tmp);
+    lib_free(tmp);
     c.external_E = true;
     return PIFEPIC_OK;
 }
@@ -875,7 +980,11 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
     const int herr = pk.err;
     c.stats = s;
     if (st) *st = s;
-    if (herr & ERR_TMA_TIMEOUT) FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
+    if (herr & ERR_TMA_TIMEOUT) {
+        szero(c.stream, c.err_word, sizeof(int));
+        cudaStreamSynchronize(c.stream);
+        FAIL(PIFEPIC_ETIMEOUT, "a node-field tile load timed out");
+    }
     if (herr & ERR_CHUNK_TIMEOUT) {
         szero(c.stream, c.err_word, sizeof(int));
         cudaStreamSynchronize(c.stream);
@@ -887,6 +996,7 @@ static pifepic_status fill_stats(pifepic_ctx* ctx, const unsigned long long* bef
         szero(c.stream, c.red_ticket, sizeof(unsigned) * 4);
         szero(c.stream, c.bar64, sizeof(unsigned long long) * BAR64_WORDS);
         szero(c.stream, c.err_word, sizeof(int));
+        szero(c.stream, c.scal + 45, sizeof(int));     // the exchange test hook, if it was set
         cudaStreamSynchronize(c.stream);
         FAIL(PIFEPIC_ETIMEOUT, "a grid barrier of the PCG solve timed out");
     }
@@ -1044,7 +1154,7 @@ pifepic_status pifepic_get_node_E(pifepic_ctx* ctx, double* E, int mem_kind) {
     k_unpack_E<<<nb256(N), 256, 0, c.stream>>>(N, c.E, tmp);
     CUDA_OK(cudaStreamSynchronize(c.stream));
     CUDA_OK(scopy(c.stream, E, tmp, sizeof(double) * 3 * N, out_kind(mem_kind)));
-    cudaFree(tmp);
+    lib_free(tmp);
     return PIFEPIC_OK;
 }
 
@@ -1057,7 +1167,7 @@ pifepic_status pifepic_get_node_E_f32(pifepic_ctx* ctx, float* E, int mem_kind) 
     k_unpack_Ef<<<nb256(N), 256, 0, c.stream>>>(N, c.Ef, tmp);
     CUDA_OK(cudaStreamSynchronize(c.stream));
     CUDA_OK(scopy(c.stream, E, tmp, sizeof(float) * 3 * N, out_kind(mem_kind)));
-    cudaFree(tmp);
+    lib_free(tmp);
     return PIFEPIC_OK;
 }
 
@@ -1155,7 +1265,7 @@ pifepic_status pifepic_get_particles(pifepic_ctx* ctx, int s, int64_t cap, doubl
         if (dst[d] && m > 0) CUDA_OK(scopy(c.stream, dst[d], src[d], sizeof(double) * m, k));
     if (ids && m > 0) CUDA_OK(scopy(c.stream, ids, flat.id, sizeof(int64_t) * m, k));
     *n = m;
-    free_parr(flat); cudaFree(nflat);
+    free_parr(flat); lib_free(nflat);
     return PIFEPIC_OK;
 }
 
@@ -1179,9 +1289,38 @@ pifepic_status pifepic_solve_field(pifepic_ctx* ctx, const double* F, const doub
         if (q) CUDA_OK(scopy(c.stream, c.qT, q, sizeof(double) * c.nit, k));
         else CUDA_OK(szero(c.stream, c.qT, sizeof(double) * c.nit));
     }
+    unsigned long long badF = 0, badq = 0;
+    CUDA_OK(count_nonfinite(c, N, Fd, &badF));
+    if (c.nit > 0 && q) CUDA_OK(count_nonfinite(c, c.nit, c.qT, &badq));
+    if (badF || badq) {
+        if (c.nit > 0) szero(c.stream, c.qT, sizeof(double) * c.nit);
+        lib_free(Fd);
+        FAIL(PIFEPIC_EINVAL, "solve_field: %llu load and %llu flux-jump values not finite", badF, badq);
+    }
     cudaError_t e = launch_solve_external(c, Fd, iters, relres);
-    cudaFree(Fd);
+    lib_free(Fd);
     if (e != cudaSuccess) FAIL(PIFEPIC_ECUDA, "field solve: %s", cudaGetErrorString(e));
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_get_memory_use(size_t* bytes) {
+    if (!bytes) return PIFEPIC_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    *bytes = g_mem_used;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_set_memory_limit(size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_limit = bytes;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_test_hold_exchange(pifepic_ctx* ctx, int extra) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (extra < 0 || extra > 1) FAIL(PIFEPIC_EINVAL, "test_hold_exchange: extra must be 0 or 1, not %d", extra);
+    CUDA_OK(scopy(c.stream, (int*)(c.scal + 45), &extra, sizeof(int), cudaMemcpyHostToDevice));
     return PIFEPIC_OK;
 }
 

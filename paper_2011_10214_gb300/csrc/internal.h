@@ -13,6 +13,15 @@
 
 namespace pf {
 
+// ---- device memory of the library ------------------------------------------
+// Every device allocation of the library goes through lib_malloc / lib_free,
+// which keep a process-wide count of the bytes held and refuse an allocation
+// that would take the count past the limit set by pifepic_set_memory_limit.
+cudaError_t lib_malloc_bytes(void** p, size_t bytes);
+cudaError_t lib_free(void* p);
+template <typename T>
+static inline cudaError_t lib_malloc(T** p, size_t bytes) { return lib_malloc_bytes((void**)p, bytes); }
+
 // ---- particle arrays (SoA) -------------------------------------------------
 struct PArr {            // FP64 mode: xi in cell units, physical velocity
     double *x, *y, *z, *vx, *vy, *vz;

@@ -660,34 +660,34 @@ cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool) {
     int* cnt = nullptr;
     long long* tot = nullptr;
     long long total = 0;
-    e = cudaMalloc(&cnt, sizeof(int) * c.nblocks);
+    e = lib_malloc(&cnt, sizeof(int) * c.nblocks);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&tot, sizeof(long long));
-    if (e != cudaSuccess) { cudaFree(cnt); return e; }
+    e = lib_malloc(&tot, sizeof(long long));
+    if (e != cudaSuccess) { lib_free(cnt); return e; }
     cudaMemsetAsync(cnt, 0, sizeof(int) * c.nblocks, c.stream);
     Launch L = make_launch(c);
     if (n > 0) k_bin_count<<<nb(n), 256, 0, c.stream>>>(L, flat, n, cnt);
     if (!q.bcap) {
-        cudaMalloc(&q.bcap, sizeof(int) * c.nblocks);
-        cudaMalloc(&q.bcount, sizeof(int) * c.nblocks);
-        cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
+        lib_malloc(&q.bcap, sizeof(int) * c.nblocks);
+        lib_malloc(&q.bcount, sizeof(int) * c.nblocks);
+        lib_malloc(&q.bstart, sizeof(long long) * c.nblocks);
     }
     k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
     k_bin_scan<<<1, BIN_SCAN_THREADS, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
     e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-    if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+    if (e != cudaSuccess) { lib_free(cnt); lib_free(tot); return e; }
     if (total > q.cap) {
         double** arr[6] = {&q.bins.x, &q.bins.y, &q.bins.z, &q.bins.vx, &q.bins.vy, &q.bins.vz};
-        for (auto a : arr) { cudaFree(*a); *a = nullptr; }
-        cudaFree(q.bins.id); q.bins.id = nullptr;
+        for (auto a : arr) { lib_free(*a); *a = nullptr; }
+        lib_free(q.bins.id); q.bins.id = nullptr;
         for (auto a : arr) {
-            e = cudaMalloc(a, sizeof(double) * total);
-            if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+            e = lib_malloc(a, sizeof(double) * total);
+            if (e != cudaSuccess) { lib_free(cnt); lib_free(tot); return e; }
         }
         if (c.track) {
-            e = cudaMalloc(&q.bins.id, sizeof(long long) * total);
-            if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+            e = lib_malloc(&q.bins.id, sizeof(long long) * total);
+            if (e != cudaSuccess) { lib_free(cnt); lib_free(tot); return e; }
         }
         q.cap = total;
     }
@@ -696,8 +696,8 @@ cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool) {
     if (n > 0) k_bin_scatter<<<nb(n), 256, 0, c.stream>>>(L, s, flat, n, c.track != 0);
     k_clamp_counts<<<dim3(nb(c.nblocks), (unsigned)c.sp.size()), 256, 0, c.stream>>>(L);
     e = cudaStreamSynchronize(c.stream);
-    cudaFree(cnt);
-    cudaFree(tot);
+    lib_free(cnt);
+    lib_free(tot);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -1004,10 +1004,10 @@ cudaError_t launch_flatten_mixed_to_f64(Ctx& c, int s, PArr flat, unsigned long 
 
 void free_parrf(PArrF& a) {
     if (a.base) {
-        cudaFree(a.base);
+        lib_free(a.base);
     } else {
-        cudaFree(a.cell); cudaFree(a.fx); cudaFree(a.fy); cudaFree(a.fz); cudaFree(a.vx); cudaFree(a.vy);
-        cudaFree(a.vz); cudaFree(a.id);
+        lib_free(a.cell); lib_free(a.fx); lib_free(a.fy); lib_free(a.fz); lib_free(a.vx); lib_free(a.vy);
+        lib_free(a.vz); lib_free(a.id);
     }
     a = PArrF{};
 }
@@ -1018,7 +1018,7 @@ cudaError_t alloc_parrf(PArrF& a, long long n, bool id) {
     const size_t m = (size_t)(n > 0 ? n : 1);
     const size_t mid = id ? sizeof(long long) * m : 0;
     char* b = nullptr;
-    cudaError_t e = cudaMalloc(&b, mid + 7 * sizeof(float) * m);
+    cudaError_t e = lib_malloc(&b, mid + 7 * sizeof(float) * m);
     if (e != cudaSuccess) return e;
     a.base = b;
     if (id) a.id = (long long*)b;
@@ -1036,28 +1036,28 @@ cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool)
     int* cnt = nullptr;
     long long* tot = nullptr;
     long long total = 0;
-    e = cudaMalloc(&cnt, sizeof(int) * c.nblocks);
+    e = lib_malloc(&cnt, sizeof(int) * c.nblocks);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&tot, sizeof(long long));
-    if (e != cudaSuccess) { cudaFree(cnt); return e; }
+    e = lib_malloc(&tot, sizeof(long long));
+    if (e != cudaSuccess) { lib_free(cnt); return e; }
     cudaMemsetAsync(cnt, 0, sizeof(int) * c.nblocks, c.stream);
     Launch L = make_launch(c);
     if (n > 0) k_bin_count<<<nb(n), 256, 0, c.stream>>>(L, flat, n, cnt);
     if (!q.bcap) {
-        cudaMalloc(&q.bcap, sizeof(int) * c.nblocks);
-        cudaMalloc(&q.bcount, sizeof(int) * c.nblocks);
-        cudaMalloc(&q.bstart, sizeof(long long) * c.nblocks);
-        cudaMalloc(&q.bstay, sizeof(int) * c.nblocks);
+        lib_malloc(&q.bcap, sizeof(int) * c.nblocks);
+        lib_malloc(&q.bcount, sizeof(int) * c.nblocks);
+        lib_malloc(&q.bstart, sizeof(long long) * c.nblocks);
+        lib_malloc(&q.bstay, sizeof(int) * c.nblocks);
     }
     cudaMemsetAsync(q.bstay, 0, sizeof(int) * c.nblocks, c.stream);
     k_bin_caps<<<nb(c.nblocks), 256, 0, c.stream>>>(c.nblocks, cnt, q.bcap, q.bcount);
     k_bin_scan<<<1, BIN_SCAN_THREADS, 0, c.stream>>>(c.nblocks, q.bcap, q.bstart, tot);
     e = cudaMemcpyAsync(&total, tot, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-    if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+    if (e != cudaSuccess) { lib_free(cnt); lib_free(tot); return e; }
     if (total > q.cap) {
         e = alloc_parrf(q.binsF, total, c.track != 0);
-        if (e != cudaSuccess) { cudaFree(cnt); cudaFree(tot); return e; }
+        if (e != cudaSuccess) { lib_free(cnt); lib_free(tot); return e; }
         q.cap = total;
     }
     L = make_launch(c);
@@ -1065,8 +1065,8 @@ cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool)
     if (n > 0) k_bin_scatter_m<<<nb(n), 256, 0, c.stream>>>(L, s, flat, n, c.track != 0);
     k_clamp_counts<<<dim3(nb(c.nblocks), (unsigned)c.sp.size()), 256, 0, c.stream>>>(L);
     e = cudaStreamSynchronize(c.stream);
-    cudaFree(cnt);
-    cudaFree(tot);
+    lib_free(cnt);
+    lib_free(tot);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -79,6 +79,7 @@ struct RegArgs {
     unsigned long long* fx;        // fixed-point exchange words: pq at [0], r.r and r.z at [FX_LINE], [2 FX_LINE];
                                    // pipelined loop: two sets of three at [(3 + 3 set + q) FX_LINE]
     int* classic;                  // MIXED: 1 once a solve found the pipelined recurrences too inexact
+    const int* hold;               // arrivals the launch's first exchange waits for beyond the grid (tests)
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -102,12 +103,15 @@ static __device__ __forceinline__ bool exchange(const Args& a, int& e, A (&v)[NV
     block_sum_t<A, NV>(v, sh);                // ends with __syncthreads: the block's z stores are issued
     const unsigned G = gridDim.x;
     A* val = (A*)a.val + (size_t)(e & 1) * 4 * G;
+    const bool first_of_launch = e == 0;
     ++e;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) __stcg(val + (size_t)q * G + blockIdx.x, v[q]);
         const unsigned long long t = atom_add_release(a.arrivals, 1ull);
-        const unsigned long long target = (t / G + 1) * G;
+        // (a test can make the launch's first exchange wait for arrivals that
+        // never come, to see the bounded wait give up and report)
+        const unsigned long long target = (t / G + 1) * G + (first_of_launch ? (unsigned long long)*a.hold : 0ull);
         int ok = 1;
         if (ld_acquire(a.arrivals) < target) {
             const long long c0 = clock64();
@@ -663,6 +667,7 @@ struct GlobArgs {
     double* val;
     unsigned long long* arrivals;
     unsigned long long* fx;         // fixed-point exchange words (as RegArgs::fx)
+    const int* hold;                // as RegArgs::hold
     PcgState* S;
     long long* it_total;
     long long* outer_total;
@@ -884,12 +889,12 @@ static void plan_pcg_reg(Ctx& c);
 // FP64 correction vector (made here, before any capture of the solve)
 void plan_pcg(Ctx& c) {
     plan_pcg_reg(c);
-    cudaFree(c.rowkind); cudaFree(c.pcg_x);
+    lib_free(c.rowkind); lib_free(c.pcg_x);
     c.rowkind = nullptr; c.pcg_x = nullptr;
     if (c.pcg_npt > 0) return;
     const long long N = c.mesh.nnodes;
-    if (cudaMalloc(&c.rowkind, sizeof(unsigned short) * N) != cudaSuccess ||
-        cudaMalloc(&c.pcg_x, sizeof(double) * N) != cudaSuccess) {
+    if (lib_malloc(&c.rowkind, sizeof(unsigned short) * N) != cudaSuccess ||
+        lib_malloc(&c.pcg_x, sizeof(double) * N) != cudaSuccess) {
         cudaGetLastError();
         return;   // the solve then reports cudaErrorNotReady
     }
@@ -980,6 +985,7 @@ static cudaError_t launch_reg(Ctx& c, cudaStream_t st, bool mixed) {
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
     a.err = c.err_word;
+    a.hold = (const int*)(c.scal + 45);
     void* args[] = {&a};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.pcg_G);
@@ -1014,6 +1020,7 @@ cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
     a.err = c.err_word;
+    a.hold = (const int*)(c.scal + 45);
     int dev = c.device, nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_glob<true>, GLOB_THREADS, 0);

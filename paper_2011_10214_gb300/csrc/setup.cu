@@ -445,7 +445,7 @@ static cudaError_t exclusive_scan(const int* in, long long n, long long* out, lo
                                   cudaStream_t st) {
     long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     long long* ts = nullptr;
-    cudaError_t e = cudaMalloc(&ts, sizeof(long long) * (ntiles > 0 ? ntiles : 1));
+    cudaError_t e = lib_malloc(&ts, sizeof(long long) * (ntiles > 0 ? ntiles : 1));
     if (e != cudaSuccess) return e;
     if (n > 0) {
         k_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, n, out, ts);
@@ -455,7 +455,7 @@ static cudaError_t exclusive_scan(const int* in, long long n, long long* out, lo
         cudaMemsetAsync(total_dev, 0, sizeof(long long), st);
     }
     e = cudaStreamSynchronize(st);
-    cudaFree(ts);
+    lib_free(ts);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -613,15 +613,15 @@ cudaError_t launch_setup(Ctx& c) {
     long long nit_alloc = 1;
     long long nmax = m.nnodes > m.ncells ? m.nnodes : m.ncells;
     int hdir[6]; double hval[6];
-    CK(cudaMalloc(&cnt, sizeof(int) * nmax));
-    CK(cudaMalloc(&scan, sizeof(long long) * nmax));
-    CK(cudaMalloc(&tot, sizeof(long long)));
-    CK(cudaMalloc(&flag, sizeof(int) * m.ncells));
-    CK(cudaMalloc(&carea, sizeof(double) * m.ncells));
-    CK(cudaMalloc(&own, sizeof(int) * m.ncells));
-    CK(cudaMalloc(&bcdir, sizeof(int) * 6));
-    CK(cudaMalloc(&bcval, sizeof(double) * 6));
-    CK(cudaMalloc(&bad, sizeof(int)));
+    CK(lib_malloc(&cnt, sizeof(int) * nmax));
+    CK(lib_malloc(&scan, sizeof(long long) * nmax));
+    CK(lib_malloc(&tot, sizeof(long long)));
+    CK(lib_malloc(&flag, sizeof(int) * m.ncells));
+    CK(lib_malloc(&carea, sizeof(double) * m.ncells));
+    CK(lib_malloc(&own, sizeof(int) * m.ncells));
+    CK(lib_malloc(&bcdir, sizeof(int) * 6));
+    CK(lib_malloc(&bcval, sizeof(double) * 6));
+    CK(lib_malloc(&bad, sizeof(int)));
 
     c.bed_outside = false;
     CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
@@ -639,11 +639,11 @@ cudaError_t launch_setup(Ctx& c) {
     c.nit = hv;
     k_narrow<<<nb(m.ncells), 256, 0, st>>>(scan, m.ncells, c.ibase);
     nit_alloc = c.nit > 0 ? c.nit : 1;
-    CK(cudaMalloc(&c.it_cell, sizeof(int) * nit_alloc));
-    CK(cudaMalloc(&c.it_t, sizeof(int) * nit_alloc));
-    CK(cudaMalloc(&c.it_data, sizeof(double) * IT_STRIDE * nit_alloc));
-    CK(cudaMalloc(&c.it_acc, sizeof(int) * nit_alloc));
-    CK(cudaMalloc(&c.qT, sizeof(double) * nit_alloc));
+    CK(lib_malloc(&c.it_cell, sizeof(int) * nit_alloc));
+    CK(lib_malloc(&c.it_t, sizeof(int) * nit_alloc));
+    CK(lib_malloc(&c.it_data, sizeof(double) * IT_STRIDE * nit_alloc));
+    CK(lib_malloc(&c.it_acc, sizeof(int) * nit_alloc));
+    CK(lib_malloc(&c.qT, sizeof(double) * nit_alloc));
     CK(cudaMemsetAsync(c.qT, 0, sizeof(double) * nit_alloc, st));
     k_interface<<<nb(m.ncells), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, c.ibase, c.it_cell, c.it_t, c.it_data);
     k_cell_area<<<nb(m.ncells), 256, 0, st>>>(m, c.imask, c.ibase, c.it_data, flag, carea);
@@ -654,9 +654,9 @@ cudaError_t launch_setup(Ctx& c) {
     {
         long long nc;
         nc = c.ncut > 0 ? c.ncut : 1;
-        CK(cudaMalloc(&c.cut_cell, sizeof(int) * nc));
-        CK(cudaMalloc(&c.cut_area, sizeof(double) * nc));
-        CK(cudaMalloc(&c.qcut, sizeof(double) * nc));
+        CK(lib_malloc(&c.cut_cell, sizeof(int) * nc));
+        CK(lib_malloc(&c.cut_area, sizeof(double) * nc));
+        CK(lib_malloc(&c.qcut, sizeof(double) * nc));
         CK(cudaMemsetAsync(c.qcut, 0, sizeof(double) * nc, st));
     }
     k_cut_list<<<nb(m.ncells), 256, 0, st>>>(m, flag, scan, carea, c.cut_cell, c.cut_area, own);
@@ -675,9 +675,9 @@ cudaError_t launch_setup(Ctx& c) {
     {
         long long np;
         np = c.npatch > 0 ? c.npatch : 1;
-        CK(cudaMalloc(&c.patch_node, sizeof(long long) * np));
-        CK(cudaMalloc(&c.patch_coef, sizeof(double) * 19 * np));
-        CK(cudaMalloc(&c.patch_coeff, sizeof(float) * 19 * np));
+        CK(lib_malloc(&c.patch_node, sizeof(long long) * np));
+        CK(lib_malloc(&c.patch_coef, sizeof(double) * 19 * np));
+        CK(lib_malloc(&c.patch_coeff, sizeof(float) * 19 * np));
     }
     k_patch_rows<<<nb(m.nnodes), 256, 0, st>>>(m, c.obj, c.Lnode, c.imask, c.ibase, c.it_data, cnt, scan,
                                                c.ntype, c.patch_node, c.patch_coef, c.patch_coeff, c.invdiag);
@@ -685,8 +685,8 @@ cudaError_t launch_setup(Ctx& c) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 done:
-    cudaFree(cnt); cudaFree(scan); cudaFree(tot); cudaFree(flag); cudaFree(carea); cudaFree(own);
-    cudaFree(bcdir); cudaFree(bcval); cudaFree(bad);
+    lib_free(cnt); lib_free(scan); lib_free(tot); lib_free(flag); lib_free(carea); lib_free(own);
+    lib_free(bcdir); lib_free(bcval); lib_free(bad);
     return err;
 }
 
@@ -694,7 +694,7 @@ done:
 // here, outside any captured graph)
 cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w) {
     void* old[] = {c.ph_tets, c.ph_Q, c.ph_carry, c.ph_cnt, c.ph_base, c.ph_tiles, c.ph_total};
-    for (void* p : old) cudaFree(p);
+    for (void* p : old) lib_free(p);
     c.ph_tets = nullptr; c.ph_Q = c.ph_carry = c.ph_base = c.ph_tiles = c.ph_total = nullptr; c.ph_cnt = nullptr;
     c.ph_ne = 0;
     const long long nit = c.nit;
@@ -707,11 +707,11 @@ cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double
     cudaError_t err = cudaSuccess;
     long long ne = 0;
     const long long n1 = nit > 0 ? nit : 1;
-    CK(cudaMalloc(&rec, sizeof(PhotoDev) * n1));
-    CK(cudaMalloc(&Qall, sizeof(long long) * n1));
-    CK(cudaMalloc(&pos, sizeof(long long) * n1));
-    CK(cudaMalloc(&flag, sizeof(int) * n1));
-    CK(cudaMalloc(&tot, sizeof(long long)));
+    CK(lib_malloc(&rec, sizeof(PhotoDev) * n1));
+    CK(lib_malloc(&Qall, sizeof(long long) * n1));
+    CK(lib_malloc(&pos, sizeof(long long) * n1));
+    CK(lib_malloc(&flag, sizeof(int) * n1));
+    CK(lib_malloc(&tot, sizeof(long long)));
     CK(cudaMemsetAsync(Qall, 0, sizeof(long long) * n1, c.stream));
     CK(cudaMemsetAsync(rec, 0, sizeof(PhotoDev) * n1, c.stream));
     if (nit > 0) {
@@ -726,13 +726,13 @@ cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double
     }
     {
         const long long m1 = ne > 0 ? ne : 1;
-        CK(cudaMalloc(&c.ph_tets, sizeof(PhotoDev) * m1));
-        CK(cudaMalloc(&c.ph_Q, sizeof(long long) * m1));
-        CK(cudaMalloc(&c.ph_carry, sizeof(long long) * m1));
-        CK(cudaMalloc(&c.ph_cnt, sizeof(int) * m1));
-        CK(cudaMalloc(&c.ph_base, sizeof(long long) * m1));
-        CK(cudaMalloc(&c.ph_tiles, sizeof(long long) * (m1 / 2048 + 2)));
-        CK(cudaMalloc(&c.ph_total, sizeof(long long)));
+        CK(lib_malloc(&c.ph_tets, sizeof(PhotoDev) * m1));
+        CK(lib_malloc(&c.ph_Q, sizeof(long long) * m1));
+        CK(lib_malloc(&c.ph_carry, sizeof(long long) * m1));
+        CK(lib_malloc(&c.ph_cnt, sizeof(int) * m1));
+        CK(lib_malloc(&c.ph_base, sizeof(long long) * m1));
+        CK(lib_malloc(&c.ph_tiles, sizeof(long long) * (m1 / 2048 + 2)));
+        CK(lib_malloc(&c.ph_total, sizeof(long long)));
         CK(cudaMemsetAsync(c.ph_carry, 0, sizeof(long long) * m1, c.stream));
         CK(cudaMemsetAsync(c.ph_total, 0, sizeof(long long), c.stream));
         if (ne > 0) k_photo_compact<<<nb(nit), 256, 0, c.stream>>>(nit, Qall, rec, pos, c.ph_tets, c.ph_Q);
@@ -742,7 +742,7 @@ cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double
         c.ph_vth = vth;
     }
 done:
-    cudaFree(rec); cudaFree(Qall); cudaFree(pos); cudaFree(flag); cudaFree(tot);
+    lib_free(rec); lib_free(Qall); lib_free(pos); lib_free(flag); lib_free(tot);
     return err;
 }
 
