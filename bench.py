@@ -26,6 +26,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# the headline metric: `value` is the plain (single-instance) rate; the line's `batched` and `served`
+# objects carry the batched rate (and its ratio to the plain one) and the served p50/p99 latency
+METRIC = "particle-steps/s incl. IFE solve, batched vs plain; served p50/p99 latency"
 BYTES_PER_PARTICLE_STEP = {"fp64": 96, "mixed": 56}     # read + write of the particle state
 
 
@@ -355,7 +358,7 @@ def run_gpu(args):
         sim_b.close()
 
     out = {
-        "metric": "particle-steps/s incl. IFE solve", "value": value, "unit": "particle-steps/s",
+        "metric": METRIC, "value": value, "unit": "particle-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if main == "fp64" else "f32+f64",
@@ -369,6 +372,14 @@ def run_gpu(args):
         "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st["phase_ms"]) if v},
         "compare": alt,
     }
+    # the metric's batched and served parts (rank 0, one GPU each; bounded)
+    if rank == 0 and not args.no_batched and args.workload == "sphere64":
+        b = measure_batch(args.instances, args.steps, args.warmup)
+        b["vs_plain"] = b["value"] / value
+        out["batched"] = b
+    if rank == 0 and not args.no_served and args.workload == "sphere64":
+        out["served"] = measure_serve(args.rate, args.served_horizon, args.max_steps, args.time_limit,
+                                      args.hbm_budget_gb, True)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:
@@ -473,7 +484,7 @@ def run_reference(args):
     cb = oracle_rate(args.workload, frac, max(1, args.steps))
     t1 = time.perf_counter()
     cfg = workload(args.workload)
-    out = {"impl": "reference", "metric": "particle-steps/s incl. IFE solve", "value": cb["value"],
+    out = {"impl": "reference", "metric": METRIC, "value": cb["value"],
            "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded Philox load and injection)", "config": cfg_desc(cfg, "fp64"),
@@ -483,15 +494,15 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def run_batch(args):
-    """64 independent sphere-charging instances (16^3..48^3 cells, R 1..8,
-    eps 2..10, 16..64 ppc/species), MIXED, one graph launch per step."""
+def measure_batch(instances, steps, warmup, autotune=True):
+    """c4: `instances` independent sphere-charging instances (16^3..48^3 cells,
+    R 1..8, eps 2..10, 16..64 ppc/species), MIXED, one graph launch per step;
+    CUDA events on the batch stream around the timed steps."""
     import numpy as np
     import torch
     from paper_2011_10214_gb300 import capi, serve
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rng = np.random.default_rng(2011102144)
-    cfgs = serve.request_distribution(rng, args.instances, big_fraction=0.0)
+    cfgs = serve.request_distribution(rng, instances, big_fraction=0.0)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     sims = []
@@ -501,58 +512,84 @@ def run_batch(args):
         sims.append(s)
     setup_s = time.perf_counter() - t0
     batch = capi.Batch(sims, stream=stream.cuda_stream)
-    best = None if args.no_autotune else serve.autotune_batch(batch)[0]
-    batch.step(args.warmup, stats=False)
+    tuned = serve.autotune_batch(batch) if autotune else None
+    batch.step(warmup, stats=False)
     torch.cuda.synchronize()
     clocks = Clocks(0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    st = batch.step(args.steps)
+    st = batch.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     pushed = sum(sum(x["pushed"]) for x in st)
-    out = {"metric": "particle-steps/s incl. IFE solve (batched)", "value": pushed / (ms / 1e3),
-           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32+f64",
-           "data": "synthetic (seeded Philox load and injection)",
-           "config": {"workload": f"{len(cfgs)} independent sphere-charging instances, n ~ U{{16..48}}^3, "
-                                  "R ~ U[1,8], eps ~ U[2,10], ppc ~ U{16..64}, MIXED",
-                      "particles": int(pushed / args.steps), "cta_nodes": best,
-                      "setup_s": setup_s},
-           "gpu_launches": int(sum(x["kernel_launches"] for x in st)), "graph_launches": args.steps,
-           "pcg_iters_per_step_max": max(x["pcg_iters_total"] for x in st) / args.steps, "clocks": ck}
+    out = {"value": pushed / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms / steps, "steps": steps,
+           "warmup": warmup, "instances": len(cfgs), "particles": int(pushed / steps),
+           "workload": f"{len(cfgs)} independent sphere-charging instances, n ~ U{{16..48}}^3 cells (h=0.5), "
+                       "R ~ U[1,8], eps ~ U[2,10], ppc ~ U{16..64} per species, MIXED, one graph launch per step",
+           "tuner": tuned, "setup_s": setup_s,
+           "gpu_launches": int(sum(x["kernel_launches"] for x in st)), "graph_launches": steps,
+           "pcg_iters_per_step_max": max(x["pcg_iters_total"] for x in st) / steps, "clocks": ck}
     batch.close()
     for s in sims:
         s.close()
+    return out
+
+
+def measure_serve(rate, horizon, max_steps, time_limit, hbm_budget_gb, overlap):
+    """c5: Poisson arrivals of sphere-charging requests (the batched
+    distribution plus 5 % at 96^3 with 64 ppc), admitted by HBM budget into one
+    running batch; latency = finish - arrival (host clock)."""
+    import numpy as np
+    import torch
+    from paper_2011_10214_gb300 import capi, serve
+    rng = np.random.default_rng(2011102145)
+    arr = serve.poisson_arrivals(rng, rate, horizon)
+    reqs = serve.request_distribution(rng, len(arr), big_fraction=0.05)
+    s_batch, s_admit = torch.cuda.Stream(), torch.cuda.Stream()
+    srv = serve.Server(int(hbm_budget_gb * 2**30), precision=capi.MIXED, steps_per_round=10, max_steps=max_steps,
+                       stream=s_batch.cuda_stream, overlap=overlap, admit_stream=s_admit.cuda_stream)
+    res = srv.run(reqs, arr, time_limit=time_limit)
+    srv.close()
+    return {"p50_s": res["p50_s"], "p99_s": res["p99_s"], "completed": res["completed"], "requests": len(arr),
+            "particle_steps_per_s": res["particle_steps_per_s"], "wall_s": res["wall_s"],
+            "admission": "overlapped (worker thread, own stream)" if overlap else "synchronous (between rounds)",
+            "workload": f"Poisson arrivals {rate}/s for {horizon} s; sphere-charging requests n ~ U{{16..48}}^3 "
+                        f"(+5% 96^3 at 64 ppc), stop at {max_steps} steps or <1% change of the area-mean surface "
+                        f"potential over 50 steps; HBM budget {hbm_budget_gb} GB"}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    b = measure_batch(args.instances, args.steps, args.warmup, autotune=not args.no_autotune)
+    out = {"metric": "particle-steps/s incl. IFE solve (batched)", "value": b["value"],
+           "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": b["ms_per_step"], "higher_is_better": True, "dtype": "f32+f64",
+           "data": "synthetic (seeded Philox load and injection)",
+           "config": {"workload": b["workload"], "particles": b["particles"], "tuner": b["tuner"],
+                      "setup_s": b["setup_s"]},
+           "gpu_launches": b["gpu_launches"], "graph_launches": b["graph_launches"],
+           "pcg_iters_per_step_max": b["pcg_iters_per_step_max"], "clocks": b["clocks"]}
     print(json.dumps(out))
 
 
 def run_serve(args):
-    """Poisson arrivals of sphere-charging requests (batched distribution plus
-    5 % at 96^3 with 64 ppc), admitted by HBM budget into one running batch."""
-    import numpy as np
+    """Both admission modes on the same arrival trace."""
     import torch
-    from paper_2011_10214_gb300 import capi, serve
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    rng = np.random.default_rng(2011102145)
-    arr = serve.poisson_arrivals(rng, args.rate, args.horizon)
-    reqs = serve.request_distribution(rng, len(arr), big_fraction=0.05)
-    stream = torch.cuda.Stream()
-    budget = int(args.hbm_budget_gb * 2**30)
-    srv = serve.Server(budget, precision=capi.MIXED, steps_per_round=10, max_steps=args.max_steps,
-                       stream=stream.cuda_stream)
-    res = srv.run(reqs, arr, time_limit=args.time_limit)
-    srv.close()
+    modes = {"sync": [False], "overlap": [True], "both": [False, True]}[args.admission]
+    res = [measure_serve(args.rate, args.horizon, args.max_steps, args.time_limit, args.hbm_budget_gb, o)
+           for o in modes]
+    main = res[-1]
     out = {"metric": "served latency p50/p99 and aggregate particle-steps/s", "unit": "s",
-           "p50_s": res["p50_s"], "p99_s": res["p99_s"], "completed": res["completed"], "requests": len(arr),
-           "particle_steps_per_s": res["particle_steps_per_s"], "wall_s": res["wall_s"],
-           "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic (seeded Poisson arrivals)",
-           "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.horizon}s; sphere-charging requests "
-                                  "n ~ U{16..48}^3 (+5% 96^3 at 64 ppc), stop at "
-                                  f"{args.max_steps} steps or <1% change of the surface potential over 50 steps",
-                      "hbm_budget_gb": args.hbm_budget_gb}}
+           "p50_s": main["p50_s"], "p99_s": main["p99_s"], "completed": main["completed"],
+           "requests": main["requests"], "particle_steps_per_s": main["particle_steps_per_s"],
+           "wall_s": main["wall_s"], "higher_is_better": False, "dtype": "f32+f64",
+           "data": "synthetic (seeded Poisson arrivals)",
+           "config": {"workload": main["workload"], "admission": main["admission"]},
+           "runs": res}
     print(json.dumps(out))
 
 
@@ -573,9 +610,13 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default nodes per CTA of the clustered solves")
     ap.add_argument("--rate", type=float, default=20.0)
-    ap.add_argument("--horizon", type=float, default=10.0)
+    ap.add_argument("--horizon", type=float, default=60.0, help="serve mode: arrival horizon in seconds")
+    ap.add_argument("--admission", default="both", choices=["sync", "overlap", "both"])
     ap.add_argument("--max-steps", type=int, default=500)
-    ap.add_argument("--time-limit", type=float, default=240.0)
+    ap.add_argument("--time-limit", type=float, default=600.0)
+    ap.add_argument("--no-batched", action="store_true", help="default line: skip the batched (c4) part")
+    ap.add_argument("--no-served", action="store_true", help="default line: skip the served (c5) part")
+    ap.add_argument("--served-horizon", type=float, default=10.0, help="default line: served arrival horizon")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--as-baseline", action="store_true")
     args = ap.parse_args()

@@ -10,10 +10,18 @@ once its area-mean surface potential changed by less than `rel_change` over
 the last `window` steps (the charging has reached its floating potential,
 Sec. 3.1.2).  Latency = finish time - arrival time.
 
+Admission overlaps the running work (overlap=True): a worker thread sets up
+each admitted request on its own CUDA stream while the main thread keeps
+stepping the batch, and the ready request joins the batch at the next round.
+With overlap=False the set-up runs between rounds on the batch's stream and
+every running member waits for it.
+
 Host-side orchestration only (admission, batch membership, stop tests); every
 step of every member runs in libpifepic's kernels.
 """
 import math
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -67,8 +75,12 @@ class Member:
 
 
 class Server:
+    """stream: the batch's CUDA stream (handle); admit_stream: the stream the
+    admission worker sets requests up on (overlap=True; None = the batch's)."""
+
     def __init__(self, hbm_budget, precision=capi.MIXED, steps_per_round=10, max_steps=500, window=50,
-                 rel_change=0.01, pcg_tol=1e-6, cta_nodes=8192, stream=None, keep_phi=False):
+                 rel_change=0.01, pcg_tol=1e-6, cta_nodes=8192, stream=None, keep_phi=False, overlap=True,
+                 admit_stream=None):
         self.budget = int(hbm_budget)
         self.precision = precision
         self.k = int(steps_per_round)
@@ -83,16 +95,68 @@ class Server:
         self.used = 0
         self.results = []
         self.keep_phi = keep_phi
+        self.overlap = bool(overlap)
+        self.inflight = 0            # handed to the admission worker, not yet in the batch
+        if self.overlap:
+            self.admit_stream = admit_stream if admit_stream is not None else stream
+            try:                     # the worker thread must use this thread's device
+                import torch
+                self.device = torch.cuda.current_device()
+            except Exception:
+                self.device = None
+            self._todo = queue.Queue()
+            self._ready = queue.Queue()
+            self._worker = threading.Thread(target=self._work, daemon=True)
+            self._worker.start()
 
-    def _admit(self, rid, cfg, arrival):
-        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=self.stream)
+    def _setup(self, cfg, stream):
+        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=stream)
         sim.solve()
         sim.leapfrog_init()
+        return sim
+
+    def _work(self):
+        """Admission worker: sets up handed-over requests on the admission
+        stream, in arrival order, while the main thread steps the batch."""
+        if self.device is not None:
+            import torch
+            torch.cuda.set_device(self.device)
+        while True:
+            item = self._todo.get()
+            if item is None:
+                return
+            rid, cfg, arrival = item
+            try:
+                self._ready.put((rid, cfg, arrival, self._setup(cfg, self.admit_stream), None))
+            except Exception as e:          # reported by the main thread
+                self._ready.put((rid, cfg, arrival, None, e))
+
+    def _join(self, rid, cfg, arrival, sim):
         self.batch.add(sim)
         m = Member(rid, cfg, arrival, sim, time.perf_counter())
         self.running.append(m)
-        self.used += estimate_bytes(cfg, self.precision)
         return m
+
+    def _join_ready(self, block=False):
+        """Add the requests the worker has finished setting up to the batch."""
+        while self.inflight:
+            try:
+                rid, cfg, arrival, sim, err = self._ready.get(block=block, timeout=0.05 if block else None)
+            except queue.Empty:
+                return
+            block = False
+            self.inflight -= 1
+            if err is not None:
+                raise err
+            self._join(rid, cfg, arrival, sim)
+
+    def _admit(self, rid, cfg, arrival):
+        self.used += estimate_bytes(cfg, self.precision)
+        if self.overlap:
+            self.inflight += 1
+            self._todo.put((rid, cfg, arrival))
+            return None
+        return self._join(rid, cfg, arrival, self._setup(cfg, self.stream))
 
     def _done(self, m):
         if m.steps >= self.max_steps:
@@ -107,25 +171,27 @@ class Server:
         """requests: list of workload dicts; arrivals: seconds after start.
         Returns per-request results and aggregate throughput."""
         t_start = time.perf_counter()
-        pending = sorted(zip(arrivals, range(len(requests)), requests))
-        queue = []
+        pending = sorted(zip(arrivals, range(len(requests)), requests), key=lambda t: (t[0], t[1]))
         pushed_total = 0
-        while pending or queue or self.running:
+        waiting = []
+        while pending or waiting or self.running or self.inflight:
             now = time.perf_counter() - t_start
             if time_limit is not None and now > time_limit:
                 break
             while pending and pending[0][0] <= now:
-                queue.append(pending.pop(0))
+                waiting.append(pending.pop(0))
             # admission by HBM budget, first come first served
-            while queue:
-                arr, rid, cfg = queue[0]
+            while waiting:
+                arr, rid, cfg = waiting[0]
                 need = estimate_bytes(cfg, self.precision)
-                if self.running and self.used + need > self.budget:
+                if (self.running or self.inflight) and self.used + need > self.budget:
                     break
-                queue.pop(0)
+                waiting.pop(0)
                 self._admit(rid, cfg, t_start + arr)
+            if self.overlap:
+                self._join_ready(block=not self.running)
             if not self.running:
-                if pending:
+                if pending and not self.inflight:
                     time.sleep(max(0.0, min(0.05, pending[0][0] - (time.perf_counter() - t_start))))
                 continue
             stats = self.batch.step(self.k)
@@ -153,6 +219,14 @@ class Server:
                     results=self.results)
 
     def close(self):
+        if self.overlap:
+            self._todo.put(None)
+            self._worker.join()
+            while not self._ready.empty():
+                item = self._ready.get()
+                if item[3] is not None:
+                    item[3].close()
+            self.inflight = 0
         for m in self.running:
             self.batch.remove(m.sim)
             m.sim.close()

@@ -81,20 +81,25 @@ def test_batched_fp64_member_matches_oracle():
     b.close(); gpu.close(); other.close()
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("overlap", [False, True])
+def test_served_results_equal_alone(overlap):
     """Three requests arriving while others run (continuous batching) give the
-    same potential as each run alone."""
+    same potential as each run alone; with overlap the admission worker sets
+    requests up on its own stream while the batch steps on another."""
+    import torch
     from paper_2011_10214_gb300 import capi, serve
     cfgs = [wl.sphere_config(12, 1.5, 8, 20, eps_in=2.0, seed_offset=21),
             wl.sphere_config(14, 2.0, 6, 20, eps_in=5.0, seed_offset=22),
             wl.sphere_config(10, 1.2, 10, 20, eps_in=8.0, seed_offset=23)]
     alone = []
     for c in cfgs:
-        srv = serve.Server(8 << 30, steps_per_round=5, max_steps=20, keep_phi=True)
+        srv = serve.Server(8 << 30, steps_per_round=5, max_steps=20, keep_phi=True, overlap=False)
         r = srv.run([c], [0.0])
         srv.close()
         alone.append(r["results"][0])
-    srv = serve.Server(8 << 30, steps_per_round=5, max_steps=20, keep_phi=True)
+    s_batch, s_admit = torch.cuda.Stream(), torch.cuda.Stream()
+    srv = serve.Server(8 << 30, steps_per_round=5, max_steps=20, keep_phi=True, overlap=overlap,
+                       stream=s_batch.cuda_stream, admit_stream=s_admit.cuda_stream)
     r = srv.run(cfgs, [0.0, 0.02, 0.04])
     srv.close()
     assert r["completed"] == 3 and r["p99_s"] >= r["p50_s"] > 0
