@@ -511,6 +511,17 @@ def measure_batch(instances, steps, warmup, autotune=True):
         s.solve(); s.leapfrog_init()
         sims.append(s)
     setup_s = time.perf_counter() - t0
+    # the same instances stepped one after another on their own (plain), for the batched-vs-plain ratio
+    alone_ms, alone_pushed = 0.0, 0
+    for s in sims:
+        s.step(2, stats=False)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        sa = s.step(4)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        alone_ms += ea.elapsed_time(eb) / 4
+        alone_pushed += sum(sa["pushed"]) / 4
     batch = capi.Batch(sims, stream=stream.cuda_stream)
     tuned = serve.autotune_batch(batch) if autotune else None
     batch.step(warmup, stats=False)
@@ -529,6 +540,10 @@ def measure_batch(instances, steps, warmup, autotune=True):
            "workload": f"{len(cfgs)} independent sphere-charging instances, n ~ U{{16..48}}^3 cells (h=0.5), "
                        "R ~ U[1,8], eps ~ U[2,10], ppc ~ U{16..64} per species, MIXED, one graph launch per step",
            "tuner": tuned, "setup_s": setup_s,
+           "alone": {"ms_per_step_sum": alone_ms, "value": alone_pushed / (alone_ms / 1e3),
+                     "note": "the same instances stepped one after another, each alone (its own solve on "
+                             "the whole GPU)"},
+           "vs_alone": (alone_ms / (ms / steps)),
            "gpu_launches": int(sum(x["kernel_launches"] for x in st)), "graph_launches": steps,
            "pcg_iters_per_step_max": max(x["pcg_iters_total"] for x in st) / steps, "clocks": ck}
     batch.close()
