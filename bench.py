@@ -29,6 +29,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the headline metric: `value` is the plain (single-instance) rate; the line's `batched` and `served`
 # objects carry the batched rate (and its ratio to the plain one) and the served p50/p99 latency
 METRIC = "particle-steps/s incl. IFE solve, batched vs plain; served p50/p99 latency"
+PRECOND = 0   # MIXED preconditioner of the measured contexts (--precond; 0 = the library's automatic choice)
 BYTES_PER_PARTICLE_STEP = {"fp64": 96, "mixed": 56}     # read + write of the particle state
 
 
@@ -206,6 +207,8 @@ def measure(cfg, precision, steps, warmup, stream, dist, local):
     from paper_2011_10214_gb300 import capi
     prec = capi.MIXED if precision == "mixed" else capi.FP64
     sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream)
+    if PRECOND:
+        sim.set_preconditioner(PRECOND)
     sim.solve()
     sim.leapfrog_init()
     if warmup > 0:
@@ -271,14 +274,23 @@ def roofline_solve(precision, st, steps, nnodes):
     alg = nnodes * SOLVE_BYTES_PER_NODE_ITER[precision] * iters
     ach = alg / (solve_ms / 1e3) / 1e9
     peaks, src = _peaks()
-    # the register-resident kernel serves meshes of at most 8 nodes per thread of a full grid
+    # the register-resident kernel serves meshes of at most 8 nodes per thread of a full grid; beyond it MIXED
+    # solves run the multigrid-preconditioned kernel (unless --precond jacobi), FP64 the global-memory one
     reg = nnodes <= NSM * 512 * 8
-    kname = "k_pcg_reg (registers)" if reg else "k_pcg_glob (global memory)"
+    mg = precision == "mixed" and (PRECOND == 2 or (PRECOND == 0 and not reg))
+    if mg:
+        # per inner iteration: the PCG's 7 FP32 passes plus the V-cycle's fine-level passes (pre-smoothing
+        # 12 B, residual 12 B, correction 8 B, post-smoothing 16 B); the coarse levels add about 1/7 more
+        alg = nnodes * (SOLVE_BYTES_PER_NODE_ITER["mixed"] + 48) * iters
+        ach = alg / (solve_ms / 1e3) / 1e9
+    kname = ("k_pcg_mg (global memory, multigrid V-cycle)" if mg else
+             "k_pcg_reg (registers)" if reg else "k_pcg_glob (global memory)")
     return {"kernel": f"{kname}: persistent PCG, one launch per solve, in the solve graph", "bound": "hbm",
             "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src,
             "alg_bytes_per_launch": alg, "avg_launch_ms": solve_ms, "iters_per_solve": iters,
-            "note": ("latency-bound: one grid exchange per inner iteration (pipelined PCG), vectors in registers "
+            "note": ("multigrid-preconditioned PCG: ~16-20 grid barriers per inner iteration, vectors in L2" if mg else
+                     "latency-bound: one grid exchange per inner iteration (pipelined PCG), vectors in registers "
                      "and L2" if precision == "mixed" else
                      "latency-bound: two grid exchanges per iteration, vectors in registers and L2")}
 
@@ -634,7 +646,11 @@ def main():
     ap.add_argument("--served-horizon", type=float, default=10.0, help="default line: served arrival horizon")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--as-baseline", action="store_true")
+    ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "multigrid"],
+                    help="MIXED field-solve preconditioner (pifepic_set_preconditioner)")
     args = ap.parse_args()
+    global PRECOND
+    PRECOND = {"auto": 0, "jacobi": 1, "multigrid": 2}[args.precond]
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":

@@ -187,6 +187,23 @@ pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_be
  * a later change).  No effect in FP64 mode.  Errors: EINVAL unless
  * 0 < reduction < 1 and 0 < margin <= 1. */
 pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double margin);
+
+/* Preconditioner of the MIXED inner PCG of a single context (Sec. 2.5 names
+ * the PCG but no preconditioner).  JACOBI: the diagonal, as the FP64 path and
+ * the oracle.  MULTIGRID: one geometric V(1,1) cycle per iteration -- coarse
+ * levels at the even nodes of each axis (plus the last node of an odd axis),
+ * trilinear prolongation with zero Dirichlet correction, restriction its
+ * transpose, Galerkin coarse operators (27-point, built at set-up), damped
+ * Jacobi smoothing (weight 0.6), the coarsest level (at most 256 nodes)
+ * solved exactly by its dense inverse.  AUTO (the default): MULTIGRID for
+ * meshes too large for the register-resident solver (more than 8 nodes per
+ * thread of a full grid, about 620,000 nodes), where the Jacobi iteration
+ * count outgrows the cap, else JACOBI.  Either solves the same system to the
+ * same stopping test.  Takes effect at once (the solve is re-planned); no
+ * effect in FP64 mode or on batched solves.  Errors: EINVAL (unknown kind),
+ * ENOMEM. */
+enum { PIFEPIC_PRECOND_AUTO = 0, PIFEPIC_PRECOND_JACOBI = 1, PIFEPIC_PRECOND_MULTIGRID = 2 };
+pifepic_status pifepic_set_preconditioner(pifepic_ctx* ctx, int kind);
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
 
 /* Species with charge q, mass m (q/m sets the push) and macro-particle

@@ -24,6 +24,7 @@ UNITS = [
     ("particles_mixed.cu", []),
     ("field.cu", []),
     ("pcg_coop.cu", []),
+    ("pcg_mg.cu", []),
     ("pcg_cluster.cu", []),
     ("batch.cu", []),
     ("capi.cu", ["--fmad=false"]),

@@ -18,6 +18,7 @@ HOST, DEVICE = 0, 1
 OBJ_NONE, OBJ_SPHERE, OBJ_CAP_CRATER, OBJ_PLANE, OBJ_RIM_CRATER = 0, 1, 2, 3, 4
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PBC_ABSORB, PBC_INJECT, PBC_REFLECT = 0, 1, 2
+PRECOND_AUTO, PRECOND_JACOBI, PRECOND_MULTIGRID = 0, 1, 2
 _PBC_NAMES = {"absorb": PBC_ABSORB, "inject": PBC_INJECT, "reflect": PBC_REFLECT}
 MAX_SPECIES = 8
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESTATE", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOTCONV"}
@@ -102,6 +103,7 @@ _sigs = {
     "pifepic_get_stats": [_ctx, C.POINTER(Stats)],
     "pifepic_solve_field": [_ctx, _dp, _dp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "pifepic_solve_field_noalloc": [_ctx, _dp, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "pifepic_set_preconditioner": [_ctx, C.c_int],
     "pifepic_get_memory_use": [C.POINTER(C.c_size_t)],
     "pifepic_set_memory_limit": [C.c_size_t],
     "pifepic_test_hold_exchange": [_ctx, C.c_int],
@@ -213,6 +215,10 @@ class Simulation:
         """MIXED refinement controls (see pifepic_set_refinement): an FP32 inner
         solve stops at max(margin tol |b|, reduction |r0|)."""
         self._ok(lib.pifepic_set_refinement(self._c, float(reduction), float(margin)), "set_refinement")
+
+    def set_preconditioner(self, kind):
+        """MIXED inner PCG preconditioner: PRECOND_AUTO, PRECOND_JACOBI or PRECOND_MULTIGRID."""
+        self._ok(lib.pifepic_set_preconditioner(self._c, int(kind)), "set_preconditioner")
 
     def set_field_bc(self, faces):
         arr = (FaceBC * 6)()

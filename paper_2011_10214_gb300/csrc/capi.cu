@@ -65,6 +65,8 @@ cudaError_t alloc_parrf(PArrF& a, long long n, bool id);
 void free_parrf(PArrF& a);
 pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, double* phi, int* iters,
                                    double* relres);
+void free_mg(Ctx& c);                         // pcg_mg.cu
+cudaError_t build_pcg_graph(Ctx& c);          // field.cu
 
 // 5-tet split tables, computed from the definition (reading of Sec. 3.1.1)
 static TetTables make_tables() {
@@ -388,6 +390,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     for (void* p : ptrs) lib_free(p);
     if (c.stat_host) cudaFreeHost(c.stat_host);
     if (c.refine > 1) { lib_free(c.Ep); lib_free(c.Efp); }
+    free_mg(c);
     for (auto& s : c.sp) {
         free_parr(s.bins); free_parr(s.mov[0]); free_parr(s.mov[1]);
         lib_free(s.bstart); lib_free(s.bcap); lib_free(s.bcount); lib_free(s.bstay); lib_free(s.mov_n);
@@ -528,6 +531,20 @@ pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double
         FAIL(PIFEPIC_EINVAL, "refinement needs 0 < reduction < 1 and 0 < margin <= 1");
     c.inner_red = reduction;
     c.inner_margin = margin;
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_set_preconditioner(pifepic_ctx* ctx, int kind) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (kind != PIFEPIC_PRECOND_AUTO && kind != PIFEPIC_PRECOND_JACOBI && kind != PIFEPIC_PRECOND_MULTIGRID)
+        FAIL(PIFEPIC_EINVAL, "unknown preconditioner %d", kind);
+    c.precond = kind;
+    if (c.have_object) {   // re-plan the solve (and its graph) for the new preconditioner
+        cudaError_t e = build_pcg_graph(c);
+        if (e == cudaErrorMemoryAllocation) FAIL(PIFEPIC_ENOMEM, "preconditioner set-up: out of memory");
+        CUDA_OK(e);
+    }
     return PIFEPIC_OK;
 }
 

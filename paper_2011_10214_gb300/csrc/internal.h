@@ -22,6 +22,17 @@ cudaError_t lib_free(void* p);
 template <typename T>
 static inline cudaError_t lib_malloc(T** p, size_t bytes) { return lib_malloc_bytes((void**)p, bytes); }
 
+// ---- multigrid levels of the MIXED field solve (pcg_mg.cu) -----------------
+constexpr int MG_MAX_LEVELS = 8;
+struct MgLevel {                  // a coarse level (27-point Galerkin rows)
+    int nx = 0, ny = 0, nz = 0;   // cells
+    int NX = 0, NY = 0, NZ = 0;   // nodes
+    long long N = 0;
+    float* coef = nullptr;        // [27][N]: coefficient plane q of offset (q%3-1, q/3%3-1, q/9-1)
+    float* dinv = nullptr;        // [N] inverse diagonal, 0 where the row is empty (Dirichlet support)
+    float *b = nullptr, *x = nullptr, *res = nullptr, *y = nullptr;   // cycle vectors [N]
+};
+
 // ---- particle arrays (SoA) -------------------------------------------------
 struct PArr {            // FP64 mode: xi in cell units, physical velocity
     double *x, *y, *z, *vx, *vy, *vz;
@@ -211,6 +222,11 @@ struct Ctx {
     // global-memory kernel; -1: not planned yet), blocks, nodes per block, z window
     int pcg_npt = -1;
     bool pcg_rows = false;            // operator rows staged in shared memory
+    int precond = PIFEPIC_PRECOND_AUTO;   // MIXED single-context solves: Jacobi or multigrid
+    int mg_nlev = 0;                  // multigrid coarse levels (0: Jacobi)
+    MgLevel mg[MG_MAX_LEVELS];        // mg[1..mg_nlev]
+    float* mg_r0 = nullptr;           // fine residual after pre-smoothing
+    float* mg_cinv = nullptr;         // dense inverse of the coarsest operator
     unsigned short* rowkind = nullptr;  // global-memory PCG (larger meshes): row kinds, [N]
     double* pcg_x = nullptr;            // and its FP64 correction vector, [N]
     int pcg_G = 1;

@@ -160,3 +160,36 @@ def test_refinement_controls():
         with pytest.raises(RuntimeError):
             sim.set_refinement(red, margin)
     sim.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_multigrid_preconditioned_solve_matches_oracle(case):
+    """MIXED solve with the geometric multigrid preconditioner (Galerkin coarse
+    levels, odd axes included, Dirichlet and interface rows, hybrid IFE
+    meshes): the oracle's FP64 solution at tol 1e-12, in a small fraction of
+    the Jacobi iterations."""
+    from paper_2011_10214_gb300 import capi
+    gpu, orc = make_pair(case, precision=capi.MIXED)
+    gpu.set_preconditioner(capi.PRECOND_MULTIGRID)
+    fs = orc.fs
+    g = np.random.default_rng(11)
+    F = g.normal(size=fs.mesh.nnodes) * fs.mesh.h ** 3
+    q = np.where(fs.it_kind == 0, g.normal(size=len(fs.it_cell)), 0.0)
+    phi_o, it_o, _ = fs.solve(F, q, tol=1e-12, maxit=5000)
+    it, rr = gpu.solve_field(F, q)
+    assert rr <= 1e-12
+    assert _rel(gpu.potential(), phi_o) <= TOL_PHI
+    assert it <= max(40, it_o // 3), (it, it_o)
+    # back to Jacobi: the same solution
+    gpu.set_preconditioner(capi.PRECOND_JACOBI)
+    gpu.solve_field(F, q)
+    assert _rel(gpu.potential(), phi_o) <= TOL_PHI
+    gpu.close()
+
+
+def test_preconditioner_choice_is_validated():
+    from paper_2011_10214_gb300 import capi
+    sim = capi.Simulation((8, 8, 8), 0.5, 0.05, precision=capi.MIXED)
+    with pytest.raises(capi.PifepicError, match="EINVAL"):
+        sim.set_preconditioner(7)
+    sim.close()
