@@ -349,11 +349,21 @@ typedef struct pifepic_batch pifepic_batch;
 pifepic_status pifepic_batch_create(pifepic_ctx** ctxs, int n, void* stream, pifepic_batch** out);
 pifepic_status pifepic_batch_add(pifepic_batch* batch, pifepic_ctx* ctx);
 pifepic_status pifepic_batch_remove(pifepic_batch* batch, pifepic_ctx* ctx);
-/* Preferred nodes per CTA of the clustered solves (2048, 4096 or 8192, the
- * default): a member gets the smallest cluster that keeps each CTA at or under
- * it.  Fewer nodes per CTA is less work per iteration and more synchronisation;
- * the serving loop's tuner picks by timing steps.  EINVAL for other values. */
+/* Preferred nodes per CTA of the clustered solves (a power of two from 2048
+ * to 65536; 8192 is the default): a member gets the smallest cluster that
+ * keeps each CTA at or under it (Jacobi clusters: also the smallest whose
+ * working set fits in shared memory).  Fewer nodes per CTA is less work per
+ * iteration and more synchronisation; the serving loop's tuner picks by timing
+ * steps.  EINVAL for other values. */
 pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* batch, int cta_nodes);
+/* Preconditioner of the batch's MIXED field solves: AUTO and MULTIGRID solve
+ * every member with a multigrid hierarchy (every MIXED context builds one at
+ * set-up) by the multigrid-preconditioned PCG on one thread-block cluster of
+ * ceil(nodes / cta_nodes) CTAs (1 to 16); JACOBI keeps the Jacobi PCG on
+ * clusters of the member's whole working set in shared memory.  FP64 batches
+ * always use Jacobi.  The graph is rebuilt on the next step.  EINVAL for an
+ * unknown kind. */
+pifepic_status pifepic_batch_set_preconditioner(pifepic_batch* batch, int kind);
 pifepic_status pifepic_batch_step(pifepic_batch* batch, int nsteps, pifepic_stats* stats);
 const char* pifepic_batch_last_error(const pifepic_batch* batch);
 void pifepic_batch_destroy(pifepic_batch* batch);

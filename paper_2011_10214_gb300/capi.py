@@ -112,6 +112,7 @@ _sigs = {
     "pifepic_batch_remove": [C.c_void_p, _ctx],
     "pifepic_batch_set_cta_nodes": [C.c_void_p, C.c_int],
     "pifepic_batch_step": [C.c_void_p, C.c_int, C.c_void_p],
+    "pifepic_batch_set_preconditioner": [C.c_void_p, C.c_int],
 }
 for _n, _a in _sigs.items():
     _f = getattr(lib, _n)
@@ -460,6 +461,10 @@ class Batch:
     def remove(self, sim):
         self._ok(lib.pifepic_batch_remove(self._b, sim._c), "batch_remove")
         self.members.remove(sim)
+
+    def set_preconditioner(self, kind):
+        """The batched MIXED solves' preconditioner (pifepic_batch_set_preconditioner)."""
+        self._ok(lib.pifepic_batch_set_preconditioner(self._b, int(kind)), "batch_set_preconditioner")
 
     def set_cta_nodes(self, cta_nodes):
         """Preferred nodes per CTA of the clustered field solves (2048, 4096, 8192)."""

@@ -8,6 +8,7 @@
 // Sec. 5); batching and serving many charging problems is this build's addition
 // on top of the same per-instance method.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -27,8 +28,9 @@ pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, 
 
 
 int cluster_size_for(long long N, long long H, bool mixed, long long cta_nodes);   // pcg_cluster.cu
+cudaError_t launch_pcg_mg_cluster(Ctx& c, int C, cudaStream_t st);                 // pcg_mg.cu
 size_t cluster_smem_for(long long N, long long H, int C, bool mixed);
-cudaError_t launch_pcg_cluster(const BatchItem* items, int count, int C, size_t smem, bool mixed, cudaStream_t st);
+cudaError_t launch_pcg_cluster(const BatchItem& item, int C, size_t smem, bool mixed, cudaStream_t st);
 cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st);                               // pcg_coop.cu
 cudaError_t launch_push(Ctx& c);
 cudaError_t launch_movers(Ctx& c);
@@ -78,9 +80,8 @@ using namespace pf;
 struct pifepic_batch {
     std::vector<pifepic_ctx*> ctx;
     cudaStream_t stream = nullptr;
-    BatchItem* items = nullptr;
-    int items_cap = 0;
     int cta_nodes = 8192;
+    int precond = PIFEPIC_PRECOND_AUTO;   // MIXED members: multigrid clusters where a hierarchy exists
     bool dirty = true;
     std::vector<long long> kernels;   // kernels per step of each instance (its share of the batch graph)
     cudaGraph_t graph = nullptr;
@@ -105,32 +106,30 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     int n = (int)b->ctx.size();
     if (n == 0) { b->dirty = false; return cudaSuccess; }
     bool mixed = b->ctx[0]->c.precision == PIFEPIC_MIXED;
-    if (n > b->items_cap) {
-        lib_free(b->items);
-        cudaError_t e = lib_malloc(&b->items, sizeof(BatchItem) * n);
-        if (e != cudaSuccess) return e;
-        b->items_cap = n;
-    }
     // solve groups: cluster size per instance (0: the one-CTA kernel), items in group order
-    std::vector<int> csize(n, -1);
+    // members solved by the multigrid cluster kernel (MIXED, with a hierarchy):
+    // csize -2, cluster size in mg_c
+    std::vector<int> csize(n, -1), mg_c(n, 0);
+    std::vector<int> mg_members;
     for (int i = 0; i < n; ++i) {
         const Ctx& c = b->ctx[i]->c;
-        if (!c.external_E) csize[i] = cluster_size_for(c.mesh.nnodes, node_halo(c.mesh), mixed, b->cta_nodes);
+        if (c.external_E) continue;
+        if (mixed && b->precond != PIFEPIC_PRECOND_JACOBI && c.mg_nlev > 0) {
+            long long C = (c.mesh.nnodes + b->cta_nodes - 1) / b->cta_nodes;
+            mg_c[i] = (int)std::max(1ll, std::min(16ll, C));
+            csize[i] = -2;
+            mg_members.push_back(i);
+            continue;
+        }
+        csize[i] = cluster_size_for(c.mesh.nnodes, node_halo(c.mesh), mixed, b->cta_nodes);
     }
     const int groups[6] = {16, 8, 4, 2, 1, 0};
     std::vector<int> order;
-    std::vector<BatchItem> h;
     for (int g : groups)
         for (int i = 0; i < n; ++i)
-            if (csize[i] == g) { order.push_back(i); h.push_back(make_item(b->ctx[i]->c)); }
-    cudaError_t e = cudaSuccess;
-    if (!h.empty()) {
-        e = cudaMemcpyAsync(b->items, h.data(), sizeof(BatchItem) * h.size(), cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) return e;
-    }
+            if (csize[i] == g) order.push_back(i);
     cudaStream_t cs;
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     cudaGraph_t g;
     e = cudaGraphCreate(&g, 0);
@@ -155,27 +154,37 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
         c.launches = l0;
     }
     // one solve launch per instance, waiting only for that instance's branch
-    size_t off = 0;
     std::vector<int> fallback;
     for (int gsz : groups) {
         for (int i : order) {
             if (csize[i] != gsz) continue;
-            const BatchItem* items = b->items + off;
-            ++off;
             if (gsz == 0) { fallback.push_back(i); continue; }
             if (e != cudaSuccess) break;
-            const Ctx& c = b->ctx[i]->c;
+            Ctx& c = b->ctx[i]->c;
             const size_t smem = cluster_smem_for(c.mesh.nnodes, node_halo(c.mesh), gsz, mixed);
             cudaGraph_t sub = nullptr;
             e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e2 = launch_pcg_cluster(items, 1, gsz, smem, mixed, cs);
+                cudaError_t e2 = launch_pcg_cluster(make_item(c), gsz, smem, mixed, cs);
                 e = cudaStreamEndCapture(cs, &sub);
                 if (e == cudaSuccess) e = e2;
             }
             if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&solve_of[i], g, &pre[i], 1, sub);
             if (sub) cudaGraphDestroy(sub);
         }
+    }
+    // multigrid members: one cluster launch each
+    for (size_t k = 0; k < mg_members.size() && e == cudaSuccess; ++k) {
+        const int i = mg_members[k];
+        cudaGraph_t sub = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = launch_pcg_mg_cluster(b->ctx[i]->c, mg_c[i], cs);
+            e = cudaStreamEndCapture(cs, &sub);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&solve_of[i], g, &pre[i], 1, sub);
+        if (sub) cudaGraphDestroy(sub);
     }
     // instances too large for a cluster: the single-instance persistent solver
     // (one cooperative launch over the device), one after another -- two
@@ -243,8 +252,16 @@ pifepic_status pifepic_batch_remove(pifepic_batch* b, pifepic_ctx* ctx) {
 }
 
 pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* b, int cta_nodes) {
-    if (!b || (cta_nodes != 2048 && cta_nodes != 4096 && cta_nodes != 8192)) return PIFEPIC_EINVAL;
+    if (!b || cta_nodes < 2048 || cta_nodes > 65536 || (cta_nodes & (cta_nodes - 1))) return PIFEPIC_EINVAL;
     if (cta_nodes != b->cta_nodes) { b->cta_nodes = cta_nodes; b->dirty = true; }
+    return PIFEPIC_OK;
+}
+
+pifepic_status pifepic_batch_set_preconditioner(pifepic_batch* b, int kind) {
+    if (!b) return PIFEPIC_EINVAL;
+    if (kind != PIFEPIC_PRECOND_AUTO && kind != PIFEPIC_PRECOND_JACOBI && kind != PIFEPIC_PRECOND_MULTIGRID)
+        return batch_fail(b, PIFEPIC_EINVAL, "unknown preconditioner");
+    if (kind != b->precond) { b->precond = kind; b->dirty = true; }
     return PIFEPIC_OK;
 }
 
@@ -290,7 +307,6 @@ void pifepic_batch_destroy(pifepic_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    lib_free(b->items);
     delete b;
 }
 

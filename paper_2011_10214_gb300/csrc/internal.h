@@ -223,7 +223,8 @@ struct Ctx {
     int pcg_npt = -1;
     bool pcg_rows = false;            // operator rows staged in shared memory
     int precond = PIFEPIC_PRECOND_AUTO;   // MIXED single-context solves: Jacobi or multigrid
-    int mg_nlev = 0;                  // multigrid coarse levels (0: Jacobi)
+    int mg_nlev = 0;                  // multigrid coarse levels (0: none)
+    bool mg_single = false;           // the context's own MIXED solve uses the multigrid cycle
     MgLevel mg[MG_MAX_LEVELS];        // mg[1..mg_nlev]
     float* mg_r0 = nullptr;           // fine residual after pre-smoothing
     float* mg_cinv = nullptr;         // dense inverse of the coarsest operator

@@ -90,14 +90,15 @@ static __device__ __forceinline__ unsigned cl_pack(int i, int j, int k) {
     return (unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22);
 }
 
+static_assert(sizeof(BatchItem) <= 4096, "the solve arguments travel as a kernel parameter");
+
 template <bool MIXED>
-__global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem* items, int C) {
+__global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem a, int C) {
     using T = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char cl_raw[];
     __shared__ ClusterShared cs;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const BatchItem& a = items[blockIdx.x / C];
     const FieldArgs& f = a.f;
     const Mesh& m = f.m;
     const long long N = m.nnodes;
@@ -273,15 +274,15 @@ int cluster_size_for(long long N, long long H, bool mixed, long long cta_nodes) 
     return best;
 }
 
-// one launch for `count` instances (items[0..count)) that share cluster size C;
-// smem = the largest per-CTA working set among them
-cudaError_t launch_pcg_cluster(const BatchItem* items, int count, int C, size_t smem, bool mixed, cudaStream_t st) {
+// one instance's solve on one cluster of C CTAs (the arguments by value, in the
+// kernel's parameter space); smem = its per-CTA working set
+cudaError_t launch_pcg_cluster(const BatchItem& item, int C, size_t smem, bool mixed, cudaStream_t st) {
     void* kern = mixed ? (void*)k_pcg_cluster<true> : (void*)k_pcg_cluster<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(C * count));
+    cfg.gridDim = dim3((unsigned)C);
     cfg.blockDim = dim3(CL_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -296,7 +297,8 @@ cudaError_t launch_pcg_cluster(const BatchItem* items, int count, int C, size_t 
     e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
     if (e != cudaSuccess) return e;
     if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    void* args[] = {(void*)&items, (void*)&C};
+    BatchItem a = item;
+    void* args[] = {(void*)&a, (void*)&C};
     return cudaLaunchKernelExC(&cfg, kern, args);
 }
 

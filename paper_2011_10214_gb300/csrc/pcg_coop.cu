@@ -851,7 +851,7 @@ cudaError_t launch_pcg_mg(Ctx& c, cudaStream_t st);   // pcg_mg.cu
 cudaError_t launch_pcg_coop(Ctx& c, cudaStream_t st) {
     bool mixed = c.precision == PIFEPIC_MIXED;
     if (c.pcg_npt < 0) plan_pcg(c);
-    if (mixed && c.mg_nlev > 0) {
+    if (mixed && c.mg_single && c.mg_nlev > 0) {
         if (!c.rowkind) return cudaErrorNotReady;
         return launch_pcg_mg(c, st);
     }

@@ -27,15 +27,24 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "field_common.cuh"
 #include "internal.h"
 #include "pcg_sync.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace pf {
 
 constexpr int MG_THREADS = 512;
+// batched (cluster) solves: smaller CTAs, two per SM, so that the latency-bound
+// passes of two systems interleave on one SM
+constexpr int MG_CL_THREADS = 256;
+constexpr int MG_CL_PER_SM = 2;
 constexpr int MG_MAX_OUTER = 12;          // refinement steps at most
 constexpr long long MG_COARSEST = 256;    // coarsening stops at or below this many nodes
 constexpr float MG_OMEGA = 0.6f;          // damped-Jacobi weight
@@ -61,6 +70,8 @@ struct MgArgs {
     long long* outer_total;
     int* err;
 };
+
+static_assert(sizeof(MgArgs) <= 4096, "the solve arguments travel as a kernel parameter");
 
 // ---- the grid transfer along one axis (n fine cells) ---------------------------------
 // coarse parents of fine index fi: count, indices and weights
@@ -278,6 +289,71 @@ __global__ void k_mg_rap(MgLevel F, MgLevel C) {
     rap_store(C, I, acc);
 }
 
+// ---- the team that solves one system ---------------------------------------------------
+// GridTeam: the whole cooperative grid (one system per launch; grid barriers and
+// exchanges over the arrival counter, bounded waits).  ClusterTeam: one
+// thread-block cluster per system (a batch of independent systems per launch;
+// the hardware cluster barrier orders global memory within the cluster, and a
+// reduction reads the C block partials through distributed shared memory).
+struct GridTeam {
+    const MgArgs& a;
+    int& e;
+    ExchShared& xs;
+    __device__ long long t0() const { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ long long size() const { return (long long)gridDim.x * blockDim.x; }
+    __device__ bool leader() const { return blockIdx.x == 0; }
+    __device__ bool sync() { return grid_barrier(a, e, xs); }
+    template <typename A, int NV>
+    __device__ bool reduce(A (&v)[NV], A (&tot)[NV]) { return exchange<A, NV>(a, e, v, tot, xs); }
+};
+
+struct ClusterSlots {
+    double sh[4 * 32];
+    double bc[4];
+    double slot[2][4];    // this CTA's partials, by reduction parity
+};
+
+struct ClusterTeam {
+    cg::cluster_group& cl;
+    int C, rank;
+    int e;
+    ClusterSlots& cs;
+    __device__ long long t0() const { return (long long)rank * blockDim.x + threadIdx.x; }
+    __device__ long long size() const { return (long long)C * blockDim.x; }
+    __device__ bool leader() const { return rank == 0; }
+    __device__ bool sync() {
+        cl.sync();
+        return true;
+    }
+    // every CTA of the cluster gets the same totals (the partials summed in rank order)
+    template <typename A, int NV>
+    __device__ bool reduce(A (&v)[NV], A (&tot)[NV]) {
+        A* sh = (A*)cs.sh;
+        block_sum_t<A, NV>(v, sh);
+        A* slot = (A*)cs.slot[e & 1];
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) slot[q] = v[q];
+        cl.sync();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                A x = (A)0;
+                if (lane < C) x = cl.map_shared_rank(slot, lane)[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) ((A*)cs.bc)[q] = x;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = ((A*)cs.bc)[q];
+        ++e;
+        return true;
+    }
+};
+
 // ---- the V-cycle ---------------------------------------------------------------------
 // A pass over the nodes [0, N) of a level, strided over the grid, four nodes
 // at a time: every node's value (its loads) before any node's store, so the
@@ -301,19 +377,20 @@ static __device__ __forceinline__ void pass4(long long N, long long t0, long lon
 }
 
 // z = M^-1 r: one V(1,1) cycle; false after a timeout
-static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb) {
+template <class Team>
+static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb) {
     const FieldArgs& f = a.f;
     const long long N = f.m.nnodes;
-    const long long TT = (long long)gridDim.x * blockDim.x;
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long TT = team.size();
+    const long long t0 = team.t0();
     const Dims d0 = dims_of(f.m);
     // level 0, down: pre-smoothing from zero, then the residual
     pass4(N, t0, TT, [&](long long n) { return MG_OMEGA * f.invdiagf[n] * __ldcg(a.r + n); },
           [&](long long n, float v) { a.x0[n] = v; });
-    if (!grid_barrier(a, e, xs)) return false;
+    if (!team.sync()) return false;
     pass4(N, t0, TT, [&](long long n) { return __ldcg(a.r + n) - mg_fine_row(f, a.x0, n, a.kind[n]); },
           [&](long long n, float v) { a.r0[n] = v; });
-    if (!grid_barrier(a, e, xs)) return false;
+    if (!team.sync()) return false;
     // coarse levels above the coarsest, down: restriction and pre-smoothing, then the residual
     for (int l = 1; l < a.nlev; ++l) {
         const MgLevel& L = a.lev[l];
@@ -326,7 +403,7 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
                   return mg_restrict(src, fd, i, j, k);
               },
               [&](long long c, float bc) { L.b[c] = bc; L.x[c] = MG_OMEGA * L.dinv[c] * bc; });
-        if (!grid_barrier(a, e, xs)) return false;
+        if (!team.sync()) return false;
         pass4(L.N, t0, TT,
               [&](long long c) {
                   int i, j, k;
@@ -334,10 +411,10 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
                   return L.b[c] - mg_coarse_row(L, L.x, c, i, j, k);
               },
               [&](long long c, float v) { L.res[c] = v; });
-        if (!grid_barrier(a, e, xs)) return false;
+        if (!team.sync()) return false;
     }
-    // the coarsest level in block 0: restriction into shared memory, then the dense inverse
-    if (blockIdx.x == 0) {
+    // the coarsest level in the team's first block: restriction into shared memory, then the dense inverse
+    if (team.leader()) {
         const MgLevel& L = a.lev[a.nlev];
         const float* src = a.nlev == 1 ? a.r0 : a.lev[a.nlev - 1].res;
         const Dims fd = a.nlev == 1 ? d0 : dims_of(a.lev[a.nlev - 1]);
@@ -354,7 +431,7 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
             L.y[c] = y;
         }
     }
-    if (!grid_barrier(a, e, xs)) return false;
+    if (!team.sync()) return false;
     // coarse levels above the coarsest, up: correction, post-smoothing
     for (int l = a.nlev - 1; l >= 1; --l) {
         const MgLevel& L = a.lev[l];
@@ -369,7 +446,7 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
                   return xc + mg_prolong(Cc.y, fd, cd, i, j, k);
               },
               [&](long long c, float v) { L.x[c] = v; });
-        if (!grid_barrier(a, e, xs)) return false;
+        if (!team.sync()) return false;
         pass4(L.N, t0, TT,
               [&](long long c) {
                   int i, j, k;
@@ -377,7 +454,7 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
                   return L.x[c] + MG_OMEGA * L.dinv[c] * (L.b[c] - mg_coarse_row(L, L.x, c, i, j, k));
               },
               [&](long long c, float v) { L.y[c] = v; });
-        if (!grid_barrier(a, e, xs)) return false;
+        if (!team.sync()) return false;
     }
     // level 0, up: coarse correction, post-smoothing into z
     {
@@ -393,7 +470,7 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
               },
               [&](long long n, float v) { a.x0[n] = v; });
     }
-    if (!grid_barrier(a, e, xs)) return false;
+    if (!team.sync()) return false;
     pass4(N, t0, TT,
           [&](long long n) {
               const float xn = __ldcg(a.x0 + n);
@@ -403,13 +480,13 @@ static __device__ bool vcycle(const MgArgs& a, int& e, ExchShared& xs, float* sb
     return true;
 }
 
-__global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
-    __shared__ ExchShared xs;
-    __shared__ float sb[MG_COARSEST];   // the coarsest right-hand side (block 0)
+// the refined multigrid-preconditioned PCG of one system, by one team
+template <class Team>
+static __device__ void mg_pcg(const MgArgs& a, Team& team, float* sb) {
     const FieldArgs& f = a.f;
     const long long N = f.m.nnodes;
-    const long long TT = (long long)gridDim.x * blockDim.x;
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long TT = team.size();
+    const long long t0 = team.t0();
     float* r = a.r;
     float* p = a.p;
     float* q = a.q;
@@ -417,7 +494,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
     const float* z = a.z;
     const double tol2 = a.S->tol2, inner_red2 = a.S->inner_red2, margin2 = a.S->margin2;
     const int maxit = a.S->maxit;
-    int e = 0, it = 0, outer = 0;
+    int it = 0, outer = 0;
     double bb = 0.0, rr = 0.0;
     bool conv = false, alive = true;
     for (;;) {
@@ -436,7 +513,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
             v3[1] += rn * rn;
         }
         double t3[3];
-        if (!(alive = exchange<double, 3>(a, e, v3, t3, xs))) break;
+        if (!(alive = team.template reduce<double, 3>(v3, t3))) break;
         if (outer == 0) bb = t3[0];
         rr = t3[1];
         conv = (bb == 0.0) || (rr <= tol2 * bb);
@@ -444,7 +521,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
         // inner target: max(margin tol |b|, reduction |r0|) (set_refinement)
         const float rr_stop = (float)fmax(margin2 * tol2 * bb, inner_red2 * rr);
         ++outer;
-        if (!(alive = vcycle(a, e, xs, sb))) break;
+        if (!(alive = vcycle(a, team, sb))) break;
         float rz = 0.0f, rr_in = (float)rr;
         bool first = true;
         for (;;) {
@@ -456,7 +533,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
                 v2[1] += rn * rn;
             }
             float t2[2];
-            if (!(alive = exchange<float, 2>(a, e, v2, t2, xs))) break;
+            if (!(alive = team.template reduce<float, 2>(v2, t2))) break;
             rr_in = t2[1];
             if (rr_in <= rr_stop || it >= maxit) break;
             const float beta = first ? 0.0f : t2[0] / rz;
@@ -473,7 +550,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
                       v1[0] += pn * qn;
                   });
             float pq[1];
-            if (!(alive = exchange<float, 1>(a, e, v1, pq, xs))) break;
+            if (!(alive = team.template reduce<float, 1>(v1, pq))) break;
             const float al = rz / pq[0];
             for (long long n = t0; n < N; n += TT) {
                 x[n] += al * p[n];
@@ -481,15 +558,15 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
             }
             ++it;
             first = false;
-            if (!(alive = vcycle(a, e, xs, sb))) break;
+            if (!(alive = vcycle(a, team, sb))) break;
         }
         if (!alive) break;
         for (long long n = t0; n < N; n += TT) a.u[n] = a.u[n] + (double)x[n];
         // the next residual reads the neighbours' new u
-        if (!(alive = grid_barrier(a, e, xs))) break;
+        if (!(alive = team.sync())) break;
     }
     for (long long n = t0; n < N; n += TT) a.phi[n] = (bb == 0.0) ? a.g[n] : a.u[n] + a.g[n];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (team.leader() && threadIdx.x == 0) {
         PcgState* S = a.S;
         S->bb = bb; S->rr = rr; S->it = it; S->outer_it = outer;
         S->converged = alive && conv;
@@ -497,6 +574,26 @@ __global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
         *a.it_total += it;
         *a.outer_total += outer;
     }
+}
+
+__global__ void __launch_bounds__(MG_THREADS, 1) k_pcg_mg(MgArgs a) {
+    __shared__ ExchShared xs;
+    __shared__ float sb[MG_COARSEST];   // the coarsest right-hand side (block 0)
+    int e = 0;
+    GridTeam team{a, e, xs};
+    mg_pcg(a, team, sb);
+}
+
+// batched: one system on one cluster of C CTAs (the grid is that cluster; the
+// arguments travel by value, in the kernel's parameter space, as every pass
+// reads them)
+__global__ void __launch_bounds__(MG_CL_THREADS, MG_CL_PER_SM) k_pcg_mg_cluster(MgArgs a, int C) {
+    __shared__ ClusterSlots cs;
+    __shared__ float sb[MG_COARSEST];
+    cg::cluster_group cl = cg::this_cluster();
+    ClusterTeam team{cl, C, (int)cl.block_rank(), 0, cs};
+    mg_pcg(a, team, sb);
+    cl.sync();   // (no CTA leaves while a peer may still read its shared slots)
 }
 
 // ---- host side -------------------------------------------------------------------------
@@ -563,16 +660,14 @@ static bool coarsest_inverse(const MgLevel& L, const std::vector<float>& coef, c
     return true;
 }
 
-// the hierarchy for the context's current operator (MIXED, with the
-// multigrid preconditioner selected); leaves mg_nlev = 0 otherwise
+// the hierarchy for the context's current operator (MIXED contexts; leaves
+// mg_nlev = 0 otherwise), and whether the context's own solve uses it
+// (mg_single; batched solves choose for themselves)
 cudaError_t plan_pcg_mg(Ctx& c) {
     free_mg(c);
+    c.mg_single = false;
     if (c.precision != PIFEPIC_MIXED) return cudaSuccess;
     const long long N0 = c.mesh.nnodes;
-    if (c.precond == PIFEPIC_PRECOND_JACOBI) return cudaSuccess;
-    // AUTO: multigrid where the register-resident Jacobi solver does not fit
-    // (planned just before this); there the Jacobi iterations grow past the cap
-    if (c.precond == PIFEPIC_PRECOND_AUTO && c.pcg_npt > 0) return cudaSuccess;
     int nx = c.mesh.nx, ny = c.mesh.ny, nz = c.mesh.nz;
     long long Nlast = N0;
     int nlev = 0;
@@ -617,10 +712,14 @@ cudaError_t plan_pcg_mg(Ctx& c) {
     if (e == cudaSuccess && !coarsest_inverse(Lc, coef, dinv, inv)) { free_mg(c); return cudaSuccess; }
     if (e == cudaSuccess) e = scopy(c.stream, c.mg_cinv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free_mg(c); return e; }
+    // AUTO: multigrid where the register-resident Jacobi solver does not fit
+    // (planned just before this); there the Jacobi iterations grow past the cap
+    c.mg_single = c.precond == PIFEPIC_PRECOND_MULTIGRID || (c.precond == PIFEPIC_PRECOND_AUTO && c.pcg_npt == 0);
     return cudaSuccess;
 }
 
-cudaError_t launch_pcg_mg(Ctx& c, cudaStream_t st) {
+// the kernel arguments of the context's multigrid solve
+MgArgs make_mg_args(Ctx& c) {
     MgArgs a;
     a.f.m = c.mesh; a.f.o = c.obj; a.f.ntype = c.ntype; a.f.coef = c.patch_coef; a.f.coeff = c.patch_coeff;
     a.f.invdiag = c.invdiag; a.f.invdiagf = c.invdiagf;
@@ -639,10 +738,41 @@ cudaError_t launch_pcg_mg(Ctx& c, cudaStream_t st) {
     a.it_total = (long long*)(c.scal + 40);
     a.outer_total = (long long*)(c.scal + 41);
     a.err = c.err_word;
+    return a;
+}
+// a batched multigrid solve: the system of c on one cluster of C CTAs (1..16)
+cudaError_t launch_pcg_mg_cluster(Ctx& c, int C, cudaStream_t st) {
+    void* kern = (void*)k_pcg_mg_cluster;
+    cudaError_t e = cudaSuccess;
+    if (C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(MG_CL_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    MgArgs a = make_mg_args(c);
+    void* args[] = {(void*)&a, (void*)&C};
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
+cudaError_t launch_pcg_mg(Ctx& c, cudaStream_t st) {
+    MgArgs a = make_mg_args(c);
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_mg, MG_THREADS, 0);
-    long long G = (long long)nsm * (per > 0 ? 1 : 1);   // one block per SM
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    long long G = nsm;                    // one block per SM
     if (G > MG_THREADS) G = MG_THREADS;   // an exchange reads one block partial per thread
     void* args[] = {&a};
     cudaLaunchConfig_t cfg = {};

@@ -234,21 +234,26 @@ class Server:
         self.batch.close()
 
 
-def autotune_batch(batch, trial_steps=2, candidates=(8192, 4096, 2048)):
-    """Pick the clustered solves' nodes per CTA (hence each member's cluster
-    size) by timing real steps of the batch (the trial steps advance the
-    members like any other step)."""
+def autotune_batch(batch, trial_steps=2, candidates=(8192, 4096, 2048),
+                   preconds=(capi.PRECOND_MULTIGRID, capi.PRECOND_JACOBI)):
+    """Pick the clustered solves' preconditioner (multigrid or Jacobi) and
+    nodes per CTA (hence each member's cluster size) by timing real steps of
+    the batch (the trial steps advance the members like any other step).
+    Returns (preconditioner, nodes per CTA, seconds per step of the pick)."""
     best, best_t = None, math.inf
-    for cn in candidates:
-        batch.set_cta_nodes(cn)
-        batch.step(1, stats=False)            # graph rebuild + warm-up
-        t0 = time.perf_counter()
-        batch.step(trial_steps, stats=False)
-        t = time.perf_counter() - t0
-        if t < best_t:
-            best, best_t = cn, t
-    batch.set_cta_nodes(best)
-    return best, best_t / trial_steps
+    for pc in preconds:
+        batch.set_preconditioner(pc)
+        for cn in candidates:
+            batch.set_cta_nodes(cn)
+            batch.step(1, stats=False)            # graph rebuild + warm-up
+            t0 = time.perf_counter()
+            batch.step(trial_steps, stats=False)
+            t = time.perf_counter() - t0
+            if t < best_t:
+                best, best_t = (pc, cn), t
+    batch.set_preconditioner(best[0])
+    batch.set_cta_nodes(best[1])
+    return best[0], best[1], best_t / trial_steps
 
 
 def poisson_arrivals(rng, rate, horizon):
