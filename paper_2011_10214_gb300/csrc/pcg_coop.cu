@@ -780,7 +780,17 @@ static void plan_pcg_reg(Ctx& c) {
     auto try_plan = [&](bool rows, size_t smem) {
         if (smem + static_smem > (size_t)smem_max) return false;
         void* kern = reg_kernel(mixed, pick, rows);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        // the function's limit is the whole opt-in budget, the same for every
+        // context (a per-context value would leave it at the last context's
+        // size, below what earlier contexts' graph nodes launch with)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        const int limit = smem_max - (int)fa.sharedSizeBytes;
+        if ((long long)smem > (long long)limit ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }

@@ -61,7 +61,8 @@ struct MgArgs {
     float* r0;                    // level-0 residual after pre-smoothing
     int nlev;                     // coarse levels 1..nlev (nlev the coarsest)
     MgLevel lev[MG_MAX_LEVELS];   // lev[1..nlev]
-    const float* cinv;            // the coarsest operator's inverse, [N][N] column-major (0 on empty rows)
+    const float* cinv;            // the coarsest operator's inverse, row-major, row stride cinv_ld (0 on empty rows)
+    int cinv_ld;                  // N rounded up to a multiple of 4 (rows start 16-byte aligned)
     double* val;
     unsigned long long* arrivals;
     const int* hold;
@@ -376,17 +377,23 @@ static __device__ __forceinline__ void pass4(long long N, long long t0, long lon
     }
 }
 
-// z = M^-1 r: one V(1,1) cycle; false after a timeout
+// the pre-smoothing step from a zero start, x0 = omega D^-1 r: no product, so
+// the passes that produce r write it node by node
+static __device__ __forceinline__ float mg_presmooth(const FieldArgs& f, long long n, float rn) {
+    return MG_OMEGA * f.invdiagf[n] * rn;
+}
+
+// z = M^-1 r: one V(1,1) cycle, entered with the pre-smoothed x0 = omega D^-1 r
+// written (not yet ordered: the cycle starts with a team barrier); rz gets this
+// thread's partials of r.z and r.r from the last pass; false after a timeout
 template <class Team>
-static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb) {
+static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb, float (&rz)[2]) {
     const FieldArgs& f = a.f;
     const long long N = f.m.nnodes;
     const long long TT = team.size();
     const long long t0 = team.t0();
     const Dims d0 = dims_of(f.m);
-    // level 0, down: pre-smoothing from zero, then the residual
-    pass4(N, t0, TT, [&](long long n) { return MG_OMEGA * f.invdiagf[n] * __ldcg(a.r + n); },
-          [&](long long n, float v) { a.x0[n] = v; });
+    // level 0, down: the residual after pre-smoothing
     if (!team.sync()) return false;
     pass4(N, t0, TT, [&](long long n) { return __ldcg(a.r + n) - mg_fine_row(f, a.x0, n, a.kind[n]); },
           [&](long long n, float v) { a.r0[n] = v; });
@@ -413,22 +420,40 @@ static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb) {
               [&](long long c, float v) { L.res[c] = v; });
         if (!team.sync()) return false;
     }
-    // the coarsest level in the team's first block: restriction into shared memory, then the dense inverse
+    // the coarsest level in the team's first block: restriction into shared
+    // memory, then y = inverse * rhs with tpr threads per row (a power of two,
+    // at most 32) whose 16-byte loads of the row all issue at once
     if (team.leader()) {
         const MgLevel& L = a.lev[a.nlev];
         const float* src = a.nlev == 1 ? a.r0 : a.lev[a.nlev - 1].res;
         const Dims fd = a.nlev == 1 ? d0 : dims_of(a.lev[a.nlev - 1]);
-        const int Nc = (int)L.N;
-        for (int c = threadIdx.x; c < Nc; c += blockDim.x) {
-            int i, j, k;
-            level_ijk(L, c, i, j, k);
-            sb[c] = mg_restrict(src, fd, i, j, k);
+        const int Nc = (int)L.N, ld = a.cinv_ld;
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+            float v = 0.0f;
+            if (c < Nc) {
+                int i, j, k;
+                level_ijk(L, c, i, j, k);
+                v = mg_restrict(src, fd, i, j, k);
+            }
+            sb[c] = v;
         }
         __syncthreads();
-        for (int c = threadIdx.x; c < Nc; c += blockDim.x) {
+        int tpr = 32;
+        while (tpr > 1 && tpr * Nc > (int)blockDim.x) tpr >>= 1;
+        const int rows = (int)blockDim.x / tpr, lane = (int)threadIdx.x % tpr, seg = ld >> 2;
+        for (int c0 = 0; c0 < Nc; c0 += rows) {
+            const int c = c0 + (int)threadIdx.x / tpr;
             float y = 0.0f;
-            for (int jj = 0; jj < Nc; ++jj) y += __ldg(a.cinv + (unsigned)jj * (unsigned)Nc + (unsigned)c) * sb[jj];
-            L.y[c] = y;
+            if (c < Nc) {
+                const float4* row = reinterpret_cast<const float4*>(a.cinv + (unsigned)c * (unsigned)ld);
+#pragma unroll 8
+                for (int s4 = lane; s4 < seg; s4 += tpr) {
+                    const float4 w = __ldg(row + s4);
+                    y += w.x * sb[4 * s4] + w.y * sb[4 * s4 + 1] + w.z * sb[4 * s4 + 2] + w.w * sb[4 * s4 + 3];
+                }
+            }
+            for (int o = tpr >> 1; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o, tpr);
+            if (lane == 0 && c < Nc) L.y[c] = y;
         }
     }
     if (!team.sync()) return false;
@@ -456,7 +481,7 @@ static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb) {
               [&](long long c, float v) { L.y[c] = v; });
         if (!team.sync()) return false;
     }
-    // level 0, up: coarse correction, post-smoothing into z
+    // level 0, up: coarse correction, post-smoothing into z with the r.z and r.r partials
     {
         const MgLevel& C1 = a.lev[1];
         const Dims cd = dims_of(C1);
@@ -471,12 +496,29 @@ static __device__ bool vcycle(const MgArgs& a, Team& team, float* sb) {
               [&](long long n, float v) { a.x0[n] = v; });
     }
     if (!team.sync()) return false;
-    pass4(N, t0, TT,
-          [&](long long n) {
-              const float xn = __ldcg(a.x0 + n);
-              return xn + MG_OMEGA * f.invdiagf[n] * (__ldcg(a.r + n) - mg_fine_row(f, a.x0, n, a.kind[n]));
-          },
-          [&](long long n, float v) { a.z[n] = v; });
+    rz[0] = 0.0f;
+    rz[1] = 0.0f;
+    for (long long n0 = t0; n0 < N; n0 += MG_UNROLL * TT) {
+        float zv[MG_UNROLL], rv[MG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < MG_UNROLL; ++u) {
+            const long long n = n0 + u * TT;
+            zv[u] = 0.0f;
+            rv[u] = 0.0f;
+            if (n < N) {
+                const float xn = __ldcg(a.x0 + n);
+                rv[u] = __ldcg(a.r + n);
+                zv[u] = xn + MG_OMEGA * f.invdiagf[n] * (rv[u] - mg_fine_row(f, a.x0, n, a.kind[n]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < MG_UNROLL; ++u) {
+            const long long n = n0 + u * TT;
+            if (n < N) a.z[n] = zv[u];
+            rz[0] += rv[u] * zv[u];
+            rz[1] += rv[u] * rv[u];
+        }
+    }
     return true;
 }
 
@@ -509,6 +551,7 @@ static __device__ void mg_pcg(const MgArgs& a, Team& team, float* sb) {
                                    : bn - apply_row64(f, n, i, j, k, [&](long long m) { return __ldcg(a.u + m); }, f.coef);
             r[n] = (float)rn;
             x[n] = 0.0f;
+            a.x0[n] = mg_presmooth(f, n, (float)rn);
             v3[0] += bn * bn;
             v3[1] += rn * rn;
         }
@@ -521,17 +564,12 @@ static __device__ void mg_pcg(const MgArgs& a, Team& team, float* sb) {
         // inner target: max(margin tol |b|, reduction |r0|) (set_refinement)
         const float rr_stop = (float)fmax(margin2 * tol2 * bb, inner_red2 * rr);
         ++outer;
-        if (!(alive = vcycle(a, team, sb))) break;
+        float v2[2];
+        if (!(alive = vcycle(a, team, sb, v2))) break;
         float rz = 0.0f, rr_in = (float)rr;
         bool first = true;
         for (;;) {
-            // r.z and r.r (the exchange also orders z before the product below)
-            float v2[2] = {0.0f, 0.0f};
-            for (long long n = t0; n < N; n += TT) {
-                const float rn = r[n], zn = __ldcg(z + n);
-                v2[0] += rn * zn;
-                v2[1] += rn * rn;
-            }
+            // r.z and r.r from the cycle's last pass (the exchange also orders z before the product below)
             float t2[2];
             if (!(alive = team.template reduce<float, 2>(v2, t2))) break;
             rr_in = t2[1];
@@ -554,11 +592,13 @@ static __device__ void mg_pcg(const MgArgs& a, Team& team, float* sb) {
             const float al = rz / pq[0];
             for (long long n = t0; n < N; n += TT) {
                 x[n] += al * p[n];
-                r[n] -= al * q[n];
+                const float rn = r[n] - al * q[n];
+                r[n] = rn;
+                a.x0[n] = mg_presmooth(f, n, rn);
             }
             ++it;
             first = false;
-            if (!(alive = vcycle(a, team, sb))) break;
+            if (!(alive = vcycle(a, team, sb, v2))) break;
         }
         if (!alive) break;
         for (long long n = t0; n < N; n += TT) a.u[n] = a.u[n] + (double)x[n];
@@ -611,7 +651,8 @@ void free_mg(Ctx& c) {
 }
 
 // the inverse of the coarsest operator (dense, FP64 Gauss-Jordan with partial
-// pivoting over its non-empty rows), column-major in FP32; false if singular
+// pivoting over its non-empty rows), row-major in FP32 with rows padded to a
+// multiple of 4 floats; false if singular
 static bool coarsest_inverse(const MgLevel& L, const std::vector<float>& coef, const std::vector<float>& dinv,
                              std::vector<float>& out) {
     const int n = (int)L.N;
@@ -654,9 +695,10 @@ static bool coarsest_inverse(const MgLevel& L, const std::vector<float>& coef, c
             }
         }
     }
-    out.assign((size_t)n * n, 0.0f);
+    const int ld = (n + 3) & ~3;
+    out.assign((size_t)n * ld, 0.0f);
     for (int r = 0; r < m; ++r)
-        for (int t = 0; t < m; ++t) out[(size_t)live[t] * n + live[r]] = (float)B[(size_t)r * m + t];
+        for (int t = 0; t < m; ++t) out[(size_t)live[r] * ld + live[t]] = (float)B[(size_t)r * m + t];
     return true;
 }
 
@@ -696,7 +738,7 @@ cudaError_t plan_pcg_mg(Ctx& c) {
         if (e == cudaSuccess) e = lib_malloc(&L.y, sizeof(float) * L.N);
     }
     if (e == cudaSuccess) e = lib_malloc(&c.mg_r0, sizeof(float) * N0);
-    if (e == cudaSuccess) e = lib_malloc(&c.mg_cinv, sizeof(float) * Nlast * Nlast);
+    if (e == cudaSuccess) e = lib_malloc(&c.mg_cinv, sizeof(float) * Nlast * ((Nlast + 3) & ~3));
     if (e != cudaSuccess) { free_mg(c); return e; }
     FieldArgs f;
     f.m = c.mesh; f.o = c.obj; f.ntype = c.ntype; f.coef = c.patch_coef; f.coeff = c.patch_coeff;
@@ -731,6 +773,7 @@ MgArgs make_mg_args(Ctx& c) {
     a.nlev = c.mg_nlev;
     for (int l = 0; l < MG_MAX_LEVELS; ++l) a.lev[l] = c.mg[l];
     a.cinv = c.mg_cinv;
+    a.cinv_ld = (int)((c.mg[c.mg_nlev].N + 3) & ~3);
     a.val = c.coop_partial;
     a.arrivals = c.bar64;
     a.hold = (const int*)(c.scal + 45);
