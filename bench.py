@@ -29,6 +29,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the headline metric: `value` is the plain (single-instance) rate; the line's `batched` and `served`
 # objects carry the batched rate (and its ratio to the plain one) and the served p50/p99 latency
 METRIC = "particle-steps/s incl. IFE solve, batched vs plain; served p50/p99 latency"
+BIN_EDGE = None   # MIXED particle-bin edge of the measured contexts (--bin-edge; None = the library's default)
 PRECOND = 0   # MIXED preconditioner of the measured contexts (--precond; 0 = the library's automatic choice)
 BYTES_PER_PARTICLE_STEP = {"fp64": 96, "mixed": 56}     # read + write of the particle state
 
@@ -206,7 +207,8 @@ def measure(cfg, precision, steps, warmup, stream, dist, local):
     import torch
     from paper_2011_10214_gb300 import capi
     prec = capi.MIXED if precision == "mixed" else capi.FP64
-    sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream)
+    sim = capi.from_config(cfg, precision=prec, stream=stream.cuda_stream,
+                           bin_edge=BIN_EDGE if prec == capi.MIXED else None)
     if PRECOND:
         sim.set_preconditioner(PRECOND)
     sim.solve()
@@ -376,7 +378,8 @@ def run_gpu(args):
         "dtype": "f64" if main == "fp64" else "f32+f64",
         "data": "synthetic (seeded Philox load and injection)",
         "config": cfg_desc(cfg, main, {"particles": int(pushed / args.steps),
-                                       "parallelism": f"replicas x{world}"}),
+                                       "parallelism": f"replicas x{world}",
+                                       "bin_edge": BIN_EDGE or 4}),
         "roofline": roof, "roofline_other": roof_other, "clocks": ck, "e2e": e2e,
         "gpu_launches": int(st["kernel_launches"]),
         "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
@@ -516,10 +519,15 @@ def measure_batch(instances, steps, warmup, autotune=True):
     rng = np.random.default_rng(2011102144)
     cfgs = serve.request_distribution(rng, instances, big_fraction=0.0)
     stream = torch.cuda.Stream()
+    # particle-bin edge per size class, by timing batches of each class (before the timed instances exist)
+    tb = time.perf_counter()
+    edges, edge_ms = serve.autotune_bin_edge(cfgs, stream=stream.cuda_stream) if autotune else ({}, {})
+    tune_s = time.perf_counter() - tb
     t0 = time.perf_counter()
     sims = []
     for c in cfgs:
-        s = capi.from_config(c, precision=capi.MIXED, stream=stream.cuda_stream)
+        s = capi.from_config(c, precision=capi.MIXED, stream=stream.cuda_stream,
+                             bin_edge=edges.get(serve.size_class(c)))
         s.solve(); s.leapfrog_init()
         sims.append(s)
     setup_s = time.perf_counter() - t0
@@ -535,7 +543,16 @@ def measure_batch(instances, steps, warmup, autotune=True):
         alone_ms += ea.elapsed_time(eb) / 4
         alone_pushed += sum(sa["pushed"]) / 4
     batch = capi.Batch(sims, stream=stream.cuda_stream)
-    tuned = serve.autotune_batch(batch) if autotune else None
+    tuned = None
+    if autotune:
+        pc, cn, sps = serve.autotune_batch(batch)
+        tuned = {"preconditioner": {capi.PRECOND_JACOBI: "jacobi", capi.PRECOND_MULTIGRID: "multigrid"}[pc],
+                 "cta_nodes": cn, "trial_ms_per_step": sps * 1e3,
+                 "bin_edge": {f"n{'<' if k[0] == 0 else '>='}32,ppc{('<=32', '<=48', '>48')[k[1]]}": e
+                              for k, e in sorted(edges.items())},
+                 "bin_edge_trial_ms": {f"{k[0]}{k[1]}": {str(e): round(t, 3) for e, t in v.items()}
+                                       for k, v in sorted(edge_ms.items())},
+                 "tune_s": tune_s}
     batch.step(warmup, stats=False)
     torch.cuda.synchronize()
     clocks = Clocks(0)
@@ -648,8 +665,11 @@ def main():
     ap.add_argument("--as-baseline", action="store_true")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "multigrid"],
                     help="MIXED field-solve preconditioner (pifepic_set_preconditioner)")
+    ap.add_argument("--bin-edge", type=int, default=None, choices=[4, 8],
+                    help="MIXED particle bins of edge^3 cells (pifepic_set_bin_edge)")
     args = ap.parse_args()
-    global PRECOND
+    global PRECOND, BIN_EDGE
+    BIN_EDGE = args.bin_edge
     PRECOND = {"auto": 0, "jacobi": 1, "multigrid": 2}[args.precond]
     if args.impl == "reference":
         run_reference(args)

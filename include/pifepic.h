@@ -206,6 +206,22 @@ enum { PIFEPIC_PRECOND_AUTO = 0, PIFEPIC_PRECOND_JACOBI = 1, PIFEPIC_PRECOND_MUL
 pifepic_status pifepic_set_preconditioner(pifepic_ctx* ctx, int kind);
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
 
+/* Particle bins (the cell blocks of Sec. 2.3's particle storage): particles
+ * are stored sorted by bins of edge^3 PIC cells, and one CTA pushes one bin
+ * and species through the bin's (edge+1)^3 node-field tile (TMA) and deposit
+ * tile in shared memory.  edge is 4 (the default) or 8; MIXED contexts only
+ * for 8.  Larger bins mean fewer bin leavers per step and fewer CTAs, and more
+ * shared memory per CTA; a bin holds at most 32767 particles per species (the
+ * rest waits in the mover list), so 8 suits up to about 48 particles per cell
+ * and species.  A particle's push is the same arithmetic for either edge; a
+ * bin's stayers deposit with weights rounded to 2^-19 of a particle and its
+ * leavers with 2^-32 weights, so node charges (whose totals stay exact) differ
+ * between edges within that rounding.  Call before the first
+ * pifepic_add_species.  Errors: EINVAL (edge not 4 or 8, or 8 in FP64),
+ * ESTATE (species exist).  pifepic_get_bin_edge returns the edge (0 for NULL). */
+pifepic_status pifepic_set_bin_edge(pifepic_ctx* ctx, int edge);
+int pifepic_get_bin_edge(const pifepic_ctx* ctx);
+
 /* Species with charge q, mass m (q/m sets the push) and macro-particle
  * weight w (charge per macro-particle = q*w; w = density*h^3/ppc).  At most
  * PIFEPIC_MAX_SPECIES. */

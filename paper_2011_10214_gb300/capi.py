@@ -104,6 +104,8 @@ _sigs = {
     "pifepic_solve_field": [_ctx, _dp, _dp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "pifepic_solve_field_noalloc": [_ctx, _dp, _dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "pifepic_set_preconditioner": [_ctx, C.c_int],
+    "pifepic_set_bin_edge": [_ctx, C.c_int],
+    "pifepic_get_bin_edge": [_ctx],
     "pifepic_get_memory_use": [C.POINTER(C.c_size_t)],
     "pifepic_set_memory_limit": [C.c_size_t],
     "pifepic_test_hold_exchange": [_ctx, C.c_int],
@@ -220,6 +222,14 @@ class Simulation:
     def set_preconditioner(self, kind):
         """MIXED inner PCG preconditioner: PRECOND_AUTO, PRECOND_JACOBI or PRECOND_MULTIGRID."""
         self._ok(lib.pifepic_set_preconditioner(self._c, int(kind)), "set_preconditioner")
+
+    def set_bin_edge(self, edge):
+        """Particle bins of edge^3 cells, 4 or 8 (pifepic_set_bin_edge; before add_species)."""
+        self._ok(lib.pifepic_set_bin_edge(self._c, int(edge)), "set_bin_edge")
+
+    @property
+    def bin_edge(self):
+        return int(lib.pifepic_get_bin_edge(self._c))
 
     def set_field_bc(self, faces):
         arr = (FaceBC * 6)()
@@ -397,12 +407,15 @@ class Simulation:
 
 
 def from_config(cfg, precision=FP64, track_ids=False, pcg_tol=1e-6, pcg_max_iter=150, load=True, inject=True,
-                stream=None):
+                stream=None, bin_edge=None):
     """Build a Simulation for a workload dict of paper_2011_10214_gb300.workloads
-    (the macro-particle weights are the workload's own, workloads.macro_weight)."""
+    (the macro-particle weights are the workload's own, workloads.macro_weight);
+    bin_edge: particle bins of bin_edge^3 cells (None: the library's default)."""
     from .workloads import macro_weight
     sim = Simulation(cfg["n"], cfg["h"], cfg["dt"], cfg.get("origin", (0.0, 0.0, 0.0)), precision, pcg_tol,
                      pcg_max_iter, track_ids, stream, cfg.get("ife_refine", 1))
+    if bin_edge is not None:
+        sim.set_bin_edge(bin_edge)
     sim.set_field_bc(cfg["face_bc"])
     ob = cfg["object"]
     if ob.get("bedrock") is not None:
@@ -467,7 +480,7 @@ class Batch:
         self._ok(lib.pifepic_batch_set_preconditioner(self._b, int(kind)), "batch_set_preconditioner")
 
     def set_cta_nodes(self, cta_nodes):
-        """Preferred nodes per CTA of the clustered field solves (2048, 4096, 8192)."""
+        """Preferred nodes per CTA of the clustered field solves (a power of two, 2048 to 65536)."""
         self._ok(lib.pifepic_batch_set_cta_nodes(self._b, int(cta_nodes)), "batch_set_cta_nodes")
 
     def step(self, nsteps=1, stats=True):

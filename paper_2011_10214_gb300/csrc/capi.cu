@@ -235,6 +235,14 @@ static void free_parr(PArr& a) {
 
 extern "C" {
 
+// particle bins of edge^3 PIC cells
+static void set_bin_grid(Ctx& c, int edge) {
+    const Mesh& pm = c.pmesh;
+    c.bin_edge = edge;
+    c.nbx = (pm.nx + edge - 1) / edge; c.nby = (pm.ny + edge - 1) / edge; c.nbz = (pm.nz + edge - 1) / edge;
+    c.nblocks = c.nbx * c.nby * c.nbz;
+}
+
 pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solver_desc* solver, void* stream,
                               pifepic_ctx** out) {
     if (!mesh || !solver || !out) return PIFEPIC_EINVAL;
@@ -276,8 +284,7 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     c.maxit = solver->pcg_max_iter > 0 ? solver->pcg_max_iter : 150;
     c.track = solver->track_ids ? 1 : 0;
     const Mesh& pm = c.pmesh;
-    c.nbx = (pm.nx + BLK - 1) / BLK; c.nby = (pm.ny + BLK - 1) / BLK; c.nbz = (pm.nz + BLK - 1) / BLK;
-    c.nblocks = c.nbx * c.nby * c.nbz;
+    set_bin_grid(c, BLK);
     for (int f = 0; f < 6; ++f) { c.bc[f].kind = PIFEPIC_BC_DIRICHLET; c.bc[f].value = 0.0; }
     long long N = m.nnodes, C = m.ncells;
     ALLOC(c.Lnode, sizeof(double) * N);
@@ -419,7 +426,8 @@ static pifepic_status encode_tmaps(pifepic_ctx* ctx) {
     EncodeFn enc = (EncodeFn)fn;
     const Mesh& m = c.pmesh;   // the push reads the node field at the PIC nodes
     cuuint64_t dims[4] = {4, (cuuint64_t)m.NX, (cuuint64_t)m.NY, (cuuint64_t)m.NZ};
-    cuuint32_t box[4] = {4, TILE, TILE, TILE};
+    const cuuint32_t tl = (cuuint32_t)c.bin_edge + 1;   // a bin's node tile
+    cuuint32_t box[4] = {4, tl, tl, tl};
     cuuint32_t es[4] = {1, 1, 1, 1};
     cuuint64_t sd[3] = {32, (cuuint64_t)m.NX * 32, (cuuint64_t)m.NX * m.NY * 32};
     CUresult r = enc(&c.tmapE, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c.Ep, dims, sd, box, es,
@@ -618,6 +626,20 @@ static pifepic_status ensure_movers(pifepic_ctx* ctx, int s, long long need) {
     q.mcap = need;
     return PIFEPIC_OK;
 }
+
+pifepic_status pifepic_set_bin_edge(pifepic_ctx* ctx, int edge) {
+    NEED(ctx);
+    Ctx& c = ctx->c;
+    if (edge != 4 && edge != 8) FAIL(PIFEPIC_EINVAL, "the bin edge is 4 or 8 cells");
+    if (edge != 4 && c.precision != PIFEPIC_MIXED) FAIL(PIFEPIC_EINVAL, "FP64 contexts bin by 4 cells");
+    if (!c.sp.empty()) FAIL(PIFEPIC_ESTATE, "set_bin_edge must precede add_species");
+    if (edge == c.bin_edge) return PIFEPIC_OK;
+    set_bin_grid(c, edge);
+    if (c.tmap_ok) return encode_tmaps(ctx);   // the node tile's box follows the bin edge
+    return PIFEPIC_OK;
+}
+
+int pifepic_get_bin_edge(const pifepic_ctx* ctx) { return ctx ? ctx->c.bin_edge : 0; }
 
 pifepic_status pifepic_add_species(pifepic_ctx* ctx, double qq, double mm, double w, int* id) {
     NEED(ctx);

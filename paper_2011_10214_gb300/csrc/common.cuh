@@ -206,9 +206,11 @@ PF_D unsigned long long warp_inc64(unsigned long long* p) {
 
 constexpr int BIN_MAX = 32767;
 constexpr int BIN_SCAN_THREADS = 1024;   // k_bin_scan's block
-// corner offsets in a (BLK+1)^3 tile, node order 000,100,010,110,001,101,011,111
+// corner offsets in a TL^3 node tile (TL = bin edge + 1), node order
+// 000,100,010,110,001,101,011,111
+template <int TL = TILE>
 PF_HD constexpr int tile_corner(int l) {
-    return (l & 1) + TILE * ((l >> 1) & 1) + TILE * TILE * ((l >> 2) & 1);
+    return (l & 1) + TL * ((l >> 1) & 1) + TL * TL * ((l >> 2) & 1);
 }
 
 // Shared-memory fixed-point deposit of one particle with native 32-bit atomics.
@@ -221,19 +223,19 @@ PF_HD constexpr int tile_corner(int l) {
 // integer as an int64 deposit.  Per copy at most BIN_MAX / 8 + 1 particles
 // reach a node, each moving a counter by less than 7 * 2^16, so both counters
 // stay inside 32 bits and tile_value() is exact.
-template <typename WT>
+template <typename WT, int TL = TILE>
 PF_D void tile_deposit(int* lo, int* hi, int base, const WT (&W)[7]) {
     int slo = 0, shi = 0;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
         const int a = (int)(W[l] & 0xFFFF), b = (int)(W[l] >> 16);
-        atomicAdd(&lo[base + 8 * tile_corner(l)], a);
-        atomicAdd(&hi[base + 8 * tile_corner(l)], b);
+        atomicAdd(&lo[base + 8 * tile_corner<TL>(l)], a);
+        atomicAdd(&hi[base + 8 * tile_corner<TL>(l)], b);
         slo += a;
         shi += b;
     }
-    atomicAdd(&lo[base + 8 * tile_corner(7)], -slo);
-    atomicAdd(&hi[base + 8 * tile_corner(7)], 65536 - shi);
+    atomicAdd(&lo[base + 8 * tile_corner<TL>(7)], -slo);
+    atomicAdd(&hi[base + 8 * tile_corner<TL>(7)], 65536 - shi);
 }
 PF_D long long tile_value(int lo, int hi) { return (long long)lo + ((long long)hi << 16); }
 

@@ -89,6 +89,7 @@ struct Launch {                     // what every particle kernel needs
     Object obj;
     double dth;                     // dt / h
     int nbx, nby, nbz, nblocks;
+    int bsh;                        // bin edge = 2^bsh cells (4 or 8)
     int nspecies;
     int track;
     const int* cell_acc;            // [ncells] surface accumulator of a hit cell
@@ -152,6 +153,7 @@ struct Ctx {
     double inner_margin = 0.5;
     int track = 0;
     int nbx = 0, nby = 0, nbz = 0, nblocks = 0;
+    int bin_edge = BLK;           // particle bins of bin_edge^3 PIC cells (MIXED: 4 or 8; FP64: 4)
 
     Object obj{};
     bool have_object = false;

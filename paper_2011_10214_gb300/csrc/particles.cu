@@ -121,8 +121,9 @@ PF_D long long list_len(const unsigned long long* n, long long cap) {
     return v < cap ? v : cap;
 }
 
+// the bin of a cell inside the mesh (non-negative indices; bin edge 2^bsh)
 PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
-    return (ci / BLK) + L.nbx * ((cj / BLK) + L.nby * (ck / BLK));
+    return (ci >> L.bsh) + L.nbx * ((cj >> L.bsh) + L.nby * (ck >> L.bsh));
 }
 
 // deposit with weights w of a cell of the IFE mesh (the PIC mesh when refine == 1)
@@ -609,6 +610,7 @@ Launch make_launch(Ctx& c) {
     L.mesh = c.pmesh; L.obj = c.obj; L.dth = c.dth;
     L.fmesh = c.mesh; L.refine = c.refine; L.rf = (double)c.refine;
     L.nbx = c.nbx; L.nby = c.nby; L.nbz = c.nbz; L.nblocks = c.nblocks;
+    L.bsh = c.bin_edge == 8 ? 3 : 2;
     L.nspecies = (int)c.sp.size();
     L.track = c.track;
     L.cell_acc = c.cell_acc;

@@ -255,45 +255,51 @@ PF_D long long list_len(const unsigned long long* n, long long cap) {
     return v < cap ? v : cap;
 }
 
+// the bin of a cell inside the mesh (non-negative indices; bin edge 2^bsh)
 PF_D int block_of(const Launch& L, int ci, int cj, int ck) {
-    return (ci / BLK) + L.nbx * ((cj / BLK) + L.nby * (ck / BLK));
+    return (ci >> L.bsh) + L.nbx * ((cj >> L.bsh) + L.nby * (ck >> L.bsh));
 }
 
 // ------------------------------------------------------------------------------------
 // fused gather + push + boundary + collection + deposit + compaction (one bin per CTA)
 // ------------------------------------------------------------------------------------
+// A bin of B^3 cells reads and deposits through a TL^3 node tile, TL = B + 1.
 // gather from the staged node-field tile; t0 = tile index of the cell's corner 0
+template <int TL>
 PF_D void gather_tile(const float4* Et, int t0, const WF& w, float& ex, float& ey, float& ez) {
     ex = 0.f; ey = 0.f; ez = 0.f;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
-        const float4 e = Et[t0 + tile_corner(l)];
+        const float4 e = Et[t0 + tile_corner<TL>(l)];
         ex += w.w[l] * e.x;
         ey += w.w[l] * e.y;
         ez += w.w[l] * e.z;
     }
 }
 
+template <int TL>
 PF_D int tile_index(int i, int j, int k, int x0, int y0, int z0) {
-    return (i - x0) + TILE * ((j - y0) + TILE * (k - z0));
+    return (i - x0) + TL * ((j - y0) + TL * (k - z0));
 }
 
 // a bin's deposit tile: 8 interleaved 32-bit copies per node (copy = lane & 7),
 // units of 2^-19 particle (see k_push_bins_m).  One particle: 7 rounded
 // weights and the remainder, so it adds exactly 2^19.
+template <int TL>
 PF_D void tile_deposit19(unsigned* Wt, int t0, const WF& w) {
     unsigned rest = 1u << 19;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
         const unsigned W = __float2uint_rn(w.w[l] * 524288.0f);
         rest -= W;
-        atomicAdd(&Wt[t0 + 8 * tile_corner(l)], W);
+        atomicAdd(&Wt[t0 + 8 * tile_corner<TL>(l)], W);
     }
-    atomicAdd(&Wt[t0 + 8 * tile_corner(7)], rest);
+    atomicAdd(&Wt[t0 + 8 * tile_corner<TL>(7)], rest);
 }
 // add the tile to the node charges (2^32 units per particle), all threads of the block
+template <int TL>
 PF_D void tile_flush19(const Launch& L, unsigned long long* W, const unsigned* Wt, int x0, int y0, int z0) {
-    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+    for (int t = threadIdx.x; t < TL * TL * TL; t += blockDim.x) {
         long long v = 0;
         for (int c = 0; c < 8; ++c) {
             long long u = (long long)Wt[t * 8 + c];
@@ -301,7 +307,7 @@ PF_D void tile_flush19(const Launch& L, unsigned long long* W, const unsigned* W
             v += u;
         }
         if (!v) continue;
-        int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        int tx = t % TL, ty = (t / TL) % TL, tz = t / (TL * TL);
         int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
         if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
             atomicAdd(&W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)(v * 8192));
@@ -326,22 +332,39 @@ PF_D void tile_flush19(const Launch& L, unsigned long long* W, const unsigned* W
 constexpr int PUSH_WARPS = 8;   // 256 threads
 constexpr int PUSH_DEPTH = 3;   // chunks in flight per warp
 
-template <bool HYBRID>
+// the push's dynamic shared memory for bins of edge B: node-field tile, deposit
+// tile, chunk counts, cp.async stages (in that order; every part a multiple of 16 bytes)
+template <int B>
+struct PushSmem {
+    static constexpr int TL = B + 1, TN = TL * TL * TL;
+    static constexpr size_t et = sizeof(float4) * TN;
+    static constexpr size_t wt = sizeof(unsigned) * 8 * TN;
+    static constexpr size_t agg = sizeof(int) * ((((BIN_MAX + 31) / 32) + 3) & ~3);
+    static constexpr size_t stg = sizeof(unsigned) * PUSH_WARPS * PUSH_DEPTH * 7 * 32;
+    static constexpr size_t bytes = et + wt + agg + stg;
+    static_assert(et % 16 == 0 && wt % 16 == 0 && agg % 16 == 0, "16-byte parts");
+};
+
+template <bool HYBRID, int B>
 __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float dthf,
                                                      const __grid_constant__ CUtensorMap tmE) {
-    __shared__ alignas(128) float4 Et[TILE_N];
+    using SM = PushSmem<B>;
+    constexpr int TL = SM::TL, TN = SM::TN;
+    extern __shared__ __align__(128) unsigned char push_smem[];
+    float4* Et = reinterpret_cast<float4*>(push_smem);   // the bin's node-field tile (TMA destination)
     // deposits of the bin's stayers in units of 2^-19 particle, 8 interleaved
     // copies per node (copy = lane & 7) so that the lanes of one atomic
     // instruction spread over the banks.  A particle adds 7 rounded weights and
     // the remainder 2^19 - sum (at least -4), so a copy, reached by at most
     // BIN_MAX / 8 + 1 particles, holds a value in [-2^14, 2^31]: exact in 32
     // bits modulo 2^32.  The flush multiplies by 2^13 (2^32 units per particle).
-    __shared__ unsigned Wt[8 * TILE_N];
+    unsigned* Wt = reinterpret_cast<unsigned*>(push_smem + SM::et);
     // stayers of chunk c plus one, for each chunk c (0: not yet published)
-    __shared__ int agg[(BIN_MAX + 31) / 32];
+    int* agg = reinterpret_cast<int*>(push_smem + SM::et + SM::wt);
     __shared__ int s_total, s_fail;   // stayers of the bin plus one; a wait gave up
     // per warp and stage: cell, fx, fy, fz, vx, vy, vz of 32 particles
-    __shared__ unsigned stg[PUSH_WARPS][PUSH_DEPTH][7][32];
+    typedef unsigned Stage[PUSH_DEPTH][7][32];
+    Stage* stg = reinterpret_cast<Stage*>(push_smem + SM::et + SM::wt + SM::agg);
     __shared__ alignas(8) unsigned long long bar;
     __shared__ unsigned sctr[NCTR];
     __shared__ int s_ok;
@@ -354,7 +377,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         return;
     }
     const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
-    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
+    const int x0 = bx * B, y0 = by * B, z0 = bz * B;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int nch = (n + 31) >> 5;
     const long long start = S.bstart[b];
@@ -377,13 +400,13 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
 #pragma unroll
     for (int d = 0; d < PUSH_DEPTH; ++d) stage(wid + d * nw, d);
     if (tid == 0) { mbar_init(&bar, 1); fence_barrier_init(); }
-    for (int t = tid; t < 8 * TILE_N; t += blockDim.x) Wt[t] = 0u;
+    for (int t = tid; t < 8 * TN; t += blockDim.x) Wt[t] = 0u;
     for (int t = tid; t < nch; t += blockDim.x) agg[t] = 0;
     if (tid < NCTR) sctr[tid] = 0u;
     if (tid == 0) { s_total = 0; s_fail = 0; }
     __syncthreads();
     if (tid == 0) {
-        mbar_expect_tx(&bar, TILE_N * (unsigned)sizeof(float4));
+        mbar_expect_tx(&bar, TN * (unsigned)sizeof(float4));
         tma_load_4d(Et, &tmE, &bar, 0, x0, y0, z0);
         bool ok = mbar_wait_bounded(&bar, 0);
         if (!ok) {
@@ -425,7 +448,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
             // kick with the field gathered at the old position, then drift
             const WF w = weights_f(p.fx, p.fy, p.fz);
             float ex, ey, ez;
-            gather_tile(Et, tile_index(p.i, p.j, p.k, x0, y0, z0), w, ex, ey, ez);
+            gather_tile<TL>(Et, tile_index<TL>(p.i, p.j, p.k, x0, y0, z0), w, ex, ey, ez);
             p.vx += kf * ex; p.vy += kf * ey; p.vz += kf * ez;
             const float xo = (float)p.i + p.fx, yo = (float)p.j + p.fy, zo = (float)p.k + p.fz;
             p.fx += p.vx * dthf; p.fy += p.vy * dthf; p.fz += p.vz * dthf;
@@ -448,12 +471,12 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         sl = sl + 1 == PUSH_DEPTH ? 0 : sl + 1;
         bool stay = false, mover = false;
         if (code == ALIVE) {
-            stay = (p.i >= x0) & (p.i < x0 + BLK) & (p.j >= y0) & (p.j < y0 + BLK) & (p.k >= z0) & (p.k < z0 + BLK);
+            stay = (p.i >= x0) & (p.i < x0 + B) & (p.j >= y0) & (p.j < y0 + B) & (p.k >= z0) & (p.k < z0 + B);
             mover = !stay;
             if (HYBRID && stay) {
                 global_deposit_f(L, S.W, p);   // hybrid grid: straight onto the IFE nodes
             } else if (stay) {   // (movers deposit in the rebin, with every mover of the step)
-                tile_deposit19(Wt, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, weights_f(p.fx, p.fy, p.fz));
+                tile_deposit19<TL>(Wt, 8 * tile_index<TL>(p.i, p.j, p.k, x0, y0, z0) + copy, weights_f(p.fx, p.fy, p.fz));
             }
         } else if (code == COLLECTED) {
             if (acc >= 0) atomicAdd(&S.surf[acc], 1ull);
@@ -507,7 +530,7 @@ __global__ void __launch_bounds__(256, 5) k_push_bins_m(Launch L, ObjF of, float
         S.bcount[b] = (s_fail || s_total == 0) ? 0 : s_total - 1;
         S.bstay[b] = S.bcount[b];
     }
-    tile_flush19(L, S.W, Wt, x0, y0, z0);
+    tile_flush19<TL>(L, S.W, Wt, x0, y0, z0);
     if (tid < NCTR && sctr[tid]) atomicAdd(&S.ctr[tid], (unsigned long long)sctr[tid]);
 }
 
@@ -712,10 +735,11 @@ __global__ void k_flatten_list_m(Launch L, int s, PArr out, unsigned long long* 
 // of split 32-bit counters (tile_deposit; integer sums, so the node charges
 // equal those of one global atomic per weight), on a finer IFE mesh straight
 // to its nodes
-template <bool HYBRID>
+template <bool HYBRID, int B>
 __global__ void k_deposit_bins_m(Launch L) {
-    __shared__ int Wlo[8 * TILE_N];
-    __shared__ int Whi[8 * TILE_N];
+    constexpr int TL = B + 1, TN = TL * TL * TL;
+    __shared__ int Wlo[8 * TN];
+    __shared__ int Whi[8 * TN];
     const SpeciesDev& S = L.sp[blockIdx.y];
     const int b = blockIdx.x;
     const int n = S.bcount[b];
@@ -730,8 +754,8 @@ __global__ void k_deposit_bins_m(Launch L) {
         return;
     }
     const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
-    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
-    for (int t = threadIdx.x; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    const int x0 = bx * B, y0 = by * B, z0 = bz * B;
+    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
     __syncthreads();
     const int copy = threadIdx.x & 7;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -742,14 +766,14 @@ __global__ void k_deposit_bins_m(Launch L) {
         unsigned W7[7];
 #pragma unroll
         for (int l = 0; l < 7; ++l) W7[l] = (unsigned)Wf[l];
-        tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
+        tile_deposit<unsigned, TL>(Wlo, Whi, 8 * tile_index<TL>(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+    for (int t = threadIdx.x; t < TN; t += blockDim.x) {
         long long v = 0;
         for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
         if (!v) continue;
-        const int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        const int tx = t % TL, ty = (t / TL) % TL, tz = t / (TL * TL);
         const int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
         if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
             atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
@@ -816,17 +840,36 @@ static InjArgs inj_args_m(Ctx& c) {
 __global__ void k_inject_counts(InjArgs a);   // particles.cu
 __global__ void k_step_advance(long long* step);
 
+// one push launch; the kernel's dynamic shared-memory limit is raised once
+// to what bins of edge B need (above the 48 KB default at B = 8)
+template <bool HYBRID, int B>
+static cudaError_t push_bins_m(dim3 grid, cudaStream_t st, const Launch& L, const ObjF& of, float dthf,
+                               const CUtensorMap& tm) {
+    static_assert(PushSmem<B>::bytes <= 200 * 1024, "push shared memory");
+    void* kern = (void*)k_push_bins_m<HYBRID, B>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PushSmem<B>::bytes);
+    if (e != cudaSuccess) return e;
+    k_push_bins_m<HYBRID, B><<<grid, 256, PushSmem<B>::bytes, st>>>(L, of, dthf, tm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_push_mixed(Ctx& c) {
     Launch L = make_launch(c);
     int ns = (int)c.sp.size();
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
-    if (c.refine == 1)
-        k_push_bins_m<false><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
+    const dim3 grid(c.nblocks, ns);
+    const ObjF of = obj_f(c.obj);
+    const float dthf = (float)c.dth;
+    cudaError_t e;
+    if (c.bin_edge == 8)
+        e = c.refine == 1 ? push_bins_m<false, 8>(grid, c.stream, L, of, dthf, c.tmapEf)
+                          : push_bins_m<true, 8>(grid, c.stream, L, of, dthf, c.tmapEf);
     else
-        k_push_bins_m<true><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, obj_f(c.obj), (float)c.dth, c.tmapEf);
+        e = c.refine == 1 ? push_bins_m<false, 4>(grid, c.stream, L, of, dthf, c.tmapEf)
+                          : push_bins_m<true, 4>(grid, c.stream, L, of, dthf, c.tmapEf);
     c.launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_movers_mixed(Ctx& c) {
@@ -924,17 +967,19 @@ cudaError_t launch_photo_mixed(Ctx& c) {
 // shared tile of split 32-bit counters with the 2^-32 weights of
 // global_deposit_f (integer sums: the node charges equal those of one global
 // atomic per weight, with an eighth of the global atomics or fewer)
+template <int B>
 __global__ void k_deposit_arrivals_m(Launch L) {
-    __shared__ int Wlo[8 * TILE_N];
-    __shared__ int Whi[8 * TILE_N];
+    constexpr int TL = B + 1, TN = TL * TL * TL;
+    __shared__ int Wlo[8 * TN];
+    __shared__ int Whi[8 * TN];
     const SpeciesDev& S = L.sp[blockIdx.y];
     const int b = blockIdx.x;
     const int n0 = S.bstay[b], n1 = S.bcount[b];   // (bcount clamped to the capacity)
     if (n1 <= n0) return;
     const long long st = S.bstart[b];
     const int bx = b % L.nbx, by = (b / L.nbx) % L.nby, bz = b / (L.nbx * L.nby);
-    const int x0 = bx * BLK, y0 = by * BLK, z0 = bz * BLK;
-    for (int t = threadIdx.x; t < 8 * TILE_N; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
+    const int x0 = bx * B, y0 = by * B, z0 = bz * B;
+    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x) { Wlo[t] = 0; Whi[t] = 0; }
     __syncthreads();
     const int copy = threadIdx.x & 7;
     for (int i = n0 + threadIdx.x; i < n1; i += blockDim.x) {
@@ -945,14 +990,14 @@ __global__ void k_deposit_arrivals_m(Launch L) {
         unsigned W7[7];
 #pragma unroll
         for (int l = 0; l < 7; ++l) W7[l] = (unsigned)Wf[l];
-        tile_deposit(Wlo, Whi, 8 * tile_index(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
+        tile_deposit<unsigned, TL>(Wlo, Whi, 8 * tile_index<TL>(p.i, p.j, p.k, x0, y0, z0) + copy, W7);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < TILE_N; t += blockDim.x) {
+    for (int t = threadIdx.x; t < TN; t += blockDim.x) {
         long long v = 0;
         for (int c = 0; c < 8; ++c) v += tile_value(Wlo[t * 8 + c], Whi[t * 8 + c]);
         if (!v) continue;
-        const int tx = t % TILE, ty = (t / TILE) % TILE, tz = t / (TILE * TILE);
+        const int tx = t % TL, ty = (t / TL) % TL, tz = t / (TL * TL);
         const int gi = x0 + tx, gj = y0 + ty, gk = z0 + tz;
         if (gi <= L.mesh.nx && gj <= L.mesh.ny && gk <= L.mesh.nz)
             atomicAdd(&S.W[node_id(L.mesh, gi, gj, gk)], (unsigned long long)v);
@@ -967,7 +1012,10 @@ cudaError_t launch_rebin_mixed(Ctx& c) {
     if (defer) k_rebin_m<true><<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
     else k_rebin_m<false><<<dim3(4 * 152, ns), 256, 0, c.stream>>>(L);
     k_clamp_counts<<<dim3(nb(c.nblocks), ns), 256, 0, c.stream>>>(L);
-    if (defer) k_deposit_arrivals_m<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    if (defer) {
+        if (c.bin_edge == 8) k_deposit_arrivals_m<8><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+        else k_deposit_arrivals_m<4><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    }
     k_step_advance<<<1, 1, 0, c.stream>>>((long long*)(c.scal + 42));
     c.launches += defer ? 4 : 3;
     return cudaGetLastError();
@@ -978,8 +1026,14 @@ cudaError_t launch_deposit_all_mixed(Ctx& c) {
     int ns = (int)c.sp.size();
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * MAX_SPECIES * c.mesh.nnodes, c.stream);
     if (ns == 0) return cudaGetLastError();
-    if (c.refine > 1) k_deposit_bins_m<true><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
-    else k_deposit_bins_m<false><<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L);
+    const dim3 grid(c.nblocks, ns);
+    if (c.bin_edge == 8) {
+        if (c.refine > 1) k_deposit_bins_m<true, 8><<<grid, 256, 0, c.stream>>>(L);
+        else k_deposit_bins_m<false, 8><<<grid, 256, 0, c.stream>>>(L);
+    } else {
+        if (c.refine > 1) k_deposit_bins_m<true, 4><<<grid, 256, 0, c.stream>>>(L);
+        else k_deposit_bins_m<false, 4><<<grid, 256, 0, c.stream>>>(L);
+    }
     k_deposit_list_m<<<dim3(64, ns), 256, 0, c.stream>>>(L);
     c.launches += 2;
     return cudaGetLastError();

@@ -76,11 +76,13 @@ class Member:
 
 class Server:
     """stream: the batch's CUDA stream (handle); admit_stream: the stream the
-    admission worker sets requests up on (overlap=True; None = the batch's)."""
+    admission worker sets requests up on (overlap=True; None = the batch's);
+    bin_edges: particle-bin edge per size class (autotune_bin_edge's picks;
+    classes not listed use the library's default)."""
 
     def __init__(self, hbm_budget, precision=capi.MIXED, steps_per_round=10, max_steps=500, window=50,
                  rel_change=0.01, pcg_tol=1e-6, cta_nodes=8192, stream=None, keep_phi=False, overlap=True,
-                 admit_stream=None):
+                 admit_stream=None, bin_edges=None):
         self.budget = int(hbm_budget)
         self.precision = precision
         self.k = int(steps_per_round)
@@ -95,6 +97,7 @@ class Server:
         self.used = 0
         self.results = []
         self.keep_phi = keep_phi
+        self.bin_edges = dict(bin_edges or {})   # size class -> particle-bin edge (autotune_bin_edge)
         self.overlap = bool(overlap)
         self.inflight = 0            # handed to the admission worker, not yet in the batch
         if self.overlap:
@@ -110,7 +113,8 @@ class Server:
             self._worker.start()
 
     def _setup(self, cfg, stream):
-        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=stream)
+        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=stream,
+                               bin_edge=self.bin_edges.get(size_class(cfg)))
         sim.solve()
         sim.leapfrog_init()
         return sim
@@ -254,6 +258,68 @@ def autotune_batch(batch, trial_steps=2, candidates=(8192, 4096, 2048),
     batch.set_preconditioner(best[0])
     batch.set_cta_nodes(best[1])
     return best[0], best[1], best_t / trial_steps
+
+
+def size_class(cfg):
+    """The tuner's instance classes: cells per side (below 32 or not) and
+    particles per cell and species (up to 32, up to 48, more)."""
+    n = cfg["n"][0]
+    ppc = max(sp["ppc"] for sp in cfg["species"])
+    return (0 if n < 32 else 1, 0 if ppc <= 32 else (1 if ppc <= 48 else 2))
+
+
+BIN_MAX = 32767   # particles of one species a bin holds (the rest waits in the mover list)
+
+
+def fits_bin(ppc, edge):
+    """A bin of edge^3 cells at ppc particles per cell and species, with the
+    library's 25 % + 64 slack, stays within BIN_MAX (else its overflow would
+    travel through the mover list every step)."""
+    return ppc * edge ** 3 * 1.25 + 64 <= BIN_MAX
+
+
+def autotune_bin_edge(cfgs, precision=capi.MIXED, edges=(4, 8), per_class=8, trial_steps=3, stream=None):
+    """Pick the particle-bin edge per size class by timing: up to per_class
+    members of the class, set up with each edge whose full bins fit (fits_bin
+    at the class's largest ppc), are stepped as one batch (graph rebuilt and
+    warmed first) and timed with CUDA events on the batch's stream.  Returns
+    ({class: edge}, {class: {edge: ms per step}})."""
+    import torch
+    st = torch.cuda.Stream() if stream is None else None
+    handle = st.cuda_stream if st is not None else stream
+    ev_stream = st if st is not None else torch.cuda.ExternalStream(stream)
+    classes = {}
+    for c in cfgs:
+        classes.setdefault(size_class(c), []).append(c)
+    picks, times = {}, {}
+    for k, members in sorted(classes.items()):
+        trial = members[:per_class]
+        times[k] = {}
+        ppc = max(sp["ppc"] for c in members for sp in c["species"])
+        for e in edges:
+            if not fits_bin(ppc, e):
+                continue
+            sims = []
+            try:
+                for c in trial:
+                    sim = capi.from_config(c, precision=precision, stream=handle, bin_edge=e)
+                    sim.solve()
+                    sim.leapfrog_init()
+                    sims.append(sim)
+                batch = capi.Batch(sims, stream=handle)
+                batch.step(1, stats=False)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ev_stream)
+                batch.step(trial_steps, stats=False)
+                e1.record(ev_stream)
+                torch.cuda.synchronize()
+                times[k][e] = e0.elapsed_time(e1) / trial_steps
+                batch.close()
+            finally:
+                for sim in sims:
+                    sim.close()
+        picks[k] = min(times[k], key=times[k].get)
+    return picks, times
 
 
 def poisson_arrivals(rng, rate, horizon):
