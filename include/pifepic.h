@@ -372,13 +372,15 @@ pifepic_status pifepic_batch_remove(pifepic_batch* batch, pifepic_ctx* ctx);
  * iteration and more synchronisation; the serving loop's tuner picks by timing
  * steps.  EINVAL for other values. */
 pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* batch, int cta_nodes);
-/* Preconditioner of the batch's MIXED field solves: AUTO and MULTIGRID solve
- * every member with a multigrid hierarchy (every MIXED context builds one at
- * set-up) by the multigrid-preconditioned PCG on one thread-block cluster of
- * ceil(nodes / cta_nodes) CTAs (1 to 16); JACOBI keeps the Jacobi PCG on
- * clusters of the member's whole working set in shared memory.  FP64 batches
- * always use Jacobi.  The graph is rebuilt on the next step.  EINVAL for an
- * unknown kind. */
+/* Preconditioner of the batch's MIXED field solves: MULTIGRID solves every
+ * member with a multigrid hierarchy (every MIXED context builds one at set-up)
+ * by the multigrid-preconditioned PCG on one thread-block cluster of
+ * ceil(nodes / cta_nodes) CTAs (1 to 16); AUTO (the default) and JACOBI keep
+ * the Jacobi PCG on clusters of the member's whole working set in shared
+ * memory (fewer iterations with multigrid, but each costs about eleven Jacobi
+ * iterations on a cluster, and the Jacobi clusters step the batch faster).
+ * FP64 batches always use Jacobi.  The graph is rebuilt on the next step.
+ * EINVAL for an unknown kind. */
 pifepic_status pifepic_batch_set_preconditioner(pifepic_batch* batch, int kind);
 pifepic_status pifepic_batch_step(pifepic_batch* batch, int nsteps, pifepic_stats* stats);
 const char* pifepic_batch_last_error(const pifepic_batch* batch);

@@ -81,7 +81,7 @@ struct pifepic_batch {
     std::vector<pifepic_ctx*> ctx;
     cudaStream_t stream = nullptr;
     int cta_nodes = 8192;
-    int precond = PIFEPIC_PRECOND_AUTO;   // MIXED members: multigrid clusters where a hierarchy exists
+    int precond = PIFEPIC_PRECOND_AUTO;   // MIXED members: MULTIGRID = multigrid clusters, else Jacobi clusters
     bool dirty = true;
     std::vector<long long> kernels;   // kernels per step of each instance (its share of the batch graph)
     cudaGraph_t graph = nullptr;
@@ -114,7 +114,7 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     for (int i = 0; i < n; ++i) {
         const Ctx& c = b->ctx[i]->c;
         if (c.external_E) continue;
-        if (mixed && b->precond != PIFEPIC_PRECOND_JACOBI && c.mg_nlev > 0) {
+        if (mixed && b->precond == PIFEPIC_PRECOND_MULTIGRID && c.mg_nlev > 0) {
             long long C = (c.mesh.nnodes + b->cta_nodes - 1) / b->cta_nodes;
             mg_c[i] = (int)std::max(1ll, std::min(16ll, C));
             csize[i] = -2;

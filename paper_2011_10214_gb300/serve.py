@@ -10,11 +10,13 @@ once its area-mean surface potential changed by less than `rel_change` over
 the last `window` steps (the charging has reached its floating potential,
 Sec. 3.1.2).  Latency = finish time - arrival time.
 
-Admission overlaps the running work (overlap=True): a worker thread sets up
-each admitted request on its own CUDA stream while the main thread keeps
-stepping the batch, and the ready request joins the batch at the next round.
-With overlap=False the set-up runs between rounds on the batch's stream and
-every running member waits for it.
+Admission overlaps the running work (overlap=True): a worker thread creates
+each admitted request and loads its particles on its own CUDA stream while the
+main thread keeps stepping the batch; at the next round the main thread runs
+the request's initial field solve and leapfrog start (a persistent solve over
+the whole device, which must not run beside the batch's clustered solves) and
+adds it to the batch.  With overlap=False the whole set-up runs between rounds
+on the batch's stream and every running member waits for it.
 
 Host-side orchestration only (admission, batch membership, stop tests); every
 step of every member runs in libpifepic's kernels.
@@ -112,16 +114,26 @@ class Server:
             self._worker = threading.Thread(target=self._work, daemon=True)
             self._worker.start()
 
-    def _setup(self, cfg, stream):
-        sim = capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=stream,
-                               bin_edge=self.bin_edges.get(size_class(cfg)))
+    def _create(self, cfg, stream):
+        """Context, object, species, particle load and injection (no solve)."""
+        return capi.from_config(cfg, precision=self.precision, pcg_tol=self.pcg_tol, stream=stream,
+                                bin_edge=self.bin_edges.get(size_class(cfg)))
+
+    @staticmethod
+    def _start(sim):
+        """The initial field solve and the leapfrog start."""
         sim.solve()
         sim.leapfrog_init()
+
+    def _setup(self, cfg, stream):
+        sim = self._create(cfg, stream)
+        self._start(sim)
         return sim
 
     def _work(self):
-        """Admission worker: sets up handed-over requests on the admission
-        stream, in arrival order, while the main thread steps the batch."""
+        """Admission worker: creates and loads handed-over requests on the
+        admission stream, in arrival order, while the main thread steps the
+        batch (the main thread starts them at the join)."""
         if self.device is not None:
             import torch
             torch.cuda.set_device(self.device)
@@ -131,7 +143,7 @@ class Server:
                 return
             rid, cfg, arrival = item
             try:
-                self._ready.put((rid, cfg, arrival, self._setup(cfg, self.admit_stream), None))
+                self._ready.put((rid, cfg, arrival, self._create(cfg, self.admit_stream), None))
             except Exception as e:          # reported by the main thread
                 self._ready.put((rid, cfg, arrival, None, e))
 
@@ -152,6 +164,7 @@ class Server:
             self.inflight -= 1
             if err is not None:
                 raise err
+            self._start(sim)
             self._join(rid, cfg, arrival, sim)
 
     def _admit(self, rid, cfg, arrival):
