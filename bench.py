@@ -29,6 +29,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the headline metric: `value` is the plain (single-instance) rate; the line's `batched` and `served`
 # objects carry the batched rate (and its ratio to the plain one) and the served p50/p99 latency
 METRIC = "particle-steps/s incl. IFE solve, batched vs plain; served p50/p99 latency"
+PROFILE_RANGE = False   # --profile-range: profiler start/stop around the timed steps (ncu --profile-from-start off)
 BIN_EDGE = None   # MIXED particle-bin edge of the measured contexts (--bin-edge; None = the library's default)
 PRECOND = 0   # MIXED preconditioner of the measured contexts (--precond; 0 = the library's automatic choice)
 BYTES_PER_PARTICLE_STEP = {"fp64": 96, "mixed": 56}     # read + write of the particle state
@@ -224,10 +225,14 @@ def measure(cfg, precision, steps, warmup, stream, dist, local):
     barrier()
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if PROFILE_RANGE:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     st = sim.step(steps)
     ev1.record(stream)
     barrier()
+    if PROFILE_RANGE:
+        torch.cuda.profiler.stop()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     pushed = sum(st["pushed"])
@@ -557,10 +562,14 @@ def measure_batch(instances, steps, warmup, autotune=True):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if PROFILE_RANGE:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     st = batch.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if PROFILE_RANGE:
+        torch.cuda.profiler.stop()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     pushed = sum(sum(x["pushed"]) for x in st)
@@ -665,11 +674,14 @@ def main():
     ap.add_argument("--as-baseline", action="store_true")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "multigrid"],
                     help="MIXED field-solve preconditioner (pifepic_set_preconditioner)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="profiler start/stop around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--bin-edge", type=int, default=None, choices=[4, 8],
                     help="MIXED particle bins of edge^3 cells (pifepic_set_bin_edge)")
     args = ap.parse_args()
-    global PRECOND, BIN_EDGE
+    global PRECOND, BIN_EDGE, PROFILE_RANGE
     BIN_EDGE = args.bin_edge
+    PROFILE_RANGE = args.profile_range
     PRECOND = {"auto": 0, "jacobi": 1, "multigrid": 2}[args.precond]
     if args.impl == "reference":
         run_reference(args)
