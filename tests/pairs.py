@@ -36,6 +36,15 @@ CASES = {
 }
 
 
+# edge cases, outside the parametrised sweeps over CASES: a box with no object
+# (no interface tets, no cut cells) and a mesh smaller than one particle bin
+EDGE_CASES = {
+    "empty_box": dict(n=(10, 9, 7), h=0.5, obj=("none",),
+                      bc=[("D", 0.0), ("D", 0.3), ("N",), ("N",), ("D", -0.2), ("N",)]),
+    "tiny": dict(n=(4, 3, 2), h=0.5, obj=("none",), bc=[("D", 0.1), ("D", -0.1), ("N",), ("D", 0.0), ("N",), ("N",)]),
+}
+
+
 def oracle_object(m, o, bed=None):
     if o[0] == "sphere":
         obj = Sphere(m, o[1], o[2], o[3], o[4])
@@ -64,11 +73,13 @@ def gpu_object(sim, o, bed=None):
         sim.set_object(capi.OBJ_RIM_CRATER, list(o[1:9]), o[9], o[10])
     elif o[0] == "plane":
         sim.set_object(capi.OBJ_PLANE, list(o[1]) + [o[2]], o[3], o[4])
+    else:
+        sim.set_object(capi.OBJ_NONE, [], 1.0, 1.0)
 
 
 def make_pair(case, dt=0.05, tol=1e-12, maxit=2000, track=True, precision=0, refine=None):
     from paper_2011_10214_gb300 import capi
-    c = CASES[case]
+    c = CASES[case] if case in CASES else EDGE_CASES[case]
     r = c.get("refine", 1) if refine is None else refine
     m = Mesh(*c["n"], c["h"])
     obj = oracle_object(m, c["obj"], c.get("bed"))
