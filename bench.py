@@ -199,7 +199,7 @@ SOLVE_BYTES_PER_NODE_ITER = {"mixed": 7 * 4, "fp64": 7 * 8}
 # DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 64^3 sphere
 # bench workload (dram__bytes_read.sum + dram__bytes_write.sum over the launch's particles); None when
 # not measured for the current kernel
-PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (930549248 + 860526336) / 32619866, "fp64": None}
+PUSH_TRAFFIC_PER_PARTICLE = {"mixed": (930762240 + 860456448) / 32619866, "fp64": None}
 NSM, DFMA_PER_CLK_SM = 152, 2          # GB300: 2 FP64 FMA per SM per clock
 
 
