@@ -373,7 +373,8 @@ pifepic_status pifepic_batch_remove(pifepic_batch* batch, pifepic_ctx* ctx);
  * steps.  EINVAL for other values. */
 pifepic_status pifepic_batch_set_cta_nodes(pifepic_batch* batch, int cta_nodes);
 /* Preconditioner of the batch's MIXED field solves: MULTIGRID solves every
- * member with a multigrid hierarchy (every MIXED context builds one at set-up)
+ * member that has a multigrid hierarchy (built for the member on the first
+ * step that needs it; meshes of at most 256 nodes have none and keep Jacobi)
  * by the multigrid-preconditioned PCG on one thread-block cluster of
  * ceil(nodes / cta_nodes) CTAs (1 to 16); AUTO (the default) and JACOBI keep
  * the Jacobi PCG on clusters of the member's whole working set in shared

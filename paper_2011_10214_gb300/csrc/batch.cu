@@ -28,6 +28,7 @@ pifepic_status finish_stats(pifepic_ctx* ctx, const unsigned long long* before, 
 
 
 int cluster_size_for(long long N, long long H, bool mixed, long long cta_nodes);   // pcg_cluster.cu
+cudaError_t build_pcg_graph(Ctx& c);                                                // field.cu
 cudaError_t launch_pcg_mg_cluster(Ctx& c, int C, cudaStream_t st);                 // pcg_mg.cu
 size_t cluster_smem_for(long long N, long long H, int C, bool mixed);
 cudaError_t launch_pcg_cluster(const BatchItem& item, int C, size_t smem, bool mixed, cudaStream_t st);
@@ -112,8 +113,15 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     std::vector<int> csize(n, -1), mg_c(n, 0);
     std::vector<int> mg_members;
     for (int i = 0; i < n; ++i) {
-        const Ctx& c = b->ctx[i]->c;
+        Ctx& c = b->ctx[i]->c;
         if (c.external_E) continue;
+        if (mixed && b->precond == PIFEPIC_PRECOND_MULTIGRID && c.mg_nlev == 0 && !c.mg_wanted) {
+            // the hierarchy on first use; the member's own solve graph is
+            // re-planned with it (its plan's buffers are replaced)
+            c.mg_wanted = true;
+            cudaError_t e = build_pcg_graph(c);
+            if (e != cudaSuccess) return e;
+        }
         if (mixed && b->precond == PIFEPIC_PRECOND_MULTIGRID && c.mg_nlev > 0) {
             long long C = (c.mesh.nnodes + b->cta_nodes - 1) / b->cta_nodes;
             mg_c[i] = (int)std::max(1ll, std::min(16ll, C));

@@ -704,11 +704,16 @@ static bool coarsest_inverse(const MgLevel& L, const std::vector<float>& coef, c
 
 // the hierarchy for the context's current operator (MIXED contexts; leaves
 // mg_nlev = 0 otherwise), and whether the context's own solve uses it
-// (mg_single; batched solves choose for themselves)
+// (mg_single).  Built only where it is used: by the context's own solve, or
+// once a batch that solves with multigrid has asked for it (mg_wanted).
 cudaError_t plan_pcg_mg(Ctx& c) {
     free_mg(c);
     c.mg_single = false;
     if (c.precision != PIFEPIC_MIXED) return cudaSuccess;
+    // AUTO: multigrid where the register-resident Jacobi solver does not fit
+    // (planned just before this); there the Jacobi iterations grow past the cap
+    const bool single = c.precond == PIFEPIC_PRECOND_MULTIGRID || (c.precond == PIFEPIC_PRECOND_AUTO && c.pcg_npt == 0);
+    if (!single && !c.mg_wanted) return cudaSuccess;
     const long long N0 = c.mesh.nnodes;
     int nx = c.mesh.nx, ny = c.mesh.ny, nz = c.mesh.nz;
     long long Nlast = N0;
@@ -754,9 +759,7 @@ cudaError_t plan_pcg_mg(Ctx& c) {
     if (e == cudaSuccess && !coarsest_inverse(Lc, coef, dinv, inv)) { free_mg(c); return cudaSuccess; }
     if (e == cudaSuccess) e = scopy(c.stream, c.mg_cinv, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free_mg(c); return e; }
-    // AUTO: multigrid where the register-resident Jacobi solver does not fit
-    // (planned just before this); there the Jacobi iterations grow past the cap
-    c.mg_single = c.precond == PIFEPIC_PRECOND_MULTIGRID || (c.precond == PIFEPIC_PRECOND_AUTO && c.pcg_npt == 0);
+    c.mg_single = single;
     return cudaSuccess;
 }
 

@@ -109,12 +109,14 @@ def test_served_results_equal_alone(overlap):
         assert np.array_equal(by[i]["phi"], a["phi"])
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_cluster_solves_match_single_instance_solves(precision):
+@pytest.mark.parametrize("precision,precond", [(0, None), (1, "jacobi"), (1, "multigrid")])
+def test_cluster_solves_match_single_instance_solves(precision, precond):
     """Members of 20^3..48^3 cells put the batched solve on clusters of 2, 4,
-    8 and 16 CTAs (FP64: the largest goes to the one-CTA kernel).  After one
-    step from the same state, each member's potential equals the same instance
-    stepped alone (persistent single-instance solver) to the solver tolerance."""
+    8 and 16 CTAs (FP64: the largest goes to the one-CTA kernel; MIXED: Jacobi
+    clusters, or multigrid clusters whose hierarchies are built on that first
+    batched step).  After one step from the same state, each member's potential
+    equals the same instance stepped alone (persistent single-instance solver)
+    to the solver tolerance."""
     from paper_2011_10214_gb300 import capi
     cfgs = [wl.sphere_config(n, 0.2 * n * 0.5, 4, 1, eps_in=3.0, seed_offset=30 + n) for n in (20, 24, 28, 36, 48)]
 
@@ -130,6 +132,8 @@ def test_cluster_solves_match_single_instance_solves(precision):
         s.close()
     sims = [fresh(cfg) for cfg in cfgs]
     b = capi.Batch(sims)
+    if precond is not None:
+        b.set_preconditioner(capi.PRECOND_MULTIGRID if precond == "multigrid" else capi.PRECOND_JACOBI)
     st = b.step(1)
     for k, (s, phi) in enumerate(zip(sims, alone)):
         assert st[k]["pcg_converged"] == 1, k
