@@ -152,7 +152,17 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem a
         for (int li = threadIdx.x; li < nown; li += CL_THREADS) {
             const long long n = b0 + li;
             const double bn = a.b[n];
-            const double rn = (f.ntype[n] == -3) ? 0.0 : bn - row(li, ldu, f.coef);
+            // (MIXED: three or more of these per solve; interior rows in closed form)
+            double rn = 0.0;
+            if (f.ntype[n] != -3) {
+                if constexpr (MIXED) {
+                    const unsigned u = pk[li];
+                    rn = bn - apply_row64(f, n, (int)(u & 2047u), (int)((u >> 11) & 2047u), (int)(u >> 22), ldu,
+                                          f.coef);
+                } else {
+                    rn = bn - row(li, ldu, f.coef);
+                }
+            }
             const T rt = (T)rn, zt = dinv[n] * rt;
             r[li] = rt;
             win[H + li] = zt;
