@@ -193,7 +193,13 @@ def cfg_desc(cfg, precision, extra=None):
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
-FP64_FLOPS_PER_PARTICLE_STEP = 80     # trilinear weights 19, gather 45, kick and drift 12, cell test 4
+# FP64 push, from an ncu capture of one k_push_bins launch on the 32^3 sphere (4,076,523 particles):
+# sm__inst_executed_pipe_fp64.sum = 18,357,080 warp instructions (4.50 per particle, 144 lane operations),
+# DADD 183,285,395 + DMUL 256,496,282 + DFMA 9,065 thread instructions (107.9 flops per particle; the kernel
+# keeps DADD and DMUL apart, no FMA contraction, for results bit-identical to the FP64 oracle)
+FP64_PIPE_WARP_INST_PER_PARTICLE = 18357080 / 4076523
+FP64_FLOPS_PER_PARTICLE_STEP = (183285395 + 256496282 + 2 * 9065) / 4076523
+FP64_LANES_PER_CLK_SM = 2              # FP64 pipe: 2 lane operations per clock per SM (GB300)
 # PCG: 7 node-vector passes per iteration (p, x, r, z updates, the operator's read of p and write of q)
 SOLVE_BYTES_PER_NODE_ITER = {"mixed": 7 * 4, "fp64": 7 * 8}
 # DRAM bytes per pushed particle of one k_push_bins_m launch, from an ncu capture of the 64^3 sphere
@@ -261,14 +267,21 @@ def roofline(precision, st, steps, ck):
                 "traffic_note": "ncu DRAM bytes per particle of a 64^3 sphere launch (54.9 B, 0.98 of the "
                                 "algorithmic 56 B), scaled to this launch's particles",
                 "peak_source": src, "alg_bytes_per_launch": alg, "avg_launch_ms": push_ms}
-    flops = per_launch * FP64_FLOPS_PER_PARTICLE_STEP
-    ach = flops / (push_ms / 1e3) / 1e9
+    # bound by the FP64 pipe: its lane operations (every FP64-pipe warp instruction x 32 lanes: DADD, DMUL,
+    # conversions, compares, roundings) per second against 152 SMs x 2 lanes/clk x max SM clock
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = NSM * DFMA_PER_CLK_SM * 2 * mhz / 1e3
+    ops = per_launch * FP64_PIPE_WARP_INST_PER_PARTICLE * 32
+    ach = ops / (push_ms / 1e3) / 1e9
+    peak = NSM * FP64_LANES_PER_CLK_SM * mhz / 1e3
+    flops = per_launch * FP64_FLOPS_PER_PARTICLE_STEP
     return {"kernel": "k_push_bins (FP64, no FMA contraction)", "bound": "alu", "achieved": round(ach, 1),
-            "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-            "alg_flops_per_launch": flops, "avg_launch_ms": push_ms,
+            "peak": round(peak, 1), "unit": "G FP64-pipe ops/s", "frac": round(ach / peak, 4), "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x max SM clock",
+            "ops_per_particle_step": round(FP64_PIPE_WARP_INST_PER_PARTICLE * 32, 1),
+            "flops_view": {"achieved_gflops": round(flops / (push_ms / 1e3) / 1e9, 1),
+                           "flops_per_particle_step": round(FP64_FLOPS_PER_PARTICLE_STEP, 1),
+                           "peak_gflops_with_fma": round(NSM * DFMA_PER_CLK_SM * 2 * mhz / 1e3, 1)},
+            "avg_launch_ms": push_ms,
             "hbm_view": {"achieved_gbs": round(per_launch * 96 / (push_ms / 1e3) / 1e9, 1),
                          "peak_gbs": peaks["hbm_gbs"]}}
 
