@@ -23,18 +23,26 @@ def _member(cfg, precision):
     return sim
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_member_alone_equals_member_in_mix(precision):
+@pytest.mark.parametrize("precision,precond", [(0, None), (1, None), (1, "multigrid")])
+def test_member_alone_equals_member_in_mix(precision, precond):
+    """Bit-identical in a batch of one and in the mix; MIXED also with the
+    multigrid clusters (hierarchies built on the first batched step)."""
     from paper_2011_10214_gb300 import capi
+
+    def batch(sims):
+        b = capi.Batch(sims)
+        if precond == "multigrid":
+            b.set_preconditioner(capi.PRECOND_MULTIGRID)
+        return b
     alone = []
     for cfg in MEMBERS:
         s = _member(cfg, precision)
-        b = capi.Batch([s])
+        b = batch([s])
         b.step(5)
         alone.append((s.potential(), s.node_charge(0), by_id(s.particles(1))))
         b.close(); s.close()
     sims = [_member(cfg, precision) for cfg in MEMBERS]
-    b = capi.Batch(sims)
+    b = batch(sims)
     stats = b.step(5)
     assert len(stats) == 3 and all(st["pcg_iters"] > 0 for st in stats)
     for s, (phi, W, P) in zip(sims, alone):
