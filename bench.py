@@ -402,6 +402,8 @@ def run_gpu(args):
         "gpu_launches": int(st["kernel_launches"]),
         "pcg_iters_per_step": st["pcg_iters_total"] / args.steps,
         "pcg_refinements_per_step": st["pcg_outer_total"] / args.steps,
+        "events_per_step": {k: [round(v / args.steps, 1) for v in st[k]]
+                            for k in ("pushed", "absorbed", "collected", "injected") if k in st},
         "phase_ms_per_step": {k: v / args.steps for k, v in zip(PHASES, st["phase_ms"]) if v},
         "compare": alt,
     }
