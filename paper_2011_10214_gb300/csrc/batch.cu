@@ -107,9 +107,10 @@ static cudaError_t build_batch_graph(pifepic_batch* b) {
     int n = (int)b->ctx.size();
     if (n == 0) { b->dirty = false; return cudaSuccess; }
     bool mixed = b->ctx[0]->c.precision == PIFEPIC_MIXED;
-    // solve groups: cluster size per instance (0: the one-CTA kernel), items in group order
-    // members solved by the multigrid cluster kernel (MIXED, with a hierarchy):
-    // csize -2, cluster size in mg_c
+    // the solve of each instance: csize = its Jacobi cluster size (0: too large
+    // for a cluster, the single-instance persistent solver); members solved by
+    // the multigrid cluster kernel (MIXED, with a hierarchy) get csize -2 and
+    // their cluster size in mg_c
     std::vector<int> csize(n, -1), mg_c(n, 0);
     std::vector<int> mg_members;
     for (int i = 0; i < n; ++i) {
