@@ -198,8 +198,11 @@ pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double
  * solved exactly by its dense inverse.  AUTO (the default): MULTIGRID for
  * meshes too large for the register-resident solver (more than 8 nodes per
  * thread of a full grid, about 620,000 nodes), where the Jacobi iteration
- * count outgrows the cap, else JACOBI.  Either solves the same system to the
- * same stopping test.  Takes effect at once (the solve is re-planned); no
+ * count outgrows the cap, else JACOBI -- until a solve of pifepic_solve or
+ * pifepic_step ends at the iteration cap without converging: from then on
+ * the context solves with MULTIGRID (meshes of at most 256 nodes have no
+ * hierarchy and keep Jacobi).  Either solves the same system to the same
+ * stopping test.  Takes effect at once (the solve is re-planned); no
  * effect in FP64 mode or on batched solves.  Errors: EINVAL (unknown kind),
  * ENOMEM. */
 enum { PIFEPIC_PRECOND_AUTO = 0, PIFEPIC_PRECOND_JACOBI = 1, PIFEPIC_PRECOND_MULTIGRID = 2 };

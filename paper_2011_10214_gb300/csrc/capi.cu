@@ -1049,6 +1049,19 @@ static cudaError_t run_solve(Ctx& c) {
     return launch_pcg(c);   // (the solve graph holds the precision's kernels)
 }
 
+// AUTO (MIXED): once a Jacobi solve of the context has ended at the iteration
+// cap without converging, its later solves run the multigrid cycle (the solve
+// is re-planned once; a mesh too small for a hierarchy keeps Jacobi)
+static pifepic_status escalate_if_capped(pifepic_ctx* ctx) {
+    Ctx& c = ctx->c;
+    if (c.precision != PIFEPIC_MIXED || c.precond != PIFEPIC_PRECOND_AUTO || c.mg_single || c.mg_escalated)
+        return PIFEPIC_OK;
+    if (c.last_conv || c.last_iters < c.maxit) return PIFEPIC_OK;
+    c.mg_escalated = true;
+    CUDA_OK(build_pcg_graph(c));
+    return PIFEPIC_OK;
+}
+
 pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
     NEED(ctx);
     Ctx& c = ctx->c;
@@ -1060,7 +1073,9 @@ pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
     else CUDA_OK(launch_deposit_all(c));
     if (!c.external_E) CUDA_OK(run_solve(c));
     CUDA_OK(cudaStreamSynchronize(c.stream));
-    return fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1, ot0);
+    pifepic_status r = fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1, ot0);
+    if (r || c.external_E) return r;
+    return escalate_if_capped(ctx);
 }
 
 pifepic_status pifepic_leapfrog_init(pifepic_ctx* ctx) {
@@ -1157,7 +1172,9 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
         pifepic_status g = check_spill((nsteps - 1) % STEP_RING);
         if (g) return g;
     }
-    return fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps, ot0);
+    pifepic_status r = fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps, ot0);
+    if (r || c.external_E || nsteps == 0) return r;
+    return escalate_if_capped(ctx);
 }
 
 pifepic_status pifepic_get_sizes(pifepic_ctx* ctx, int64_t* nn, int64_t* nc, int64_t* nit, int64_t* ncut) {

@@ -231,6 +231,7 @@ struct Ctx {
     float* mg_r0 = nullptr;           // fine residual after pre-smoothing
     float* mg_cinv = nullptr;         // dense inverse of the coarsest operator
     bool mg_wanted = false;           // a batch solves this context with multigrid: keep a hierarchy
+    bool mg_escalated = false;        // AUTO: a Jacobi solve ended at the cap unconverged; multigrid since
     unsigned short* rowkind = nullptr;  // global-memory PCG (larger meshes): row kinds, [N]
     double* pcg_x = nullptr;            // and its FP64 correction vector, [N]
     int pcg_G = 1;

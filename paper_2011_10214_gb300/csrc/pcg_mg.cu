@@ -711,8 +711,11 @@ cudaError_t plan_pcg_mg(Ctx& c) {
     c.mg_single = false;
     if (c.precision != PIFEPIC_MIXED) return cudaSuccess;
     // AUTO: multigrid where the register-resident Jacobi solver does not fit
-    // (planned just before this); there the Jacobi iterations grow past the cap
-    const bool single = c.precond == PIFEPIC_PRECOND_MULTIGRID || (c.precond == PIFEPIC_PRECOND_AUTO && c.pcg_npt == 0);
+    // (planned just before this), where the Jacobi iterations grow past the
+    // cap; and once a Jacobi solve of this context has ended at the cap
+    // unconverged (mostly Neumann faces: poorly conditioned for Jacobi)
+    const bool single = c.precond == PIFEPIC_PRECOND_MULTIGRID ||
+                        (c.precond == PIFEPIC_PRECOND_AUTO && (c.pcg_npt == 0 || c.mg_escalated));
     if (!single && !c.mg_wanted) return cudaSuccess;
     const long long N0 = c.mesh.nnodes;
     int nx = c.mesh.nx, ny = c.mesh.ny, nz = c.mesh.nz;

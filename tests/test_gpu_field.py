@@ -193,3 +193,28 @@ def test_preconditioner_choice_is_validated():
     with pytest.raises(capi.PifepicError, match="EINVAL"):
         sim.set_preconditioner(7)
     sim.close()
+
+
+def test_auto_moves_to_multigrid_after_a_capped_jacobi_solve():
+    """AUTO (MIXED): the crater's Jacobi solve stops at a cap of 40 unconverged
+    at tol 1e-12; the next solve runs the multigrid cycle and converges within
+    the same cap to the oracle's potential.  An explicit JACOBI stays capped."""
+    from paper_2011_10214_gb300 import capi
+    from tests.pairs import add_species_both, explicit_particles
+    for precond in ("auto", "jacobi"):
+        gpu, orc = make_pair("crater", precision=1, maxit=40)
+        orc.maxit = 5000                      # the oracle solves to the tolerance
+        if precond == "jacobi":
+            gpu.set_preconditioner(capi.PRECOND_JACOBI)
+        add_species_both(gpu, orc, -1.0, 1.0, 0.01)
+        explicit_particles(gpu, orc, 0, 4000, 5, 1.0)
+        st1 = gpu.solve()
+        assert st1["pcg_converged"] == 0 and st1["pcg_iters"] == 40
+        st2 = gpu.solve()
+        if precond == "auto":
+            assert st2["pcg_converged"] == 1 and st2["pcg_iters"] < 40
+            orc.solve()
+            assert _rel(gpu.potential(), orc.phi) <= TOL_PHI
+        else:
+            assert st2["pcg_converged"] == 0 and st2["pcg_iters"] == 40
+        gpu.close()
