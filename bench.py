@@ -286,7 +286,7 @@ def roofline(precision, st, steps, ck):
                          "peak_gbs": peaks["hbm_gbs"]}}
 
 
-def roofline_solve(precision, st, steps, nnodes):
+def roofline_solve(precision, st, steps, nnodes, solver):
     """The field solve: algorithmic node-vector bytes of the PCG iterations over the solve graph's time
     (the persistent PCG kernel plus the short RHS, start-vector and node-field kernels around it)."""
     solve_ms = st["phase_ms"][5] / steps
@@ -294,10 +294,8 @@ def roofline_solve(precision, st, steps, nnodes):
     alg = nnodes * SOLVE_BYTES_PER_NODE_ITER[precision] * iters
     ach = alg / (solve_ms / 1e3) / 1e9
     peaks, src = _peaks()
-    # the register-resident kernel serves meshes of at most 8 nodes per thread of a full grid; beyond it MIXED
-    # solves run the multigrid-preconditioned kernel (unless --precond jacobi), FP64 the global-memory one
-    reg = nnodes <= NSM * 512 * 8
-    mg = precision == "mixed" and (PRECOND == 2 or (PRECOND == 0 and not reg))
+    # the solver the library ran (pifepic_get_solver: 1 registers, 2 global memory, 3 multigrid)
+    reg, mg = solver == 1, solver == 3
     if mg:
         # per inner iteration: the PCG's 7 FP32 passes plus the V-cycle's fine-level passes (pre-smoothing
         # 12 B, residual 12 B, correction 8 B, post-smoothing 16 B); the coarse levels add about 1/7 more
@@ -336,7 +334,7 @@ def run_gpu(args):
     value = total / secs
     nnodes = sim.sizes()["nnodes"]
     roof_push = roofline(main, st, args.steps, ck)
-    roof_solve = roofline_solve(main, st, args.steps, nnodes)
+    roof_solve = roofline_solve(main, st, args.steps, nnodes, sim.solver)
     # the longer of the two phases is the dominant kernel; the other is reported beside it
     if roof_solve["avg_launch_ms"] > roof_push["avg_launch_ms"]:
         roof, roof_other = roof_solve, roof_push

@@ -207,6 +207,12 @@ pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double
  * ENOMEM. */
 enum { PIFEPIC_PRECOND_AUTO = 0, PIFEPIC_PRECOND_JACOBI = 1, PIFEPIC_PRECOND_MULTIGRID = 2 };
 pifepic_status pifepic_set_preconditioner(pifepic_ctx* ctx, int kind);
+/* The persistent solver the context's next solve runs (after AUTO's choices):
+ * 1 = Jacobi PCG with the vectors in registers (meshes of at most 8 nodes per
+ * thread of a full grid), 2 = Jacobi PCG with the vectors in global memory,
+ * 3 = multigrid-preconditioned PCG (MIXED); 0 for a NULL context. */
+enum { PIFEPIC_SOLVER_REGISTERS = 1, PIFEPIC_SOLVER_GLOBAL = 2, PIFEPIC_SOLVER_MULTIGRID = 3 };
+int pifepic_get_solver(const pifepic_ctx* ctx);
 pifepic_status pifepic_set_field_bc(pifepic_ctx* ctx, const pifepic_face_bc bc[6]);
 
 /* Particle bins (the cell blocks of Sec. 2.3's particle storage): particles

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpifepic.so")
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 OBJ_NONE, OBJ_SPHERE, OBJ_CAP_CRATER, OBJ_PLANE, OBJ_RIM_CRATER = 0, 1, 2, 3, 4
+SOLVER_REGISTERS, SOLVER_GLOBAL, SOLVER_MULTIGRID = 1, 2, 3
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PBC_ABSORB, PBC_INJECT, PBC_REFLECT = 0, 1, 2
 PRECOND_AUTO, PRECOND_JACOBI, PRECOND_MULTIGRID = 0, 1, 2
@@ -106,6 +107,7 @@ _sigs = {
     "pifepic_set_preconditioner": [_ctx, C.c_int],
     "pifepic_set_bin_edge": [_ctx, C.c_int],
     "pifepic_get_bin_edge": [_ctx],
+    "pifepic_get_solver": [_ctx],
     "pifepic_get_memory_use": [C.POINTER(C.c_size_t)],
     "pifepic_set_memory_limit": [C.c_size_t],
     "pifepic_test_hold_exchange": [_ctx, C.c_int],
@@ -230,6 +232,11 @@ class Simulation:
     @property
     def bin_edge(self):
         return int(lib.pifepic_get_bin_edge(self._c))
+
+    @property
+    def solver(self):
+        """The persistent solver of the next solve: SOLVER_REGISTERS, SOLVER_GLOBAL or SOLVER_MULTIGRID."""
+        return int(lib.pifepic_get_solver(self._c))
 
     def set_field_bc(self, faces):
         arr = (FaceBC * 6)()

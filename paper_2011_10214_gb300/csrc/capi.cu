@@ -641,6 +641,13 @@ pifepic_status pifepic_set_bin_edge(pifepic_ctx* ctx, int edge) {
 
 int pifepic_get_bin_edge(const pifepic_ctx* ctx) { return ctx ? ctx->c.bin_edge : 0; }
 
+int pifepic_get_solver(const pifepic_ctx* ctx) {
+    if (!ctx) return 0;
+    const Ctx& c = ctx->c;
+    if (c.precision == PIFEPIC_MIXED && c.mg_single && c.mg_nlev > 0) return PIFEPIC_SOLVER_MULTIGRID;
+    return c.pcg_npt > 0 ? PIFEPIC_SOLVER_REGISTERS : PIFEPIC_SOLVER_GLOBAL;
+}
+
 pifepic_status pifepic_add_species(pifepic_ctx* ctx, double qq, double mm, double w, int* id) {
     NEED(ctx);
     Ctx& c = ctx->c;

@@ -208,8 +208,10 @@ def test_auto_moves_to_multigrid_after_a_capped_jacobi_solve():
             gpu.set_preconditioner(capi.PRECOND_JACOBI)
         add_species_both(gpu, orc, -1.0, 1.0, 0.01)
         explicit_particles(gpu, orc, 0, 4000, 5, 1.0)
+        assert gpu.solver == capi.SOLVER_REGISTERS
         st1 = gpu.solve()
         assert st1["pcg_converged"] == 0 and st1["pcg_iters"] == 40
+        assert gpu.solver == (capi.SOLVER_MULTIGRID if precond == "auto" else capi.SOLVER_REGISTERS)
         st2 = gpu.solve()
         if precond == "auto":
             assert st2["pcg_converged"] == 1 and st2["pcg_iters"] < 40
