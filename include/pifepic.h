@@ -144,7 +144,13 @@ typedef struct {
     double surface_potential;                  /* area-mean phi on Gamma_h      */
     double phase_ms[8];                        /* GPU time per phase, this call:
                                                   push, movers, inject, rebin,
-                                                  rhs, pcg, node_E, other        */
+                                                  rhs, pcg, node_E, other.  In
+                                                  pifepic_step the waiting
+                                                  list's push and the injection
+                                                  run beside the bins' push: the
+                                                  push phase covers them, the
+                                                  movers phase holds what
+                                                  outlasts it, inject is 0      */
     int64_t pcg_outer_total;                   /* MIXED refinement steps in this
                                                   call (FP64 residuals - 1 per
                                                   solve)                         */
@@ -198,8 +204,9 @@ pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double
  * solved exactly by its dense inverse.  AUTO (the default): MULTIGRID for
  * meshes too large for the register-resident solver (more than 8 nodes per
  * thread of a full grid, about 620,000 nodes), where the Jacobi iteration
- * count outgrows the cap, else JACOBI -- until a solve of pifepic_solve or
- * pifepic_step ends at the iteration cap without converging: from then on
+ * count outgrows the cap, else JACOBI -- until a warm-started solve of
+ * pifepic_solve or pifepic_step (any but the context's first, which starts
+ * from zero) ends at the iteration cap without converging: from then on
  * the context solves with MULTIGRID (meshes of at most 256 nodes have no
  * hierarchy and keep Jacobi).  Either solves the same system to the same
  * stopping test.  Takes effect at once (the solve is re-planned); no

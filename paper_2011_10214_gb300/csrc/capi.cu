@@ -388,6 +388,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (!ctx) return;
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
+    if (c.side) cudaStreamSynchronize(c.side);
     void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q,
                     c.z ? (void*)(c.z - c.zguard) : nullptr, c.zf ? (void*)(c.zf - c.zguard) : nullptr,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
@@ -408,6 +409,9 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     if (c.pcg_graph) cudaGraphDestroy(c.pcg_graph);
     if (c.ev_ok) for (int e = 0; e < 16; ++e) cudaEventDestroy(c.ev[e]);
     for (cudaEvent_t e : c.step_ev) cudaEventDestroy(e);
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
+    if (c.side) cudaStreamDestroy(c.side);
     if (c.spill_host) cudaFreeHost(c.spill_host);
     delete ctx;
 }
@@ -1056,14 +1060,15 @@ static cudaError_t run_solve(Ctx& c) {
     return launch_pcg(c);   // (the solve graph holds the precision's kernels)
 }
 
-// AUTO (MIXED): once a Jacobi solve of the context has ended at the iteration
-// cap without converging, its later solves run the multigrid cycle (the solve
-// is re-planned once; a mesh too small for a hierarchy keeps Jacobi)
+// AUTO (MIXED): once a warm-started Jacobi solve of the context (any but its
+// first, which starts from zero) has ended at the iteration cap without
+// converging, its later solves run the multigrid cycle (the solve is
+// re-planned once; a mesh too small for a hierarchy keeps Jacobi)
 static pifepic_status escalate_if_capped(pifepic_ctx* ctx) {
     Ctx& c = ctx->c;
     if (c.precision != PIFEPIC_MIXED || c.precond != PIFEPIC_PRECOND_AUTO || c.mg_single || c.mg_escalated)
         return PIFEPIC_OK;
-    if (c.last_conv || c.last_iters < c.maxit) return PIFEPIC_OK;
+    if (c.solves_done < 2 || c.last_conv || c.last_iters < c.maxit) return PIFEPIC_OK;
     c.mg_escalated = true;
     CUDA_OK(build_pcg_graph(c));
     return PIFEPIC_OK;
@@ -1082,6 +1087,7 @@ pifepic_status pifepic_solve(pifepic_ctx* ctx, pifepic_stats* st) {
     CUDA_OK(cudaStreamSynchronize(c.stream));
     pifepic_status r = fill_stats(ctx, before, st, nullptr, it0, l0, c.external_E ? 0 : 1, ot0);
     if (r || c.external_E) return r;
+    c.solves_done += 1;
     return escalate_if_capped(ctx);
 }
 
@@ -1117,6 +1123,15 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
         c.step_ev.resize(6 * STEP_RING);
         for (auto& e : c.step_ev) CUDA_OK(cudaEventCreate(&e));
     }
+    if (!c.side) {
+        // the highest priority: the side stream's few blocks are scheduled as
+        // the push's blocks retire, instead of after the whole push
+        int lo = 0, hi = 0;
+        CUDA_OK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CUDA_OK(cudaStreamCreateWithPriority(&c.side, cudaStreamNonBlocking, hi));
+        CUDA_OK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+        CUDA_OK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+    }
     if (!c.spill_host && cudaMallocHost(&c.spill_host, sizeof(unsigned long long) * STEP_RING) != cudaSuccess) {
         cudaGetLastError();
         c.spill_host = nullptr;
@@ -1149,11 +1164,32 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
         if (unread[slot]) CUDA_OK(read_set(slot));
         cudaEvent_t* ev = &c.step_ev[6 * slot];
         CUDA_OK(cudaEventRecord(ev[0], c.stream));
-        CUDA_OK(mixed ? launch_push_mixed(c) : launch_push(c));
-        CUDA_OK(cudaEventRecord(ev[1], c.stream));
-        CUDA_OK(mixed ? launch_movers_mixed(c) : launch_movers(c));
-        CUDA_OK(cudaEventRecord(ev[2], c.stream));
-        CUDA_OK(mixed ? launch_inject_mixed(c) : launch_inject(c));
+        CUDA_OK(mixed ? launch_push_prep_mixed(c) : launch_push_prep(c));
+        // the waiting list's push and the injection only append to the step's
+        // mover list and add to the surface accumulators (atomics), so they run
+        // on the side stream beside the bins' push; the rebin waits for both
+        CUDA_OK(cudaEventRecord(c.ev_fork, c.stream));
+        CUDA_OK(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+        {
+            cudaStream_t keep = c.stream;
+            c.stream = c.side;
+            cudaError_t e1 = mixed ? launch_movers_mixed(c) : launch_movers(c);
+            if (e1 == cudaSuccess) e1 = mixed ? launch_inject_mixed(c) : launch_inject(c);
+            c.stream = keep;
+            // the join is recorded and awaited whatever happened, so that no
+            // side-stream work outlives the main stream's view of the step
+            cudaError_t e2 = cudaEventRecord(c.ev_join, c.side);
+            cudaError_t e3 = e1 == cudaSuccess && e2 == cudaSuccess
+                                 ? (mixed ? launch_push_bins_mixed(c) : launch_push_bins(c)) : cudaSuccess;
+            cudaError_t e4 = cudaEventRecord(ev[1], c.stream);
+            cudaError_t e5 = e2 == cudaSuccess ? cudaStreamWaitEvent(c.stream, c.ev_join, 0) : cudaStreamSynchronize(c.side);
+            CUDA_OK(e1);
+            CUDA_OK(e2);
+            CUDA_OK(e3);
+            CUDA_OK(e4);
+            CUDA_OK(e5);
+        }
+        CUDA_OK(cudaEventRecord(ev[2], c.stream));   // (the side stream's time beyond the push)
         CUDA_OK(cudaEventRecord(ev[3], c.stream));
         CUDA_OK(mixed ? launch_rebin_mixed(c) : launch_rebin(c));
         CUDA_OK(cudaEventRecord(ev[4], c.stream));
@@ -1181,6 +1217,7 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
     }
     pifepic_status r = fill_stats(ctx, before, st, ph, it0, l0, c.external_E ? 0 : nsteps, ot0);
     if (r || c.external_E || nsteps == 0) return r;
+    c.solves_done += nsteps;
     return escalate_if_capped(ctx);
 }
 

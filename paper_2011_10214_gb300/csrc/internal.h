@@ -232,6 +232,9 @@ struct Ctx {
     float* mg_cinv = nullptr;         // dense inverse of the coarsest operator
     bool mg_wanted = false;           // a batch solves this context with multigrid: keep a hierarchy
     bool mg_escalated = false;        // AUTO: a Jacobi solve ended at the cap unconverged; multigrid since
+    long long solves_done = 0;        // field solves of pifepic_solve and pifepic_step so far
+    cudaStream_t side = nullptr;      // movers and injection beside the push (pifepic_step)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     unsigned short* rowkind = nullptr;  // global-memory PCG (larger meshes): row kinds, [N]
     double* pcg_x = nullptr;            // and its FP64 correction vector, [N]
     int pcg_G = 1;
@@ -337,7 +340,9 @@ cudaError_t launch_build_bins(Ctx& c, int s, PArr flat, long long n, bool fresh_
 cudaError_t launch_flatten(Ctx& c, int s, PArr flat, unsigned long long* nflat);
 cudaError_t launch_deposit_all(Ctx& c);
 cudaError_t launch_half_kick(Ctx& c);
-cudaError_t launch_push(Ctx& c);
+cudaError_t launch_push(Ctx& c);        // launch_push_prep + launch_push_bins
+cudaError_t launch_push_prep(Ctx& c);
+cudaError_t launch_push_bins(Ctx& c);
 cudaError_t launch_movers(Ctx& c);
 cudaError_t launch_inject(Ctx& c);
 cudaError_t launch_rebin(Ctx& c);
@@ -345,7 +350,9 @@ cudaError_t launch_rebin(Ctx& c);
 // MIXED mode
 cudaError_t launch_flatten_mixed_to_f64(Ctx& c, int s, PArr flat, unsigned long long* nflat);
 cudaError_t launch_build_bins_mixed(Ctx& c, int s, PArr flat, long long n, bool fresh_caps);
-cudaError_t launch_push_mixed(Ctx& c);
+cudaError_t launch_push_mixed(Ctx& c);  // launch_push_prep_mixed + launch_push_bins_mixed
+cudaError_t launch_push_prep_mixed(Ctx& c);
+cudaError_t launch_push_bins_mixed(Ctx& c);
 cudaError_t launch_movers_mixed(Ctx& c);
 cudaError_t launch_inject_mixed(Ctx& c);
 cudaError_t launch_rebin_mixed(Ctx& c);

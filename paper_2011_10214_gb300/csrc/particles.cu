@@ -726,15 +726,26 @@ cudaError_t launch_half_kick(Ctx& c) {
 }
 
 // push of all bins (+ node-field tiles by TMA) and of waiting movers
-cudaError_t launch_push(Ctx& c) {
-    Launch L = make_launch(c);
+// what precedes a push: the step's mover-list counts and node charges start at zero
+cudaError_t launch_push_prep(Ctx& c) {
     int ns = (int)c.sp.size();
     for (int s = 0; s < ns; ++s)
         cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_bins(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
     k_push_bins<<<dim3(c.nblocks, ns), 256, 0, c.stream>>>(L, c.tmapE);
     c.launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_push(Ctx& c) {
+    cudaError_t e = launch_push_prep(c);
+    return e == cudaSuccess ? launch_push_bins(c) : e;
 }
 
 cudaError_t launch_movers(Ctx& c) {

@@ -853,11 +853,22 @@ static cudaError_t push_bins_m(dim3 grid, cudaStream_t st, const Launch& L, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_push_mixed(Ctx& c) {
-    Launch L = make_launch(c);
+// what precedes a push: the step's mover-list counts and node charges start at zero
+cudaError_t launch_push_prep_mixed(Ctx& c) {
     int ns = (int)c.sp.size();
     for (int s = 0; s < ns; ++s) cudaMemsetAsync(c.sp[s].mov_n + 1, 0, sizeof(unsigned long long), c.stream);
     cudaMemsetAsync(c.Wall, 0, sizeof(unsigned long long) * ns * c.mesh.nnodes, c.stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_mixed(Ctx& c) {
+    cudaError_t e = launch_push_prep_mixed(c);
+    return e == cudaSuccess ? launch_push_bins_mixed(c) : e;
+}
+
+cudaError_t launch_push_bins_mixed(Ctx& c) {
+    Launch L = make_launch(c);
+    int ns = (int)c.sp.size();
     const dim3 grid(c.nblocks, ns);
     const ObjF of = obj_f(c.obj);
     const float dthf = (float)c.dth;

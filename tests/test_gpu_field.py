@@ -196,9 +196,11 @@ def test_preconditioner_choice_is_validated():
 
 
 def test_auto_moves_to_multigrid_after_a_capped_jacobi_solve():
-    """AUTO (MIXED): the crater's Jacobi solve stops at a cap of 40 unconverged
-    at tol 1e-12; the next solve runs the multigrid cycle and converges within
-    the same cap to the oracle's potential.  An explicit JACOBI stays capped."""
+    """AUTO (MIXED): the crater's Jacobi solves stop at a cap of 40 unconverged
+    at tol 1e-12.  The first (cold) solve changes nothing; after the second
+    (warm-started) one the context runs the multigrid cycle, and its next solve
+    converges within the same cap to the oracle's potential.  An explicit
+    JACOBI stays capped."""
     from paper_2011_10214_gb300 import capi
     from tests.pairs import add_species_both, explicit_particles
     for precond in ("auto", "jacobi"):
@@ -209,6 +211,9 @@ def test_auto_moves_to_multigrid_after_a_capped_jacobi_solve():
         add_species_both(gpu, orc, -1.0, 1.0, 0.01)
         explicit_particles(gpu, orc, 0, 4000, 5, 1.0)
         assert gpu.solver == capi.SOLVER_REGISTERS
+        st0 = gpu.solve()
+        assert st0["pcg_converged"] == 0 and st0["pcg_iters"] == 40
+        assert gpu.solver == capi.SOLVER_REGISTERS        # a cold start at the cap is not a reason
         st1 = gpu.solve()
         assert st1["pcg_converged"] == 0 and st1["pcg_iters"] == 40
         assert gpu.solver == (capi.SOLVER_MULTIGRID if precond == "auto" else capi.SOLVER_REGISTERS)
