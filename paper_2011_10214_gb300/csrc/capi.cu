@@ -260,6 +260,16 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     Ctx& c = ctx->c;
     c.stream = (cudaStream_t)stream;
     CUDA_OK(cudaGetDevice(&c.device));
+    {
+        // pifepic_step's side stream (the waiting list's push and the injection
+        // beside the push) at the highest priority: its few blocks are scheduled
+        // as the push's blocks retire, instead of after the whole push
+        int lo = 0, hi = 0;
+        CUDA_OK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CUDA_OK(cudaStreamCreateWithPriority(&c.side, cudaStreamNonBlocking, hi));
+        CUDA_OK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+        CUDA_OK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+    }
     // the PIC mesh, and the IFE mesh: the PIC mesh with each cell split rf^3 times
     auto make_mesh = [](int nx, int ny, int nz, double h) {
         Mesh q{};
@@ -1122,15 +1132,6 @@ pifepic_status pifepic_step(pifepic_ctx* ctx, int nsteps, pifepic_stats* st) {
     if (c.step_ev.empty()) {
         c.step_ev.resize(6 * STEP_RING);
         for (auto& e : c.step_ev) CUDA_OK(cudaEventCreate(&e));
-    }
-    if (!c.side) {
-        // the highest priority: the side stream's few blocks are scheduled as
-        // the push's blocks retire, instead of after the whole push
-        int lo = 0, hi = 0;
-        CUDA_OK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        CUDA_OK(cudaStreamCreateWithPriority(&c.side, cudaStreamNonBlocking, hi));
-        CUDA_OK(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
-        CUDA_OK(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
     }
     if (!c.spill_host && cudaMallocHost(&c.spill_host, sizeof(unsigned long long) * STEP_RING) != cudaSuccess) {
         cudaGetLastError();
