@@ -416,6 +416,14 @@ static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
 // device count of solves (PCG start extrapolation), scalar slot 43
 static long long* solve_hist(Ctx& c) { return (long long*)(c.scal + 43); }
 
+// one node per thread: 256-thread blocks, or 64-thread ones for a mesh whose
+// 256-thread grid would leave most SMs idle (these kernels are FP64-bound)
+static int node_threads(long long N) { return N < 152LL * 256 ? 64 : 256; }
+static unsigned node_blocks(long long N) {
+    const int t = node_threads(N);
+    return (unsigned)((N + t - 1) / t);
+}
+
 static FieldArgs fargs(Ctx& c) {
     FieldArgs f;
     f.m = c.mesh; f.o = c.obj; f.ntype = c.ntype; f.coef = c.patch_coef; f.coeff = c.patch_coeff;
@@ -475,14 +483,16 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
         if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
         if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
     }
-    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, Fext, solve_hist(c));
+    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, Fext,
+                                                       solve_hist(c));
     k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_pcg_coop(c, st);
     if (e != cudaSuccess) return e;
     if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
-    else k_node_E<<<nb(N), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    else k_node_E<<<node_blocks(N), node_threads(N), 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi,
+                                                               c.E, c.Ef);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_E_to_pic(c, st, c.precision != PIFEPIC_MIXED);
@@ -495,14 +505,16 @@ cudaError_t launch_solve_prefix(Ctx& c, cudaStream_t st) {
     long long N = c.mesh.nnodes;
     if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
     if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
-    k_rhs<<<nb(N), 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr, solve_hist(c));
+    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr,
+                                                       solve_hist(c));
     k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     return cudaGetLastError();
 }
 cudaError_t launch_solve_suffix(Ctx& c, cudaStream_t st) {
     FieldArgs f = fargs(c);
     if (c.precision == PIFEPIC_MIXED) launch_node_E_f(c, st);
-    else k_node_E<<<nb(c.mesh.nnodes), 256, 0, st>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
+    else k_node_E<<<node_blocks(c.mesh.nnodes), node_threads(c.mesh.nnodes), 0, st>>>(
+        f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, c.Ef);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_E_to_pic(c, st, c.precision != PIFEPIC_MIXED);
@@ -658,8 +670,8 @@ cudaError_t launch_node_E_tables(Ctx& c) {
 // push reads is left as the step made it)
 cudaError_t launch_node_E64(Ctx& c) {
     FieldArgs f = fargs(c);
-    k_node_E<<<nb(c.mesh.nnodes), 256, 0, c.stream>>>(f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E,
-                                                      nullptr);
+    k_node_E<<<node_blocks(c.mesh.nnodes), node_threads(c.mesh.nnodes), 0, c.stream>>>(
+        f, c.Lnode, c.imask, c.ibase, c.it_data, c.qT, c.phi, c.E, nullptr);
     return cudaGetLastError();
 }
 

@@ -758,12 +758,16 @@ static void plan_pcg_reg(Ctx& c) {
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const long long N = c.mesh.nnodes;
     const size_t tsz = mixed ? sizeof(float) : sizeof(double);
-    long long G = (N + REG_THREADS - 1) / REG_THREADS;
-    if (G > nsm) G = nsm;          // one 512-thread block per SM (registers allow no more)
+    // one 512-thread block per SM (registers allow no more), on every SM even
+    // for a small mesh: the FP64 passes (FP64 mode, and MIXED's refinement
+    // residuals) run at 1/58 of the FP32 rate here, and spread over the device
+    long long G = nsm;
+    if (G > N) G = N;
     if (G > REG_THREADS) G = REG_THREADS;   // exchange totals: one partial per thread
     if (G > 255) G = 255;          // the fixed-point exchange counts arrivals in 8 bits
     if (G < 1) G = 1;
     const long long M = (N + G - 1) / G;
+    G = (N + M - 1) / M;           // every block owns at least one node
     const long long npt = (M + REG_THREADS - 1) / REG_THREADS;
     int pick = npt <= 1 ? 1 : npt <= 2 ? 2 : npt <= 4 ? 4 : npt <= 8 ? 8 : 0;
     if (!pick) return;
