@@ -188,10 +188,12 @@ pifepic_status pifepic_set_bedrock(pifepic_ctx* ctx, double z_bed, double eps_be
  * Each inner solve stops once its FP32 residual norm is at most
  * max(margin * pcg_tol * ||b||, reduction * ||r0||), r0 the FP64 residual it
  * started from; the refinement ends when the FP64 residual meets pcg_tol.
- * Defaults reduction = 1e-4, margin = 0.5.  Takes effect at the next solve;
- * call before the context joins a batch (a batch's captured step does not see
- * a later change).  No effect in FP64 mode.  Errors: EINVAL unless
- * 0 < reduction < 1 and 0 < margin <= 1. */
+ * Defaults reduction = 1e-4, margin = 0.5.  A batch's Jacobi clusters use a
+ * reduction of at most 1e-6 (their two-exchange loop then meets pcg_tol after
+ * one refinement step).  Takes effect at the next solve; call before the
+ * context joins a batch (a batch's captured step does not see a later
+ * change).  No effect in FP64 mode.  Errors: EINVAL unless 0 < reduction < 1
+ * and 0 < margin <= 1. */
 pifepic_status pifepic_set_refinement(pifepic_ctx* ctx, double reduction, double margin);
 
 /* Preconditioner of the MIXED inner PCG of a single context (Sec. 2.5 names
