@@ -63,13 +63,13 @@ static __device__ __forceinline__ T ldx(const T* x, long long i) {
     else return x[i];
 }
 
-// y_n = (A x)_n for the IFE operator; Dirichlet rows give 0 (x is 0 there).
-// ld(m) returns x_m (from global memory or from a shared-memory window).
+// y_n = (A x)_n for the IFE operator, the node's type ty (ntype) given;
+// Dirichlet rows give 0 (x is 0 there).  ld(m) returns x_m (from global
+// memory or from a shared-memory window).
 template <typename T, typename LD>
-static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n, int i, int j, int k, LD ld,
+static __device__ __forceinline__ T apply_row_ty(const FieldArgs& f, long long n, int i, int j, int k, int ty, LD ld,
                                                  const T* coef) {
     const Mesh& m = f.m;
-    int ty = f.ntype[n];
     if (ty == -3) return (T)0;
     const long long sx = 1, sy = m.NX, sz = (long long)m.NX * m.NY;
     bool xm = i > 0, xp = i < m.nx, ym = j > 0, yp = j < m.ny, zm = k > 0, zp = k < m.nz;
@@ -135,6 +135,13 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
 
 // (A x)_n in FP64 for the refinement residual: a regular row with all six
 // neighbours present (no interface tet, not Dirichlet) takes the interior
+// the same with the node's type read from ntype
+template <typename T, typename LD>
+static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n, int i, int j, int k, LD ld,
+                                                 const T* coef) {
+    return apply_row_ty<T>(f, n, i, j, k, f.ntype[n], ld, coef);
+}
+
 // closed form of apply_row_ld's regular branch -- eps [(4 or 6) h x_n - 4 h/6
 // (six face neighbours) - (even nodes) 2 h/12 (twelve edge neighbours)], the
 // same sums in the same order, without the per-node integer weights and their

@@ -36,6 +36,7 @@ namespace pf {
 
 constexpr int CL_THREADS = 1024;
 constexpr int CL_MAX_OUTER = 12;   // MIXED: refinement steps at most
+constexpr int CL_TY_LOAD = 16383;  // a patch index of 14 bits at most is kept in the row kind
 
 // nodes per CTA at most: the working set of one CTA must fit in shared memory
 constexpr int cl_max_nodes(bool mixed) { return mixed ? 8192 : 4096; }
@@ -127,11 +128,28 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem a
         using R = typename std::remove_cv<typename std::remove_pointer<decltype(cf)>::type>::type;
         return apply_row_ld<R>(f, b0 + li, (int)(u & 2047u), (int)((u >> 11) & 2047u), (int)(u >> 22), ld, cf);
     };
+    // an interface (patch) row keeps its patch index in the kind bits that a
+    // patch row leaves unused (0-7 and 10-15), so that its product reads the
+    // coefficients without first loading ntype; CL_TY_LOAD: index too large
+    auto patch_row = [&](int li, unsigned kd, auto ld, const auto* cf) {
+        const unsigned u = pk[li];
+        const int i = (int)(u & 2047u), j = (int)((u >> 11) & 2047u), k = (int)(u >> 22);
+        const int t = (int)((kd & 0xFFu) | ((kd >> 10) << 8));
+        const int ty = t == CL_TY_LOAD ? f.ntype[b0 + li] : t;
+        using R = typename std::remove_cv<typename std::remove_pointer<decltype(cf)>::type>::type;
+        return apply_row_ty<R>(f, b0 + li, i, j, k, ty, ld, cf);
+    };
     for (int li = threadIdx.x; li < nown; li += CL_THREADS) {
         int i, j, k;
         node_ijk(m, b0 + li, i, j, k);
         pk[li] = cl_pack(i, j, k);
-        kind[li] = row_kind(f, b0 + li, i, j, k);
+        unsigned kd = row_kind(f, b0 + li, i, j, k);
+        if (kd & RK_GENERAL) {
+            int ty = f.ntype[b0 + li];
+            if (ty > CL_TY_LOAD) ty = CL_TY_LOAD;
+            kd |= (unsigned)(ty & 0xFF) | ((unsigned)(ty >> 8) << 10);
+        }
+        kind[li] = (unsigned short)kd;
     }
     // window halves outside the instance's nodes stay zero (never read with a
     // non-zero coefficient, but inside the buffer)
@@ -197,7 +215,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_pcg_cluster(const BatchItem a
                 const T* wc = win + ((int)H + li);
                 T az;
                 if (kd & RK_DIRICHLET) az = (T)0;
-                else if (kd & RK_GENERAL) az = row(li, ldw, coef);
+                else if (kd & RK_GENERAL) az = patch_row(li, kd, ldw, coef);
                 else az = regular_row_masked<T>(wc, NXw, NXYw, kd, hT, h_over6<T>(m), h_over12<T>(m), epsP, epsM);
                 const T zl = wc[0];
                 T pl, ql;
