@@ -133,8 +133,6 @@ static __device__ __forceinline__ T apply_row_ty(const FieldArgs& f, long long n
     return eps * y;
 }
 
-// (A x)_n in FP64 for the refinement residual: a regular row with all six
-// neighbours present (no interface tet, not Dirichlet) takes the interior
 // the same with the node's type read from ntype
 template <typename T, typename LD>
 static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n, int i, int j, int k, LD ld,
@@ -142,6 +140,8 @@ static __device__ __forceinline__ T apply_row_ld(const FieldArgs& f, long long n
     return apply_row_ty<T>(f, n, i, j, k, f.ntype[n], ld, coef);
 }
 
+// (A x)_n in FP64 for the refinement residual: a regular row with all six
+// neighbours present (no interface tet, not Dirichlet) takes the interior
 // closed form of apply_row_ld's regular branch -- eps [(4 or 6) h x_n - 4 h/6
 // (six face neighbours) - (even nodes) 2 h/12 (twelve edge neighbours)], the
 // same sums in the same order, without the per-node integer weights and their
