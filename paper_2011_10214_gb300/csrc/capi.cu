@@ -298,7 +298,6 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
     for (int f = 0; f < 6; ++f) { c.bc[f].kind = PIFEPIC_BC_DIRICHLET; c.bc[f].value = 0.0; }
     long long N = m.nnodes, C = m.ncells;
     ALLOC(c.Lnode, sizeof(double) * N);
-    ALLOC(c.Lpos, N);
     ALLOC(c.ntype, sizeof(int) * N);
     ALLOC(c.gdir, sizeof(double) * N);
     ALLOC(c.lift, sizeof(double) * N);
@@ -399,7 +398,7 @@ void pifepic_destroy(pifepic_ctx* ctx) {
     Ctx& c = ctx->c;
     if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
     if (c.side) cudaStreamSynchronize(c.side);
-    void* ptrs[] = {c.Lnode, c.Lpos, c.it_dataf, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q,
+    void* ptrs[] = {c.Lnode, c.ne_row, c.ne_coef, c.ne_qoff, c.ne_q, c.ne_qc, c.ntype, c.gdir, c.lift, c.invdiag, c.invdiagf, c.phi, c.phi_prev, c.u, c.b, c.r, c.p, c.q,
                     c.z ? (void*)(c.z - c.zguard) : nullptr, c.zf ? (void*)(c.zf - c.zguard) : nullptr,
                     c.rf, c.pf, c.qf, c.uf, c.E, c.Ef, c.Wall, c.surfall, c.ctrall, c.imask, c.ibase, c.cell_acc,
                     c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut, c.patch_node,
@@ -460,16 +459,15 @@ static pifepic_status do_setup(pifepic_ctx* ctx) {
     Ctx& c = ctx->c;
     // free a previous interface set-up
     void* old[] = {c.it_cell, c.it_t, c.it_data, c.it_acc, c.qT, c.cut_cell, c.cut_area, c.qcut,
-                   c.patch_node, c.patch_coef, c.patch_coeff, c.surfall, c.it_dataf};
+                   c.patch_node, c.patch_coef, c.patch_coeff, c.surfall};
     for (void* p : old) lib_free(p);
     c.it_cell = c.it_t = c.it_acc = c.cut_cell = nullptr;
     c.it_data = c.qT = c.cut_area = c.qcut = c.patch_coef = nullptr;
-    c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr; c.it_dataf = nullptr;
+    c.patch_node = nullptr; c.patch_coeff = nullptr; c.surfall = nullptr;
     cudaError_t se = launch_setup(c);
     if (c.bed_outside) FAIL(PIFEPIC_EINVAL, "the bedrock must lie inside the object (a bedrock node has L >= 0)");
     CUDA_OK(se);
-    ALLOC(c.it_dataf, sizeof(float) * 32 * (c.nit > 0 ? c.nit : 1));
-    CUDA_OK(launch_node_E_tables(c));
+    CUDA_OK(launch_node_rows(c));
     ALLOC(c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1));
     CUDA_OK(szero(c.stream, c.surfall, sizeof(unsigned long long) * MAX_SPECIES * (c.ncut > 0 ? c.ncut : 1)));
     for (size_t s = 0; s < c.sp.size(); ++s) c.sp[s].surf = c.surfall + s * (c.ncut > 0 ? c.ncut : 1);

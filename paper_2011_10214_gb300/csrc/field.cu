@@ -24,15 +24,12 @@
 namespace pf {
 
 __constant__ TetTables cTf;
-__constant__ float cGradF[2][5][4][3];   // cTf.grad in FP32
-__constant__ float cVolF[5];
-// A node's share of one cube, summed over the cube's tets that contain it: the
-// node is local corner c8 of a cube of parity p; G[p][c8][corner][d] = sum over
-// those tets t and their vertices v at that corner of vol_t grad_t,v[d] (h = 1)
-// and V[p][c8] = sum of their vol_t.  Away from interface tets the node field
-// is -(sum over present cubes of G phi) / (h sum of V).
-__constant__ float cNodeG[2][8][8][3];
-__constant__ float cNodeV[2][8];
+// Interior-regular nodes (all eight cubes present, none holding an interface
+// tet): every tet around the node lies on one side, so the node field is one
+// fixed 27-point stencil per node parity P, cFold[P][3 nb + d] with
+// nb = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): minus the sum over the node's tets of
+// vol_t grad_t (h = 1) at neighbour nb, over the sum of vol_t; E = cFold phi / h.
+__constant__ float cFold[2][81];
 
 // ---- right-hand side ----------------------------------------------------------
 struct RhsArgs {
@@ -59,8 +56,16 @@ __global__ void k_qtets(long long nit, const int* it_acc, const double* qcut, do
     qT[T] = a >= 0 ? qcut[a] : 0.0;
 }
 
-__global__ void k_rhs(FieldArgs f, RhsArgs a, const unsigned char* imask, const int* ibase, const double* it_data,
-                      const double* qT, const double* lift, double* b, const double* Fext, long long* hist) {
+// the flux-jump terms of a node's right-hand side (the node rows of the set-up)
+struct FluxRows {
+    const int* row;
+    const int* qoff;
+    const int4* q;
+    const double* qc;
+};
+
+__global__ void k_rhs(FieldArgs f, RhsArgs a, FluxRows fr, const double* qT, const double* lift, double* b,
+                      const double* Fext, long long* hist) {
     const Mesh& m = f.m;
     long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     // solves so far, this one included (capped at 3): the start-vector kernel
@@ -78,32 +83,10 @@ __global__ void k_rhs(FieldArgs f, RhsArgs a, const unsigned char* imask, const 
             F = F + (a.coefs[s] * 2.3283064365386963e-10) * (double)(long long)a.W[(long long)s * m.nnodes + n];
     }
     if (ty >= 0 && qT) {   // touches interface tets: flux-jump load (none when qT is NULL)
-        int i, j, k;
-        node_ijk(m, n, i, j, k);
-        // the cubes' masks and first records first (independent loads), then
-        // each interface tet's record index from the mask (no load chain)
-        unsigned mk[8];
-        int T0[8];
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            int aa, bb, cc; loff(c8, aa, bb, cc);
-            const int ci = i - aa, cj = j - bb, ck = k - cc;
-            const bool in = !(ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz);
-            const long long cell = in ? cell_id(m, ci, cj, ck) : 0;
-            mk[c8] = in ? imask[cell] : 0u;
-            T0[c8] = in ? ibase[cell] : 0;
-        }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            if (!mk[c8]) continue;
-            int aa, bb, cc; loff(c8, aa, bb, cc);
-            const int p = (i - aa + j - bb + k - cc) & 1;
-            for (int t = 0; t < 5; ++t) {
-                if (!((mk[c8] >> t) & 1)) continue;
-                const int T = T0[c8] + __popc(mk[c8] & ((1u << t) - 1u));
-                for (int v = 0; v < 4; ++v)
-                    if (cTf.vert[p][t][v] == c8) F += qT[T] * it_data[(long long)T * IT_STRIDE + IT_C + v];
-            }
+        const int r = fr.row[n];
+        if (r >= 0) {
+            const int e1 = fr.qoff[r + 1];
+            for (int e = fr.qoff[r]; e < e1; ++e) F += qT[fr.q[e].x] * fr.qc[e];
         }
     }
     b[n] = F - lift[n];
@@ -212,168 +195,76 @@ __global__ void k_node_E(FieldArgs f, const double* L, const unsigned char* imas
     if (Ef) Ef[n] = make_float4((float)e.x, (float)e.y, (float)e.z, 0.0f);
 }
 
-// FP32 copies of what the node field reads, made once per set-up
-__global__ void k_node_E_tables(long long nit, const double* it_data, float* itf, long long N, const double* L,
-                                unsigned char* Lpos) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < nit) {
-        const double* rec = it_data + t * IT_STRIDE;
-        float* o = itf + t * 32;
-        for (int q = 0; q < 15; ++q) o[q] = (float)rec[IT_GP + q];
-        for (int q = 0; q < 15; ++q) o[15 + q] = (float)rec[IT_GM + q];
-        // |o[30]| = the + piece's volume; negative on the bedrock plane, whose
-        // + piece is not plasma
-        o[30] = rec[IT_KIND] == 0.0 ? (float)rec[IT_VOLP] : -(float)rec[IT_VOLP];
-        o[31] = (float)rec[IT_VOLM];
-    }
-    if (t < N) Lpos[t] = L[t] >= 0.0 ? 1 : 0;
-}
-
 // Node field in FP32 (MIXED steps; the push reads only this copy).  Same
 // reading as k_node_E: minus the volume-weighted mean of the element
 // gradients around the node, plasma-side pieces preferred.  A block covers a
 // 32 x 4 x 2 brick of nodes and stages phi of the brick and a one-node halo
-// (34 x 6 x 4) in shared memory, converted to FP32 once.
+// (34 x 6 x 4) in shared memory, converted to FP32 once.  An interior-regular
+// node applies its parity's 27-point stencil (cFold); any other node its row of
+// the set-up (27 x 3 coefficients and the q_T terms of its interface tets).
 constexpr int NE_BX = 32, NE_BY = 4, NE_BZ = 2;
 constexpr int NE_TX = NE_BX + 2, NE_TY = NE_BY + 2, NE_TZ = NE_BZ + 2;
-__global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, const unsigned char* Lpos,
-                                                                    const unsigned char* imask, const int* ibase,
-                                                                    const float* itf, const double* qT,
+constexpr int NE_FOLD = 97;   // the parity tables' stride in shared memory (not a multiple of the 32 banks)
+__global__ void __launch_bounds__(NE_BX * NE_BY * NE_BZ) k_node_E_f(Mesh m, const int* row, long long R,
+                                                                    const float* coef, const int* qoff,
+                                                                    const int4* qent, const double* qT,
                                                                     const double* phi, float4* Ef) {
     __shared__ float ph[NE_TX * NE_TY * NE_TZ];
-    // the interface-tet masks of the cubes around the brick's nodes
-    constexpr int CX = NE_BX + 1, CY = NE_BY + 1, CZ = NE_BZ + 1;
-    __shared__ unsigned char smk[CX * CY * CZ];
-    __shared__ int sib[CX * CY * CZ];                      // and their first interface record
-    __shared__ unsigned char sLp[NE_TX * NE_TY * NE_TZ];   // Lpos of the staged nodes
-    // the per-cube tables (neighbouring nodes differ in parity, so a warp's
-    // table reads diverge; constant memory would serialise them)
-    __shared__ float sG[2][8][8][3];
-    __shared__ float sV[2][8];
+    __shared__ float sF[2 * NE_FOLD];
     const int i0 = blockIdx.x * NE_BX, j0 = blockIdx.y * NE_BY, k0 = blockIdx.z * NE_BZ;
     const int tid = threadIdx.x + NE_BX * (threadIdx.y + NE_BY * threadIdx.z);
-    for (int q = tid; q < 2 * 8 * 8 * 3; q += NE_BX * NE_BY * NE_BZ) (&sG[0][0][0][0])[q] = (&cNodeG[0][0][0][0])[q];
-    if (tid < 16) (&sV[0][0])[tid] = (&cNodeV[0][0])[tid];
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y, k = k0 + threadIdx.z;
+    const bool mine = i < m.NX && j < m.NY && k < m.NZ;
+    const long long n = mine ? node_id(m, i, j, k) : 0;
+    const int r = mine ? row[n] : -1;
+    for (int q = tid; q < 2 * 81; q += NE_BX * NE_BY * NE_BZ) sF[(q / 81) * NE_FOLD + q % 81] = (&cFold[0][0])[q];
     for (int q = tid; q < NE_TX * NE_TY * NE_TZ; q += NE_BX * NE_BY * NE_BZ) {
         const int gi = i0 - 1 + q % NE_TX, gj = j0 - 1 + (q / NE_TX) % NE_TY, gk = k0 - 1 + q / (NE_TX * NE_TY);
         const bool in = gi >= 0 && gj >= 0 && gk >= 0 && gi < m.NX && gj < m.NY && gk < m.NZ;
-        const long long nid = in ? node_id(m, gi, gj, gk) : 0;
-        ph[q] = in ? (float)phi[nid] : 0.0f;
-        sLp[q] = in ? Lpos[nid] : (unsigned char)0;
-    }
-    for (int q = tid; q < CX * CY * CZ; q += NE_BX * NE_BY * NE_BZ) {
-        const int ci = i0 - 1 + q % CX, cj = j0 - 1 + (q / CX) % CY, ck = k0 - 1 + q / (CX * CY);
-        const bool in = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
-        const long long cell = in ? cell_id(m, ci, cj, ck) : 0;
-        smk[q] = in ? imask[cell] : (unsigned char)0;
-        sib[q] = in ? ibase[cell] : 0;
+        ph[q] = in ? (float)phi[node_id(m, gi, gj, gk)] : 0.0f;
     }
     __syncthreads();
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y, k = k0 + threadIdx.z;
-    if (i >= m.NX || j >= m.NY || k >= m.NZ) return;
-    const float ih = 1.0f / (float)m.h, V3 = (float)m.h * (float)m.h * (float)m.h;
-    // a node whose cubes hold no interface tet: every tet around it lies on one
-    // side, so the plasma-side preference changes nothing; the closed form
-    bool regular = true;
+    if (!mine) return;
+    // the node in the staged brick; neighbour nb at ph[c + off(nb)]
+    const float* c = ph + (threadIdx.x + 1) + NE_TX * ((threadIdx.y + 1) + NE_TY * (threadIdx.z + 1));
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+    if (r < 0) {
+        const float* F = sF + ((i + j + k) & 1) * NE_FOLD;
 #pragma unroll
-    for (int c8 = 0; c8 < 8; ++c8) {
-        const int ci = i - (c8 & 1), cj = j - ((c8 >> 1) & 1), ck = k - ((c8 >> 2) & 1);
-        const bool present = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
-        if (present && smk[(ci - i0 + 1) + CX * ((cj - j0 + 1) + CY * (ck - k0 + 1))]) regular = false;
-    }
-    if (regular) {
-        float e[3] = {0.f, 0.f, 0.f}, vol = 0.f;
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            const int a = c8 & 1, b = (c8 >> 1) & 1, c = (c8 >> 2) & 1;
-            const int ci = i - a, cj = j - b, ck = k - c;
-            const bool present = ci >= 0 && cj >= 0 && ck >= 0 && ci < m.nx && cj < m.ny && ck < m.nz;
-            const int p = (ci + cj + ck) & 1;
-            const float w = present ? 1.0f : 0.0f;
-            // the cube's corner (ci, cj, ck) in the staged brick (halo entries are zero)
-            const int tb = (ci - i0 + 1) + NE_TX * ((cj - j0 + 1) + NE_TY * (ck - k0 + 1));
-#pragma unroll
-            for (int cn = 0; cn < 8; ++cn) {
-                const float f = w * ph[tb + (cn & 1) + NE_TX * (((cn >> 1) & 1) + NE_TY * ((cn >> 2) & 1))];
-                e[0] += sG[p][c8][cn][0] * f;
-                e[1] += sG[p][c8][cn][1] * f;
-                e[2] += sG[p][c8][cn][2] * f;
-            }
-            vol += w * sV[p][c8];
+        for (int nb = 0; nb < 27; ++nb) {
+            const float f = c[(nb % 3 - 1) + NE_TX * ((nb / 3 % 3 - 1) + NE_TY * (nb / 9 - 1))];
+            e0 += F[3 * nb] * f;
+            e1 += F[3 * nb + 1] * f;
+            e2 += F[3 * nb + 2] * f;
         }
-        const float s = -ih / vol;
-        Ef[node_id(m, i, j, k)] = make_float4(s * e[0], s * e[1], s * e[2], 0.f);
-        return;
-    }
-    float apl[3] = {0.f, 0.f, 0.f}, vpl = 0.f, aal[3] = {0.f, 0.f, 0.f}, val = 0.f;
-    for (int c8 = 0; c8 < 8; ++c8) {
-        const int a = c8 & 1, b = (c8 >> 1) & 1, c = (c8 >> 2) & 1;
-        const int ci = i - a, cj = j - b, ck = k - c;
-        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
-        const int cq = (ci - i0 + 1) + CX * ((cj - j0 + 1) + CY * (ck - k0 + 1));
-        const unsigned mk = smk[cq];
-        const int p = (ci + cj + ck) & 1;
-        int T = sib[cq];
-        // the cube's corner (ci, cj, ck) in the staged brick
-        const int tb = (ci - i0 + 1) + NE_TX * ((cj - j0 + 1) + NE_TY * (ck - k0 + 1));
-        for (int t = 0; t < 5; ++t) {
-            const bool itet = (mk >> t) & 1;
-            bool has = false;
-            for (int v = 0; v < 4; ++v) has |= (cTf.vert[p][t][v] == c8);
-            if (has) {
-                float pv[4];
-                int lv0 = 0;
-                for (int v = 0; v < 4; ++v) {
-                    const int lv = cTf.vert[p][t][v];
-                    if (v == 0) lv0 = lv;
-                    pv[v] = ph[tb + (lv & 1) + NE_TX * (((lv >> 1) & 1) + NE_TY * ((lv >> 2) & 1))];
-                }
-                if (itet) {
-                    const float* rec = itf + (long long)T * 32;
-                    const float qt = (float)qT[T];
-                    float gp[3], gm[3];
-                    for (int d = 0; d < 3; ++d) {
-                        gp[d] = pv[0] * rec[d] + pv[1] * rec[3 + d] + pv[2] * rec[6 + d] + pv[3] * rec[9 + d] +
-                                qt * rec[12 + d];
-                        gm[d] = pv[0] * rec[15 + d] + pv[1] * rec[18 + d] + pv[2] * rec[21 + d] +
-                                pv[3] * rec[24 + d] + qt * rec[27 + d];
-                    }
-                    const float vp = fabsf(rec[30]), vm = rec[31];
-                    if (rec[30] > 0.f) {
-                        for (int d = 0; d < 3; ++d) apl[d] += vp * gp[d];
-                        vpl += vp;
-                    }
-                    for (int d = 0; d < 3; ++d) aal[d] += vp * gp[d] + vm * gm[d];
-                    val += vp + vm;
-                } else {
-                    float g[3];
-                    for (int d = 0; d < 3; ++d)
-                        g[d] = (pv[0] * cGradF[p][t][0][d] + pv[1] * cGradF[p][t][1][d] +
-                                pv[2] * cGradF[p][t][2][d] + pv[3] * cGradF[p][t][3][d]) * ih;
-                    const float V = cVolF[t] * V3;
-                    const int a0 = lv0 & 1, b0 = (lv0 >> 1) & 1, c0 = (lv0 >> 2) & 1;
-                    if (sLp[tb + a0 + NE_TX * (b0 + NE_TY * c0)]) {
-                        for (int d = 0; d < 3; ++d) apl[d] += V * g[d];
-                        vpl += V;
-                    }
-                    for (int d = 0; d < 3; ++d) aal[d] += V * g[d];
-                    val += V;
-                }
-            }
-            if (itet) ++T;
+        const float ih = 1.0f / (float)m.h;
+        e0 *= ih; e1 *= ih; e2 *= ih;
+    } else {
+        const float* cf = coef + r;
+#pragma unroll
+        for (int nb = 0; nb < 27; ++nb) {
+            const float f = c[(nb % 3 - 1) + NE_TX * ((nb / 3 % 3 - 1) + NE_TY * (nb / 9 - 1))];
+            e0 += cf[(3 * nb) * R] * f;
+            e1 += cf[(3 * nb + 1) * R] * f;
+            e2 += cf[(3 * nb + 2) * R] * f;
+        }
+        const int q1 = qoff[r + 1];
+        for (int q = qoff[r]; q < q1; ++q) {
+            const int4 w = qent[q];
+            const float qt = (float)qT[w.x];
+            e0 += __int_as_float(w.y) * qt;
+            e1 += __int_as_float(w.z) * qt;
+            e2 += __int_as_float(w.w) * qt;
         }
     }
-    float4 e;
-    if (vpl > 0.f) e = make_float4(-apl[0] / vpl, -apl[1] / vpl, -apl[2] / vpl, 0.f);
-    else e = make_float4(-aal[0] / val, -aal[1] / val, -aal[2] / val, 0.f);
-    Ef[node_id(m, i, j, k)] = e;
+    Ef[n] = make_float4(e0, e1, e2, 0.f);
 }
 
 static void launch_node_E_f(const Ctx& c, cudaStream_t st) {
     const Mesh& m = c.mesh;
     dim3 grid((m.NX + NE_BX - 1) / NE_BX, (m.NY + NE_BY - 1) / NE_BY, (m.NZ + NE_BZ - 1) / NE_BZ);
-    k_node_E_f<<<grid, dim3(NE_BX, NE_BY, NE_BZ), 0, st>>>(m, c.Lpos, c.imask, c.ibase, c.it_dataf, c.qT, c.phi,
-                                                          c.Ef);
+    k_node_E_f<<<grid, dim3(NE_BX, NE_BY, NE_BZ), 0, st>>>(m, c.ne_row, c.ne_nrows, c.ne_coef, c.ne_qoff, c.ne_q,
+                                                          c.qT, c.phi, c.Ef);
 }
 
 
@@ -448,6 +339,8 @@ static RhsArgs rargs(Ctx& c) {
     return a;
 }
 
+static FluxRows flux_rows(const Ctx& c) { return FluxRows{c.ne_row, c.ne_qoff, c.ne_q, c.ne_qc}; }
+
 cudaError_t launch_field_lift(Ctx& c) {
     FieldArgs f = fargs(c);
     k_matvec<<<nb(c.mesh.nnodes), 256, 0, c.stream>>>(f, c.gdir, c.lift);
@@ -483,7 +376,7 @@ static cudaError_t solve_sequence(Ctx& c, cudaStream_t st, const double* Fext) {
         if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
         if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
     }
-    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, Fext,
+    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, flux_rows(c), c.qT, c.lift, c.b, Fext,
                                                        solve_hist(c));
     k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     cudaError_t e = cudaGetLastError();
@@ -505,7 +398,7 @@ cudaError_t launch_solve_prefix(Ctx& c, cudaStream_t st) {
     long long N = c.mesh.nnodes;
     if (c.ncut > 0) k_qcut<<<nb(c.ncut), 256, 0, st>>>(a, c.cut_area, c.qcut);
     if (c.nit > 0) k_qtets<<<nb(c.nit), 256, 0, st>>>(c.nit, c.it_acc, c.qcut, c.qT);
-    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, c.imask, c.ibase, c.it_data, c.qT, c.lift, c.b, nullptr,
+    k_rhs<<<node_blocks(N), node_threads(N), 0, st>>>(f, a, flux_rows(c), c.qT, c.lift, c.b, nullptr,
                                                        solve_hist(c));
     k_u_from_phi<<<nb(N), 256, 0, st>>>(N, c.ntype, c.phi, c.phi_prev, c.gdir, c.u, solve_hist(c));
     return cudaGetLastError();
@@ -660,12 +553,6 @@ cudaError_t gather_stats(Ctx& c, StatPack* out, bool diag) {
     return cudaSuccess;
 }
 
-cudaError_t launch_node_E_tables(Ctx& c) {
-    long long n = c.nit > c.mesh.nnodes ? c.nit : c.mesh.nnodes;
-    k_node_E_tables<<<nb(n), 256, 0, c.stream>>>(c.nit, c.it_data, c.it_dataf, c.mesh.nnodes, c.Lnode, c.Lpos);
-    return cudaGetLastError();
-}
-
 // FP64 node field from the current phi into E only (the FP32 copy the MIXED
 // push reads is left as the step made it)
 cudaError_t launch_node_E64(Ctx& c) {
@@ -676,13 +563,9 @@ cudaError_t launch_node_E64(Ctx& c) {
 }
 
 cudaError_t set_field_tables(const TetTables& t) {
-    float g[2][5][4][3], v[5];
-    for (int p = 0; p < 2; ++p)
-        for (int q = 0; q < 5; ++q)
-            for (int a = 0; a < 4; ++a)
-                for (int d = 0; d < 3; ++d) g[p][q][a][d] = (float)t.grad[p][q][a][d];
-    for (int q = 0; q < 5; ++q) v[q] = (float)t.vol[q];
-    // per-cube node tables (see cNodeG), summed in FP64
+    // per cube of parity p holding the node at its local corner c8: G = sum
+    // over the cube's tets containing it of vol_t grad_t at each corner (h = 1),
+    // V = sum of their vol_t; summed in FP64
     double G[2][8][8][3] = {}, V[2][8] = {};
     for (int p = 0; p < 2; ++p)
         for (int q = 0; q < 5; ++q)
@@ -692,18 +575,25 @@ cudaError_t set_field_tables(const TetTables& t) {
                 for (int b = 0; b < 4; ++b)
                     for (int d = 0; d < 3; ++d) G[p][c8][t.vert[p][q][b]][d] += t.vol[q] * t.grad[p][q][b][d];
             }
-    float Gf[2][8][8][3], Vf[2][8];
-    for (int p = 0; p < 2; ++p)
+    // the eight cubes around a node of parity P: the cube with the node at its
+    // corner c8 = (a, b, c) has parity P + a + b + c, and its corner (x, y, z) is
+    // the node's neighbour (x - a, y - b, z - c)
+    double F[2][27][3] = {}, W[2] = {};
+    for (int P = 0; P < 2; ++P)
         for (int c8 = 0; c8 < 8; ++c8) {
-            Vf[p][c8] = (float)V[p][c8];
-            for (int cn = 0; cn < 8; ++cn)
-                for (int d = 0; d < 3; ++d) Gf[p][c8][cn][d] = (float)G[p][c8][cn][d];
+            const int a = c8 & 1, b = (c8 >> 1) & 1, cc = (c8 >> 2) & 1, pc = (P + a + b + cc) & 1;
+            W[P] += V[pc][c8];
+            for (int cn = 0; cn < 8; ++cn) {
+                const int nb = ((cn & 1) - a + 1) + 3 * (((cn >> 1) & 1) - b + 1) + 9 * (((cn >> 2) & 1) - cc + 1);
+                for (int d = 0; d < 3; ++d) F[P][nb][d] += G[pc][c8][cn][d];
+            }
         }
+    float Ff[2][81];
+    for (int P = 0; P < 2; ++P)
+        for (int nb = 0; nb < 27; ++nb)
+            for (int d = 0; d < 3; ++d) Ff[P][3 * nb + d] = (float)(-F[P][nb][d] / W[P]);
     cudaError_t e = cudaMemcpyToSymbol(cTf, &t, sizeof(TetTables));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGradF, g, sizeof(g));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cVolF, v, sizeof(v));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cNodeG, Gf, sizeof(Gf));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cNodeV, Vf, sizeof(Vf));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cFold, Ff, sizeof(Ff));
     return e;
 }
 
@@ -867,7 +757,7 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
     unsigned gb = nb(N);
     cudaStream_t st = c.stream;
     k_na_state<<<1, 1, 0, st>>>(S, ticket, c.tol * c.tol, c.maxit);
-    k_rhs<<<gb, 256, 0, st>>>(f, a, c.imask, c.ibase, c.it_data, q, c.lift, bvec, F, nullptr);
+    k_rhs<<<gb, 256, 0, st>>>(f, a, flux_rows(c), q, c.lift, bvec, F, nullptr);
     cudaMemsetAsync(u, 0, sizeof(double) * N, st);
     k_matvec<<<gb, 256, 0, st>>>(f, u, qv);
     k_na_init<<<gb, 256, 0, st>>>(f, bvec, qv, r, p, partial, ticket, S);

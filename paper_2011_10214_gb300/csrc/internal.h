@@ -192,8 +192,17 @@ struct Ctx {
     int* it_cell = nullptr;
     int* it_t = nullptr;
     double* it_data = nullptr;     // IT_STRIDE doubles per tet
-    float* it_dataf = nullptr;     // [nit][32] FP32 node-field subset: GP(15), GM(15), VOLP, VOLM
-    unsigned char* Lpos = nullptr; // per node: level set >= 0 (plasma side)
+    // node rows (launch_node_rows): a node that is not interior-regular has row
+    // ne_row[n] >= 0 (else -1): its node field is sum over the 27 neighbours of
+    // ne_coef[(3 nb + d) R + row] phi_nb plus sum over its interface tets of the
+    // FP32 coefficients in ne_q times q_T; ne_qc holds each such tet's FP64
+    // unit-jump load at the node (the right-hand side's flux-jump term)
+    int* ne_row = nullptr;         // [nnodes]
+    long long ne_nrows = 0;        // R
+    float* ne_coef = nullptr;      // [81][R]
+    int* ne_qoff = nullptr;        // [R + 1]: the row's interface tets, ne_q[ne_qoff[row] .. ne_qoff[row + 1])
+    int4* ne_q = nullptr;          // {T, 3 FP32 coefficients as bits}
+    double* ne_qc = nullptr;       // FP64 unit-jump load of tet T at the node
     int* it_acc = nullptr;
     double* qT = nullptr;
     // cut cells
@@ -317,7 +326,7 @@ enum {
 // ---- launchers ---------------------------------------------------------------
 cudaError_t set_tet_tables(const TetTables& t);
 cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
-cudaError_t launch_node_E_tables(Ctx& c);              // field.cu: it_dataf, Lpos
+cudaError_t launch_node_rows(Ctx& c);                  // setup.cu: ne_row, ne_coef, ne_qoff, ne_q, ne_qc
 cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w);  // setup.cu
 cudaError_t launch_photo(Ctx& c);                      // particles.cu: one step of emission (FP64)
 cudaError_t launch_photo_mixed(Ctx& c);                // particles_mixed.cu

@@ -690,6 +690,178 @@ done:
     return err;
 }
 
+// ---------------------------------------------------------------------------
+// Node rows (once per set-up).  The node field is minus the volume-weighted
+// mean of the element gradients around a node, plasma-side pieces preferred
+// (the reading of Sec. 2.1 that k_node_E follows); on a fixed mesh and object
+// that is a linear map of the potential at the node's 27 neighbours and of q_T
+// on the interface tets containing the node.  A node that is not interior-
+// regular (a cube absent, or a cube holding an interface tet) gets a row: those
+// 27 x 3 coefficients in FP32 and its interface tets {T, 3 FP32 coefficients};
+// the same tet list, with each tet's unit-jump load at the node in FP64, is
+// the right-hand side's flux-jump term of the node (in the order the cubes and
+// tets are visited, so the sums are those of visiting the cubes).
+// ---------------------------------------------------------------------------
+__global__ void k_node_rows_count(Mesh m, const unsigned char* mask, int* need, int* nq) {
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes) return;
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    bool irregular = i == 0 || j == 0 || k == 0 || i == m.nx || j == m.ny || k == m.nz;
+    int q = 0;
+    for (int c8 = 0; c8 < 8; ++c8) {
+        int a, b, cc; loff(c8, a, b, cc);
+        int ci = i - a, cj = j - b, ck = k - cc;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
+        unsigned mk = mask[cell_id(m, ci, cj, ck)];
+        if (!mk) continue;
+        irregular = true;
+        int p = (ci + cj + ck) & 1;
+        for (int t = 0; t < 5; ++t) {
+            if (!((mk >> t) & 1)) continue;
+            for (int v = 0; v < 4; ++v)
+                if (cT.vert[p][t][v] == c8) ++q;
+        }
+    }
+    need[n] = irregular ? 1 : 0;
+    nq[n] = q;
+}
+
+constexpr int NR_T = 64;   // threads per block of the row fill (a 27 x 3 FP64 accumulator each in shared memory)
+
+// visits the tets containing node (i, j, k): f(tet T or -1, cube parity p, tet t, the node's vertex index kk, cube
+// corner (ci, cj, ck), cube corner offset (a, b, cc) of the node)
+template <typename F>
+static __device__ __forceinline__ void for_node_tets(const Mesh& m, int i, int j, int k, const unsigned char* mask,
+                                                     const int* ibase, F f) {
+    for (int c8 = 0; c8 < 8; ++c8) {
+        int a, b, cc; loff(c8, a, b, cc);
+        int ci = i - a, cj = j - b, ck = k - cc;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= m.nx || cj >= m.ny || ck >= m.nz) continue;
+        long long cell = cell_id(m, ci, cj, ck);
+        unsigned mk = mask[cell];
+        int p = (ci + cj + ck) & 1;
+        int T = ibase[cell];
+        for (int t = 0; t < 5; ++t) {
+            bool itet = (mk >> t) & 1;
+            int kk = -1;
+            for (int v = 0; v < 4; ++v)
+                if (cT.vert[p][t][v] == c8) kk = v;
+            if (kk >= 0) f(itet ? T : -1, p, t, kk, ci, cj, ck, a, b, cc);
+            if (itet) ++T;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NR_T) k_node_rows_fill(Mesh m, const unsigned char* mask, const int* ibase,
+                                                         const double* it_data, const double* L, const int* need,
+                                                         const long long* rowscan, const long long* qscan,
+                                                         long long R, int* row, float* coef, int* qoff, int4* qent,
+                                                         double* qc) {
+    __shared__ double acc[NR_T][81];
+    long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= m.nnodes) return;
+    if (!need[n]) { row[n] = -1; return; }
+    int i = (int)(n % m.NX), j = (int)((n / m.NX) % m.NY), k = (int)(n / ((long long)m.NX * m.NY));
+    const long long r = rowscan[n], q0 = qscan[n];
+    row[n] = (int)r;
+    qoff[r] = (int)q0;
+    const double ih = 1.0 / m.h, V3 = m.h * m.h * m.h;
+    // a piece is plasma: the + piece of a surface tet with volume, or a regular tet whose first vertex is outside
+    // the object
+    double vpl = 0.0, val = 0.0;
+    for_node_tets(m, i, j, k, mask, ibase, [&](int T, int p, int t, int, int ci, int cj, int ck, int, int, int) {
+        if (T >= 0) {
+            const double* rec = it_data + (long long)T * IT_STRIDE;
+            if (rec[IT_VOLP] > 0.0 && rec[IT_KIND] == 0.0) vpl += rec[IT_VOLP];
+            val += rec[IT_VOLP] + rec[IT_VOLM];
+        } else {
+            int a0, b0, c0; loff(cT.vert[p][t][0], a0, b0, c0);
+            const double V = cT.vol[t] * V3;
+            if (L[node_id(m, ci + a0, cj + b0, ck + c0)] >= 0.0) vpl += V;
+            val += V;
+        }
+    });
+    // the plasma pieces alone where there are some, else every piece
+    const bool pl_only = vpl > 0.0;
+    const double vol = pl_only ? vpl : val;
+    double* A = acc[threadIdx.x];
+    for (int q = 0; q < 81; ++q) A[q] = 0.0;
+    long long e = q0;
+    for_node_tets(m, i, j, k, mask, ibase,
+                  [&](int T, int p, int t, int kk, int ci, int cj, int ck, int a, int b, int cc) {
+        int nbv[4];
+        for (int v = 0; v < 4; ++v) {
+            int av, bv, cv; loff(cT.vert[p][t][v], av, bv, cv);
+            nbv[v] = (av - a + 1) + 3 * (bv - b + 1) + 9 * (cv - cc + 1);
+        }
+        if (T >= 0) {
+            const double* rec = it_data + (long long)T * IT_STRIDE;
+            const double vp = rec[IT_VOLP], vm = rec[IT_VOLM];
+            const bool plus = vp > 0.0 && rec[IT_KIND] == 0.0;
+            const double wp = pl_only ? (plus ? vp : 0.0) : vp, wm = pl_only ? 0.0 : vm;
+            for (int v = 0; v < 4; ++v)
+                for (int d = 0; d < 3; ++d)
+                    A[nbv[v] * 3 + d] += wp * rec[IT_GP + 3 * v + d] + wm * rec[IT_GM + 3 * v + d];
+            float cq[3];
+            for (int d = 0; d < 3; ++d)
+                cq[d] = (float)(-(wp * rec[IT_GP + 12 + d] + wm * rec[IT_GM + 12 + d]) / vol);
+            qent[e] = make_int4(T, __float_as_int(cq[0]), __float_as_int(cq[1]), __float_as_int(cq[2]));
+            qc[e] = rec[IT_C + kk];
+            ++e;
+        } else {
+            int a0, b0, c0; loff(cT.vert[p][t][0], a0, b0, c0);
+            const bool plus = L[node_id(m, ci + a0, cj + b0, ck + c0)] >= 0.0;
+            const double w = (pl_only && !plus) ? 0.0 : cT.vol[t] * V3 * ih;
+            for (int v = 0; v < 4; ++v)
+                for (int d = 0; d < 3; ++d) A[nbv[v] * 3 + d] += w * cT.grad[p][t][v][d];
+        }
+    });
+    for (int q = 0; q < 81; ++q) coef[(long long)q * R + r] = (float)(-A[q] / vol);
+}
+
+cudaError_t launch_node_rows(Ctx& c) {
+    const Mesh& m = c.mesh;
+    const long long N = m.nnodes;
+    void* old[] = {c.ne_row, c.ne_coef, c.ne_qoff, c.ne_q, c.ne_qc};
+    for (void* p : old) lib_free(p);
+    c.ne_row = nullptr; c.ne_coef = nullptr; c.ne_qoff = nullptr; c.ne_q = nullptr; c.ne_qc = nullptr;
+    c.ne_nrows = 0;
+    cudaStream_t st = c.stream;
+    int *need = nullptr, *nq = nullptr;
+    long long *rowscan = nullptr, *qscan = nullptr, *tot = nullptr;
+    long long R = 0, Q = 0;
+    cudaError_t err = cudaSuccess;
+    CK(lib_malloc(&need, sizeof(int) * N));
+    CK(lib_malloc(&nq, sizeof(int) * N));
+    CK(lib_malloc(&rowscan, sizeof(long long) * N));
+    CK(lib_malloc(&qscan, sizeof(long long) * N));
+    CK(lib_malloc(&tot, sizeof(long long)));
+    k_node_rows_count<<<nb(N), 256, 0, st>>>(m, c.imask, need, nq);
+    CK(cudaGetLastError());
+    CK(exclusive_scan(need, N, rowscan, tot, st));
+    CK(scopy(st, &R, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(exclusive_scan(nq, N, qscan, tot, st));
+    CK(scopy(st, &Q, tot, sizeof(long long), cudaMemcpyDeviceToHost));
+    {
+        const long long r1 = R > 0 ? R : 1, q1 = Q > 0 ? Q : 1;
+        int qend = (int)Q;
+        CK(lib_malloc(&c.ne_row, sizeof(int) * N));
+        CK(lib_malloc(&c.ne_coef, sizeof(float) * 81 * r1));
+        CK(lib_malloc(&c.ne_qoff, sizeof(int) * (r1 + 1)));
+        CK(lib_malloc(&c.ne_q, sizeof(int4) * q1));
+        CK(lib_malloc(&c.ne_qc, sizeof(double) * q1));
+        c.ne_nrows = R;
+        k_node_rows_fill<<<(unsigned)((N + NR_T - 1) / NR_T), NR_T, 0, st>>>(
+            m, c.imask, c.ibase, c.it_data, c.Lnode, need, rowscan, qscan, R, c.ne_row, c.ne_coef, c.ne_qoff, c.ne_q,
+            c.ne_qc);
+        CK(cudaGetLastError());
+        CK(scopy(st, c.ne_qoff + R, &qend, sizeof(int), cudaMemcpyHostToDevice));
+    }
+done:
+    lib_free(need); lib_free(nq); lib_free(rowscan); lib_free(qscan); lib_free(tot);
+    return err;
+}
+
 // emission set-up for the context's photo species (all buffers (re)allocated
 // here, outside any captured graph)
 cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w) {
