@@ -243,13 +243,22 @@ def measure(cfg, precision, steps, warmup, stream, dist, local):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     pushed = sum(st["pushed"])
-    t = torch.tensor([ms / 1e3, float(pushed)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        t = torch.stack([tmax[0], t[1]])
-    return sim, st, float(t[0]), float(t[1]), pushed, ck
+    secs, total = combine_ranks(ms / 1e3, pushed, dist, "cuda")
+    return sim, st, secs, total, pushed, ck
+
+
+def combine_ranks(seconds, pushed, dist, device):
+    """Whole-job figures of the replicas: the slowest rank's time (max over
+    ranks) and the particle-steps of all ranks (sum); one rank's own without
+    a process group."""
+    import torch
+    if dist is None:
+        return float(seconds), float(pushed)
+    tmax = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(pushed)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
 
 
 def roofline(precision, st, steps, ck):
