@@ -168,8 +168,11 @@ const char* pifepic_last_error(const pifepic_ctx* ctx);
 
 /* Object and field boundary set-up (Sec. 2.1, Sec. 3.1.2, Sec. 5.2.2): node
  * level set, tet classification, per-interface-tet linear IFE basis (a 4x4
- * FP64 solve each), stiffness patch rows, cut cells.  Must precede particle
- * calls.  set_field_bc may be called before or after set_object. */
+ * FP64 solve each), stiffness patch rows, cut cells, and the node rows of the
+ * node field (for every node on a face or next to an interface tet: its
+ * 27 x 3 coefficients and interface-tet terms, about 330 bytes a node).  Must
+ * precede particle calls.  set_field_bc may be called before or after
+ * set_object. */
 pifepic_status pifepic_set_object(pifepic_ctx* ctx, const pifepic_object_desc* obj);
 
 /* A second dielectric layer of the object (Sec. 5.2.1: the lunar regolith lies
