@@ -384,15 +384,16 @@ def run_gpu(args):
                 capi.lib.pifepic_get_potential(sim2._c, phi_host.ctypes.data, capi.HOST)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            rates.append(pushed2 / (t1 - t0))
+            secs2, total2 = combine_ranks(t1 - t0, pushed2, dist, "cuda")   # the whole job over the replicas
+            rates.append(total2 / secs2)
             sim2.close()
         e2e = {"value": sorted(rates)[len(rates) // 2], "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(h2d / args.steps),
-               "d2h_bytes_per_step": int(phi_host.nbytes + 512),
+               "h2d_bytes_per_step": int(world * h2d / args.steps),
+               "d2h_bytes_per_step": int(world * (phi_host.nbytes + 512)),
                "passes": [round(r, 1) for r in rates],
                "note": "median of %d passes, each on a fresh context: initial particle state h2d (amortised over "
-                       "the steps), the initial solve, then per step the step and the phi and stats d2h"
-                       % E2E_PASSES}
+                       "the steps), the initial solve, then per step the step and the phi and stats d2h; the "
+                       "replicas' particle-steps over the slowest rank's time" % E2E_PASSES}
     sim.close()
 
     # the other precision on the same workload, for the FP32-refined vs plain FP64 comparison
