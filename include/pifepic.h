@@ -9,7 +9,9 @@
  *  - Every call returns a pifepic_status; 0 is success.  The library never
  *    aborts, throws or prints.  After a non-zero status,
  *    pifepic_last_error(ctx) returns a context-owned, NUL-terminated message
- *    that stays valid until the next call on the same context.
+ *    that stays valid until the next call on the same context; the same
+ *    message also goes to the log callback, if one is set
+ *    (pifepic_set_log_callback).
  *  - Units are the plasma units the paper's experiments are stated in
  *    (Sec. 3.1, Sec. 5.1): lengths in Debye lengths, time in 1/omega_pe,
  *    potential in kT_e/e, density in the reference density, eps_0 = 1.
@@ -165,6 +167,14 @@ pifepic_status pifepic_create(const pifepic_mesh_desc* mesh, const pifepic_solve
                               void* stream, pifepic_ctx** out);
 void pifepic_destroy(pifepic_ctx* ctx);
 const char* pifepic_last_error(const pifepic_ctx* ctx);
+
+/* Optional log sink.  Every error message that pifepic_last_error or
+ * pifepic_batch_last_error returns is also passed to fn, with user, on the
+ * calling thread, when the error is recorded (the message is valid during the
+ * call only).  NULL (the default) turns it off.  Process-wide: set it while no
+ * other thread calls the library. */
+typedef void (*pifepic_log_fn)(const char* message, void* user);
+void pifepic_set_log_callback(pifepic_log_fn fn, void* user);
 
 /* Object and field boundary set-up (Sec. 2.1, Sec. 3.1.2, Sec. 5.2.2): node
  * level set, tet classification, per-interface-tet linear IFE basis (a 4x4

@@ -130,9 +130,27 @@ lib.pifepic_batch_destroy.argtypes = [C.c_void_p]
 lib.pifepic_batch_destroy.restype = None
 lib.pifepic_batch_last_error.argtypes = [C.c_void_p]
 lib.pifepic_batch_last_error.restype = C.c_char_p
+LOG_FN = C.CFUNCTYPE(None, C.c_char_p, C.c_void_p)
+lib.pifepic_set_log_callback.argtypes = [LOG_FN, C.c_void_p]
+lib.pifepic_set_log_callback.restype = None
 
 EXPORTED = sorted(list(_sigs) + ["pifepic_destroy", "pifepic_last_error", "pifepic_batch_destroy",
-                                 "pifepic_batch_last_error"])
+                                 "pifepic_batch_last_error", "pifepic_set_log_callback"])
+
+_log_keep = None   # the ctypes callback object must outlive its registration
+
+
+def set_log_callback(fn):
+    """Pass every error message the library records to fn(message: str)
+    (pifepic_set_log_callback); None turns it off."""
+    global _log_keep
+    if fn is None:
+        lib.pifepic_set_log_callback(LOG_FN(), None)
+        _log_keep = None
+        return
+    cb = LOG_FN(lambda msg, user: fn(msg.decode(errors="replace")))
+    lib.pifepic_set_log_callback(cb, None)
+    _log_keep = cb
 
 
 class PifepicError(RuntimeError):

@@ -99,6 +99,7 @@ struct pifepic_batch {
 
 static pifepic_status batch_fail(pifepic_batch* b, pifepic_status st, const std::string& m) {
     b->err = m;
+    log_error(m.c_str());
     return st;
 }
 

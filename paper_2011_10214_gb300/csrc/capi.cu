@@ -170,6 +170,14 @@ __global__ void k_seq_id(long long n, long long base, long long* id) {
     if (i < n) id[i] = base + i;
 }
 
+// the optional log sink (pifepic_set_log_callback)
+static std::atomic<pifepic_log_fn> g_log_fn{nullptr};
+static std::atomic<void*> g_log_user{nullptr};
+void log_error(const char* message) {
+    const pifepic_log_fn fn = g_log_fn.load(std::memory_order_acquire);
+    if (fn) fn(message, g_log_user.load(std::memory_order_relaxed));
+}
+
 }  // namespace pf
 
 using namespace pf;
@@ -180,6 +188,7 @@ using namespace pf;
         char _b[512];                                                                \
         snprintf(_b, sizeof(_b), __VA_ARGS__);                                       \
         ctx->c.err = _b;                                                             \
+        log_error(_b);                                                               \
         return code;                                                                 \
     } while (0)
 #define CUDA_OK(x)                                                                            \
@@ -426,6 +435,12 @@ void pifepic_destroy(pifepic_ctx* ctx) {
 }
 
 const char* pifepic_last_error(const pifepic_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+
+void pifepic_set_log_callback(pifepic_log_fn fn, void* user) {
+    g_log_user.store(user, std::memory_order_relaxed);
+    g_log_fn.store(fn, std::memory_order_release);
+}
 
 static pifepic_status encode_tmaps(pifepic_ctx* ctx) {
     Ctx& c = ctx->c;

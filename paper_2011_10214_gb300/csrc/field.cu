@@ -721,17 +721,23 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
         snprintf(b, sizeof(b), "solve_field_noalloc: mesh has %lld nodes; the fixed scratch holds at most %lld",
                  N, NOALLOC_MAX_NODES);
         c.err = b;
+        log_error(b);
         return PIFEPIC_EINVAL;
     }
     // the scratch address is per device and the kernels run on the context's
     // stream, so the context's device must be the current one
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) { c.err = "solve_field_noalloc: no current device"; return PIFEPIC_ECUDA; }
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        c.err = "solve_field_noalloc: no current device";
+        log_error(c.err.c_str());
+        return PIFEPIC_ECUDA;
+    }
     if (dev != c.device || dev < 0 || dev >= 64) {
         char b[160];
         snprintf(b, sizeof(b), "solve_field_noalloc: current device %d is not the context's device %d", dev,
                  c.device);
         c.err = b;
+        log_error(b);
         return PIFEPIC_EINVAL;
     }
     void* base_ptr = g_noalloc_dev[dev].load(std::memory_order_acquire);
@@ -739,6 +745,7 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
         cudaError_t e = cudaGetSymbolAddress(&base_ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !base_ptr) {
             c.err = std::string("solve_field_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            log_error(c.err.c_str());
             return PIFEPIC_ECUDA;
         }
         g_noalloc_dev[dev].store(base_ptr, std::memory_order_release);
@@ -773,6 +780,7 @@ pifepic_status solve_field_noalloc(Ctx& c, const double* F, const double* q, dou
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         c.err = std::string("solve_field_noalloc: ") + cudaGetErrorString(e);
+        log_error(c.err.c_str());
         return PIFEPIC_ECUDA;
     }
     if (iters) *iters = hs.it;

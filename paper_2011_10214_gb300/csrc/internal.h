@@ -326,6 +326,7 @@ enum {
 // ---- launchers ---------------------------------------------------------------
 cudaError_t set_tet_tables(const TetTables& t);
 cudaError_t launch_setup(Ctx& c);                      // S0 (setup.cu)
+void log_error(const char* message);                   // capi.cu: to the log callback, if set
 cudaError_t launch_node_rows(Ctx& c);                  // setup.cu: ne_row, ne_coef, ne_qoff, ne_q, ne_qc
 cudaError_t launch_photo_setup(Ctx& c, const double* sun, double density, double vth, double w);  // setup.cu
 cudaError_t launch_photo(Ctx& c);                      // particles.cu: one step of emission (FP64)
